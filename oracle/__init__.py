@@ -1,0 +1,227 @@
+"""CPU oracle for exact top-k closeness (arXiv 1704.01077) -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+may import this module.  It wraps ``oracle.c`` (plain C, built with gcc) through
+ctypes and shares nothing with the CUDA library.
+
+Functions and what pins them (see ``tests/test_oracle.py``):
+  bfs_sums        textbook BFS per source        Floyd-Warshall, closed forms, networkx
+  floyd_warshall  all pairs on <= 64 vertices    exhaustive small graphs vs BFS
+  topk            exact (S, r) ordering          Fraction-based brute force
+  farness         IEEE doubles from integers     Python float arithmetic on the same ops
+  degree_order    computeBoundsDeg               numpy lexsort
+  scc             Tarjan                         mutual reachability by brute force
+  alpha_omega     Algorithm 6                    alpha <= r <= omega, exact hand-built DAGs
+  tree_sums       Algorithm 2                    BFS on random trees
+  cut_bounds      Lemma 1 per level              invariants: <= S, non-decreasing, ends at S
+  bfscut          Algorithm 1 + Algorithm 4      textbook top-k on thousands of graphs
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("edges_visited", ctypes.c_uint64), ("bfs_started", ctypes.c_uint64),
+                ("bfs_cut", ctypes.c_uint64), ("bfs_finished", ctypes.c_uint64)]
+
+
+_lib = None
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def _bind(lib):
+    """Declares the C signatures on a loaded oracle library."""
+    lib.orc_bfs_sums.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u32p, _u64p, _u32p,
+                                 ctypes.c_int]
+    lib.orc_floyd_warshall.argtypes = [ctypes.c_uint32, _u32p, _u32p, _u64p, _u32p]
+    lib.orc_topk.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_uint32, _u32p, _u32p]
+    lib.orc_cmp_farness.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
+    lib.orc_farness.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, _dp, _dp]
+    lib.orc_farness.restype = None
+    lib.orc_degree_order.argtypes = [ctypes.c_uint32, _u32p, _u32p]
+    lib.orc_scc.argtypes = [ctypes.c_uint32, _u32p, _u32p, _u32p]
+    lib.orc_scc.restype = ctypes.c_int64
+    lib.orc_alpha_omega.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, _u32p, _u32p]
+    lib.orc_cut_min.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p]
+    lib.orc_cut_min.restype = None
+    lib.orc_tree_sums.argtypes = [ctypes.c_uint32, _u32p, _u32p, _u64p]
+    lib.orc_cut_bounds.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u64p,
+                                   ctypes.c_int]
+    lib.orc_bfscut.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p, _u32p,
+                               _u64p, _u32p, _u32p, ctypes.POINTER(Counters), _u64p, _u32p]
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def _p(a, t):
+    if a is None:
+        return ctypes.cast(None, t)
+    return a.ctypes.data_as(t)
+
+
+def _csr(g):
+    off = np.ascontiguousarray(g.offsets, dtype=np.uint32)
+    col = np.ascontiguousarray(g.cols, dtype=np.uint32)
+    if col.size == 0:
+        col = np.zeros(1, np.uint32)
+    return off, col
+
+
+def _check(rc):
+    if rc < 0:
+        raise RuntimeError(f"oracle call failed with code {rc}")
+    return rc
+
+
+def bfs_sums(g, sources=None, threads: int = 0):
+    """Textbook BFS: (S, r) for each source (all vertices by default)."""
+    off, col = _csr(g)
+    srcs = None if sources is None else np.ascontiguousarray(sources, dtype=np.uint32)
+    cnt = g.n if srcs is None else len(srcs)
+    S = np.zeros(max(cnt, 1), np.uint64)
+    r = np.zeros(max(cnt, 1), np.uint32)
+    _check(_load().orc_bfs_sums(g.n, _p(off, _u32p), _p(col, _u32p), cnt, _p(srcs, _u32p),
+                                _p(S, _u64p), _p(r, _u32p), threads))
+    return S[:cnt], r[:cnt]
+
+
+def floyd_warshall(g):
+    off, col = _csr(g)
+    S = np.zeros(max(g.n, 1), np.uint64)
+    r = np.zeros(max(g.n, 1), np.uint32)
+    _check(_load().orc_floyd_warshall(g.n, _p(off, _u32p), _p(col, _u32p), _p(S, _u64p), _p(r, _u32p)))
+    return S[: g.n], r[: g.n]
+
+
+def topk(S, r, k):
+    """Exact top-k ids by farness then id, and the count of vertices tied with the k-th."""
+    n = len(S)
+    S = np.ascontiguousarray(S, dtype=np.uint64)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    ids = np.zeros(max(min(k, n), 1), np.uint32)
+    tied = ctypes.c_uint32(0)
+    cnt = _check(_load().orc_topk(n, _p(S, _u64p), _p(r, _u32p), k, _p(ids, _u32p), ctypes.byref(tied)))
+    return ids[:cnt], int(tied.value)
+
+
+def cmp_farness(Sa, ra, Sb, rb) -> int:
+    return int(_load().orc_cmp_farness(Sa, ra, Sb, rb))
+
+
+def farness(n, S, r):
+    f = ctypes.c_double()
+    c = ctypes.c_double()
+    _load().orc_farness(n, int(S), int(r), ctypes.byref(f), ctypes.byref(c))
+    return f.value, c.value
+
+
+def degree_order(g):
+    off, _ = _csr(g)
+    order = np.zeros(max(g.n, 1), np.uint32)
+    _check(_load().orc_degree_order(g.n, _p(off, _u32p), _p(order, _u32p)))
+    return order[: g.n]
+
+
+def scc(g):
+    off, col = _csr(g)
+    comp = np.zeros(max(g.n, 1), np.uint32)
+    nc = _check(_load().orc_scc(g.n, _p(off, _u32p), _p(col, _u32p), _p(comp, _u32p)))
+    return comp[: g.n], int(nc)
+
+
+def alpha_omega(g):
+    off, col = _csr(g)
+    a = np.zeros(max(g.n, 1), np.uint32)
+    o = np.zeros(max(g.n, 1), np.uint32)
+    _check(_load().orc_alpha_omega(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), _p(a, _u32p),
+                                   _p(o, _u32p)))
+    return a[: g.n], o[: g.n]
+
+
+def tree_sums(g):
+    off, col = _csr(g)
+    S = np.zeros(max(g.n, 1), np.uint64)
+    _check(_load().orc_tree_sums(g.n, _p(off, _u32p), _p(col, _u32p), _p(S, _u64p)))
+    return S[: g.n]
+
+
+def cut_bounds(g, v, maxlev=256):
+    off, col = _csr(g)
+    L = np.zeros(maxlev, np.uint64)
+    cnt = _check(_load().orc_cut_bounds(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), v,
+                                        _p(L, _u64p), maxlev))
+    return L[:cnt]
+
+
+def cut_min(Sd, d, nd, g, lo, hi):
+    """(L, r): the r in [max(lo, nd), hi] minimising the Lemma 1 farness bound."""
+    L = ctypes.c_uint64()
+    r = ctypes.c_uint64()
+    _load().orc_cut_min(Sd, d, nd, g, lo, hi, ctypes.byref(L), ctypes.byref(r))
+    return int(L.value), int(r.value)
+
+
+@dataclass
+class TopK:
+    ids: np.ndarray
+    S: np.ndarray
+    r: np.ndarray
+    n_tied: int
+    counters: Counters | None = None
+    all_S: np.ndarray | None = None
+    all_r: np.ndarray | None = None
+
+
+def bfscut(g, k, order=None, want_all=False) -> TopK:
+    """Algorithm 1 + BFSCut, one source at a time, in degree order (or `order`)."""
+    off, col = _csr(g)
+    kk = min(k, g.n)
+    ids = np.zeros(max(kk, 1), np.uint32)
+    S = np.zeros(max(kk, 1), np.uint64)
+    r = np.zeros(max(kk, 1), np.uint32)
+    tied = ctypes.c_uint32(0)
+    ctr = Counters()
+    order_a = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
+    allS = np.zeros(max(g.n, 1), np.uint64) if want_all else None
+    allr = np.zeros(max(g.n, 1), np.uint32) if want_all else None
+    cnt = _check(_load().orc_bfscut(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), k,
+                                    _p(order_a, _u32p), _p(ids, _u32p), _p(S, _u64p), _p(r, _u32p),
+                                    ctypes.byref(tied), ctypes.byref(ctr), _p(allS, _u64p), _p(allr, _u32p)))
+    return TopK(ids[:cnt], S[:cnt], r[:cnt], int(tied.value), ctr,
+                None if allS is None else allS[: g.n], None if allr is None else allr[: g.n])
+
+
+def textbook_topk(g, k, threads: int = 0) -> TopK:
+    """Textbook algorithm: BFS from every vertex, then the exact top-k."""
+    S, r = bfs_sums(g, threads=threads)
+    ids, tied = topk(S, r, k)
+    return TopK(ids, S[ids], r[ids], tied)

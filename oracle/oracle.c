@@ -1,0 +1,714 @@
+/*
+ * CPU oracle for exact top-k closeness centrality (Bergamini, Borassi,
+ * Crescenzi, Marino, Meyerhenke, "Computing top-k Closeness Centrality Faster
+ * in Unweighted Graphs", arXiv 1704.01077).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+ * CUDA path is checked against.  It shares no code, header, table or helper
+ * with the CUDA library and must never be linked into, or called by, the
+ * product path.  Only the tests, the package's smoke check and the benchmark's
+ * CPU-baseline leg use it.
+ *
+ * Graph input everywhere: CSR, uint32 row offsets off[0..n], uint32 column ids
+ * col[0..off[n]), out-arcs of each vertex (undirected graphs hold both arc
+ * directions).
+ *
+ * Definitions followed (Section 2, notation table):
+ *   R(v) = vertices reachable from v (v included), r(v) = |R(v)|,
+ *   S(v) = sum over w in R(v) of d(v,w),
+ *   f(v) = (n-1) S(v) / (r(v)-1)^2,  c(v) = 1/f(v), and c(v) = 0 when r(v) = 1.
+ *
+ * Parity status of each function is stated beside it.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef unsigned __int128 u128;
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOMEM -3
+
+/* ---------------------------------------------------------------------- */
+/* Textbook BFS (Section 1: "the textbook algorithm", one BFS per vertex)  */
+/* ---------------------------------------------------------------------- */
+
+/* BFS from one source with a FIFO queue; returns S(v), r(v), arcs scanned.
+ * dist must hold n entries set to UINT32_MAX and is restored on return. */
+static void bfs_one(uint32_t n, const uint32_t *off, const uint32_t *col, uint32_t s,
+                    uint32_t *dist, uint32_t *queue, uint64_t *S_out, uint32_t *r_out) {
+  (void)n;
+  uint32_t head = 0, tail = 0;
+  uint64_t S = 0;
+  dist[s] = 0;
+  queue[tail++] = s;
+  while (head < tail) {
+    uint32_t u = queue[head++];
+    for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t w = col[e];
+      if (dist[w] == UINT32_MAX) {
+        dist[w] = dist[u] + 1;
+        S += dist[w];
+        queue[tail++] = w;
+      }
+    }
+  }
+  for (uint32_t i = 0; i < tail; ++i) dist[queue[i]] = UINT32_MAX;
+  *S_out = S;
+  *r_out = tail;
+}
+
+/* S(v) and r(v) for the listed sources (all vertices if srcs == NULL).
+ * Pinned by: Floyd-Warshall on small graphs, closed forms, networkx. */
+int orc_bfs_sums(uint32_t n, const uint32_t *off, const uint32_t *col, uint32_t nsrc,
+                 const uint32_t *srcs, uint64_t *S, uint32_t *r, int nthreads) {
+  if (n == 0) return ORC_OK;
+  int rc = ORC_OK;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+  {
+    uint32_t *dist = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    uint32_t *queue = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    if (!dist || !queue) {
+      rc = ORC_ENOMEM;
+    } else {
+      for (uint32_t i = 0; i < n; ++i) dist[i] = UINT32_MAX;
+      int64_t cnt = srcs ? (int64_t)nsrc : (int64_t)n;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+      for (int64_t i = 0; i < cnt; ++i) {
+        uint32_t s = srcs ? srcs[i] : (uint32_t)i;
+        bfs_one(n, off, col, s, dist, queue, &S[i], &r[i]);
+      }
+    }
+    free(dist);
+    free(queue);
+  }
+  (void)nthreads;
+  return rc;
+}
+
+/* All-pairs distances by Floyd-Warshall on a dense matrix (n <= 64); an
+ * independent route to S(v) and r(v) used to pin the BFS above. */
+int orc_floyd_warshall(uint32_t n, const uint32_t *off, const uint32_t *col, uint64_t *S, uint32_t *r) {
+  if (n > 64) return ORC_EINVAL;
+  const uint32_t INF = 1u << 20;
+  uint32_t D[64][64];
+  for (uint32_t i = 0; i < n; ++i)
+    for (uint32_t j = 0; j < n; ++j) D[i][j] = (i == j) ? 0 : INF;
+  for (uint32_t u = 0; u < n; ++u)
+    for (uint32_t e = off[u]; e < off[u + 1]; ++e) D[u][col[e]] = 1;
+  for (uint32_t m = 0; m < n; ++m)
+    for (uint32_t i = 0; i < n; ++i)
+      for (uint32_t j = 0; j < n; ++j)
+        if (D[i][m] + D[m][j] < D[i][j]) D[i][j] = D[i][m] + D[m][j];
+  for (uint32_t i = 0; i < n; ++i) {
+    uint64_t s = 0;
+    uint32_t c = 0;
+    for (uint32_t j = 0; j < n; ++j)
+      if (D[i][j] < INF) { s += D[i][j]; ++c; }
+    S[i] = s;
+    r[i] = c;
+  }
+  return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Exact ordering by farness                                               */
+/* ---------------------------------------------------------------------- */
+
+/* Compares f(a) with f(b) exactly: f = (n-1) S / (r-1)^2, (n-1) cancels, so
+ * compare S_a (r_b-1)^2 with S_b (r_a-1)^2 in 128-bit integers.  r = 1 means
+ * closeness 0, i.e. farness +infinity (Section 2).  Returns -1, 0, 1. */
+static int cmp_farness(uint64_t Sa, uint32_t ra, uint64_t Sb, uint32_t rb) {
+  int inf_a = ra <= 1, inf_b = rb <= 1;
+  if (inf_a || inf_b) return inf_a - inf_b;
+  u128 lhs = (u128)Sa * (u128)((uint64_t)(rb - 1) * (uint64_t)(rb - 1));
+  u128 rhs = (u128)Sb * (u128)((uint64_t)(ra - 1) * (uint64_t)(ra - 1));
+  return (lhs > rhs) - (lhs < rhs);
+}
+
+int orc_cmp_farness(uint64_t Sa, uint32_t ra, uint64_t Sb, uint32_t rb) {
+  return cmp_farness(Sa, ra, Sb, rb);
+}
+
+typedef struct {
+  uint64_t S;
+  uint32_t r;
+  uint32_t id;
+} entry_t;
+
+static int cmp_entry(const void *pa, const void *pb) {
+  const entry_t *a = (const entry_t *)pa, *b = (const entry_t *)pb;
+  int c = cmp_farness(a->S, a->r, b->S, b->r);
+  if (c) return c;
+  return (a->id > b->id) - (a->id < b->id);
+}
+
+/* Top-k by closeness (Section 4: the k vertices of smallest farness), ties
+ * broken by id; n_tied = number of vertices whose farness equals that of the
+ * k-th returned vertex (the paper returns all of them).  Returns the number of
+ * ids written, min(k, n). */
+int orc_topk(uint32_t n, const uint64_t *S, const uint32_t *r, uint32_t k, uint32_t *ids,
+             uint32_t *n_tied) {
+  if (n == 0 || k == 0) { if (n_tied) *n_tied = 0; return 0; }
+  entry_t *e = (entry_t *)malloc((size_t)n * sizeof(entry_t));
+  if (!e) return ORC_ENOMEM;
+  for (uint32_t v = 0; v < n; ++v) { e[v].S = S[v]; e[v].r = r[v]; e[v].id = v; }
+  qsort(e, n, sizeof(entry_t), cmp_entry);
+  uint32_t kk = k < n ? k : n;
+  for (uint32_t i = 0; i < kk; ++i) ids[i] = e[i].id;
+  if (n_tied) {
+    uint32_t t = 0;
+    for (uint32_t v = 0; v < n; ++v)
+      if (cmp_farness(S[v], r[v], e[kk - 1].S, e[kk - 1].r) == 0) ++t;
+    *n_tied = t;
+  }
+  free(e);
+  return (int)kk;
+}
+
+/* f(v) and c(v) in IEEE double from the exact integers: one rounded product
+ * and one rounded quotient each (Section 2's definitions). */
+void orc_farness(uint32_t n, uint64_t S, uint32_t r, double *farness, double *closeness) {
+  if (r <= 1) {
+    *farness = INFINITY;
+    *closeness = 0.0;
+    return;
+  }
+  double num = (double)(n - 1) * (double)S;
+  double den = (double)((uint64_t)(r - 1) * (uint64_t)(r - 1));
+  *farness = num / den;
+  *closeness = den / num;
+}
+
+/* ---------------------------------------------------------------------- */
+/* computeBoundsDeg (Section 4): vertices by decreasing degree             */
+/* ---------------------------------------------------------------------- */
+
+/* Counting sort by out-degree, largest first; equal degrees keep increasing
+ * id order (the sort is stable).  Pinned by numpy lexsort in the tests. */
+int orc_degree_order(uint32_t n, const uint32_t *off, uint32_t *order) {
+  if (n == 0) return ORC_OK;
+  uint32_t maxd = 0;
+  for (uint32_t v = 0; v < n; ++v) {
+    uint32_t d = off[v + 1] - off[v];
+    if (d > maxd) maxd = d;
+  }
+  uint32_t *start = (uint32_t *)calloc((size_t)maxd + 2, sizeof(uint32_t));
+  if (!start) return ORC_ENOMEM;
+  /* bucket b holds degree maxd - b, so bucket 0 is the largest degree */
+  for (uint32_t v = 0; v < n; ++v) start[maxd - (off[v + 1] - off[v]) + 1]++;
+  for (uint32_t b = 0; b <= maxd; ++b) start[b + 1] += start[b];
+  for (uint32_t v = 0; v < n; ++v) order[start[maxd - (off[v + 1] - off[v])]++] = v;
+  free(start);
+  return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Strongly connected components (Tarjan), iterative                        */
+/* ---------------------------------------------------------------------- */
+
+/* comp[v] = index of v's SCC; components are numbered in the order Tarjan's
+ * algorithm completes them, which is a reverse topological order of the SCC
+ * DAG (a component is completed after every component it reaches).
+ * Returns the number of components.  Pinned by mutual reachability checks. */
+int64_t orc_scc(uint32_t n, const uint32_t *off, const uint32_t *col, uint32_t *comp) {
+  if (n == 0) return 0;
+  uint32_t *index = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *low = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *stack = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint8_t *onstack = (uint8_t *)calloc(n, 1);
+  uint32_t *cs_v = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *cs_e = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  if (!index || !low || !stack || !onstack || !cs_v || !cs_e) {
+    free(index); free(low); free(stack); free(onstack); free(cs_v); free(cs_e);
+    return ORC_ENOMEM;
+  }
+  const uint32_t UNV = UINT32_MAX;
+  for (uint32_t v = 0; v < n; ++v) index[v] = UNV;
+  uint32_t next_index = 0, sp = 0, ncomp = 0;
+  for (uint32_t root = 0; root < n; ++root) {
+    if (index[root] != UNV) continue;
+    uint32_t csp = 0;
+    cs_v[csp] = root;
+    cs_e[csp] = off[root];
+    ++csp;
+    index[root] = low[root] = next_index++;
+    stack[sp++] = root;
+    onstack[root] = 1;
+    while (csp > 0) {
+      uint32_t v = cs_v[csp - 1];
+      if (cs_e[csp - 1] < off[v + 1]) {
+        uint32_t w = col[cs_e[csp - 1]++];
+        if (index[w] == UNV) {
+          index[w] = low[w] = next_index++;
+          stack[sp++] = w;
+          onstack[w] = 1;
+          cs_v[csp] = w;
+          cs_e[csp] = off[w];
+          ++csp;
+        } else if (onstack[w] && index[w] < low[v]) {
+          low[v] = index[w];
+        }
+      } else {
+        if (low[v] == index[v]) {
+          uint32_t w;
+          do {
+            w = stack[--sp];
+            onstack[w] = 0;
+            comp[w] = ncomp;
+          } while (w != v);
+          ++ncomp;
+        }
+        --csp;
+        if (csp > 0) {
+          uint32_t u = cs_v[csp - 1];
+          if (low[v] < low[u]) low[u] = low[v];
+        }
+      }
+    }
+  }
+  free(index); free(low); free(stack); free(onstack); free(cs_v); free(cs_e);
+  return (int64_t)ncomp;
+}
+
+/* ---------------------------------------------------------------------- */
+/* alpha / omega bounds on r(v) (Section 8.4, Algorithm 6)                  */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * alpha(v) <= r(v) <= omega(v).  Steps, in the paper's order:
+ *  1. SCC DAG (V, E, w) with w(C) = |C| and E a set (no repeated SCC arcs).
+ *  2. C~ = the biggest SCC; ties go to the SCC holding the smallest vertex id.
+ *     Its reach is computed exactly by one BFS: alpha = omega = r(C~).
+ *  3. In reverse topological order, for every other X:
+ *       alpha(X) = w(X) + max over successors Y of alpha(Y)
+ *       omega(X) = w(X) + sum over successors Y of omega(Y)
+ *     and if X reaches C~, omega(X) = w(X) + omega(C~) + sum of omega(Y) over
+ *     successors Y that are not reachable from C~.
+ *  4. omega is clamped to n (the sums may exceed n).
+ * Undirected graphs: alpha = omega = size of the connected component.
+ * Pinned by alpha <= r <= omega against brute-force reach, exact values on
+ * hand-built DAGs, and exactness on the biggest SCC.
+ */
+int orc_alpha_omega(uint32_t n, const uint32_t *off, const uint32_t *col, int directed,
+                    uint32_t *alpha, uint32_t *omega) {
+  if (n == 0) return ORC_OK;
+  uint32_t *comp = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  if (!comp) return ORC_ENOMEM;
+  int64_t nc64 = orc_scc(n, off, col, comp);
+  if (nc64 < 0) { free(comp); return (int)nc64; }
+  uint32_t nc = (uint32_t)nc64;
+  uint64_t *w = (uint64_t *)calloc(nc, sizeof(uint64_t));
+  uint32_t *minid = (uint32_t *)malloc((size_t)nc * sizeof(uint32_t));
+  if (!w || !minid) { free(comp); free(w); free(minid); return ORC_ENOMEM; }
+  for (uint32_t c = 0; c < nc; ++c) minid[c] = UINT32_MAX;
+  for (uint32_t v = 0; v < n; ++v) {
+    w[comp[v]]++;
+    if (v < minid[comp[v]]) minid[comp[v]] = v;
+  }
+  if (!directed) {
+    /* undirected: every SCC is a connected component and r(v) is its size */
+    for (uint32_t v = 0; v < n; ++v) alpha[v] = omega[v] = (uint32_t)w[comp[v]];
+    free(comp); free(w); free(minid);
+    return ORC_OK;
+  }
+  /* condensation arcs, deduplicated per source component */
+  uint64_t m = off[n];
+  uint32_t *cdeg = (uint32_t *)calloc((size_t)nc + 1, sizeof(uint32_t));
+  uint32_t *carc = (uint32_t *)malloc((size_t)(m ? m : 1) * sizeof(uint32_t));
+  uint32_t *mark = (uint32_t *)malloc((size_t)nc * sizeof(uint32_t));
+  uint32_t *members_off = (uint32_t *)calloc((size_t)nc + 1, sizeof(uint32_t));
+  uint32_t *members = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint64_t *A = (uint64_t *)calloc(nc, sizeof(uint64_t));
+  uint64_t *O = (uint64_t *)calloc(nc, sizeof(uint64_t));
+  uint8_t *from_big = (uint8_t *)calloc(nc, 1);
+  uint8_t *to_big = (uint8_t *)calloc(nc, 1);
+  uint32_t *coff = (uint32_t *)malloc(((size_t)nc + 1) * sizeof(uint32_t));
+  if (!cdeg || !carc || !mark || !members_off || !members || !A || !O || !from_big || !to_big || !coff) {
+    free(comp); free(w); free(minid); free(cdeg); free(carc); free(mark); free(members_off);
+    free(members); free(A); free(O); free(from_big); free(to_big); free(coff);
+    return ORC_ENOMEM;
+  }
+  for (uint32_t v = 0; v < n; ++v) members_off[comp[v] + 1]++;
+  for (uint32_t c = 0; c < nc; ++c) members_off[c + 1] += members_off[c];
+  {
+    uint32_t *fill = (uint32_t *)malloc((size_t)nc * sizeof(uint32_t));
+    if (!fill) return ORC_ENOMEM;
+    memcpy(fill, members_off, (size_t)nc * sizeof(uint32_t));
+    for (uint32_t v = 0; v < n; ++v) members[fill[comp[v]]++] = v;
+    free(fill);
+  }
+  for (uint32_t c = 0; c < nc; ++c) mark[c] = UINT32_MAX;
+  uint64_t na = 0;
+  for (uint32_t c = 0; c < nc; ++c) {
+    coff[c] = (uint32_t)na;
+    for (uint32_t i = members_off[c]; i < members_off[c + 1]; ++i) {
+      uint32_t v = members[i];
+      for (uint32_t e = off[v]; e < off[v + 1]; ++e) {
+        uint32_t d = comp[col[e]];
+        if (d != c && mark[d] != c) {
+          mark[d] = c;
+          carc[na++] = d;
+        }
+      }
+    }
+  }
+  coff[nc] = (uint32_t)na;
+  /* biggest SCC, ties to the one holding the smallest vertex id */
+  uint32_t big = 0;
+  for (uint32_t c = 1; c < nc; ++c)
+    if (w[c] > w[big] || (w[c] == w[big] && minid[c] < minid[big])) big = c;
+  /* exact reach of the biggest SCC: BFS over the condensation from it */
+  uint32_t *q = mark; /* reuse as a queue */
+  uint32_t qh = 0, qt = 0;
+  from_big[big] = 1;
+  q[qt++] = big;
+  uint64_t reach_big = 0;
+  while (qh < qt) {
+    uint32_t c = q[qh++];
+    reach_big += w[c];
+    for (uint32_t i = coff[c]; i < coff[c + 1]; ++i)
+      if (!from_big[carc[i]]) { from_big[carc[i]] = 1; q[qt++] = carc[i]; }
+  }
+  /* Tarjan numbers components in reverse topological order: successors of c
+   * have smaller numbers, so increasing c is the order Algorithm 6 needs.
+   * "X reaches C~" is known once every successor is processed. */
+  for (uint32_t c = 0; c < nc; ++c) {
+    if (c == big) {
+      A[c] = O[c] = reach_big;
+      to_big[c] = 1;
+      continue;
+    }
+    uint64_t a = 0, o = 0, o2 = 0;
+    int reaches = 0;
+    for (uint32_t i = coff[c]; i < coff[c + 1]; ++i) {
+      uint32_t y = carc[i];
+      if (A[y] > a) a = A[y];
+      o += O[y];
+      if (!from_big[y]) o2 += O[y];
+      if (to_big[y]) reaches = 1;
+    }
+    if (reaches) {
+      to_big[c] = 1;
+      o = o2 + O[big];
+    }
+    A[c] = a + w[c];
+    O[c] = o + w[c];
+    if (O[c] > n) O[c] = n;
+  }
+  for (uint32_t v = 0; v < n; ++v) {
+    alpha[v] = (uint32_t)A[comp[v]];
+    omega[v] = (uint32_t)(O[comp[v]] > n ? n : O[comp[v]]);
+  }
+  free(comp); free(w); free(minid); free(cdeg); free(carc); free(mark); free(members_off);
+  free(members); free(A); free(O); free(from_big); free(to_big); free(coff);
+  return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Closeness on trees (Section 5, Algorithm 2)                              */
+/* ---------------------------------------------------------------------- */
+
+/* Level counts of every vertex advance together: |N_1(s)| = deg(s); at level 2
+ * |N_2(s)| = sum over neighbours w of |N_1(w)| minus deg(s); at level k > 2 it
+ * is the sum of |N_{k-1}(w)| over neighbours minus |N_{k-2}(s)| (deg(s) - 1)
+ * (Eq. 2).  S(s) accumulates k |N_k(s)| until every count is zero.  Exact on
+ * trees (Prop. 2); used to pin the BFS on trees.  Input must be a tree. */
+int orc_tree_sums(uint32_t n, const uint32_t *off, const uint32_t *col, uint64_t *S) {
+  if (n == 0) return ORC_OK;
+  int64_t *prev2 = (int64_t *)calloc(n, sizeof(int64_t));
+  int64_t *prev1 = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  int64_t *cur = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  if (!prev2 || !prev1 || !cur) { free(prev2); free(prev1); free(cur); return ORC_ENOMEM; }
+  for (uint32_t s = 0; s < n; ++s) {
+    prev1[s] = (int64_t)(off[s + 1] - off[s]);
+    S[s] = (uint64_t)prev1[s];
+  }
+  for (uint32_t level = 2;; ++level) {
+    int any = 0;
+    for (uint32_t s = 0; s < n; ++s) {
+      int64_t deg = (int64_t)(off[s + 1] - off[s]);
+      int64_t sum = 0;
+      for (uint32_t e = off[s]; e < off[s + 1]; ++e) sum += prev1[col[e]];
+      if (level == 2)
+        cur[s] = sum - deg;
+      else
+        cur[s] = sum - prev2[s] * (deg - 1);
+    }
+    for (uint32_t s = 0; s < n; ++s) {
+      prev2[s] = prev1[s];
+      prev1[s] = cur[s];
+      if (cur[s] > 0) {
+        S[s] += (uint64_t)level * (uint64_t)cur[s];
+        any = 1;
+      }
+    }
+    if (!any || level > n + 1) break;
+  }
+  free(prev2); free(prev1); free(cur);
+  return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* BFSCut lower bound (Section 6, Lemma 1 with the Section 8.2 reading)     */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * After BFS from v has discovered every level up to d:
+ *   S_d  = sum of d(v,w) over the ball of radius d,   n_d = size of the ball,
+ *   g    = upper bound on |Gamma_{d+1}(v)|: the sum of outdeg(w) over
+ *          Gamma_d(v) for directed graphs, of deg(w)-1 for undirected graphs
+ *          at d >= 1, and deg(v) at d = 0.
+ * Lemma 1 gives S(v) >= S_d - |Gamma_{d+1}| + (d+2)(r - n_d) for the true
+ * r = r(v), with |Gamma_{d+1}| <= g.  Because also |Gamma_{d+1}| <= r - n_d,
+ *   L_d(r) = S_d + (d+1)(r - n_d) + max(0, r - n_d - g)
+ * is a lower bound on S(v) at r = r(v).  r(v) lies in [max(alpha, n_d), omega];
+ * L_d(r)/(r-1)^2 is minimised over that interval at an end point or at the
+ * kink r = n_d + g (it is linear on each side of the kink, and a linear L makes
+ * the ratio's minimum fall at an end point of the piece, Lemma 2).
+ *
+ * Returns 1 if the farness bound exceeds the threshold (Sx, rx) strictly at
+ * every candidate r, i.e. the vertex can be abandoned.  have_x = 0 means fewer
+ * than k vertices are known and nothing is abandoned.
+ */
+static uint64_t cut_L(uint64_t Sd, uint32_t d, uint64_t nd, uint64_t g, uint64_t r) {
+  uint64_t rem = r - nd;
+  uint64_t extra = rem > g ? rem - g : 0;
+  return Sd + (uint64_t)(d + 1) * rem + extra;
+}
+
+/* The candidate r in [max(lo, nd), hi] minimising L_d(r)/(r-1)^2, compared
+ * exactly; writes that r and L_d(r).  r <= 1 stands for farness +infinity and
+ * is never chosen while another candidate exists. */
+static void cut_min(uint64_t Sd, uint32_t d, uint64_t nd, uint64_t g, uint64_t lo, uint64_t hi,
+                    uint64_t *L_best, uint64_t *r_best) {
+  if (lo < nd) lo = nd;
+  if (hi < lo) hi = lo;
+  uint64_t cand[3];
+  int nc = 0;
+  cand[nc++] = lo;
+  cand[nc++] = hi;
+  uint64_t kink = nd + g;
+  if (kink > lo && kink < hi) cand[nc++] = kink;
+  uint64_t bl = cut_L(Sd, d, nd, g, cand[0]), br = cand[0];
+  for (int i = 1; i < nc; ++i) {
+    uint64_t r = cand[i], L = cut_L(Sd, d, nd, g, r);
+    if (r <= 1) continue;
+    if (br <= 1) { bl = L; br = r; continue; }
+    u128 lhs = (u128)L * (u128)((br - 1) * (br - 1));
+    u128 rhs = (u128)bl * (u128)((r - 1) * (r - 1));
+    if (lhs < rhs) { bl = L; br = r; }
+  }
+  *L_best = bl;
+  *r_best = br;
+}
+
+void orc_cut_min(uint64_t Sd, uint32_t d, uint64_t nd, uint64_t g, uint64_t lo, uint64_t hi,
+                 uint64_t *L_best, uint64_t *r_best) {
+  cut_min(Sd, d, nd, g, lo, hi, L_best, r_best);
+}
+
+static int cut_exceeds(uint64_t Sd, uint32_t d, uint64_t nd, uint64_t g, uint64_t lo, uint64_t hi,
+                       int have_x, uint64_t Sx, uint32_t rx) {
+  if (!have_x) return 0;
+  uint64_t L, r;
+  cut_min(Sd, d, nd, g, lo, hi, &L, &r);
+  if (r <= 1) return 1; /* farness +infinity exceeds any finite x */
+  /* L/(r-1)^2 > Sx/(rx-1)^2 ?  (rx > 1: x is a finite farness) */
+  u128 lhs = (u128)L * (u128)((uint64_t)(rx - 1) * (uint64_t)(rx - 1));
+  u128 rhs = (u128)Sx * (u128)((r - 1) * (r - 1));
+  return lhs > rhs;
+}
+
+/* The level-granular bound sequence L_0, L_1, ... of one source at its true
+ * r(v), for the invariant tests (L_d <= S(v), non-decreasing, L_last = S(v)).
+ * Returns the number of levels written (at most maxlev). */
+int orc_cut_bounds(uint32_t n, const uint32_t *off, const uint32_t *col, int directed, uint32_t v,
+                   uint64_t *Lout, int maxlev) {
+  uint32_t *dist = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *queue = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  if (!dist || !queue) { free(dist); free(queue); return ORC_ENOMEM; }
+  uint64_t Sfull;
+  uint32_t rfull;
+  for (uint32_t i = 0; i < n; ++i) dist[i] = UINT32_MAX;
+  bfs_one(n, off, col, v, dist, queue, &Sfull, &rfull);
+  /* level-by-level pass */
+  uint32_t head = 0, tail = 0;
+  dist[v] = 0;
+  queue[tail++] = v;
+  uint64_t Sd = 0, nd = 1, g = off[v + 1] - off[v];
+  uint32_t d = 0;
+  int nl = 0;
+  while (1) {
+    if (nl < maxlev) Lout[nl] = cut_L(Sd, d, nd, g, rfull);
+    ++nl;
+    uint32_t level_end = tail;
+    uint64_t cnt = 0, gs = 0;
+    while (head < level_end) {
+      uint32_t u = queue[head++];
+      for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+        uint32_t w = col[e];
+        if (dist[w] == UINT32_MAX) {
+          dist[w] = d + 1;
+          queue[tail++] = w;
+          ++cnt;
+          gs += (off[w + 1] - off[w]) - (directed ? 0u : 1u);
+        }
+      }
+    }
+    if (cnt == 0) break;
+    ++d;
+    Sd += (uint64_t)d * cnt;
+    nd += cnt;
+    g = gs;
+  }
+  for (uint32_t i = 0; i < tail; ++i) dist[queue[i]] = UINT32_MAX;
+  free(dist); free(queue);
+  return nl < maxlev ? nl : maxlev;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 1 with updateBoundsBFSCut (DegCut), sequential                 */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+  uint64_t edges_visited; /* arcs scanned by the expanded BFS levels */
+  uint64_t bfs_started;
+  uint64_t bfs_cut;
+  uint64_t bfs_finished;
+} orc_counters;
+
+/* insert (S, r, id) into the sorted top list of capacity k */
+static void top_insert(entry_t *top, uint32_t *cnt, uint32_t k, uint64_t S, uint32_t r, uint32_t id) {
+  entry_t e = {S, r, id};
+  if (*cnt == k && cmp_entry(&e, &top[k - 1]) >= 0) return;
+  uint32_t i = *cnt < k ? (*cnt)++ : k - 1;
+  while (i > 0 && cmp_entry(&e, &top[i - 1]) < 0) { top[i] = top[i - 1]; --i; }
+  top[i] = e;
+}
+
+/*
+ * Algorithm 1 with computeBoundsDeg (L = 0, Q in decreasing degree order, or
+ * the caller's order) and updateBoundsBFSCut (Algorithm 4) evaluated once per
+ * completed level, r(v) bounded by alpha/omega (Algorithm 6; exact for
+ * undirected graphs).  Vertices of out-degree 0 have r = 1 (closeness 0) and
+ * are never searched.
+ *
+ * Readings where the paper leaves a choice:
+ *  - A vertex is abandoned only when its farness bound is strictly greater
+ *    than x, the k-th smallest farness found so far, so that every vertex tied
+ *    with the final k-th is fully searched (Section 4 asks for all of them).
+ *  - x is refreshed after each finished BFS (one source at a time).
+ *  - The bound is checked before each level is expanded, including level 0.
+ *
+ * Outputs: ids/S/r of the top min(k, n) (ties by id), n_tied, counters, and
+ * optionally per-vertex S/r of every finished BFS (r = 0 if not finished).
+ */
+int orc_bfscut(uint32_t n, const uint32_t *off, const uint32_t *col, int directed, uint32_t k,
+               const uint32_t *order_in, uint32_t *ids, uint64_t *S_out, uint32_t *r_out,
+               uint32_t *n_tied, orc_counters *ctr, uint64_t *allS, uint32_t *allr) {
+  if (k == 0 || n == 0) { if (n_tied) *n_tied = 0; return 0; }
+  int rc = ORC_OK;
+  uint32_t *order = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *alpha = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *omega = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *dist = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *queue = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint64_t *fS = (uint64_t *)calloc(n, sizeof(uint64_t));
+  uint32_t *fr = (uint32_t *)calloc(n, sizeof(uint32_t));
+  uint32_t kk = k < n ? k : n;
+  entry_t *top = (entry_t *)malloc((size_t)kk * sizeof(entry_t));
+  if (!order || !alpha || !omega || !dist || !queue || !fS || !fr || !top) { rc = ORC_ENOMEM; goto done; }
+  if (order_in)
+    memcpy(order, order_in, (size_t)n * sizeof(uint32_t));
+  else if ((rc = orc_degree_order(n, off, order)) != ORC_OK)
+    goto done;
+  if ((rc = orc_alpha_omega(n, off, col, directed, alpha, omega)) != ORC_OK) goto done;
+  for (uint32_t i = 0; i < n; ++i) dist[i] = UINT32_MAX;
+  orc_counters c = {0, 0, 0, 0};
+  uint32_t ntop = 0;
+  for (uint32_t oi = 0; oi < n; ++oi) {
+    uint32_t v = order[oi];
+    if (off[v + 1] == off[v]) continue; /* r(v) = 1: closeness 0 */
+    int have_x = ntop == kk;
+    uint64_t Sx = have_x ? top[kk - 1].S : 0;
+    uint32_t rx = have_x ? top[kk - 1].r : 0;
+    c.bfs_started++;
+    uint32_t head = 0, tail = 0;
+    dist[v] = 0;
+    queue[tail++] = v;
+    uint64_t Sd = 0, nd = 1, g = off[v + 1] - off[v];
+    uint32_t d = 0;
+    int cut = 0;
+    while (1) {
+      if (cut_exceeds(Sd, d, nd, g, alpha[v], omega[v], have_x, Sx, rx)) { cut = 1; break; }
+      uint32_t level_end = tail;
+      uint64_t cnt = 0, gs = 0;
+      while (head < level_end) {
+        uint32_t u = queue[head++];
+        c.edges_visited += off[u + 1] - off[u];
+        for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+          uint32_t w = col[e];
+          if (dist[w] == UINT32_MAX) {
+            dist[w] = d + 1;
+            queue[tail++] = w;
+            ++cnt;
+            gs += (off[w + 1] - off[w]) - (directed ? 0u : 1u);
+          }
+        }
+      }
+      if (cnt == 0) break;
+      ++d;
+      Sd += (uint64_t)d * cnt;
+      nd += cnt;
+      g = gs;
+    }
+    for (uint32_t i = 0; i < tail; ++i) dist[queue[i]] = UINT32_MAX;
+    if (cut) {
+      c.bfs_cut++;
+      continue;
+    }
+    c.bfs_finished++;
+    fS[v] = Sd;
+    fr[v] = (uint32_t)nd;
+    top_insert(top, &ntop, kk, Sd, (uint32_t)nd, v);
+  }
+  /* fewer than kk finished: fill with r = 1 vertices in id order */
+  for (uint32_t v = 0; v < n && ntop < kk; ++v)
+    if (off[v + 1] == off[v]) top_insert(top, &ntop, kk, 0, 1, v);
+  for (uint32_t i = 0; i < kk; ++i) {
+    ids[i] = top[i].id;
+    if (S_out) S_out[i] = top[i].S;
+    if (r_out) r_out[i] = top[i].r;
+  }
+  if (n_tied) {
+    uint32_t t = 0;
+    const entry_t *last = &top[kk - 1];
+    for (uint32_t v = 0; v < n; ++v) {
+      if (off[v + 1] == off[v]) {
+        if (last->r <= 1) ++t;
+      } else if (fr[v] && cmp_farness(fS[v], fr[v], last->S, last->r) == 0) {
+        ++t;
+      }
+    }
+    *n_tied = t;
+  }
+  if (allS) memcpy(allS, fS, (size_t)n * sizeof(uint64_t));
+  if (allr) memcpy(allr, fr, (size_t)n * sizeof(uint32_t));
+  if (ctr) *ctr = c;
+  rc = (int)kk;
+done:
+  free(order); free(alpha); free(omega); free(dist); free(queue); free(fS); free(fr); free(top);
+  return rc;
+}

@@ -1,0 +1,74 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case copies oracle.c to a temporary directory, plants one mistake (a
+dropped term, a wrong sign or index, a transposed operand, a weakened
+comparison), builds it, swaps it in for the real library and checks that at
+least one pin from test_oracle.py fails.  Nothing here touches the real build
+or any GPU."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle as pins
+
+MUTANTS = {
+    "bfs_dropped_distance": ("S += dist[w];", "S += dist[w] - (dist[w] > 1);",
+                             [pins.test_bfs_equals_floyd_warshall_random]),
+    "bfs_level_off_by_one": ("dist[w] = dist[u] + 1;\n        S += dist[w];",
+                             "dist[w] = dist[u] + 1 + (u == 0);\n        S += dist[w];",
+                             [pins.test_bfs_equals_floyd_warshall_random]),
+    "fw_wrong_index": ("if (D[i][m] + D[m][j] < D[i][j]) D[i][j] = D[i][m] + D[m][j];",
+                       "if (D[i][m] + D[j][m] < D[i][j]) D[i][j] = D[i][m] + D[j][m];",
+                       [lambda: pins.test_bfs_equals_floyd_warshall_exhaustive(4, True)]),
+    "order_transposed_operand": ("u128 lhs = (u128)Sa * (u128)((uint64_t)(rb - 1) * (uint64_t)(rb - 1));",
+                                 "u128 lhs = (u128)Sa * (u128)((uint64_t)(ra - 1) * (uint64_t)(rb - 1));",
+                                 [pins.test_topk_against_fraction_brute_force]),
+    "closeness_inverted": ("*closeness = den / num;", "*closeness = num / den;",
+                           [pins.test_closeness_against_networkx]),
+    "cut_bound_wrong_slope": ("return Sd + (uint64_t)(d + 1) * rem + extra;",
+                              "return Sd + (uint64_t)(d + 2) * rem + extra;",
+                              [pins.test_cut_bound_invariants]),
+    "cut_bound_missing_kink": ("if (kink > lo && kink < hi) cand[nc++] = kink;", "(void)kink;",
+                               [pins.test_cut_min_is_minimum_over_whole_interval]),
+    "cut_non_strict": ("return lhs > rhs;\n}", "return lhs >= rhs;\n}",
+                       [pins.test_bfscut_equals_textbook_small_random]),
+    "gamma_wrong_sign_undirected": ("gs += (off[w + 1] - off[w]) - (directed ? 0u : 1u);\n        }\n      }\n    }\n    if (cnt == 0) break;\n    ++d;\n    Sd += (uint64_t)d * cnt;\n    nd += cnt;\n    g = gs;\n  }\n  for",
+                                    "gs += (off[w + 1] - off[w]) - (directed ? 0u : 1u) - 1u;\n        }\n      }\n    }\n    if (cnt == 0) break;\n    ++d;\n    Sd += (uint64_t)d * cnt;\n    nd += cnt;\n    g = gs;\n  }\n  for",
+                                    [pins.test_cut_bound_invariants]),
+    "alpha_too_big": ("A[c] = a + w[c];", "A[c] = a + w[c] + (a > 0);",
+                      [pins.test_alpha_omega_bracket_reach_and_exact_on_biggest_scc]),
+    "omega_drops_biggest": ("o = o2 + O[big];", "o = o2;",
+                            [pins.test_alpha_omega_hand_built_dag]),
+    "tree_level2_off": ("cur[s] = sum - deg;", "cur[s] = sum - deg + 1;",
+                        [lambda: pins.test_tree_algorithm_matches_bfs(3)]),
+    "degree_order_unstable": ("for (uint32_t v = 0; v < n; ++v) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
+                              "for (uint32_t v = n; v-- > 0;) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
+                              [pins.test_degree_order_matches_lexsort]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new, checks = MUTANTS[name]
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    path = tmp_path / "oracle_mut.c"
+    path.write_text(src.replace(old, new))
+    lib = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", str(lib),
+                           str(path), "-lm"])
+    saved = oracle._load()
+    oracle._lib = oracle._bind(ctypes.CDLL(str(lib)))
+    try:
+        caught = False
+        for check in checks:
+            try:
+                check()
+            except AssertionError:
+                caught = True
+        assert caught, f"planted mistake {name} passed every pin"
+    finally:
+        oracle._lib = saved
