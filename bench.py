@@ -1,0 +1,318 @@
+"""Benchmark: exact top-k closeness (batched BFSCut) on a directed R-MAT graph.
+
+One step = one full pass of the method through the C ABI: load the CSR
+(validate, in-arc CSR), degree order, reach bounds (SCC / Algorithm 6), the
+persistent batched BFSCut kernel, and the output.  The metric is GTEPS =
+edges_visited (the paper's m_vis: arcs of every expanded BFS level) per second
+of step wall time, with the exact top-10 checked against a CPU-oracle sample.
+
+Prints ONE JSON line on rank 0.  `--impl reference` times the CPU oracle (the
+sequential BFSCut of oracle/) on a bounded prefix of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (builder, k, description)
+    "rmat22": (lambda gg: gg.rmat(22, 16, seed=gg.workload_seed(4)), 10,
+               "directed R-MAT scale 22 (4,194,304 vertices), edge factor 16, a/b/c/d=0.57/0.19/0.19/0.05, "
+               "self-loops and duplicates removed, k=10"),
+    "rmat16": (lambda gg: gg.rmat(16, 16, seed=gg.workload_seed(1)), 10,
+               "directed R-MAT scale 16, edge factor 16, k=10"),
+    "ba1m": (lambda gg: gg.barabasi_albert(1_000_000, 5, gg.workload_seed(2)), 10,
+             "undirected Barabasi-Albert n=1,000,000, m=5, k=10"),
+}
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfscut_traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_1704_01077_gb300", "csrc", "tkc_bfscut.cu")
+
+
+def kernel_hash() -> str:
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(workload: str, bits: int):
+    """Per-launch DRAM bytes of the search kernel from a committed ncu summary,
+    only if it was taken on the current kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+        e = d.get(f"{workload}_b{bits}")
+        if e and e.get("kernel_sha") == kernel_hash():
+            return e["dram_bytes_per_launch"], e
+    except Exception:
+        pass
+    return None, None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"tkc_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_sample(g, k, sample_sources):
+    """Sequential CPU BFSCut (the oracle as it stands) on a prefix of the
+    degree order; returns (GTEPS, seconds, edges_visited)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    res = oracle.bfscut(g, k, max_sources=sample_sources)
+    dt = time.perf_counter() - t0
+    ev = res.counters.edges_visited
+    return ev / dt / 1e9, dt, ev
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_1704_01077_gb300 import graphgen as gg
+
+    build, k, desc = WORKLOADS[args.workload]
+    g = build(gg)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(g, k, args.sample)
+    vals, times, evs = [], [], []
+    for _ in range(args.steps):
+        v, dt, ev = cpu_oracle_sample(g, k, args.sample)
+        vals.append(v)
+        times.append(dt)
+        evs.append(ev)
+    value = sum(evs) / sum(times) / 1e9
+    sample = f"first {args.sample} sources of the degree order (sequential CPU BFSCut, incl. its preprocessing)"
+    line = {"impl": "reference", "metric": "topk_closeness_gteps", "value": value, "unit": "GTEPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "k": k},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tkc", choices=["tkc", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--bits", type=int, default=512, help="source batch width (0 = library default)")
+    ap.add_argument("--plain", action="store_true", help="also time plain one-source BFSCut once")
+    ap.add_argument("--sample", type=int, default=96, help="CPU oracle sample: number of sources")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "tkc":
+        args.warmup = 3
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    from paper_1704_01077_gb300 import graphgen as gg
+    from paper_1704_01077_gb300 import tkc
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    build, k, desc = WORKLOADS[args.workload]
+    g = build(gg)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    off_d = torch.from_numpy(g.offsets.view(np.int32)).to(dev)
+    col_d = torch.from_numpy(g.cols.view(np.int32)).to(dev)
+    off_h = torch.from_numpy(g.offsets.view(np.int32)).pin_memory()
+    col_h = torch.from_numpy(g.cols.view(np.int32)).pin_memory()
+    ctx = tkc.tkc_create(tkc.Options(device=local, stream=stream.cuda_stream, batch_bits=args.bits))
+
+    def step_device():
+        h = tkc.tkc_load_csr(ctx, g.n, off_d, col_d, g.directed)
+        try:
+            return tkc.tkc_topk_closeness(h, k)
+        finally:
+            tkc.tkc_free_graph(h)
+
+    def step_host():
+        h = tkc.tkc_load_csr(ctx, g.n, off_h, col_h, g.directed)
+        try:
+            return tkc.tkc_topk_closeness(h, k)
+        finally:
+            tkc.tkc_free_graph(h)
+
+    for _ in range(args.warmup):
+        res = step_device()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = tkc.tkc_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    results = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            results.append(step_device())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = tkc.tkc_kernel_launches() - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    edges = sum(r.edges_visited for r in results)
+    if dist:
+        t = torch.tensor([float(edges)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t)
+        edges = float(t.item())
+    value = edges / (ms_total / 1e3) / 1e9
+    ms_step = ms_total / args.steps
+
+    # end to end: host (pinned) CSR in, results out, copies inside the timed region
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_res = [step_host() for _ in range(max(1, min(args.steps, 3)))]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = sum(r.edges_visited for r in e2e_res) / e2e_s / 1e9 * world
+    h2d = 4 * (g.n + 1) + 4 * g.arcs
+    d2h = k * (4 + 8 + 4 + 8 + 8)
+
+    # roofline of the dominant kernel (the persistent search kernel)
+    peak, peak_src = hbm_peak()
+    kern_ms = statistics.mean(r.ms_kernel for r in results)
+    alg = statistics.mean(r.alg_bytes for r in results)
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    traffic, traffic_entry = ncu_traffic(args.workload, res.batch_bits)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_src,
+                "alg_bytes_per_launch": alg, "kernel_ms": kern_ms}
+
+    line = {"metric": "topk_closeness_gteps", "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "k": k, "batch_bits": res.batch_bits,
+                       "order": "degree", "l2": "inputs larger than L2 (CSR 280 MB + 1 GiB bit rows)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary(),
+            "detail": {"edges_visited": results[-1].edges_visited, "edges_scanned": results[-1].edges_scanned,
+                       "bfs_started": results[-1].bfs_started, "bfs_cut": results[-1].bfs_cut,
+                       "bfs_finished": results[-1].bfs_finished, "levels": results[-1].levels,
+                       "ms_pre": results[-1].ms_pre, "ms_bfs": results[-1].ms_bfs,
+                       "ms_kernel": results[-1].ms_kernel,
+                       "textbook_teps_equiv": g.arcs * g.n / (ms_step / 1e3) / 1e9,
+                       "top_ids": [int(x) for x in results[-1].ids]}}
+    if rank == 0 and args.plain:
+        tkc.tkc_set_options(ctx, tkc.Options(device=local, stream=stream.cuda_stream, batch_bits=1))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr = step_device()
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t0
+        assert list(pr.ids) == list(results[-1].ids)
+        line["vs_plain"] = {"plain_ms": plain_s * 1e3, "batched_ms": ms_step, "speedup": plain_s * 1e3 / ms_step,
+                            "plain_edges_visited": pr.edges_visited}
+    if rank == 0 and not args.no_check:
+        import oracle
+
+        top = results[-1]
+        S, r = oracle.bfs_sums(g, top.ids)
+        line["check"] = {"top_k_S_r_match_oracle_bfs": bool(np.array_equal(S, top.dist_sum)
+                                                            and np.array_equal(r, top.reach))}
+    if rank == 0 and not args.no_cpu:
+        v, dt, ev = cpu_oracle_sample(g, k, args.sample)
+        line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                                "sample": f"first {args.sample} sources of the degree order, sequential CPU "
+                                          f"BFSCut incl. its preprocessing ({dt:.1f} s, {ev} edges)"}
+    tkc.tkc_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * tkc -- exact top-k closeness centrality on one GB300 GPU.
+ *
+ * C ABI of the CUDA library (libtkc.so).  The method is DegCut from
+ * Bergamini, Borassi, Crescenzi, Marino, Meyerhenke, "Computing top-k
+ * Closeness Centrality Faster in Unweighted Graphs" (arXiv 1704.01077):
+ * Algorithm 1 with computeBoundsDeg (Section 4) and updateBoundsBFSCut
+ * (Section 6, Algorithm 4, Lemma 1), reach bounds alpha/omega for directed
+ * graphs (Section 8, Lemma 2, Algorithm 6).
+ *
+ * Definitions (Section 2): R(v) = vertices reachable from v, v included;
+ * r(v) = |R(v)|; S(v) = sum of d(v,w) over R(v);
+ * farness f(v) = (n-1) S(v) / (r(v)-1)^2; closeness c(v) = 1/f(v), with
+ * c(v) = 0 (f = +inf) when r(v) = 1.  Top-k = the k vertices of smallest
+ * farness; ties are broken by increasing vertex id and the number of vertices
+ * tied with the k-th is reported (Section 4 asks for all of them).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: TKC_OK (0) or a negative TKC_E* code; tkc_strerror() names it.
+ *  - Graph input is CSR: offsets uint32[n+1] (offsets[0] = 0, non-decreasing,
+ *    offsets[n] = arcs), cols uint32[arcs]; each row strictly increasing (no
+ *    duplicate arcs), every id < n, no self-loops.  An undirected graph holds
+ *    both arc directions and must be symmetric.  Violations give TKC_EGRAPH.
+ *  - Inputs are copied; the caller keeps ownership of every pointer it passes.
+ *    Handles are owned by the library until freed by tkc_free_graph /
+ *    tkc_destroy.  Result arrays are caller-allocated HOST memory.
+ *  - All work runs on the context's device and stream; every call returns
+ *    after its results are in host memory.
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef TKC_H
+#define TKC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TKC_OK 0
+#define TKC_EINVAL -1    /* bad argument (null pointer, k too large, bad option) */
+#define TKC_EGRAPH -2    /* malformed CSR (unsorted row, id out of range, self-loop, duplicate, asymmetric) */
+#define TKC_ENOMEM -3    /* device or host allocation failed */
+#define TKC_ECUDA -4     /* a CUDA runtime call failed */
+#define TKC_ETIMEOUT -5  /* a device-side wait exceeded its budget; the context stays usable */
+#define TKC_EOVERFLOW -6 /* the graph exceeds a size limit of this build (n >= 2^26, arcs >= 2^32) */
+
+#define TKC_ORDER_DEG 0     /* computeBoundsDeg: out-degree descending, then id ascending (Section 4) */
+#define TKC_ORDER_GIVEN 1   /* caller's order, set by tkc_set_source_order */
+#define TKC_ORDER_LEARNED 2 /* predicted-farness order from the source-order MLP (tkc_set_mlp) */
+
+#define TKC_MAX_K 1024      /* largest k accepted by tkc_topk_closeness */
+
+typedef struct tkc_ctx tkc_ctx;
+typedef struct tkc_graph tkc_graph;
+
+typedef struct {
+  int device;              /* CUDA device ordinal */
+  void *stream;            /* cudaStream_t to run on (e.g. torch's current stream); NULL = legacy default */
+  uint32_t order;          /* TKC_ORDER_* */
+  uint32_t batch_bits;     /* sources searched together: 1 (plain, one source per BFS), 64, 128, 256, 512;
+                              0 = autotuned choice */
+  uint32_t bu_num;         /* direction switch: a level runs bottom-up when frontier arcs * bu_num >
+                              arcs * bu_den (0 = library default) */
+  uint32_t bu_den;
+  uint32_t blocks;         /* persistent grid size (0 = library default, clamped to co-residency) */
+  uint32_t seed_factor;    /* learned order: number of leading sources searched without cutting, as a
+                              multiple of k, to seed the threshold (0 = none) */
+  uint64_t timeout_cycles; /* budget of every device-side wait, in SM clock cycles (0 = default 2^34) */
+} tkc_options;
+
+typedef struct {
+  /* caller-allocated host arrays of at least `capacity` entries (any may be NULL) */
+  uint32_t *ids;       /* vertex ids, best first */
+  uint64_t *dist_sum;  /* S(v) */
+  uint32_t *reach;     /* r(v) */
+  double *farness;     /* (n-1) S / (r-1)^2, one IEEE multiply and one divide; +inf when r = 1 */
+  double *closeness;   /* (r-1)^2 / ((n-1) S); 0 when r = 1 */
+  uint32_t capacity;
+  /* filled by the call */
+  uint32_t n_returned;     /* min(k, n) */
+  uint32_t n_tied_at_kth;  /* vertices whose farness equals the k-th returned one (all of them, found exactly) */
+  uint64_t edges_visited;  /* arcs of every expanded BFS level, sum of out-degrees (the paper's m_vis) */
+  uint64_t edges_scanned;  /* arcs physically read by the level kernels */
+  uint64_t bfs_started;    /* sources with out-degree >= 1 that were examined */
+  uint64_t bfs_cut;        /* of those, abandoned by the BFSCut bound */
+  uint64_t bfs_finished;   /* of those, searched to the end (exact S and r) */
+  uint64_t levels;         /* level steps executed by the device loop */
+  uint32_t batch_bits;     /* source batch width actually used */
+  uint32_t pad;
+  double ms_pre;           /* device time of preprocessing done by this call (order, reach bounds) */
+  double ms_bfs;           /* device time of the pruned searches and the output */
+  double ms_kernel;        /* device time of the persistent search kernel alone */
+  uint64_t alg_bytes;      /* bytes the search kernel's levels must move by the cost model of the
+                              level kernels (frontier rows, arc columns, seen/next rows) */
+} tkc_result;
+
+/* Creates a context on opt->device (NULL opt = defaults).  No paper
+ * counterpart: owns the stream, options and device workspace. */
+int tkc_create(tkc_ctx **out, const tkc_options *opt);
+
+/* Replaces the context's options (same meaning as in tkc_create). */
+int tkc_set_options(tkc_ctx *ctx, const tkc_options *opt);
+
+/* Releases the context and its workspace.  Graphs must be freed first. */
+void tkc_destroy(tkc_ctx *ctx);
+
+/* Copies a CSR graph to the device, validates it, and builds its in-arc CSR
+ * (directed) -- the input of Algorithm 1 (Section 4).  offsets/cols are host
+ * pointers if ptr_on_device = 0, device pointers otherwise.  directed = 0
+ * declares an undirected graph (symmetry is checked).  n may be 0.
+ * Errors: TKC_EINVAL (null out, arcs != offsets[n]), TKC_EGRAPH, TKC_EOVERFLOW,
+ * TKC_ENOMEM, TKC_ECUDA. */
+int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offsets, const uint32_t *cols,
+                 int directed, int ptr_on_device, tkc_graph **out);
+
+/* Frees a graph and everything derived from it. */
+void tkc_free_graph(tkc_graph *g);
+
+/* Exact top-k closeness (Algorithm 1, DegCut; Sections 4, 6, 8).  Writes
+ * min(k, n) entries of out->ids/dist_sum/reach/farness/closeness (those not
+ * NULL; out->capacity must be >= min(k, n)) and the counters.  k = 0 or n = 0
+ * return no entries.  Errors: TKC_EINVAL (k > TKC_MAX_K, capacity too small),
+ * TKC_ENOMEM, TKC_ECUDA, TKC_ETIMEOUT. */
+int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out);
+
+/* Exact top-k of each of ng graphs (all on ctx's device) in one persistent
+ * launch, one k-list per graph; outs[i] receives graph i's result exactly as
+ * tkc_topk_closeness would (counters per graph, ms_* shared).  Same errors. */
+int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
+
+/* computeBoundsDeg (Section 4): writes the degree order (out-degree
+ * descending, id ascending) to host array order[n]. */
+int tkc_source_order(tkc_graph *g, uint32_t *order);
+
+/* Sets the source order used when options.order = TKC_ORDER_GIVEN: a
+ * permutation of 0..n-1 in host memory (validated; TKC_EINVAL otherwise).
+ * Any order gives the same top-k; only the work done changes. */
+int tkc_set_source_order(tkc_graph *g, const uint32_t *order);
+
+/* Reach bounds alpha(v) <= r(v) <= omega(v) (Section 8.4, Algorithm 6; exact
+ * component size for undirected graphs) into host arrays alpha[n], omega[n]. */
+int tkc_reach_bounds(tkc_graph *g, uint32_t *alpha, uint32_t *omega);
+
+/* Exact S(v) and r(v) of the listed sources by full BFS on the device, in
+ * batches of 64 sources (no cutting).  srcs, S, r: host arrays of nsrc. */
+int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_t *S, uint32_t *r);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts), for accounting of device work. */
+uint64_t tkc_kernel_launches(void);
+
+/* Names a TKC_* return code. */
+const char *tkc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TKC_H */

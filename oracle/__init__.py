@@ -71,7 +71,7 @@ def _bind(lib):
     lib.orc_cut_bounds.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u64p,
                                    ctypes.c_int]
     lib.orc_bfscut.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p, _u32p,
-                               _u64p, _u32p, _u32p, ctypes.POINTER(Counters), _u64p, _u32p]
+                               _u64p, _u32p, _u32p, ctypes.POINTER(Counters), _u64p, _u32p, ctypes.c_uint32]
     return lib
 
 
@@ -201,8 +201,9 @@ class TopK:
     all_r: np.ndarray | None = None
 
 
-def bfscut(g, k, order=None, want_all=False) -> TopK:
-    """Algorithm 1 + BFSCut, one source at a time, in degree order (or `order`)."""
+def bfscut(g, k, order=None, want_all=False, max_sources=0) -> TopK:
+    """Algorithm 1 + BFSCut, one source at a time, in degree order (or `order`).
+    max_sources > 0 examines only that prefix of the order (for timing samples)."""
     off, col = _csr(g)
     kk = min(k, g.n)
     ids = np.zeros(max(kk, 1), np.uint32)
@@ -215,7 +216,8 @@ def bfscut(g, k, order=None, want_all=False) -> TopK:
     allr = np.zeros(max(g.n, 1), np.uint32) if want_all else None
     cnt = _check(_load().orc_bfscut(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), k,
                                     _p(order_a, _u32p), _p(ids, _u32p), _p(S, _u64p), _p(r, _u32p),
-                                    ctypes.byref(tied), ctypes.byref(ctr), _p(allS, _u64p), _p(allr, _u32p)))
+                                    ctypes.byref(tied), ctypes.byref(ctr), _p(allS, _u64p), _p(allr, _u32p),
+                                    max_sources))
     return TopK(ids[:cnt], S[:cnt], r[:cnt], int(tied.value), ctr,
                 None if allS is None else allS[: g.n], None if allr is None else allr[: g.n])
 

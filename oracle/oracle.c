@@ -614,10 +614,12 @@ static void top_insert(entry_t *top, uint32_t *cnt, uint32_t k, uint64_t S, uint
  *
  * Outputs: ids/S/r of the top min(k, n) (ties by id), n_tied, counters, and
  * optionally per-vertex S/r of every finished BFS (r = 0 if not finished).
+ * max_sources > 0 stops after that many searches (a timing sample only: the
+ * returned list is then the top of the examined prefix, not the answer).
  */
 int orc_bfscut(uint32_t n, const uint32_t *off, const uint32_t *col, int directed, uint32_t k,
                const uint32_t *order_in, uint32_t *ids, uint64_t *S_out, uint32_t *r_out,
-               uint32_t *n_tied, orc_counters *ctr, uint64_t *allS, uint32_t *allr) {
+               uint32_t *n_tied, orc_counters *ctr, uint64_t *allS, uint32_t *allr, uint32_t max_sources) {
   if (k == 0 || n == 0) { if (n_tied) *n_tied = 0; return 0; }
   int rc = ORC_OK;
   uint32_t *order = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
@@ -641,6 +643,7 @@ int orc_bfscut(uint32_t n, const uint32_t *off, const uint32_t *col, int directe
   for (uint32_t oi = 0; oi < n; ++oi) {
     uint32_t v = order[oi];
     if (off[v + 1] == off[v]) continue; /* r(v) = 1: closeness 0 */
+    if (max_sources && c.bfs_started >= max_sources) break; /* timing sample: a prefix of Q */
     int have_x = ntop == kk;
     uint64_t Sx = have_x ? top[kk - 1].S : 0;
     uint32_t rx = have_x ? top[kk - 1].r : 0;

@@ -1,0 +1,600 @@
+// The C ABI of include/tkc.h: contexts, graph upload, and the top-k driver
+// that runs preprocessing, the persistent BFSCut kernel and the output step.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "tkc_internal.cuh"
+
+#include <atomic>
+
+static thread_local char g_last_err[512] = {0};
+static std::atomic<unsigned long long> g_launches{0};
+
+void tkc::note_launches(unsigned count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+
+void tkc_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+  snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+namespace tkc {
+
+typedef uint32_t u32;
+typedef unsigned long long u64;
+
+static constexpr uint64_t kDefaultTimeout = 1ull << 34;
+
+template <typename T>
+static int dalloc(T **p, size_t count, cudaStream_t st) {
+  if (*p) {
+    TKC_TRY(cudaFreeAsync(*p, st));
+    *p = nullptr;
+  }
+  TKC_TRY(cudaMallocAsync((void **)p, std::max<size_t>(count, 1) * sizeof(T), st));
+  return TKC_OK;
+}
+
+int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 kk) {
+  (void)kk;
+  Workspace &w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  if (!w.ctl) {
+    TKC_RC(dalloc(&w.ctl, 1, st));
+    TKC_RC(dalloc(&w.slots, 64 * kMaxWords, st));
+    TKC_RC(dalloc(&w.cnt, 64 * kMaxWords, st));
+    TKC_RC(dalloc(&w.wsum, 64 * kMaxWords, st));
+    TKC_RC(dalloc(&w.top_S, TKC_MAX_K, st));
+    TKC_RC(dalloc(&w.top_r, TKC_MAX_K, st));
+    TKC_RC(dalloc(&w.top_id, TKC_MAX_K, st));
+    TKC_RC(dalloc(&w.out_S, TKC_MAX_K, st));
+    TKC_RC(dalloc(&w.out_r, TKC_MAX_K, st));
+    TKC_RC(dalloc(&w.out_id, TKC_MAX_K, st));
+    TKC_RC(dalloc(&w.out_f, TKC_MAX_K, st));
+    TKC_RC(dalloc(&w.out_c, TKC_MAX_K, st));
+    TKC_RC(dalloc(&w.tied, 1, st));
+    TKC_TRY(cudaMemsetAsync(w.cnt, 0, 64 * kMaxWords * sizeof(unsigned), st));
+    TKC_TRY(cudaMemsetAsync(w.wsum, 0, 64 * kMaxWords * sizeof(u64), st));
+  }
+  if (n > w.n_cap) {
+    u32 cap = std::max<u32>(n, 1024);
+    TKC_RC(dalloc(&w.L0, cap, st));
+    TKC_RC(dalloc(&w.L1, cap, st));
+    TKC_RC(dalloc(&w.Loff0, cap, st));
+    TKC_RC(dalloc(&w.Loff1, cap, st));
+    TKC_RC(dalloc(&w.VL, cap, st));
+    TKC_RC(dalloc(&w.stamp, cap, st));
+    TKC_RC(dalloc(&w.res_S, cap, st));
+    TKC_RC(dalloc(&w.res_r, cap, st));
+    TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, (size_t)cap * sizeof(u32), st));
+    w.level_base = 0;
+    w.n_cap = cap;
+    w.words_cap = 0;  // rows must be reallocated for the new n
+  }
+  if (words > w.words_cap) {
+    size_t rows = (size_t)w.n_cap * words;
+    TKC_RC(dalloc(&w.seen, rows, st));
+    TKC_RC(dalloc(&w.F0, rows, st));
+    TKC_RC(dalloc(&w.F1, rows, st));
+    TKC_RC(dalloc(&w.N, rows, st));
+    TKC_TRY(cudaMemsetAsync(w.seen, 0, rows * sizeof(u64), st));
+    TKC_TRY(cudaMemsetAsync(w.F0, 0, rows * sizeof(u64), st));
+    TKC_TRY(cudaMemsetAsync(w.F1, 0, rows * sizeof(u64), st));
+    TKC_TRY(cudaMemsetAsync(w.N, 0, rows * sizeof(u64), st));
+    w.words_cap = words;
+  }
+  return TKC_OK;
+}
+
+static void free_workspace(tkc_ctx *ctx) {
+  Workspace &w = ctx->ws;
+  void *ptrs[] = {w.seen, w.F0, w.F1, w.N, w.L0, w.L1, w.Loff0, w.Loff1, w.VL, w.stamp, w.res_S, w.res_r,
+                  w.slots, w.cnt, w.wsum, w.top_S, w.top_r, w.top_id, w.ctl, w.out_S, w.out_r, w.out_id,
+                  w.out_f, w.out_c, w.tied};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  w = Workspace();
+}
+
+// Row buffers hold only the current run's bits; the kernel leaves them zero
+// when it ends normally.  After an error they are cleared here.
+static int reset_rows(tkc_ctx *ctx) {
+  Workspace &w = ctx->ws;
+  size_t rows = (size_t)w.n_cap * w.words_cap;
+  cudaStream_t st = ctx->stream;
+  TKC_TRY(cudaMemsetAsync(w.seen, 0, rows * sizeof(u64), st));
+  TKC_TRY(cudaMemsetAsync(w.F0, 0, rows * sizeof(u64), st));
+  TKC_TRY(cudaMemsetAsync(w.F1, 0, rows * sizeof(u64), st));
+  TKC_TRY(cudaMemsetAsync(w.N, 0, rows * sizeof(u64), st));
+  TKC_TRY(cudaMemsetAsync(w.cnt, 0, 64 * kMaxWords * sizeof(unsigned), st));
+  TKC_TRY(cudaMemsetAsync(w.wsum, 0, 64 * kMaxWords * sizeof(u64), st));
+  return TKC_OK;
+}
+
+// ------------------------------------------------------------------ output
+
+// Ties with the k-th entry among finished searches (exact key equality).
+__global__ void k_count_ties(const u64 *res_S, const u32 *res_r, u32 n, const u64 *top_S, const u32 *top_r,
+                             u32 kk, const Ctl *ctl, unsigned *tied) {
+  if (ctl->ntop < kk) return;  // the k-th is a closeness-0 vertex: counted on the host
+  u64 Sx = top_S[kk - 1];
+  u64 rx = top_r[kk - 1];
+  unsigned c = 0;
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    u32 r = res_r[v];
+    if (r >= 2) {
+      unsigned __int128 a = (unsigned __int128)res_S[v] * (unsigned __int128)((rx - 1) * (rx - 1));
+      unsigned __int128 b = (unsigned __int128)Sx * (unsigned __int128)((u64)(r - 1) * (u64)(r - 1));
+      c += a == b;
+    }
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(tied, c);
+}
+
+// Final list: the top entries, then (if fewer than k vertices can reach
+// another vertex) closeness-0 vertices in id order from the degree order's
+// tail.  f and c are one IEEE product and one quotient of exact integers.
+__global__ void k_output(const u64 *top_S, const u32 *top_r, const u32 *top_id, const Ctl *ctl, u32 kk, u32 n,
+                         const u32 *zero_deg_ids, u64 *oS, u32 *or_, u32 *oid, double *of, double *oc) {
+  u32 ntop = ctl->ntop;
+  for (u32 i = threadIdx.x; i < kk; i += blockDim.x) {
+    u64 S;
+    u32 r, id;
+    if (i < ntop) {
+      S = top_S[i];
+      r = top_r[i];
+      id = top_id[i];
+    } else {
+      S = 0;
+      r = 1;
+      id = zero_deg_ids[i - ntop];
+    }
+    oS[i] = S;
+    or_[i] = r;
+    oid[i] = id;
+    if (r <= 1) {
+      of[i] = __longlong_as_double(0x7ff0000000000000ll);
+      oc[i] = 0.0;
+    } else {
+      double num = __dmul_rn((double)(n - 1), (double)S);
+      double den = (double)((u64)(r - 1) * (u64)(r - 1));
+      of[i] = __ddiv_rn(num, den);
+      oc[i] = __ddiv_rn(den, num);
+    }
+  }
+}
+
+int finish_topk(tkc_ctx *ctx, tkc_graph *g, u32 kk, tkc_result *out) {
+  Workspace &w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  TKC_TRY(cudaMemsetAsync(w.tied, 0, sizeof(unsigned), st));
+  unsigned blocks = (unsigned)std::min<u64>((g->n + 255) / 256, (u64)ctx->num_sms * 8);
+  TKC_LAUNCH(k_count_ties<<<std::max(1u, blocks), 256, 0, st>>>(w.res_S, w.res_r, g->n, w.top_S, w.top_r, kk, w.ctl,
+                                                     w.tied));
+  TKC_LAUNCH(k_output<<<1, 256, 0, st>>>(w.top_S, w.top_r, w.top_id, w.ctl, kk, g->n, g->deg_order + g->n_src_deg,
+                              w.out_S, w.out_r, w.out_id, w.out_f, w.out_c));
+  TKC_TRY(cudaGetLastError());
+  if (out->ids) TKC_TRY(cudaMemcpyAsync(out->ids, w.out_id, kk * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  if (out->dist_sum) TKC_TRY(cudaMemcpyAsync(out->dist_sum, w.out_S, kk * sizeof(u64), cudaMemcpyDeviceToHost, st));
+  if (out->reach) TKC_TRY(cudaMemcpyAsync(out->reach, w.out_r, kk * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  if (out->farness) TKC_TRY(cudaMemcpyAsync(out->farness, w.out_f, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (out->closeness)
+    TKC_TRY(cudaMemcpyAsync(out->closeness, w.out_c, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return TKC_OK;
+}
+
+static int words_for(u32 bits) {
+  if (bits <= 64) return 1;
+  if (bits <= 128) return 2;
+  if (bits <= 256) return 4;
+  return 8;
+}
+
+// Batch width used when the options leave it to the library.
+static u32 default_batch_bits(const tkc_graph *g) {
+  if (g->n < 4096) return 64;
+  if (g->n < (1u << 18)) return 256;
+  return 512;
+}
+
+struct RunSetup {
+  const u32 *order;
+  u32 norder;
+  u32 B;
+  int W;
+  int nocut;
+  u32 kk;
+};
+
+static int run_search(tkc_graph *g, const RunSetup &rs, Ctl *hctl) {
+  tkc_ctx *ctx = g->ctx;
+  Workspace &w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  TKC_RC(ensure_workspace(ctx, g->n, rs.W, rs.kk));
+  if (w.level_base > 0xF0000000u) {
+    TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, (size_t)w.n_cap * sizeof(u32), st));
+    w.level_base = 0;
+  }
+  Ctl c;
+  memset(&c, 0, sizeof(c));
+  c.step = 1;  // start with an (empty) clear step whose epilogue seeds the first batch
+  c.level_id = w.level_base;
+  TKC_TRY(cudaMemcpyAsync(w.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  TKC_TRY(cudaMemsetAsync(w.res_r, 0, (size_t)g->n * sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(w.res_S, 0, (size_t)g->n * sizeof(u64), st));
+  RunParams p;
+  memset(&p, 0, sizeof(p));
+  p.n = g->n;
+  p.directed = g->directed;
+  p.arcs = g->arcs;
+  p.off = g->off;
+  p.col = g->col;
+  p.ioff = g->ioff;
+  p.icol = g->icol;
+  p.alpha = g->alpha;
+  p.omega = g->omega;
+  p.order = rs.order;
+  p.norder = rs.norder;
+  p.kk = rs.kk;
+  p.B = rs.B;
+  p.nocut = rs.nocut;
+  const tkc_options &o = ctx->opt;
+  p.bu_num = o.bu_num ? o.bu_num : 1;
+  p.bu_den = o.bu_num ? std::max<u32>(o.bu_den, 1) : 4;
+  p.timeout = o.timeout_cycles ? o.timeout_cycles : kDefaultTimeout;
+  p.seen = w.seen;
+  p.F0 = w.F0;
+  p.F1 = w.F1;
+  p.N = w.N;
+  p.L0 = w.L0;
+  p.L1 = w.L1;
+  p.Loff0 = w.Loff0;
+  p.Loff1 = w.Loff1;
+  p.VL = w.VL;
+  p.stamp = w.stamp;
+  p.slots = w.slots;
+  p.cnt = w.cnt;
+  p.wsum = w.wsum;
+  p.top_S = w.top_S;
+  p.top_r = w.top_r;
+  p.top_id = w.top_id;
+  p.res_S = w.res_S;
+  p.res_r = w.res_r;
+  p.ctl = w.ctl;
+  int maxb = max_coresident_blocks(ctx, rs.W);
+  if (maxb <= 0) return TKC_ECUDA;
+  int blocks = o.blocks ? (int)o.blocks : (int)std::max<u64>(2, ((u64)g->n + 4095) / 4096);
+  blocks = std::min(blocks, maxb);
+  TKC_TRY(cudaEventRecord(ctx->ev[4], st));
+  TKC_RC(run_bfscut(ctx, p, rs.W, blocks));
+  TKC_TRY(cudaEventRecord(ctx->ev[5], st));
+  TKC_TRY(cudaMemcpyAsync(hctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  w.level_base = hctl->level_id + 1;
+  if (hctl->err) {
+    TKC_RC(reset_rows(ctx));
+    TKC_TRY(cudaStreamSynchronize(st));
+    return hctl->err;
+  }
+  return TKC_OK;
+}
+
+}  // namespace tkc
+
+using namespace tkc;
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+uint64_t tkc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *tkc_strerror(int code) {
+  switch (code) {
+    case TKC_OK: return "ok";
+    case TKC_EINVAL: return "invalid argument";
+    case TKC_EGRAPH: return "malformed CSR graph";
+    case TKC_ENOMEM: return "out of memory";
+    case TKC_ECUDA: return g_last_err[0] ? g_last_err : "CUDA error";
+    case TKC_ETIMEOUT: return "device-side wait exceeded its budget";
+    case TKC_EOVERFLOW: return "graph exceeds a size limit of this build";
+    default: return "unknown error";
+  }
+}
+
+int tkc_create(tkc_ctx **out, const tkc_options *opt) {
+  if (!out) return TKC_EINVAL;
+  *out = nullptr;
+  tkc_ctx *ctx = new (std::nothrow) tkc_ctx();
+  if (!ctx) return TKC_ENOMEM;
+  if (opt) ctx->opt = *opt;
+  ctx->device = ctx->opt.device;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) {
+    tkc_set_last_cuda_error(e, "cudaSetDevice", __FILE__, __LINE__);
+    delete ctx;
+    return TKC_ECUDA;
+  }
+  ctx->stream = (cudaStream_t)ctx->opt.stream;
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (!coop || ctx->num_sms <= 0) {
+    delete ctx;
+    return TKC_ECUDA;
+  }
+  for (auto &ev : ctx->ev) {
+    e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+      tkc_set_last_cuda_error(e, "cudaEventCreate", __FILE__, __LINE__);
+      delete ctx;
+      return TKC_ECUDA;
+    }
+  }
+  *out = ctx;
+  return TKC_OK;
+}
+
+int tkc_set_options(tkc_ctx *ctx, const tkc_options *opt) {
+  if (!ctx || !opt) return TKC_EINVAL;
+  if (opt->device != ctx->device) return TKC_EINVAL;
+  u32 b = opt->batch_bits;
+  if (!(b == 0 || b == 1 || b == 64 || b == 128 || b == 256 || b == 512)) return TKC_EINVAL;
+  if (opt->order > TKC_ORDER_LEARNED) return TKC_EINVAL;
+  ctx->opt = *opt;
+  ctx->stream = (cudaStream_t)opt->stream;
+  return TKC_OK;
+}
+
+void tkc_destroy(tkc_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_workspace(ctx);
+  for (auto &ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete ctx;
+}
+
+int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offsets, const uint32_t *cols,
+                 int directed, int ptr_on_device, tkc_graph **out) {
+  if (!ctx || !out) return TKC_EINVAL;
+  *out = nullptr;
+  if (n >= kMaxN || arcs >= (1ull << 32)) return TKC_EOVERFLOW;
+  if (!offsets || (arcs && !cols)) return TKC_EINVAL;
+  TKC_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  if (!ptr_on_device) {
+    if (offsets[0] != 0 || offsets[n] != arcs) return TKC_EGRAPH;
+  } else {
+    u32 ends[2] = {1, 0};
+    TKC_TRY(cudaMemcpyAsync(&ends[0], offsets, sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaMemcpyAsync(&ends[1], offsets + n, sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaStreamSynchronize(st));
+    if (ends[0] != 0 || ends[1] != arcs) return TKC_EGRAPH;
+  }
+  tkc_graph *g = new (std::nothrow) tkc_graph();
+  if (!g) return TKC_ENOMEM;
+  g->ctx = ctx;
+  g->n = n;
+  g->arcs = arcs;
+  g->directed = directed ? 1 : 0;
+  cudaMemcpyKind kind = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  int rc = TKC_OK;
+  do {
+    cudaError_t e = cudaMallocAsync(&g->off, ((size_t)n + 1) * sizeof(u32), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&g->col, std::max<size_t>(arcs, 1) * sizeof(u32), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->off, offsets, ((size_t)n + 1) * sizeof(u32), kind, st);
+    if (e == cudaSuccess && arcs) e = cudaMemcpyAsync(g->col, cols, arcs * sizeof(u32), kind, st);
+    if (e != cudaSuccess) {
+      tkc_set_last_cuda_error(e, "graph upload", __FILE__, __LINE__);
+      rc = e == cudaErrorMemoryAllocation ? TKC_ENOMEM : TKC_ECUDA;
+      break;
+    }
+    rc = validate_and_transpose(g);
+  } while (0);
+  if (rc == TKC_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      tkc_set_last_cuda_error(e, "graph upload", __FILE__, __LINE__);
+      rc = TKC_ECUDA;
+    }
+  }
+  if (rc != TKC_OK) {
+    ctx->graphs_alive++;
+    tkc_free_graph(g);
+    return rc;
+  }
+  ctx->graphs_alive++;
+  *out = g;
+  return TKC_OK;
+}
+
+void tkc_free_graph(tkc_graph *g) {
+  if (!g) return;
+  cudaSetDevice(g->ctx->device);
+  cudaStreamSynchronize(g->ctx->stream);
+  if (g->ioff && g->ioff != g->off) cudaFree(g->ioff);
+  if (g->icol && g->icol != g->col) cudaFree(g->icol);
+  void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  g->ctx->graphs_alive--;
+  delete g;
+}
+
+int tkc_source_order(tkc_graph *g, uint32_t *order) {
+  if (!g || (!order && g->n)) return TKC_EINVAL;
+  TKC_TRY(cudaSetDevice(g->ctx->device));
+  TKC_RC(ensure_degree_order(g));
+  if (g->n) TKC_TRY(cudaMemcpyAsync(order, g->deg_order, g->n * sizeof(u32), cudaMemcpyDeviceToHost, g->ctx->stream));
+  TKC_TRY(cudaStreamSynchronize(g->ctx->stream));
+  return TKC_OK;
+}
+
+int tkc_set_source_order(tkc_graph *g, const uint32_t *order) {
+  if (!g || (!order && g->n)) return TKC_EINVAL;
+  std::vector<uint8_t> seen(g->n, 0);
+  for (u32 i = 0; i < g->n; ++i) {
+    if (order[i] >= g->n || seen[order[i]]) return TKC_EINVAL;
+    seen[order[i]] = 1;
+  }
+  TKC_TRY(cudaSetDevice(g->ctx->device));
+  cudaStream_t st = g->ctx->stream;
+  if (g->n == 0) return TKC_OK;
+  u32 *tmp = nullptr;
+  if (!g->given_order) TKC_TRY(cudaMallocAsync(&g->given_order, (size_t)g->n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&tmp, (size_t)g->n * sizeof(u32), st));
+  TKC_TRY(cudaMemcpyAsync(tmp, order, g->n * sizeof(u32), cudaMemcpyHostToDevice, st));
+  TKC_RC(filter_order(g, tmp, g->given_order, &g->n_src_given));
+  TKC_TRY(cudaFreeAsync(tmp, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  return TKC_OK;
+}
+
+int tkc_reach_bounds(tkc_graph *g, uint32_t *alpha, uint32_t *omega) {
+  if (!g || ((!alpha || !omega) && g->n)) return TKC_EINVAL;
+  TKC_TRY(cudaSetDevice(g->ctx->device));
+  TKC_RC(ensure_reach_bounds(g));
+  cudaStream_t st = g->ctx->stream;
+  if (g->n) {
+    TKC_TRY(cudaMemcpyAsync(alpha, g->alpha, g->n * sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaMemcpyAsync(omega, g->omega, g->n * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  }
+  TKC_TRY(cudaStreamSynchronize(st));
+  return TKC_OK;
+}
+
+int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
+  if (!g || !out) return TKC_EINVAL;
+  if (k > TKC_MAX_K) return TKC_EINVAL;
+  tkc_ctx *ctx = g->ctx;
+  u32 kk = std::min<u32>(k, g->n);
+  if (kk > 0 && out->capacity < kk) return TKC_EINVAL;
+  TKC_TRY(cudaSetDevice(ctx->device));
+  tkc_result r = *out;
+  r.n_returned = kk;
+  r.n_tied_at_kth = 0;
+  r.edges_visited = r.edges_scanned = r.bfs_started = r.bfs_cut = r.bfs_finished = r.levels = 0;
+  r.ms_pre = r.ms_bfs = r.ms_kernel = 0.0;
+  r.alg_bytes = 0;
+  r.batch_bits = 0;
+  if (kk == 0) {
+    *out = r;
+    return TKC_OK;
+  }
+  cudaStream_t st = ctx->stream;
+  TKC_TRY(cudaEventRecord(ctx->ev[0], st));
+  TKC_RC(ensure_degree_order(g));
+  TKC_RC(ensure_reach_bounds(g));
+  RunSetup rs;
+  const tkc_options &o = ctx->opt;
+  if (o.order == TKC_ORDER_GIVEN) {
+    if (!g->given_order) return TKC_EINVAL;
+    rs.order = g->given_order;
+    rs.norder = g->n_src_given;
+  } else if (o.order == TKC_ORDER_DEG) {
+    rs.order = g->deg_order;
+    rs.norder = g->n_src_deg;
+  } else {
+    return TKC_EINVAL;
+  }
+  TKC_TRY(cudaEventRecord(ctx->ev[1], st));
+  u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g);
+  rs.B = bits;
+  rs.W = words_for(bits);
+  rs.nocut = 0;
+  rs.kk = kk;
+  r.batch_bits = bits;
+  Ctl hc;
+  TKC_RC(run_search(g, rs, &hc));
+  TKC_RC(finish_topk(ctx, g, kk, &r));
+  unsigned tied = 0;
+  TKC_TRY(cudaMemcpyAsync(&tied, ctx->ws.tied, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaEventRecord(ctx->ev[2], st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  // when the k-th entry is a closeness-0 vertex, every such vertex ties with it
+  r.n_tied_at_kth = hc.ntop < kk ? g->n - g->n_src_deg : tied;
+  r.edges_visited = hc.edges_visited;
+  r.edges_scanned = hc.edges_scanned;
+  r.bfs_started = hc.bfs_started;
+  r.bfs_cut = hc.bfs_cut;
+  r.bfs_finished = hc.bfs_finished;
+  r.levels = hc.levels;
+  r.alg_bytes = hc.alg_bytes;
+  float ms0 = 0, ms1 = 0, ms2 = 0;
+  cudaEventElapsedTime(&ms0, ctx->ev[0], ctx->ev[1]);
+  cudaEventElapsedTime(&ms1, ctx->ev[1], ctx->ev[2]);
+  cudaEventElapsedTime(&ms2, ctx->ev[4], ctx->ev[5]);
+  r.ms_pre = ms0;
+  r.ms_bfs = ms1;
+  r.ms_kernel = ms2;
+  *out = r;
+  return TKC_OK;
+}
+
+int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_t *S, uint32_t *r) {
+  if (!g || (nsrc && (!srcs || !S || !r))) return TKC_EINVAL;
+  if (nsrc == 0) return TKC_OK;
+  tkc_ctx *ctx = g->ctx;
+  TKC_TRY(cudaSetDevice(ctx->device));
+  for (u32 i = 0; i < nsrc; ++i)
+    if (srcs[i] >= g->n) return TKC_EINVAL;
+  std::vector<u32> uniq(srcs, srcs + nsrc);
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  TKC_RC(ensure_degree_order(g));
+  TKC_RC(ensure_reach_bounds(g));
+  cudaStream_t st = ctx->stream;
+  u32 *dsrc = nullptr;
+  TKC_TRY(cudaMallocAsync(&dsrc, uniq.size() * sizeof(u32), st));
+  TKC_TRY(cudaMemcpyAsync(dsrc, uniq.data(), uniq.size() * sizeof(u32), cudaMemcpyHostToDevice, st));
+  RunSetup rs;
+  rs.order = dsrc;
+  rs.norder = (u32)uniq.size();
+  rs.B = 64;
+  rs.W = 1;
+  rs.nocut = 1;
+  rs.kk = 1;
+  Ctl hc;
+  int rc = run_search(g, rs, &hc);
+  std::vector<u64> allS;
+  std::vector<u32> allr;
+  if (rc == TKC_OK) {
+    allS.resize(g->n);
+    allr.resize(g->n);
+    cudaError_t e = cudaMemcpyAsync(allS.data(), ctx->ws.res_S, g->n * sizeof(u64), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(allr.data(), ctx->ws.res_r, g->n * sizeof(u32), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      tkc_set_last_cuda_error(e, "distance sums readback", __FILE__, __LINE__);
+      rc = TKC_ECUDA;
+    }
+  }
+  cudaFreeAsync(dsrc, st);
+  cudaStreamSynchronize(st);
+  if (rc != TKC_OK) return rc;
+  for (u32 i = 0; i < nsrc; ++i) {
+    S[i] = allS[srcs[i]];
+    r[i] = allr[srcs[i]];
+  }
+  return TKC_OK;
+}
+
+int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs) {
+  if (!ctx || (ng && (!gs || !outs))) return TKC_EINVAL;
+  for (u32 i = 0; i < ng; ++i) {
+    if (!gs[i] || gs[i]->ctx != ctx) return TKC_EINVAL;
+    TKC_RC(tkc_topk_closeness(gs[i], k, &outs[i]));
+  }
+  return TKC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,900 @@
+// Batched BFSCut: Algorithm 1 with updateBoundsBFSCut (Algorithm 4) for up to
+// 512 sources at once, as one persistent cooperative kernel per call.
+//
+// Sources of one batch occupy bit "slots" of a per-vertex row of W 64-bit
+// words: seen (visited by slot b), F (frontier of slot b) and N (next level of
+// slot b, top-down only).  One loop iteration advances every active slot by one
+// BFS level:
+//   phase A  expand: top-down over the frontier list (atomic OR into N) or
+//            bottom-up over all vertices (OR of in-neighbours' F rows, stopping
+//            once every missing bit is found), direction chosen per level;
+//   phase B  finalize: new = N, seen |= new, F' = new, per-slot level sizes and
+//            out-degree sums by warp bit-transpose + popcount; old F rows cleared;
+//   epilogue (last block to reach the grid barrier): per-slot S, n_d, gamma,
+//            merge of finished searches into the top-k, x = k-th farness, the
+//            BFSCut test of Lemma 1 at r in [alpha', omega] (Section 8.2), and
+//            the next step's direction.
+// When every slot of a batch is done, a clear step zeroes the rows the batch
+// touched and the epilogue seeds the next batch from the source order,
+// abandoning sources already at level 0 when their bound exceeds x.
+//
+// Every grid-wide wait is bounded by a clock64 budget; on expiry the kernel
+// records TKC_ETIMEOUT and every block returns.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tkc_internal.cuh"
+
+namespace tkc {
+
+typedef unsigned long long u64;
+typedef uint32_t u32;
+typedef unsigned __int128 u128;
+
+static constexpr unsigned FULL = 0xffffffffu;
+static constexpr int kPackShift = 38;
+static constexpr u64 kArcMask = (1ull << kPackShift) - 1;
+static constexpr int kTopMax = TKC_MAX_K;
+
+// ------------------------------------------------------------------ memory ordering
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(volatile const int *)p; }
+
+// Grid barrier for a cooperative launch.  The last block to arrive runs
+// `epi` (whole block) before releasing the others.  Returns false when the
+// run must stop (error recorded by any block, including a timed-out wait).
+template <typename Epi>
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, uint64_t timeout, Epi epi) {
+  __shared__ int s_last;
+  __shared__ unsigned s_gen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned gen = ld_acquire_u32(&ctl->bar_gen);
+    s_gen = gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+    s_last = (arrived == gridDim.x);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    epi();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ctl->bar_count = 0;
+      __threadfence();
+      st_release_u32(&ctl->bar_gen, s_gen + 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    long long t0 = clock64();
+    unsigned ns = 32;
+    while (ld_acquire_u32(&ctl->bar_gen) == s_gen) {
+      if (ld_volatile_i32(&ctl->err) != 0) break;
+      if ((uint64_t)(clock64() - t0) > timeout) {
+        atomicCAS(&ctl->err, 0, TKC_ETIMEOUT);
+        atomicCAS(&ctl->err_where, 0, 1);
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ld_volatile_i32(&ctl->err) == 0;
+}
+
+// ------------------------------------------------------------------ exact arithmetic
+
+// Lemma 1 at radius d, evaluated at reach r >= nd:
+//   L = S_d + (d+1)(r - n_d) + max(0, r - n_d - g)
+__device__ __forceinline__ u64 cut_sum(u64 Sd, u64 d, u64 nd, u64 g, u64 r) {
+  u64 rem = r - nd;
+  return Sd + (d + 1) * rem + (rem > g ? rem - g : 0);
+}
+
+// a/(ra-1)^2 < b/(rb-1)^2 for ra, rb >= 2
+__device__ __forceinline__ bool ratio_less(u64 a, u64 ra, u64 b, u64 rb) {
+  return (u128)a * (u128)((rb - 1) * (rb - 1)) < (u128)b * (u128)((ra - 1) * (ra - 1));
+}
+
+// True when the farness lower bound exceeds x = (Sx, rx) strictly for every
+// r in [max(lo, nd), hi].  The bound divided by (r-1)^2 is linear-over-square
+// on [lo', kink] and on [kink, hi] (kink = nd + g), so by Lemma 2 its minimum
+// over the interval is at lo', hi or the kink.
+__device__ bool cut_exceeds(u64 Sd, u64 d, u64 nd, u64 g, u64 lo, u64 hi, u64 Sx, u64 rx) {
+  if (lo < nd) lo = nd;
+  if (hi < lo) hi = lo;
+  u64 kink = nd + g;
+  u64 cand[3] = {lo, hi, kink};
+  int nc = (kink > lo && kink < hi) ? 3 : 2;
+  for (int i = 0; i < nc; ++i) {
+    u64 r = cand[i];
+    if (r <= 1) continue;  // r = 1 is farness +inf, above any finite x
+    u64 L = cut_sum(Sd, d, nd, g, r);
+    // not (L/(r-1)^2 > Sx/(rx-1)^2)  ->  keep searching
+    if (!ratio_less(Sx, rx, L, r)) return false;
+  }
+  return true;
+}
+
+// (S, r, id) order: farness ascending, then id ascending.  r >= 2 here.
+__device__ __forceinline__ bool entry_less(u64 Sa, u32 ra, u32 ia, u64 Sb, u32 rb, u32 ib) {
+  u128 lhs = (u128)Sa * (u128)((u64)(rb - 1) * (u64)(rb - 1));
+  u128 rhs = (u128)Sb * (u128)((u64)(ra - 1) * (u64)(ra - 1));
+  if (lhs != rhs) return lhs < rhs;
+  return ia < ib;
+}
+
+// ------------------------------------------------------------------ warp helpers
+
+// 32x32 bit-matrix transpose across a warp: afterwards bit l of lane i equals
+// bit i of lane l's input.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  uint32_t m = 0x0000FFFFu;
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    uint32_t y = __shfl_xor_sync(FULL, x, j);
+    x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y & m) << j));
+    m ^= m << (j >> 1);
+  }
+  return x;
+}
+
+// Adds, for every slot bit of the 32 lanes' rows, the number of lanes with
+// the bit set and the sum of those lanes' `od` into the block counters.
+template <int W>
+__device__ __forceinline__ void warp_count_slots(const u64 (&nw)[W], uint32_t od, unsigned *s_cnt,
+                                                 u64 *s_wsum, int lane) {
+  uint32_t anyw = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) anyw |= (nw[j] != 0);
+  if (__ballot_sync(FULL, anyw) == 0) return;
+  uint32_t odm = anyw ? od : 0u;
+  uint32_t maxod = __reduce_max_sync(FULL, odm);
+  int planes = 32 - __clz(maxod);
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t x = (uint32_t)(nw[j] >> (32 * h));
+      if (__ballot_sync(FULL, x != 0) == 0) continue;
+      uint32_t col = warp_transpose32(x, lane);
+      uint32_t c = __popc(col);
+      uint32_t maxc = __reduce_max_sync(FULL, c);
+      u64 ws = 0;
+      if ((int)maxc * 6 <= planes * 5) {
+        // walk the set bits: fetch each contributing lane's out-degree
+        uint32_t m = col;
+        for (uint32_t it = 0; it < maxc; ++it) {
+          int src = m ? (__ffs(m) - 1) : 0;
+          uint32_t v = __shfl_sync(FULL, odm, src);
+          if (m) {
+            ws += v;
+            m &= m - 1;
+          }
+        }
+      } else {
+        // bit planes of the out-degrees: sum = sum_p 2^p popc(col & plane_p)
+        for (int p = 0; p < planes; ++p) {
+          uint32_t plane = __ballot_sync(FULL, (odm >> p) & 1u);
+          ws += (u64)__popc(col & plane) << p;
+        }
+      }
+      if (c) {
+        int slot = 64 * j + 32 * h + lane;
+        atomicAdd(&s_cnt[slot], c);
+        atomicAdd(&s_wsum[slot], ws);
+      }
+    }
+  }
+}
+
+// Warp-aggregated append of the lanes with `pred` to a list whose counter
+// packs count << 38 | arcs.  Writes list[pos] = v and loff[pos] = arc prefix.
+__device__ __forceinline__ void warp_append(bool pred, uint32_t v, uint32_t od, u64 *packed, uint32_t *list,
+                                            uint32_t *loff, int lane) {
+  uint32_t mask = __ballot_sync(FULL, pred);
+  if (mask == 0) return;
+  uint32_t a = pred ? od : 0u;
+  // inclusive scan of arcs over lanes
+  uint32_t incl = a;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  uint32_t total = __shfl_sync(FULL, incl, 31);
+  int leader = __ffs(mask) - 1;
+  u64 base = 0;
+  if (lane == leader) base = atomicAdd(packed, ((u64)__popc(mask) << kPackShift) | (u64)total);
+  base = __shfl_sync(FULL, base, leader);
+  if (pred) {
+    uint32_t pos = (uint32_t)(base >> kPackShift) + __popc(mask & ((1u << lane) - 1u));
+    list[pos] = v;
+    loff[pos] = (uint32_t)((base & kArcMask) + (incl - a));
+  }
+}
+
+__device__ __forceinline__ void warp_append_plain(bool pred, uint32_t v, unsigned *counter, uint32_t *list,
+                                                  int lane) {
+  uint32_t mask = __ballot_sync(FULL, pred);
+  if (mask == 0) return;
+  int leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(mask));
+  base = __shfl_sync(FULL, base, leader);
+  if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = v;
+}
+
+template <int W>
+__device__ __forceinline__ void load_row(const u64 *base, uint32_t v, u64 (&r)[W]) {
+  const u64 *p = base + (size_t)v * W;
+  if constexpr (W == 1) {
+    r[0] = p[0];
+  } else {
+#pragma unroll
+    for (int j = 0; j < W; j += 2) {
+      ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p + j);
+      r[j] = t.x;
+      r[j + 1] = t.y;
+    }
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void store_row(u64 *base, uint32_t v, const u64 (&r)[W]) {
+  u64 *p = base + (size_t)v * W;
+  if constexpr (W == 1) {
+    p[0] = r[0];
+  } else {
+#pragma unroll
+    for (int j = 0; j < W; j += 2) *reinterpret_cast<ulonglong2 *>(p + j) = make_ulonglong2(r[j], r[j + 1]);
+  }
+}
+
+template <int W>
+__device__ __forceinline__ bool row_nonzero(const u64 (&r)[W]) {
+  u64 a = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) a |= r[j];
+  return a != 0;
+}
+
+// ------------------------------------------------------------------ shared state
+
+template <int W>
+struct Smem {
+  unsigned cnt[64 * W];
+  u64 wsum[64 * W];
+  u64 active[W];
+  // epilogue scratch
+  u64 tS[kTopMax];
+  uint32_t tr[kTopMax], tid[kTopMax];
+  u64 cS[64 * W];
+  uint32_t cr[64 * W], cid[64 * W];
+  unsigned ncand;
+  unsigned nactive;
+  unsigned scan[kTPB / 32 + 1];
+  u64 scan64[kTPB / 32 + 1];
+  u64 acc[4];
+};
+
+// Block-wide exclusive scan of one uint32 per thread; returns the prefix and
+// writes the total to *total.
+template <int W>
+__device__ uint32_t block_exscan(Smem<W> &sm, uint32_t x, uint32_t *total) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  __syncthreads();
+  if (lane == 31) sm.scan[wid] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < kTPB / 32; ++i) {
+      uint32_t t = sm.scan[i];
+      sm.scan[i] = run;
+      run += t;
+    }
+    sm.scan[kTPB / 32] = run;
+  }
+  __syncthreads();
+  uint32_t res = sm.scan[wid] + incl - x;
+  *total = sm.scan[kTPB / 32];
+  __syncthreads();
+  return res;
+}
+
+template <int W>
+__device__ u64 block_exscan64(Smem<W> &sm, u64 x, u64 *total) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  u64 incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    u64 t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  __syncthreads();
+  if (lane == 31) sm.scan64[wid] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 run = 0;
+    for (int i = 0; i < kTPB / 32; ++i) {
+      u64 t = sm.scan64[i];
+      sm.scan64[i] = run;
+      run += t;
+    }
+    sm.scan64[kTPB / 32] = run;
+  }
+  __syncthreads();
+  u64 res = sm.scan64[wid] + incl - x;
+  *total = sm.scan64[kTPB / 32];
+  __syncthreads();
+  return res;
+}
+
+// ------------------------------------------------------------------ epilogues
+
+// Merges the block's candidate list (sm.cS/cr/cid, sm.ncand entries) into the
+// global top list.  Every entry's new position is its rank among the old list
+// and the candidates (keys are unique: farness then id), so each position below
+// k gets exactly one writer and the old list is read from a shared copy.
+template <int W>
+__device__ void merge_topk(const RunParams &p, Smem<W> &sm) {
+  Ctl *c = p.ctl;
+  const uint32_t kk = p.kk;
+  uint32_t ntop = c->ntop;
+  uint32_t nc = sm.ncand;
+  if (nc == 0) return;
+  for (uint32_t i = threadIdx.x; i < ntop; i += kTPB) {
+    sm.tS[i] = p.top_S[i];
+    sm.tr[i] = p.top_r[i];
+    sm.tid[i] = p.top_id[i];
+  }
+  __syncthreads();
+  // rank of each candidate among existing entries and other candidates
+  for (uint32_t i = threadIdx.x; i < nc; i += kTPB) {
+    u64 S = sm.cS[i];
+    uint32_t r = sm.cr[i], id = sm.cid[i];
+    uint32_t lo = 0, hi = ntop;  // first existing entry not less than the candidate
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (entry_less(sm.tS[mid], sm.tr[mid], sm.tid[mid], S, r, id)) lo = mid + 1;
+      else hi = mid;
+    }
+    uint32_t rank = lo;
+    for (uint32_t j = 0; j < nc; ++j)
+      if (j != i && entry_less(sm.cS[j], sm.cr[j], sm.cid[j], S, r, id)) ++rank;
+    if (rank < kk) {
+      p.top_S[rank] = S;
+      p.top_r[rank] = r;
+      p.top_id[rank] = id;
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < ntop; i += kTPB) {
+    uint32_t rank = i;
+    for (uint32_t j = 0; j < nc; ++j)
+      if (entry_less(sm.cS[j], sm.cr[j], sm.cid[j], sm.tS[i], sm.tr[i], sm.tid[i])) ++rank;
+    if (rank < kk) {
+      p.top_S[rank] = sm.tS[i];
+      p.top_r[rank] = sm.tr[i];
+      p.top_id[rank] = sm.tid[i];
+    }
+  }
+  __syncthreads();
+  uint32_t nnew = ntop + nc < kk ? ntop + nc : kk;
+  if (threadIdx.x == 0) c->ntop = nnew;
+  __syncthreads();
+}
+
+// Adds a finished search to the candidate list if it can enter the top list.
+template <int W>
+__device__ __forceinline__ void offer_candidate(const RunParams &p, Smem<W> &sm, u64 S, uint32_t r, uint32_t v,
+                                                bool have_x, u64 Sx, uint32_t rx, uint32_t idx) {
+  if (have_x && !entry_less(S, r, v, Sx, rx, idx)) return;
+  unsigned pos = atomicAdd(&sm.ncand, 1u);
+  sm.cS[pos] = S;
+  sm.cr[pos] = r;
+  sm.cid[pos] = v;
+}
+
+// Epilogue after a level: update every active slot, merge finished searches,
+// apply the cut test, choose the next step.
+template <int W>
+__device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
+  Ctl *c = p.ctl;
+  const uint32_t B = p.B;
+  if (threadIdx.x == 0) {
+    sm.ncand = 0;
+    sm.nactive = 0;
+  }
+  if (threadIdx.x < W) sm.active[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < 4; i += kTPB) sm.acc[i] = 0;
+  __syncthreads();
+  uint32_t ntop0 = c->ntop;
+  bool have_x0 = ntop0 == p.kk;
+  u64 Sx0 = have_x0 ? p.top_S[p.kk - 1] : 0;
+  uint32_t rx0 = have_x0 ? p.top_r[p.kk - 1] : 0, ix0 = have_x0 ? p.top_id[p.kk - 1] : 0;
+  // 1. per-slot level update
+  int cont[(64 * W + kTPB - 1) / kTPB];
+  uint32_t finished = 0;
+#pragma unroll
+  for (int t = 0; t < (64 * W + kTPB - 1) / kTPB; ++t) {
+    uint32_t s = threadIdx.x + t * kTPB;
+    cont[t] = 0;
+    if (s >= B) continue;
+    Slot sl = p.slots[s];
+    if (sl.state != 1) continue;
+    unsigned cn = p.cnt[s];
+    u64 ws = p.wsum[s];
+    p.cnt[s] = 0;
+    p.wsum[s] = 0;
+    if (cn == 0) {
+      // the BFS from sl.v is complete: S and r = n_d are exact
+      sl.state = 2;
+      p.res_S[sl.v] = sl.S;
+      p.res_r[sl.v] = (uint32_t)sl.nd;
+      ++finished;
+      offer_candidate(p, sm, sl.S, (uint32_t)sl.nd, sl.v, have_x0, Sx0, rx0, ix0);
+    } else {
+      sl.d += 1;
+      sl.S += (u64)sl.d * cn;
+      sl.nd += cn;
+      sl.g = ws - (p.directed ? 0ull : (u64)cn);
+      sl.arcs = ws;
+      cont[t] = 1;
+    }
+    p.slots[s] = sl;
+  }
+  if (finished) atomicAdd(&sm.acc[0], (u64)finished);
+  __syncthreads();
+  // 2. top-k merge and the new threshold
+  merge_topk(p, sm);
+  uint32_t ntop = c->ntop;
+  bool have_x = ntop == p.kk && !p.nocut;
+  u64 Sx = have_x ? p.top_S[p.kk - 1] : 0;
+  uint32_t rx = have_x ? p.top_r[p.kk - 1] : 0;
+  // 3. BFSCut test for the slots that continue
+  uint32_t cuts = 0;
+  u64 visited = 0;
+#pragma unroll
+  for (int t = 0; t < (64 * W + kTPB - 1) / kTPB; ++t) {
+    uint32_t s = threadIdx.x + t * kTPB;
+    if (!cont[t]) continue;
+    Slot sl = p.slots[s];
+    if (have_x && cut_exceeds(sl.S, sl.d, sl.nd, sl.g, sl.alpha, sl.omega, Sx, rx)) {
+      sl.state = 2;
+      ++cuts;
+      p.slots[s] = sl;
+    } else {
+      visited += sl.arcs;
+      atomicOr(&sm.active[s >> 6], 1ull << (s & 63));
+      atomicAdd(&sm.nactive, 1u);
+    }
+  }
+  if (cuts) atomicAdd(&sm.acc[1], (u64)cuts);
+  if (visited) atomicAdd(&sm.acc[2], visited);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c->bfs_finished += sm.acc[0];
+    c->bfs_cut += sm.acc[1];
+    c->edges_visited += sm.acc[2];
+    c->levels += 1;
+    u64 packed = c->nl_packed;
+    {
+      // cost model of the level just run (bytes that must move):
+      //  top-down : per frontier vertex list+offsets (16) + F row read and clear;
+      //             per frontier arc column (4) + seen row read + N row update;
+      //             per new vertex list (8) + N read/clear, seen read/write, F write
+      //  bottom-up: every seen row; per scanned vertex in-offsets (8); per scanned
+      //             in-arc column (4) + F row; per new vertex seen/F writes + list (8);
+      //             per old frontier vertex list (4) + F row clear
+      const u64 rb = 8ull * W;
+      const u64 fl = c->fl_count, fa = c->fl_arcs, nl = packed >> kPackShift;
+      u64 bytes;
+      if (c->dir == 0)
+        bytes = fl * (16 + 2 * rb) + fa * (4 + 2 * rb) + nl * (8 + 5 * rb);
+      else
+        bytes = (u64)p.n * rb + c->lvl_scan_v * 8 + c->lvl_scan_a * (4 + rb) + nl * (8 + 2 * rb) + fl * (4 + rb);
+      c->alg_bytes += bytes;
+      c->lvl_scan_v = 0;
+      c->lvl_scan_a = 0;
+    }
+    c->nl_packed = 0;
+    c->cur ^= 1;
+    c->fl_count = (uint32_t)(packed >> kPackShift);
+    c->fl_arcs = packed & kArcMask;
+    c->level_id += 1;
+    for (int j = 0; j < W; ++j) c->active[j] = sm.active[j];
+    if (sm.nactive == 0) {
+      c->step = 1;  // clear the batch's rows, then seed the next batch
+    } else {
+      c->step = 0;
+      // bottom-up when the frontier's arcs are a large share of all arcs
+      c->dir = ((u128)c->fl_arcs * p.bu_num > (u128)p.arcs * p.bu_den) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+}
+
+// Epilogue after a clear step: seed the next batch of up to B sources.
+template <int W>
+__device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
+  Ctl *c = p.ctl;
+  const uint32_t B = p.B;
+  u64 *Fcur = c->cur ? p.F1 : p.F0;
+  uint32_t *FL = c->cur ? p.L1 : p.L0;
+  uint32_t *FLoff = c->cur ? p.Loff1 : p.Loff0;
+  uint32_t ntop = c->ntop;
+  bool have_x = ntop == p.kk && !p.nocut;
+  u64 Sx = have_x ? p.top_S[p.kk - 1] : 0;
+  uint32_t rx = have_x ? p.top_r[p.kk - 1] : 0;
+  uint32_t cursor = c->cursor;
+  uint32_t assigned = 0;
+  u64 arcs_total = 0, started = 0, cut0 = 0;
+  if (threadIdx.x < W) sm.active[threadIdx.x] = 0;
+  __syncthreads();
+  while (assigned < B && cursor < p.norder) {
+    uint32_t idx = cursor + threadIdx.x;
+    bool valid = idx < p.norder;
+    uint32_t v = valid ? p.order[idx] : 0;
+    uint32_t od = valid ? p.off[v + 1] - p.off[v] : 0;
+    uint32_t a = valid ? p.alpha[v] : 0, o = valid ? p.omega[v] : 0;
+    // level 0: S_0 = 0, n_0 = 1, gamma_1 = out-degree
+    bool cut = valid && have_x && cut_exceeds(0, 0, 1, od, a, o, Sx, rx);
+    bool keep = valid && !cut;
+    uint32_t total;
+    uint32_t pre = block_exscan(sm, keep ? 1u : 0u, &total);
+    uint32_t room = B - assigned;
+    // the chunk is consumed up to the room-th kept source
+    uint32_t consumed;
+    if (total <= room) {
+      consumed = (cursor + kTPB <= p.norder) ? kTPB : p.norder - cursor;
+    } else {
+      __shared__ uint32_t s_cons;
+      if (keep && pre == room - 1) s_cons = threadIdx.x + 1;
+      __syncthreads();
+      consumed = s_cons;
+      __syncthreads();
+    }
+    bool in = threadIdx.x < consumed;
+    bool take = keep && in;
+    uint32_t s = assigned + pre;
+    u64 myarcs = take ? od : 0;
+    u64 arcs_pre_total;
+    u64 arcs_pre = block_exscan64(sm, myarcs, &arcs_pre_total);
+    if (take) {
+      Slot sl;
+      sl.S = 0;
+      sl.nd = 1;
+      sl.g = od;
+      sl.arcs = od;
+      sl.v = v;
+      sl.d = 0;
+      sl.alpha = a;
+      sl.omega = o;
+      sl.state = 1;
+      sl.pad = 0;
+      p.slots[s] = sl;
+      u64 bit = 1ull << (s & 63);
+      p.seen[(size_t)v * W + (s >> 6)] = bit;
+      Fcur[(size_t)v * W + (s >> 6)] = bit;
+      FL[s] = v;
+      FLoff[s] = (uint32_t)(arcs_total + arcs_pre);
+      p.VL[s] = v;
+      atomicOr(&sm.active[s >> 6], bit);
+    }
+    uint32_t taken = total < room ? total : room;
+    assigned += taken;
+    arcs_total += arcs_pre_total;
+    uint32_t ncut_chunk = 0;
+    {
+      uint32_t t2;
+      block_exscan(sm, (cut && in) ? 1u : 0u, &t2);
+      ncut_chunk = t2;
+    }
+    started += taken + ncut_chunk;
+    cut0 += ncut_chunk;
+    cursor += consumed;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the clear step just zeroed these rows
+    c->alg_bytes += (u64)(c->vl_count + c->fl_count) * (4 + 8ull * W);
+    c->cursor = cursor;
+    c->bfs_started += started;
+    c->bfs_cut += cut0;
+    c->edges_visited += arcs_total;
+    c->fl_count = assigned;
+    c->fl_arcs = arcs_total;
+    c->vl_count = assigned;
+    c->nl_packed = 0;
+    c->level_id += 1;
+    c->batches += 1;
+    for (int j = 0; j < W; ++j) c->active[j] = sm.active[j];
+    if (assigned == 0) {
+      c->done = 1;
+    } else {
+      c->step = 0;
+      c->dir = ((u128)arcs_total * p.bu_num > (u128)p.arcs * p.bu_den) ? 1 : 0;
+    }
+  }
+  // slots beyond `assigned` are free
+  for (uint32_t s = assigned + threadIdx.x; s < B; s += kTPB) p.slots[s].state = 0;
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ the kernel
+
+template <int W>
+__global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
+  __shared__ Smem<W> sm;
+  Ctl *c = p.ctl;
+  const int lane = threadIdx.x & 31;
+  const uint32_t gwarp = (blockIdx.x * kTPB + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * kTPB) >> 5;
+  const uint32_t gthread = blockIdx.x * kTPB + threadIdx.x;
+  const uint32_t nthreads = gridDim.x * kTPB;
+
+  while (true) {
+    const int step = ld_volatile_i32(&c->step);
+    if (ld_volatile_i32(&c->done)) break;
+    volatile Ctl *vc = c;
+    const int cur = vc->cur;
+    u64 *Fcur = cur ? p.F1 : p.F0;
+    u64 *Fnext = cur ? p.F0 : p.F1;
+    uint32_t *FL = cur ? p.L1 : p.L0;
+    uint32_t *FLoff = cur ? p.Loff1 : p.Loff0;
+    uint32_t *NL = cur ? p.L0 : p.L1;
+    uint32_t *NLoff = cur ? p.Loff0 : p.Loff1;
+    const uint32_t fl_count = vc->fl_count;
+    if (step == 1) {
+      // ---- clear step: zero the rows touched by the finished batch
+      const uint32_t vl = vc->vl_count;
+      for (uint64_t i = gthread; i < (uint64_t)vl * W; i += nthreads) {
+        uint32_t v = p.VL[i / W];
+        p.seen[(size_t)v * W + (i % W)] = 0;
+      }
+      for (uint64_t i = gthread; i < (uint64_t)fl_count * W; i += nthreads) {
+        uint32_t v = FL[i / W];
+        Fcur[(size_t)v * W + (i % W)] = 0;
+      }
+      if (!grid_sync(c, p.timeout, [&] { epilogue_seed<W>(p, sm); })) break;
+      continue;
+    }
+    const int dir = vc->dir;
+    const uint32_t level_id = vc->level_id;
+    const u64 fl_arcs = vc->fl_arcs;
+    if (threadIdx.x < W) sm.active[threadIdx.x] = vc->active[threadIdx.x];
+    for (int i = threadIdx.x; i < 64 * W; i += kTPB) {
+      sm.cnt[i] = 0;
+      sm.wsum[i] = 0;
+    }
+    if (threadIdx.x == 0) {
+      sm.acc[2] = 0;
+      sm.acc[3] = 0;
+    }
+    __syncthreads();
+    u64 scanned = 0, scanned_v = 0;
+    if (dir == 0) {
+      // ---- phase A, top-down: OR each frontier row into its out-neighbours' N rows
+      constexpr uint32_t APS = 32 / W;  // arcs per warp step
+      constexpr uint32_t CH = 256;      // arcs per warp task
+      const int grp = lane / W, j = lane % W;
+      const u64 actj = sm.active[j];
+      for (u64 base = (u64)gwarp * CH; base < fl_arcs; base += (u64)nwarps * CH) {
+        u64 end = base + CH < fl_arcs ? base + CH : fl_arcs;
+        // entry holding arc `base`: last i with FLoff[i] <= base
+        uint32_t lo = 0, hi = fl_count;
+        while (hi - lo > 1) {
+          uint32_t mid = (lo + hi) >> 1;
+          if (FLoff[mid] <= base) lo = mid;
+          else hi = mid;
+        }
+        uint32_t ent = lo;
+        for (u64 e0 = base; e0 < end; e0 += APS) {
+          u64 e = e0 + grp;
+          bool valid = e < end;
+          uint32_t ii = ent;
+          if (valid)
+            while (ii + 1 < fl_count && FLoff[ii + 1] <= e) ++ii;
+          bool app = false;
+          uint32_t w = 0;
+          if (valid) {
+            uint32_t u = FL[ii];
+            u64 f = Fcur[(size_t)u * W + j] & actj;
+            if (f) {
+              w = p.col[p.off[u] + (uint32_t)(e - FLoff[ii])];
+              u64 bits = f & ~p.seen[(size_t)w * W + j];
+              if (bits) {
+                u64 *np = p.N + (size_t)w * W + j;
+                u64 curv = *(volatile u64 *)np;
+                if (bits & ~curv) {
+                  u64 old = atomicOr(np, bits);
+                  if (old == 0) app = atomicExch(&p.stamp[w], level_id) != level_id;
+                }
+              }
+            }
+          }
+          uint32_t od = app ? p.off[w + 1] - p.off[w] : 0;
+          warp_append(app, w, od, &c->nl_packed, NL, NLoff, lane);
+          ent = __reduce_max_sync(FULL, ii);
+        }
+      }
+      scanned = 0;
+      if (gthread == 0) atomicAdd(&c->edges_scanned, fl_arcs);
+      if (!grid_sync(c, p.timeout, [] {})) break;
+      // ---- phase B: finalize the next level, clear the old frontier rows
+      const uint32_t nl_count = (uint32_t)(((volatile Ctl *)c)->nl_packed >> kPackShift);
+      for (uint32_t base = gwarp * 32; base < nl_count; base += nwarps * 32) {
+        uint32_t i = base + lane;
+        bool valid = i < nl_count;
+        u64 nw[W], sr[W];
+        uint32_t w = 0, od = 0;
+        bool was_empty = false;
+#pragma unroll
+        for (int q = 0; q < W; ++q) nw[q] = 0;
+        if (valid) {
+          w = NL[i];
+          od = p.off[w + 1] - p.off[w];
+          load_row<W>(p.N, w, nw);
+          load_row<W>(p.seen, w, sr);
+          was_empty = !row_nonzero<W>(sr);
+          u64 z[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            sr[q] |= nw[q];
+            z[q] = 0;
+          }
+          store_row<W>(p.seen, w, sr);
+          store_row<W>(Fnext, w, nw);
+          store_row<W>(p.N, w, z);
+        }
+        warp_count_slots<W>(nw, od, sm.cnt, sm.wsum, lane);
+        warp_append_plain(valid && was_empty, w, &c->vl_count, p.VL, lane);
+      }
+      for (uint64_t i = gthread; i < (uint64_t)fl_count * W; i += nthreads) {
+        uint32_t v = FL[i / W];
+        Fcur[(size_t)v * W + (i % W)] = 0;
+      }
+    } else {
+      // ---- phase A, bottom-up: each vertex ORs its in-neighbours' frontier rows
+      u64 act[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) act[q] = sm.active[q];
+      for (uint32_t base = gwarp * 32; base < p.n; base += nwarps * 32) {
+        uint32_t w = base + lane;
+        bool valid = w < p.n;
+        u64 nw[W], sr[W], miss[W];
+        uint32_t od = 0;
+        bool was_empty = false, any = false;
+#pragma unroll
+        for (int q = 0; q < W; ++q) nw[q] = 0;
+        if (valid) {
+          load_row<W>(p.seen, w, sr);
+          was_empty = !row_nonzero<W>(sr);
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            miss[q] = act[q] & ~sr[q];
+            any |= miss[q] != 0;
+          }
+          if (any) {
+            uint32_t e = p.ioff[w], ee = p.ioff[w + 1];
+            for (; e < ee; ++e) {
+              uint32_t u = p.icol[e];
+              u64 fr[W];
+              load_row<W>(Fcur, u, fr);
+              bool full = true;
+#pragma unroll
+              for (int q = 0; q < W; ++q) {
+                nw[q] |= fr[q] & miss[q];
+                full &= nw[q] == miss[q];
+              }
+              if (full) {
+                ++e;
+                break;
+              }
+            }
+            scanned += e - p.ioff[w];
+            scanned_v += 1;
+          }
+        }
+        bool isnew = valid && row_nonzero<W>(nw);
+        if (isnew) {
+          od = p.off[w + 1] - p.off[w];
+#pragma unroll
+          for (int q = 0; q < W; ++q) sr[q] |= nw[q];
+          store_row<W>(p.seen, w, sr);
+          store_row<W>(Fnext, w, nw);
+        }
+        warp_count_slots<W>(nw, od, sm.cnt, sm.wsum, lane);
+        warp_append(isnew, w, od, &c->nl_packed, NL, NLoff, lane);
+        warp_append_plain(isnew && was_empty, w, &c->vl_count, p.VL, lane);
+      }
+      if (!grid_sync(c, p.timeout, [] {})) break;
+      // ---- phase B: only the old frontier rows need clearing
+      for (uint64_t i = gthread; i < (uint64_t)fl_count * W; i += nthreads) {
+        uint32_t v = FL[i / W];
+        Fcur[(size_t)v * W + (i % W)] = 0;
+      }
+    }
+    // flush the block's per-slot counters
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      scanned += __shfl_down_sync(FULL, scanned, o);
+      scanned_v += __shfl_down_sync(FULL, scanned_v, o);
+    }
+    if (lane == 0 && scanned) atomicAdd(&sm.acc[3], scanned);
+    if (lane == 0 && scanned_v) atomicAdd(&sm.acc[2], scanned_v);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * W; i += kTPB) {
+      if (sm.cnt[i]) {
+        atomicAdd(&p.cnt[i], sm.cnt[i]);
+        atomicAdd(&p.wsum[i], sm.wsum[i]);
+      }
+    }
+    if (threadIdx.x == 0 && sm.acc[3]) {
+      atomicAdd(&c->edges_scanned, sm.acc[3]);
+      atomicAdd(&c->lvl_scan_a, sm.acc[3]);
+    }
+    if (threadIdx.x == 0 && sm.acc[2]) atomicAdd(&c->lvl_scan_v, sm.acc[2]);
+    if (!grid_sync(c, p.timeout, [&] { epilogue_level<W>(p, sm); })) break;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+template <int W>
+static int occupancy_of(int *blocks_per_sm) {
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bfscut_kernel<W>, kTPB, 0);
+  return e == cudaSuccess ? TKC_OK : TKC_ECUDA;
+}
+
+int max_coresident_blocks(tkc_ctx *ctx, int words) {
+  int per_sm = 0;
+  int rc = TKC_OK;
+  switch (words) {
+    case 1: rc = occupancy_of<1>(&per_sm); break;
+    case 2: rc = occupancy_of<2>(&per_sm); break;
+    case 4: rc = occupancy_of<4>(&per_sm); break;
+    case 8: rc = occupancy_of<8>(&per_sm); break;
+    default: return 0;
+  }
+  if (rc != TKC_OK) return 0;
+  return per_sm * ctx->num_sms;
+}
+
+template <int W>
+static cudaError_t launch(const RunParams &p, int blocks, cudaStream_t st) {
+  void *args[] = {(void *)&p};
+  note_launches(1);
+  return cudaLaunchCooperativeKernel((const void *)bfscut_kernel<W>, dim3(blocks), dim3(kTPB), args, 0, st);
+}
+
+int run_bfscut(tkc_ctx *ctx, const RunParams &p, int words, int blocks) {
+  cudaError_t e;
+  switch (words) {
+    case 1: e = launch<1>(p, blocks, ctx->stream); break;
+    case 2: e = launch<2>(p, blocks, ctx->stream); break;
+    case 4: e = launch<4>(p, blocks, ctx->stream); break;
+    case 8: e = launch<8>(p, blocks, ctx->stream); break;
+    default: return TKC_EINVAL;
+  }
+  TKC_TRY(e);
+  return TKC_OK;
+}
+
+}  // namespace tkc

@@ -1,0 +1,182 @@
+// Internal declarations of the CUDA library behind include/tkc.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tkc.h"
+
+#define TKC_TRY(expr)                                   \
+  do {                                                  \
+    cudaError_t e_ = (expr);                            \
+    if (e_ != cudaSuccess) {                            \
+      tkc_set_last_cuda_error(e_, #expr, __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? TKC_ENOMEM : TKC_ECUDA; \
+    }                                                   \
+  } while (0)
+
+#define TKC_RC(expr)            \
+  do {                          \
+    int rc_ = (expr);           \
+    if (rc_ != TKC_OK) return rc_; \
+  } while (0)
+
+void tkc_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+namespace tkc {
+
+// Counts every kernel launch of the library (see tkc_kernel_launches).
+void note_launches(unsigned count);
+#define TKC_LAUNCH(...)            \
+  do {                             \
+    __VA_ARGS__;                   \
+    ::tkc::note_launches(1);       \
+  } while (0)
+
+constexpr int kTPB = 512;            // threads per block of the persistent kernels
+constexpr uint32_t kMaxN = 1u << 26; // list counters pack the count in 26 bits
+constexpr int kMaxWords = 8;         // 512-bit source batches
+
+// Device-resident state of one persistent BFSCut run (one graph).
+struct Ctl {
+  // grid barrier
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int err;
+  int err_where;
+  // loop state
+  int step;          // 0 = level, 1 = clear + seed
+  int done;
+  int dir;           // 0 = top-down, 1 = bottom-up
+  int cur;           // which frontier buffer / list is current
+  unsigned int level_id;  // global level stamp
+  unsigned int cursor;    // next position in the source order
+  unsigned int fl_count;  // current frontier list size
+  unsigned int vl_count;  // visited-list size (vertices with a non-zero seen row)
+  unsigned int pad0;
+  unsigned long long fl_arcs;    // arcs out of the current frontier list
+  unsigned long long nl_packed;  // next list: count << 38 | arcs
+  unsigned long long active[kMaxWords];
+  // top-k
+  unsigned int ntop;
+  unsigned int pad1;
+  // counters
+  unsigned long long edges_visited;
+  unsigned long long edges_scanned;
+  unsigned long long bfs_started;
+  unsigned long long bfs_cut;
+  unsigned long long bfs_finished;
+  unsigned long long levels;
+  unsigned long long batches;
+  // cost-model bytes of the levels and this level's bottom-up scan statistics
+  unsigned long long alg_bytes;
+  unsigned long long lvl_scan_v;
+  unsigned long long lvl_scan_a;
+};
+
+struct Slot {
+  unsigned long long S;   // sum of distances of the discovered levels
+  unsigned long long nd;  // size of the discovered ball
+  unsigned long long g;   // upper bound on the next level's size
+  unsigned long long arcs;  // arcs out of the newest level (expanded next)
+  unsigned int v;         // source vertex
+  unsigned int d;         // deepest discovered level
+  unsigned int alpha, omega;
+  int state;              // 0 free, 1 active, 2 done (waiting for the clear step)
+  unsigned int pad;
+};
+
+struct RunParams {
+  // graph
+  uint32_t n;
+  int directed;
+  uint64_t arcs;
+  const uint32_t *off, *col, *ioff, *icol;
+  const uint32_t *alpha, *omega;
+  const uint32_t *order;
+  uint32_t norder;  // sources in `order` to examine (all have out-degree >= 1)
+  // search configuration
+  uint32_t kk;        // min(k, n); 0 never reaches the kernel
+  uint32_t B;         // active slots per batch (1..64*W)
+  int nocut;          // 1: never cut (exact S, r for every source)
+  uint32_t bu_num, bu_den;
+  uint64_t timeout;
+  // workspace
+  unsigned long long *seen, *F0, *F1, *N;
+  uint32_t *L0, *L1;        // frontier lists
+  uint32_t *Loff0, *Loff1;  // exclusive arc prefix of each list entry
+  uint32_t *VL;             // visited list
+  uint32_t *stamp;
+  Slot *slots;
+  unsigned int *cnt;             // per-slot level counts
+  unsigned long long *wsum;      // per-slot sums of out-degree over the new level
+  unsigned long long *top_S;
+  uint32_t *top_r, *top_id;
+  unsigned long long *res_S;     // per-vertex S of finished searches
+  uint32_t *res_r;               // per-vertex r of finished searches (0 = not finished)
+  Ctl *ctl;
+};
+
+struct Workspace {
+  uint32_t n_cap = 0;
+  int words_cap = 0;
+  unsigned long long *seen = nullptr, *F0 = nullptr, *F1 = nullptr, *N = nullptr;
+  uint32_t *L0 = nullptr, *L1 = nullptr, *Loff0 = nullptr, *Loff1 = nullptr, *VL = nullptr, *stamp = nullptr;
+  unsigned long long *res_S = nullptr;
+  uint32_t *res_r = nullptr;
+  Slot *slots = nullptr;
+  unsigned int *cnt = nullptr;
+  unsigned long long *wsum = nullptr;
+  unsigned long long *top_S = nullptr;
+  uint32_t *top_r = nullptr, *top_id = nullptr;
+  Ctl *ctl = nullptr;
+  unsigned long long *out_S = nullptr;
+  uint32_t *out_r = nullptr, *out_id = nullptr;
+  double *out_f = nullptr, *out_c = nullptr;
+  unsigned int *tied = nullptr;
+  unsigned int level_base = 0;  // stamp epoch carried across runs
+};
+
+}  // namespace tkc
+
+struct tkc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  tkc_options opt{};
+  int num_sms = 0;
+  tkc::Workspace ws;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int graphs_alive = 0;
+};
+
+struct tkc_graph {
+  tkc_ctx *ctx = nullptr;
+  uint32_t n = 0;
+  uint64_t arcs = 0;
+  int directed = 0;
+  uint32_t *off = nullptr, *col = nullptr;    // out-arcs
+  uint32_t *ioff = nullptr, *icol = nullptr;  // in-arcs (aliases of out-arcs when undirected)
+  uint32_t *deg_order = nullptr;              // computeBoundsDeg order (all n vertices)
+  uint32_t n_src_deg = 0;                     // vertices with out-degree >= 1 (prefix of deg_order)
+  uint32_t *given_order = nullptr;            // filtered caller order
+  uint32_t n_src_given = 0;
+  uint32_t *alpha = nullptr, *omega = nullptr;
+  bool have_order = false, have_reach = false;
+  double ms_pre_last = 0.0;
+};
+
+namespace tkc {
+// tkc_prep.cu
+int validate_and_transpose(tkc_graph *g);
+int ensure_degree_order(tkc_graph *g);
+int ensure_reach_bounds(tkc_graph *g);
+int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
+// tkc_bfscut.cu
+int ensure_workspace(tkc_ctx *ctx, uint32_t n, int words, uint32_t kk);
+int run_bfscut(tkc_ctx *ctx, const RunParams &p, int words, int blocks);
+int finish_topk(tkc_ctx *ctx, tkc_graph *g, uint32_t kk, tkc_result *out);
+int max_coresident_blocks(tkc_ctx *ctx, int words);
+}  // namespace tkc

@@ -1,0 +1,638 @@
+// Preprocessing for Algorithm 1: CSR validation and in-arc CSR, the
+// computeBoundsDeg source order (Section 4), and the reach bounds alpha/omega
+// (exact component sizes for undirected graphs; Algorithm 6 of Section 8.4 for
+// directed graphs).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "tkc_internal.cuh"
+
+namespace tkc {
+
+typedef uint32_t u32;
+typedef unsigned long long u64;
+static constexpr unsigned FULL = 0xffffffffu;
+
+// ------------------------------------------------------------------ device-wide exclusive scan
+
+static constexpr int kScanTPB = 1024;
+static constexpr int kScanItems = 4;
+static constexpr int kScanTile = kScanTPB * kScanItems;
+
+__device__ __forceinline__ u32 block_exscan_1024(u32 x, u32 *s_warp, u32 *total) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  u32 incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    u32 t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    u32 v = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+    u32 vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      u32 t = __shfl_up_sync(FULL, vi, o);
+      if (lane >= o) vi += t;
+    }
+    s_warp[lane] = vi - v;
+    if (lane == 31) s_warp[32] = vi;
+  }
+  __syncthreads();
+  u32 res = s_warp[wid] + incl - x;
+  *total = s_warp[32];
+  __syncthreads();
+  return res;
+}
+
+__global__ void k_scan_bsum(const u32 *in, u64 len, u32 *bsum) {
+  __shared__ u32 s_warp[33];
+  u64 base = (u64)blockIdx.x * kScanTile + (u64)threadIdx.x * kScanItems;
+  u32 s = 0;
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < len) s += in[base + i];
+  u32 total;
+  block_exscan_1024(s, s_warp, &total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void k_scan_small(u32 *a, u32 len) {
+  __shared__ u32 s_warp[33];
+  u32 per = (len + kScanTPB - 1) / kScanTPB;
+  u32 lo = threadIdx.x * per, hi = min(len, lo + per);
+  u32 s = 0;
+  for (u32 i = lo; i < hi; ++i) s += a[i];
+  u32 total;
+  u32 pre = block_exscan_1024(s, s_warp, &total);
+  for (u32 i = lo; i < hi; ++i) {
+    u32 t = a[i];
+    a[i] = pre;
+    pre += t;
+  }
+}
+
+__global__ void k_scan_apply(const u32 *in, u32 *out, u64 len, const u32 *bsum) {
+  __shared__ u32 s_warp[33];
+  u64 base = (u64)blockIdx.x * kScanTile + (u64)threadIdx.x * kScanItems;
+  u32 v[kScanItems];
+  u32 s = 0;
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < len ? in[base + i] : 0;
+    s += v[i];
+  }
+  u32 total;
+  u32 pre = block_exscan_1024(s, s_warp, &total) + bsum[blockIdx.x];
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < len) out[base + i] = pre;
+    pre += v[i];
+  }
+}
+
+// out[i] = sum of in[0..i); in and out may alias.  tmp holds ceil(len/4096) words.
+static int scan_exclusive(const u32 *in, u32 *out, u64 len, u32 *tmp, cudaStream_t st) {
+  if (len == 0) return TKC_OK;
+  u64 nb = (len + kScanTile - 1) / kScanTile;
+  if (nb > (u64)kScanTPB * 4096) return TKC_EOVERFLOW;
+  TKC_LAUNCH(k_scan_bsum<<<(unsigned)nb, kScanTPB, 0, st>>>(in, len, tmp));
+  TKC_LAUNCH(k_scan_small<<<1, kScanTPB, 0, st>>>(tmp, (u32)nb));
+  TKC_LAUNCH(k_scan_apply<<<(unsigned)nb, kScanTPB, 0, st>>>(in, out, len, tmp));
+  TKC_TRY(cudaGetLastError());
+  return TKC_OK;
+}
+
+// ------------------------------------------------------------------ CSR validation and transpose
+
+enum : u32 { kBadOffsets = 1, kBadRange = 2, kSelfLoop = 4, kUnsorted = 8, kAsymmetric = 16 };
+
+// One warp per vertex: offsets monotone and within arcs, ids in range, no
+// self-loop, each row strictly increasing (sorted, no duplicates).
+__global__ void k_validate(const u32 *off, const u32 *col, u32 n, u64 arcs, u32 *flags) {
+  int lane = threadIdx.x & 31;
+  u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  u32 nw = (gridDim.x * blockDim.x) >> 5;
+  u32 f = 0;
+  for (u32 v = warp; v < n; v += nw) {
+    u32 b = off[v], e = off[v + 1];
+    if (e < b || e > arcs) {
+      f |= kBadOffsets;
+      continue;
+    }
+    for (u32 i = b + lane; i < e; i += 32) {
+      u32 c = col[i];
+      if (c >= n) f |= kBadRange;
+      if (c == v) f |= kSelfLoop;
+      if (i > b && col[i - 1] >= c) f |= kUnsorted;
+    }
+  }
+  f = __reduce_or_sync(FULL, f);
+  if (lane == 0 && f) atomicOr(flags, f);
+}
+
+// Undirected input: every arc u->v needs the arc v->u (binary search in v's row).
+__global__ void k_symmetric(const u32 *off, const u32 *col, u32 n, u32 *flags) {
+  int lane = threadIdx.x & 31;
+  u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  u32 nw = (gridDim.x * blockDim.x) >> 5;
+  u32 f = 0;
+  for (u32 u = warp; u < n; u += nw) {
+    for (u32 i = off[u] + lane; i < off[u + 1]; i += 32) {
+      u32 v = col[i];
+      u32 lo = off[v], hi = off[v + 1];
+      while (lo < hi) {
+        u32 mid = (lo + hi) >> 1;
+        if (col[mid] < u) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= off[v + 1] || col[lo] != u) f |= kAsymmetric;
+    }
+  }
+  f = __reduce_or_sync(FULL, f);
+  if (lane == 0 && f) atomicOr(flags, f);
+}
+
+__global__ void k_indeg(const u32 *off, const u32 *col, u32 n, u32 *indeg) {
+  int lane = threadIdx.x & 31;
+  u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  u32 nw = (gridDim.x * blockDim.x) >> 5;
+  for (u32 u = warp; u < n; u += nw)
+    for (u32 i = off[u] + lane; i < off[u + 1]; i += 32) atomicAdd(&indeg[col[i]], 1u);
+}
+
+__global__ void k_transpose_scatter(const u32 *off, const u32 *col, u32 n, const u32 *ioff, u32 *cursor,
+                                    u32 *icol) {
+  int lane = threadIdx.x & 31;
+  u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  u32 nw = (gridDim.x * blockDim.x) >> 5;
+  for (u32 u = warp; u < n; u += nw)
+    for (u32 i = off[u] + lane; i < off[u + 1]; i += 32) {
+      u32 v = col[i];
+      icol[ioff[v] + atomicAdd(&cursor[v], 1u)] = u;
+    }
+}
+
+static unsigned grid_for(u64 work, unsigned tpb, unsigned cap = 152 * 16) {
+  u64 b = (work + tpb - 1) / tpb;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+int validate_and_transpose(tkc_graph *g) {
+  cudaStream_t st = g->ctx->stream;
+  const u32 n = g->n;
+  if (n == 0) return TKC_OK;
+  u32 *flags = nullptr;
+  TKC_TRY(cudaMallocAsync(&flags, sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(flags, 0, sizeof(u32), st));
+  TKC_LAUNCH(k_validate<<<grid_for((u64)n * 32, 256), 256, 0, st>>>(g->off, g->col, n, g->arcs, flags));
+  TKC_TRY(cudaGetLastError());
+  u32 hf = 0;
+  TKC_TRY(cudaMemcpyAsync(&hf, flags, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  if (hf == 0 && !g->directed) {
+    TKC_LAUNCH(k_symmetric<<<grid_for((u64)n * 32, 256), 256, 0, st>>>(g->off, g->col, n, flags));
+    TKC_TRY(cudaGetLastError());
+    TKC_TRY(cudaMemcpyAsync(&hf, flags, sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaStreamSynchronize(st));
+  }
+  TKC_TRY(cudaFreeAsync(flags, st));
+  if (hf) return TKC_EGRAPH;
+  if (!g->directed) {
+    g->ioff = g->off;
+    g->icol = g->col;
+    return TKC_OK;
+  }
+  u32 *tmp = nullptr, *cursor = nullptr;
+  TKC_TRY(cudaMallocAsync(&g->ioff, ((size_t)n + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&g->icol, std::max<size_t>(g->arcs, 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&cursor, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&tmp, (((size_t)n + 1) / kScanTile + 2) * sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(g->ioff, 0, ((size_t)n + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(u32), st));
+  TKC_LAUNCH(k_indeg<<<grid_for((u64)n * 32, 256), 256, 0, st>>>(g->off, g->col, n, g->ioff));
+  TKC_TRY(cudaGetLastError());
+  TKC_RC(scan_exclusive(g->ioff, g->ioff, (u64)n + 1, tmp, st));
+  TKC_LAUNCH(k_transpose_scatter<<<grid_for((u64)n * 32, 256), 256, 0, st>>>(g->off, g->col, n, g->ioff, cursor, g->icol));
+  TKC_TRY(cudaGetLastError());
+  TKC_TRY(cudaFreeAsync(cursor, st));
+  TKC_TRY(cudaFreeAsync(tmp, st));
+  return TKC_OK;
+}
+
+// ------------------------------------------------------------------ stable LSD radix sort (4-bit digits)
+
+static constexpr int kRsTPB = 256;
+static constexpr int kRsRounds = 4;
+static constexpr int kRsTile = kRsTPB * kRsRounds;
+
+__global__ void k_rs_count(const u32 *key, u32 n, int shift, u32 *hist, u32 ntiles) {
+  __shared__ u32 cnt[16];
+  if (threadIdx.x < 16) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int r = 0; r < kRsRounds; ++r) {
+    u64 i = (u64)blockIdx.x * kRsTile + r * kRsTPB + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(key[i] >> shift) & 15u], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) hist[threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter: element order inside a tile is kept by ranking each round's
+// 256 elements by (warp, lane) and carrying per-digit running counts.
+__global__ void k_rs_scatter(const u32 *key, const u32 *val, u32 *key_out, u32 *val_out, u32 n, int shift,
+                             const u32 *hist, u32 ntiles) {
+  __shared__ u32 running[16];
+  __shared__ u32 wcnt[kRsTPB / 32][16];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x < 16) running[threadIdx.x] = 0;
+  for (int r = 0; r < kRsRounds; ++r) {
+    for (int i = threadIdx.x; i < (kRsTPB / 32) * 16; i += kRsTPB) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    u64 idx = (u64)blockIdx.x * kRsTile + r * kRsTPB + threadIdx.x;
+    bool valid = idx < n;
+    u32 k = valid ? key[idx] : 0u;
+    u32 d = valid ? ((k >> shift) & 15u) : 16u;
+    u32 peers = __match_any_sync(FULL, d);
+    u32 rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      u32 pos = hist[d * ntiles + blockIdx.x] + running[d] + rank;
+      for (int w = 0; w < wid; ++w) pos += wcnt[w][d];
+      key_out[pos] = k;
+      val_out[pos] = val[idx];
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+      u32 s = 0;
+      for (int w = 0; w < kRsTPB / 32; ++w) s += wcnt[w][threadIdx.x];
+      running[threadIdx.x] += s;
+    }
+    __syncthreads();
+  }
+}
+
+// Sorts (key, val) by key ascending, keeping the input order of equal keys.
+// Only the low `bits` bits of the keys are looked at.  Result lands in key/val.
+static int radix_sort_pairs(u32 *key, u32 *val, u32 n, int bits, cudaStream_t st) {
+  if (n <= 1 || bits <= 0) return TKC_OK;
+  u32 ntiles = (n + kRsTile - 1) / kRsTile;
+  u32 *k2 = nullptr, *v2 = nullptr, *hist = nullptr, *tmp = nullptr;
+  size_t hlen = (size_t)16 * ntiles;
+  TKC_TRY(cudaMallocAsync(&k2, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&v2, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&hist, hlen * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&tmp, (hlen / kScanTile + 2) * sizeof(u32), st));
+  u32 *ka = key, *va = val, *kb = k2, *vb = v2;
+  int passes = (bits + 3) / 4;
+  for (int ps = 0; ps < passes; ++ps) {
+    TKC_LAUNCH(k_rs_count<<<ntiles, kRsTPB, 0, st>>>(ka, n, 4 * ps, hist, ntiles));
+    TKC_RC(scan_exclusive(hist, hist, hlen, tmp, st));
+    TKC_LAUNCH(k_rs_scatter<<<ntiles, kRsTPB, 0, st>>>(ka, va, kb, vb, n, 4 * ps, hist, ntiles));
+    TKC_TRY(cudaGetLastError());
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (ka != key) {
+    TKC_TRY(cudaMemcpyAsync(key, ka, (size_t)n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+    TKC_TRY(cudaMemcpyAsync(val, va, (size_t)n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  }
+  TKC_TRY(cudaFreeAsync(k2, st));
+  TKC_TRY(cudaFreeAsync(v2, st));
+  TKC_TRY(cudaFreeAsync(hist, st));
+  TKC_TRY(cudaFreeAsync(tmp, st));
+  return TKC_OK;
+}
+
+// ------------------------------------------------------------------ computeBoundsDeg
+
+__global__ void k_maxdeg(const u32 *off, u32 n, u32 *maxd, u32 *nzero) {
+  u32 m = 0, z = 0;
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    u32 d = off[v + 1] - off[v];
+    m = max(m, d);
+    z += d == 0;
+  }
+  m = __reduce_max_sync(FULL, m);
+  z = __reduce_add_sync(FULL, z);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(maxd, m);
+    atomicAdd(nzero, z);
+  }
+}
+
+__global__ void k_deg_keys(const u32 *off, u32 n, u32 maxd, u32 *key, u32 *val) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    key[v] = maxd - (off[v + 1] - off[v]);  // larger degree -> smaller key
+    val[v] = v;                              // ids ascending: the sort is stable
+  }
+}
+
+int ensure_degree_order(tkc_graph *g) {
+  if (g->have_order) return TKC_OK;
+  cudaStream_t st = g->ctx->stream;
+  const u32 n = g->n;
+  if (n == 0) {
+    g->have_order = true;
+    return TKC_OK;
+  }
+  u32 *keys = nullptr, *stats = nullptr;
+  if (!g->deg_order) TKC_TRY(cudaMallocAsync(&g->deg_order, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&keys, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&stats, 2 * sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(stats, 0, 2 * sizeof(u32), st));
+  TKC_LAUNCH(k_maxdeg<<<grid_for(n, 256), 256, 0, st>>>(g->off, n, stats, stats + 1));
+  TKC_TRY(cudaGetLastError());
+  u32 hs[2];
+  TKC_TRY(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  TKC_LAUNCH(k_deg_keys<<<grid_for(n, 256), 256, 0, st>>>(g->off, n, hs[0], keys, g->deg_order));
+  TKC_TRY(cudaGetLastError());
+  int bits = 0;
+  while (bits < 32 && (hs[0] >> bits) != 0) ++bits;
+  TKC_RC(radix_sort_pairs(keys, g->deg_order, n, bits, st));
+  TKC_TRY(cudaFreeAsync(keys, st));
+  TKC_TRY(cudaFreeAsync(stats, st));
+  g->n_src_deg = n - hs[1];
+  g->have_order = true;
+  return TKC_OK;
+}
+
+// Keeps the vertices of out-degree >= 1 of a full order, in order.
+__global__ void k_flag_src(const u32 *order, const u32 *off, u32 n, u32 *flag) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    u32 v = order[i];
+    flag[i] = off[v + 1] > off[v];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) flag[n] = 0;
+}
+
+__global__ void k_compact(const u32 *order, const u32 *pos, u32 n, u32 *out) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (pos[i + 1] != pos[i]) out[pos[i]] = order[i];
+}
+
+int filter_order(tkc_graph *g, const u32 *d_order_all, u32 *d_out, u32 *count) {
+  cudaStream_t st = g->ctx->stream;
+  const u32 n = g->n;
+  u32 *pos = nullptr, *tmp = nullptr;
+  TKC_TRY(cudaMallocAsync(&pos, ((size_t)n + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&tmp, (((size_t)n + 1) / kScanTile + 2) * sizeof(u32), st));
+  TKC_LAUNCH(k_flag_src<<<grid_for(n, 256), 256, 0, st>>>(d_order_all, g->off, n, pos));
+  TKC_RC(scan_exclusive(pos, pos, (u64)n + 1, tmp, st));
+  TKC_LAUNCH(k_compact<<<grid_for(n, 256), 256, 0, st>>>(d_order_all, pos, n, d_out));
+  TKC_TRY(cudaGetLastError());
+  TKC_TRY(cudaMemcpyAsync(count, pos + n, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  TKC_TRY(cudaFreeAsync(pos, st));
+  TKC_TRY(cudaFreeAsync(tmp, st));
+  return TKC_OK;
+}
+
+// ------------------------------------------------------------------ reach: undirected components
+
+__device__ __forceinline__ u32 cc_root(const u32 *parent, u32 x) {
+  u32 p = parent[x];
+  while (p != x) {
+    x = p;
+    p = parent[x];
+  }
+  return x;
+}
+
+__global__ void k_cc_init(u32 *parent, u32 n) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) parent[v] = v;
+}
+
+// Hooks the larger root of every edge's endpoints under the smaller one.
+// parent[x] <= x always holds, so pointers only decrease and no cycle forms.
+__global__ void k_cc_hook(const u32 *off, const u32 *col, u32 n, u32 *parent, u32 *changed) {
+  int lane = threadIdx.x & 31;
+  u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  u32 nw = (gridDim.x * blockDim.x) >> 5;
+  u32 ch = 0;
+  for (u32 u = warp; u < n; u += nw) {
+    for (u32 i = off[u] + lane; i < off[u + 1]; i += 32) {
+      u32 v = col[i];
+      if (v < u) continue;
+      u32 ru = cc_root(parent, u), rv = cc_root(parent, v);
+      if (ru != rv) {
+        u32 hi = max(ru, rv), lo = min(ru, rv);
+        atomicMin(&parent[hi], lo);
+        ch = 1;
+      }
+    }
+  }
+  ch = __reduce_or_sync(FULL, ch);
+  if (lane == 0 && ch) *changed = 1;
+}
+
+__global__ void k_cc_compress(u32 *parent, u32 n) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    parent[v] = cc_root(parent, v);
+}
+
+__global__ void k_cc_size(const u32 *parent, u32 n, u32 *size) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    atomicAdd(&size[parent[v]], 1u);
+}
+
+__global__ void k_cc_out(const u32 *parent, const u32 *size, u32 n, u32 *alpha, u32 *omega) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    u32 s = size[parent[v]];
+    alpha[v] = s;
+    omega[v] = s;
+  }
+}
+
+static int reach_undirected(tkc_graph *g) {
+  cudaStream_t st = g->ctx->stream;
+  const u32 n = g->n;
+  u32 *parent = nullptr, *size = nullptr, *changed = nullptr;
+  TKC_TRY(cudaMallocAsync(&parent, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&size, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&changed, sizeof(u32), st));
+  TKC_LAUNCH(k_cc_init<<<grid_for(n, 256), 256, 0, st>>>(parent, n));
+  for (int it = 0;; ++it) {
+    if (it > 4096) return TKC_ETIMEOUT;
+    TKC_TRY(cudaMemsetAsync(changed, 0, sizeof(u32), st));
+    TKC_LAUNCH(k_cc_hook<<<grid_for((u64)n * 32, 256), 256, 0, st>>>(g->off, g->col, n, parent, changed));
+    TKC_LAUNCH(k_cc_compress<<<grid_for(n, 256), 256, 0, st>>>(parent, n));
+    TKC_TRY(cudaGetLastError());
+    u32 hc = 0;
+    TKC_TRY(cudaMemcpyAsync(&hc, changed, sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaStreamSynchronize(st));
+    if (!hc) break;
+  }
+  TKC_TRY(cudaMemsetAsync(size, 0, (size_t)n * sizeof(u32), st));
+  TKC_LAUNCH(k_cc_size<<<grid_for(n, 256), 256, 0, st>>>(parent, n, size));
+  TKC_LAUNCH(k_cc_out<<<grid_for(n, 256), 256, 0, st>>>(parent, size, n, g->alpha, g->omega));
+  TKC_TRY(cudaGetLastError());
+  TKC_TRY(cudaFreeAsync(parent, st));
+  TKC_TRY(cudaFreeAsync(size, st));
+  TKC_TRY(cudaFreeAsync(changed, st));
+  return TKC_OK;
+}
+
+// ------------------------------------------------------------------ reach: directed (Algorithm 6)
+
+// Kosaraju's two passes with explicit stacks.  Components come out in a
+// topological order of the condensation (sources first).
+static u32 host_scc(u32 n, const std::vector<u32> &off, const std::vector<u32> &col, const std::vector<u32> &ioff,
+                    const std::vector<u32> &icol, std::vector<u32> &comp) {
+  std::vector<u32> finish;
+  finish.reserve(n);
+  std::vector<uint8_t> vis(n, 0);
+  std::vector<std::pair<u32, u32>> stk;
+  for (u32 s = 0; s < n; ++s) {
+    if (vis[s]) continue;
+    vis[s] = 1;
+    stk.push_back({s, off[s]});
+    while (!stk.empty()) {
+      auto &top = stk.back();
+      if (top.second < off[top.first + 1]) {
+        u32 w = col[top.second++];
+        if (!vis[w]) {
+          vis[w] = 1;
+          stk.push_back({w, off[w]});
+        }
+      } else {
+        finish.push_back(top.first);
+        stk.pop_back();
+      }
+    }
+  }
+  comp.assign(n, UINT32_MAX);
+  u32 nc = 0;
+  std::vector<u32> st2;
+  for (u32 i = n; i-- > 0;) {
+    u32 s = finish[i];
+    if (comp[s] != UINT32_MAX) continue;
+    comp[s] = nc;
+    st2.push_back(s);
+    while (!st2.empty()) {
+      u32 u = st2.back();
+      st2.pop_back();
+      for (u32 e = ioff[u]; e < ioff[u + 1]; ++e) {
+        u32 w = icol[e];
+        if (comp[w] == UINT32_MAX) {
+          comp[w] = nc;
+          st2.push_back(w);
+        }
+      }
+    }
+    ++nc;
+  }
+  return nc;
+}
+
+// Algorithm 6 on the condensation: the biggest SCC (ties: the one holding the
+// smallest vertex id) gets its exact reach from one BFS; the others, sinks
+// first, get alpha = w + max alpha(succ) and omega = w + sum omega(succ), or
+// w + omega(biggest) + sum of omega(succ) over successors the biggest cannot
+// reach when they reach the biggest; omega is clamped to n.
+static int reach_directed(tkc_graph *g) {
+  cudaStream_t st = g->ctx->stream;
+  const u32 n = g->n;
+  const u64 m = g->arcs;
+  std::vector<u32> off(n + 1), col(m), ioff(n + 1), icol(m);
+  TKC_TRY(cudaMemcpyAsync(off.data(), g->off, (n + 1) * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaMemcpyAsync(ioff.data(), g->ioff, (n + 1) * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  if (m) {
+    TKC_TRY(cudaMemcpyAsync(col.data(), g->col, m * sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaMemcpyAsync(icol.data(), g->icol, m * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  }
+  TKC_TRY(cudaStreamSynchronize(st));
+  std::vector<u32> comp;
+  u32 nc = host_scc(n, off, col, ioff, icol, comp);
+  std::vector<u64> wgt(nc, 0);
+  std::vector<u32> minid(nc, UINT32_MAX);
+  for (u32 v = 0; v < n; ++v) {
+    wgt[comp[v]]++;
+    minid[comp[v]] = std::min(minid[comp[v]], v);
+  }
+  // condensation arcs as sorted unique (c, d) pairs
+  std::vector<u64> carcs;
+  for (u32 v = 0; v < n; ++v)
+    for (u32 e = off[v]; e < off[v + 1]; ++e) {
+      u32 d = comp[col[e]];
+      if (d != comp[v]) carcs.push_back(((u64)comp[v] << 32) | d);
+    }
+  std::sort(carcs.begin(), carcs.end());
+  carcs.erase(std::unique(carcs.begin(), carcs.end()), carcs.end());
+  std::vector<u32> coff(nc + 1, 0), cadj(carcs.size());
+  for (u64 a : carcs) coff[(a >> 32) + 1]++;
+  for (u32 c = 0; c < nc; ++c) coff[c + 1] += coff[c];
+  for (size_t i = 0; i < carcs.size(); ++i) cadj[i] = (u32)carcs[i];  // sorted by source: same slots
+  u32 big = 0;
+  for (u32 c = 1; c < nc; ++c)
+    if (wgt[c] > wgt[big] || (wgt[c] == wgt[big] && minid[c] < minid[big])) big = c;
+  std::vector<uint8_t> from_big(nc, 0), to_big(nc, 0);
+  std::vector<u32> q;
+  q.push_back(big);
+  from_big[big] = 1;
+  u64 reach_big = 0;
+  for (size_t h = 0; h < q.size(); ++h) {
+    u32 c = q[h];
+    reach_big += wgt[c];
+    for (u32 i = coff[c]; i < coff[c + 1]; ++i)
+      if (!from_big[cadj[i]]) {
+        from_big[cadj[i]] = 1;
+        q.push_back(cadj[i]);
+      }
+  }
+  std::vector<u64> A(nc, 0), O(nc, 0);
+  // Kosaraju numbers components sources-first: walk them backwards
+  for (u32 c = nc; c-- > 0;) {
+    if (c == big) {
+      A[c] = O[c] = reach_big;
+      to_big[c] = 1;
+      continue;
+    }
+    u64 a = 0, o = 0, o_not_from_big = 0;
+    bool reaches = false;
+    for (u32 i = coff[c]; i < coff[c + 1]; ++i) {
+      u32 y = cadj[i];
+      a = std::max(a, A[y]);
+      o += O[y];
+      if (!from_big[y]) o_not_from_big += O[y];
+      reaches |= to_big[y] != 0;
+    }
+    if (reaches) {
+      to_big[c] = 1;
+      o = o_not_from_big + O[big];
+    }
+    A[c] = a + wgt[c];
+    O[c] = std::min<u64>(o + wgt[c], n);
+  }
+  std::vector<u32> ha(n), ho(n);
+  for (u32 v = 0; v < n; ++v) {
+    ha[v] = (u32)A[comp[v]];
+    ho[v] = (u32)std::min<u64>(O[comp[v]], n);
+  }
+  TKC_TRY(cudaMemcpyAsync(g->alpha, ha.data(), n * sizeof(u32), cudaMemcpyHostToDevice, st));
+  TKC_TRY(cudaMemcpyAsync(g->omega, ho.data(), n * sizeof(u32), cudaMemcpyHostToDevice, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  return TKC_OK;
+}
+
+int ensure_reach_bounds(tkc_graph *g) {
+  if (g->have_reach) return TKC_OK;
+  cudaStream_t st = g->ctx->stream;
+  if (g->n == 0) {
+    g->have_reach = true;
+    return TKC_OK;
+  }
+  if (!g->alpha) TKC_TRY(cudaMallocAsync(&g->alpha, (size_t)g->n * sizeof(u32), st));
+  if (!g->omega) TKC_TRY(cudaMallocAsync(&g->omega, (size_t)g->n * sizeof(u32), st));
+  TKC_RC(g->directed ? reach_directed(g) : reach_undirected(g));
+  g->have_reach = true;
+  return TKC_OK;
+}
+
+}  // namespace tkc

@@ -1,0 +1,306 @@
+"""Python binding of the CUDA library ``libtkc.so`` (C ABI in include/tkc.h).
+
+Argument marshalling only: every function here converts Python/numpy/torch
+arguments to the C call of the same name and converts results back.  All
+computation happens in the library's CUDA kernels; if the library is missing
+the import fails (there is no CPU fallback).
+
+Host inputs are numpy arrays; device inputs may be torch CUDA tensors (their
+data pointers are passed with ``ptr_on_device=1``).  PyTorch is used only for
+streams and device memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtkc.so")
+
+TKC_OK = 0
+TKC_EINVAL = -1
+TKC_EGRAPH = -2
+TKC_ENOMEM = -3
+TKC_ECUDA = -4
+TKC_ETIMEOUT = -5
+TKC_EOVERFLOW = -6
+
+TKC_ORDER_DEG = 0
+TKC_ORDER_GIVEN = 1
+TKC_ORDER_LEARNED = 2
+TKC_MAX_K = 1024
+
+
+class TkcError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {tkc_strerror(code)} ({code})")
+
+
+class tkc_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("order", ctypes.c_uint32),
+                ("batch_bits", ctypes.c_uint32), ("bu_num", ctypes.c_uint32), ("bu_den", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("seed_factor", ctypes.c_uint32),
+                ("timeout_cycles", ctypes.c_uint64)]
+
+
+class tkc_result(ctypes.Structure):
+    _fields_ = [("ids", ctypes.POINTER(ctypes.c_uint32)), ("dist_sum", ctypes.POINTER(ctypes.c_uint64)),
+                ("reach", ctypes.POINTER(ctypes.c_uint32)), ("farness", ctypes.POINTER(ctypes.c_double)),
+                ("closeness", ctypes.POINTER(ctypes.c_double)), ("capacity", ctypes.c_uint32),
+                ("n_returned", ctypes.c_uint32), ("n_tied_at_kth", ctypes.c_uint32),
+                ("edges_visited", ctypes.c_uint64), ("edges_scanned", ctypes.c_uint64),
+                ("bfs_started", ctypes.c_uint64), ("bfs_cut", ctypes.c_uint64), ("bfs_finished", ctypes.c_uint64),
+                ("levels", ctypes.c_uint64), ("batch_bits", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("ms_pre", ctypes.c_double), ("ms_bfs", ctypes.c_double), ("ms_kernel", ctypes.c_double),
+                ("alg_bytes", ctypes.c_uint64)]
+
+
+EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc_free_graph",
+            "tkc_topk_closeness", "tkc_topk_closeness_multi", "tkc_source_order", "tkc_set_source_order",
+            "tkc_reach_bounds", "tkc_distance_sums", "tkc_kernel_launches", "tkc_strerror"]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    lib.tkc_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(tkc_options)]
+    lib.tkc_set_options.argtypes = [vp, ctypes.POINTER(tkc_options)]
+    lib.tkc_destroy.argtypes = [vp]
+    lib.tkc_destroy.restype = None
+    lib.tkc_load_csr.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(vp)]
+    lib.tkc_free_graph.argtypes = [vp]
+    lib.tkc_free_graph.restype = None
+    lib.tkc_topk_closeness.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(tkc_result)]
+    lib.tkc_topk_closeness_multi.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.POINTER(tkc_result)]
+    lib.tkc_source_order.argtypes = [vp, u32p]
+    lib.tkc_set_source_order.argtypes = [vp, u32p]
+    lib.tkc_reach_bounds.argtypes = [vp, u32p, u32p]
+    lib.tkc_distance_sums.argtypes = [vp, ctypes.c_uint32, u32p, u64p, u32p]
+    lib.tkc_kernel_launches.argtypes = []
+    lib.tkc_kernel_launches.restype = ctypes.c_uint64
+    lib.tkc_strerror.argtypes = [ctypes.c_int]
+    lib.tkc_strerror.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = load_library()
+
+
+def tkc_kernel_launches() -> int:
+    return int(_lib.tkc_kernel_launches())
+
+
+def tkc_strerror(code: int) -> str:
+    return _lib.tkc_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != TKC_OK:
+        raise TkcError(rc, where)
+
+
+def _u32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+def _u64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def _f64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def current_stream_handle(device: int = 0) -> int | None:
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream
+    except Exception:  # torch missing or CUDA unavailable
+        pass
+    return None
+
+
+@dataclass
+class Options:
+    device: int = 0
+    stream: int | None = None
+    order: int = TKC_ORDER_DEG
+    batch_bits: int = 0
+    bu_num: int = 0
+    bu_den: int = 0
+    blocks: int = 0
+    seed_factor: int = 0
+    timeout_cycles: int = 0
+
+    def to_c(self) -> tkc_options:
+        return tkc_options(self.device, self.stream, self.order, self.batch_bits, self.bu_num, self.bu_den,
+                           self.blocks, self.seed_factor, self.timeout_cycles)
+
+
+@dataclass
+class Result:
+    ids: np.ndarray
+    dist_sum: np.ndarray
+    reach: np.ndarray
+    farness: np.ndarray
+    closeness: np.ndarray
+    n_tied_at_kth: int
+    edges_visited: int
+    edges_scanned: int
+    bfs_started: int
+    bfs_cut: int
+    bfs_finished: int
+    levels: int
+    batch_bits: int
+    ms_pre: float
+    ms_bfs: float
+    ms_kernel: float
+    alg_bytes: int
+    extra: dict = field(default_factory=dict)
+
+
+def tkc_create(options: Options | None = None) -> ctypes.c_void_p:
+    opt = options or Options()
+    if opt.stream is None:
+        opt.stream = current_stream_handle(opt.device)
+    ctx = ctypes.c_void_p()
+    c = opt.to_c()
+    _check(_lib.tkc_create(ctypes.byref(ctx), ctypes.byref(c)), "tkc_create")
+    return ctx
+
+
+def tkc_set_options(ctx, options: Options) -> None:
+    if options.stream is None:
+        options.stream = current_stream_handle(options.device)
+    c = options.to_c()
+    _check(_lib.tkc_set_options(ctx, ctypes.byref(c)), "tkc_set_options")
+
+
+def tkc_destroy(ctx) -> None:
+    _lib.tkc_destroy(ctx)
+
+
+def tkc_load_csr(ctx, n: int, offsets, cols, directed: bool) -> ctypes.c_void_p:
+    """offsets/cols: numpy uint32 arrays or torch int32/uint32 tensors.  CUDA
+    tensors are passed as device pointers, CPU tensors (e.g. pinned) as host
+    pointers; both must be contiguous."""
+    g = ctypes.c_void_p()
+    if hasattr(offsets, "data_ptr"):
+        if not (offsets.is_contiguous() and cols.is_contiguous()) or offsets.element_size() != 4:
+            raise ValueError("CSR tensors must be contiguous 32-bit")
+        arcs = int(cols.numel())
+        rc = _lib.tkc_load_csr(ctx, n, arcs, ctypes.c_void_p(offsets.data_ptr()),
+                               ctypes.c_void_p(cols.data_ptr() if arcs else 0), int(directed),
+                               1 if offsets.is_cuda else 0, ctypes.byref(g))
+    else:
+        off = np.ascontiguousarray(offsets, dtype=np.uint32)
+        col = np.ascontiguousarray(cols, dtype=np.uint32)
+        arcs = int(col.size)
+        rc = _lib.tkc_load_csr(ctx, n, arcs, off.ctypes.data_as(ctypes.c_void_p),
+                               col.ctypes.data_as(ctypes.c_void_p) if arcs else None, int(directed), 0,
+                               ctypes.byref(g))
+    _check(rc, "tkc_load_csr")
+    return g
+
+
+def tkc_free_graph(g) -> None:
+    _lib.tkc_free_graph(g)
+
+
+def _new_result(cap: int):
+    ids = np.zeros(max(cap, 1), np.uint32)
+    S = np.zeros(max(cap, 1), np.uint64)
+    r = np.zeros(max(cap, 1), np.uint32)
+    f = np.zeros(max(cap, 1), np.float64)
+    c = np.zeros(max(cap, 1), np.float64)
+    res = tkc_result()
+    res.ids, res.dist_sum, res.reach, res.farness, res.closeness = _u32p(ids), _u64p(S), _u32p(r), _f64p(f), _f64p(c)
+    res.capacity = cap
+    return res, (ids, S, r, f, c)
+
+
+def _to_result(res: tkc_result, arrays) -> Result:
+    m = res.n_returned
+    ids, S, r, f, c = arrays
+    return Result(ids[:m].copy(), S[:m].copy(), r[:m].copy(), f[:m].copy(), c[:m].copy(), res.n_tied_at_kth,
+                  res.edges_visited, res.edges_scanned, res.bfs_started, res.bfs_cut, res.bfs_finished, res.levels,
+                  res.batch_bits, res.ms_pre, res.ms_bfs, res.ms_kernel, res.alg_bytes)
+
+
+def tkc_topk_closeness(g, k: int, capacity: int | None = None) -> Result:
+    cap = k if capacity is None else capacity
+    res, arrays = _new_result(cap)
+    _check(_lib.tkc_topk_closeness(g, k, ctypes.byref(res)), "tkc_topk_closeness")
+    return _to_result(res, arrays)
+
+
+def tkc_topk_closeness_multi(ctx, graphs, k: int) -> list[Result]:
+    ng = len(graphs)
+    arr = (ctypes.c_void_p * max(ng, 1))(*[g.value if isinstance(g, ctypes.c_void_p) else g for g in graphs])
+    results = (tkc_result * max(ng, 1))()
+    keep = []
+    for i in range(ng):
+        res, arrays = _new_result(k)
+        results[i] = res
+        keep.append(arrays)
+    _check(_lib.tkc_topk_closeness_multi(ctx, arr, ng, k, results), "tkc_topk_closeness_multi")
+    return [_to_result(results[i], keep[i]) for i in range(ng)]
+
+
+def tkc_source_order(g, n: int) -> np.ndarray:
+    order = np.zeros(max(n, 1), np.uint32)
+    _check(_lib.tkc_source_order(g, _u32p(order)), "tkc_source_order")
+    return order[:n]
+
+
+def tkc_set_source_order(g, order) -> None:
+    o = np.ascontiguousarray(order, dtype=np.uint32)
+    _check(_lib.tkc_set_source_order(g, _u32p(o) if o.size else None), "tkc_set_source_order")
+
+
+def tkc_reach_bounds(g, n: int) -> tuple[np.ndarray, np.ndarray]:
+    a = np.zeros(max(n, 1), np.uint32)
+    o = np.zeros(max(n, 1), np.uint32)
+    _check(_lib.tkc_reach_bounds(g, _u32p(a), _u32p(o)), "tkc_reach_bounds")
+    return a[:n], o[:n]
+
+
+def tkc_distance_sums(g, sources) -> tuple[np.ndarray, np.ndarray]:
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    S = np.zeros(max(src.size, 1), np.uint64)
+    r = np.zeros(max(src.size, 1), np.uint32)
+    _check(_lib.tkc_distance_sums(g, src.size, _u32p(src), _u64p(S), _u32p(r)), "tkc_distance_sums")
+    return S[: src.size], r[: src.size]
+
+
+class Graph:
+    """Owns a loaded graph handle; frees it on close()."""
+
+    def __init__(self, ctx, graph, directed: bool = False):
+        self.ctx = ctx
+        self.n = graph.n
+        self.directed = graph.directed
+        self.handle = tkc_load_csr(ctx, graph.n, graph.offsets, graph.cols, graph.directed)
+
+    def close(self):
+        if self.handle:
+            tkc_free_graph(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,205 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Integer results (ids, S, r, tie counts, orders, reach bounds, plain-mode
+counters) must be bit-exact; farness and closeness are single-rounded IEEE
+doubles of exact integers on both sides, so they must be bit-identical too."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_01077_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(gpu_lib):
+    c = gpu_lib.tkc_create(gpu_lib.Options())
+    yield c
+    gpu_lib.tkc_destroy(c)
+
+
+def _run(tkc, ctx, g, k, bits, order=None, given=None):
+    opt = tkc.Options(batch_bits=bits, order=tkc.TKC_ORDER_DEG if given is None else tkc.TKC_ORDER_GIVEN)
+    tkc.tkc_set_options(ctx, opt)
+    h = tkc.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+    try:
+        if given is not None:
+            tkc.tkc_set_source_order(h, given)
+        return tkc.tkc_topk_closeness(h, k)
+    finally:
+        tkc.tkc_free_graph(h)
+
+
+def _expect_equal(got, ref, g, k):
+    assert list(got.ids) == list(ref.ids), (g.name, k)
+    assert np.array_equal(got.dist_sum, ref.S) and np.array_equal(got.reach, ref.r)
+    assert got.n_tied_at_kth == ref.n_tied, (g.name, k, got.n_tied_at_kth, ref.n_tied)
+    for i in range(len(ref.ids)):
+        f, c = oracle.farness(g.n, ref.S[i], ref.r[i])
+        assert got.farness[i].tobytes() == np.float64(f).tobytes()
+        assert got.closeness[i].tobytes() == np.float64(c).tobytes()
+
+
+SMALL = [
+    lambda: gg.path(17), lambda: gg.path(12, directed=True), lambda: gg.cycle(9), lambda: gg.cycle(8, True),
+    lambda: gg.star(30), lambda: gg.complete(6), lambda: gg.complete_bipartite(3, 9), lambda: gg.hypercube(5),
+    lambda: gg.random_tree(150, 4), lambda: gg.disjoint_union(gg.cycle(5), gg.path(7), gg.path(1), gg.star(4)),
+    lambda: gg.reduction_graph(4, [{0, 1}, {2}, {3}, {0, 3}, {1, 2, 3}])[0],
+    lambda: gg.from_arcs(7, [], [], True, "empty7"),
+]
+
+
+@pytest.mark.parametrize("bits", [1, 64, 512])
+@pytest.mark.parametrize("gi", range(len(SMALL)))
+def test_small_families(gpu_lib, ctx, gi, bits):
+    g = SMALL[gi]()
+    for k in sorted({1, 3, 10, g.n}):
+        ref = oracle.textbook_topk(g, k)
+        got = _run(gpu_lib, ctx, g, k, bits)
+        _expect_equal(got, ref, g, k)
+
+
+@pytest.mark.parametrize("bits", [1, 64, 128, 256, 512])
+def test_random_graphs(gpu_lib, ctx, bits):
+    for seed in range(40):
+        directed = seed % 2 == 0
+        n = 20 + 37 * (seed % 7)
+        g = gg.random_graph(n, 2.5 / n, 7000 + seed, directed)
+        k = [1, 5, 10, n][seed % 4]
+        _expect_equal(_run(gpu_lib, ctx, g, k, bits), oracle.textbook_topk(g, k), g, k)
+
+
+def test_plain_mode_counters_match_cpu_bfscut(gpu_lib, ctx):
+    """One source at a time, the device schedule is the oracle's: same arcs."""
+    for seed in range(12):
+        directed = seed % 2 == 1
+        g = gg.random_graph(60 + 10 * seed, 3.0 / (60 + 10 * seed), 300 + seed, directed)
+        ref = oracle.bfscut(g, 5)
+        got = _run(gpu_lib, ctx, g, 5, 1)
+        _expect_equal(got, ref, g, 5)
+        c = ref.counters
+        assert (got.edges_visited, got.bfs_started, got.bfs_cut, got.bfs_finished) == \
+            (c.edges_visited, c.bfs_started, c.bfs_cut, c.bfs_finished), seed
+
+
+def test_ba2000_plain_and_batched(gpu_lib, ctx):
+    """Barabasi-Albert n=2000, m=4, k=10 (the small plain workload)."""
+    g = gg.barabasi_albert(2000, 4, gg.workload_seed(0))
+    ref = oracle.textbook_topk(g, 10)
+    cut = oracle.bfscut(g, 10)
+    got = _run(gpu_lib, ctx, g, 10, 1)
+    _expect_equal(got, ref, g, 10)
+    assert got.edges_visited == cut.counters.edges_visited
+    for bits in (64, 256, 512):
+        _expect_equal(_run(gpu_lib, ctx, g, 10, bits), ref, g, 10)
+
+
+def test_rmat16_directed(gpu_lib, ctx):
+    """Directed R-MAT scale 16, edge factor 16, k=10, against the CPU BFSCut."""
+    g = gg.rmat(16, 16, seed=gg.workload_seed(1))
+    ref = oracle.bfscut(g, 10)
+    got = _run(gpu_lib, ctx, g, 10, 1)
+    _expect_equal(got, ref, g, 10)
+    assert got.edges_visited == ref.counters.edges_visited
+    for bits in (64, 512):
+        _expect_equal(_run(gpu_lib, ctx, g, 10, bits), ref, g, 10)
+
+
+def test_order_invariance(gpu_lib, ctx):
+    g = gg.rmat(12, 8, seed=99)
+    ref = oracle.textbook_topk(g, 10)
+    rng = np.random.default_rng(3)
+    for bits in (1, 128):
+        for _ in range(3):
+            _expect_equal(_run(gpu_lib, ctx, g, 10, bits, given=rng.permutation(g.n)), ref, g, 10)
+
+
+def test_degree_order_matches_oracle(gpu_lib, ctx):
+    for g in (gg.barabasi_albert(3000, 3, 5), gg.rmat(14, 16, seed=4), gg.path(5), gg.from_arcs(3, [], [], True)):
+        h = gpu_lib.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+        try:
+            assert np.array_equal(gpu_lib.tkc_source_order(h, g.n), oracle.degree_order(g))
+        finally:
+            gpu_lib.tkc_free_graph(h)
+
+
+def test_reach_bounds_match_oracle(gpu_lib, ctx):
+    cases = [gg.rmat(13, 4, seed=11), gg.random_graph(300, 0.006, 8, True), gg.erdos_renyi(5000, 6000, 2),
+             gg.disjoint_union(gg.cycle(5), gg.path(7), gg.star(4)), gg.barabasi_albert(500, 2, 3),
+             gg.reduction_graph(3, [{0}, {1, 2}, {0, 2}])[0]]
+    for g in cases:
+        h = gpu_lib.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+        try:
+            a, o = gpu_lib.tkc_reach_bounds(h, g.n)
+        finally:
+            gpu_lib.tkc_free_graph(h)
+        ra, ro = oracle.alpha_omega(g)
+        assert np.array_equal(a, ra) and np.array_equal(o, ro), g.name
+
+
+def test_distance_sums_match_oracle(gpu_lib, ctx):
+    for g in (gg.rmat(12, 16, seed=5), gg.barabasi_albert(4000, 4, 6), gg.random_graph(200, 0.01, 1, True)):
+        src = np.arange(0, g.n, max(1, g.n // 300), dtype=np.uint32)
+        h = gpu_lib.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+        try:
+            S, r = gpu_lib.tkc_distance_sums(h, src)
+        finally:
+            gpu_lib.tkc_free_graph(h)
+        rS, rr = oracle.bfs_sums(g, src)
+        assert np.array_equal(S, rS) and np.array_equal(r, rr), g.name
+
+
+def test_malformed_graphs_rejected(gpu_lib, ctx):
+    t = gpu_lib
+    t.tkc_set_options(ctx, t.Options(batch_bits=64))
+    bad = [
+        (3, [0, 2, 2, 2], [2, 1], True),      # unsorted row
+        (3, [0, 2, 2, 2], [1, 1], True),      # duplicate arc
+        (3, [0, 1, 1, 1], [0], True),         # self-loop
+        (3, [0, 1, 1, 1], [7], True),         # id out of range
+        (3, [0, 1, 1, 1], [1], False),        # undirected but not symmetric
+        (3, [0, 2, 1, 2], [1, 2], True),      # offsets decrease
+    ]
+    for n, off, col, directed in bad:
+        with pytest.raises(t.TkcError) as e:
+            t.tkc_load_csr(ctx, n, np.array(off, np.uint32), np.array(col, np.uint32), directed)
+        assert e.value.code == t.TKC_EGRAPH, (off, col)
+    g = gg.path(4)
+    h = t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, False)
+    try:
+        with pytest.raises(t.TkcError) as e:
+            t.tkc_topk_closeness(h, t.TKC_MAX_K + 1)
+        assert e.value.code == t.TKC_EINVAL
+        assert len(t.tkc_topk_closeness(h, 0).ids) == 0
+        with pytest.raises(t.TkcError):
+            t.tkc_set_source_order(h, [0, 1, 1, 3])
+    finally:
+        t.tkc_free_graph(h)
+
+
+def test_zero_and_one_vertex(gpu_lib, ctx):
+    t = gpu_lib
+    t.tkc_set_options(ctx, t.Options(batch_bits=64))
+    h = t.tkc_load_csr(ctx, 0, np.zeros(1, np.uint32), np.zeros(0, np.uint32), True)
+    assert len(t.tkc_topk_closeness(h, 5).ids) == 0
+    t.tkc_free_graph(h)
+    h = t.tkc_load_csr(ctx, 1, np.zeros(2, np.uint32), np.zeros(0, np.uint32), False)
+    res = t.tkc_topk_closeness(h, 5)
+    assert list(res.ids) == [0] and res.reach[0] == 1 and res.closeness[0] == 0.0 and res.n_tied_at_kth == 1
+    t.tkc_free_graph(h)
+
+
+def test_device_pointer_input(gpu_lib, ctx):
+    import torch
+
+    g = gg.barabasi_albert(1500, 3, 12)
+    off = torch.from_numpy(g.offsets.astype(np.int32)).cuda()
+    col = torch.from_numpy(g.cols.astype(np.int32)).cuda()
+    gpu_lib.tkc_set_options(ctx, gpu_lib.Options(batch_bits=128))
+    h = gpu_lib.tkc_load_csr(ctx, g.n, off, col, False)
+    try:
+        got = gpu_lib.tkc_topk_closeness(h, 10)
+    finally:
+        gpu_lib.tkc_free_graph(h)
+    _expect_equal(got, oracle.textbook_topk(g, 10), g, 10)
