@@ -172,7 +172,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tkc", choices=["tkc", "reference"])
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
-    ap.add_argument("--bits", type=int, default=512, help="source batch width (0 = library default)")
+    ap.add_argument("--bits", type=int, default=0, help="source batch width (0 = library default)")
     ap.add_argument("--plain", action="store_true", help="also time plain one-source BFSCut once")
     ap.add_argument("--sample", type=int, default=96, help="CPU oracle sample: number of sources")
     ap.add_argument("--no-cpu", action="store_true")

@@ -61,7 +61,7 @@ typedef struct {
   uint32_t batch_bits;     /* sources searched together: 1 (plain, one source per BFS), 64, 128, 256, 512;
                               0 = autotuned choice */
   uint32_t bu_num;         /* direction switch: a level runs bottom-up when frontier arcs * bu_num >
-                              arcs * bu_den (0 = library default) */
+                              arcs * bu_den (bu_num = 0: library default, 8/1) */
   uint32_t bu_den;
   uint32_t blocks;         /* persistent grid size (0 = library default, clamped to co-residency) */
   uint32_t seed_factor;    /* learned order: number of leading sources searched without cutting, as a

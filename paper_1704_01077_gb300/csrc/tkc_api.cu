@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -71,6 +72,10 @@ int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 kk) {
     TKC_RC(dalloc(&w.stamp, cap, st));
     TKC_RC(dalloc(&w.res_S, cap, st));
     TKC_RC(dalloc(&w.res_r, cap, st));
+    TKC_RC(dalloc(&w.FB0, cap / 32 + 1, st));
+    TKC_RC(dalloc(&w.FB1, cap / 32 + 1, st));
+    TKC_TRY(cudaMemsetAsync(w.FB0, 0, ((size_t)cap / 32 + 1) * sizeof(u32), st));
+    TKC_TRY(cudaMemsetAsync(w.FB1, 0, ((size_t)cap / 32 + 1) * sizeof(u32), st));
     TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, (size_t)cap * sizeof(u32), st));
     w.level_base = 0;
     w.n_cap = cap;
@@ -93,7 +98,7 @@ int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 kk) {
 
 static void free_workspace(tkc_ctx *ctx) {
   Workspace &w = ctx->ws;
-  void *ptrs[] = {w.seen, w.F0, w.F1, w.N, w.L0, w.L1, w.Loff0, w.Loff1, w.VL, w.stamp, w.res_S, w.res_r,
+  void *ptrs[] = {w.seen, w.F0, w.F1, w.N, w.FB0, w.FB1, w.L0, w.L1, w.Loff0, w.Loff1, w.VL, w.stamp, w.res_S, w.res_r,
                   w.slots, w.cnt, w.wsum, w.top_S, w.top_r, w.top_id, w.ctl, w.out_S, w.out_r, w.out_id,
                   w.out_f, w.out_c, w.tied};
   for (void *p : ptrs)
@@ -111,6 +116,8 @@ static int reset_rows(tkc_ctx *ctx) {
   TKC_TRY(cudaMemsetAsync(w.F0, 0, rows * sizeof(u64), st));
   TKC_TRY(cudaMemsetAsync(w.F1, 0, rows * sizeof(u64), st));
   TKC_TRY(cudaMemsetAsync(w.N, 0, rows * sizeof(u64), st));
+  TKC_TRY(cudaMemsetAsync(w.FB0, 0, ((size_t)w.n_cap / 32 + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(w.FB1, 0, ((size_t)w.n_cap / 32 + 1) * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(w.cnt, 0, 64 * kMaxWords * sizeof(unsigned), st));
   TKC_TRY(cudaMemsetAsync(w.wsum, 0, 64 * kMaxWords * sizeof(u64), st));
   return TKC_OK;
@@ -199,8 +206,7 @@ static int words_for(u32 bits) {
 // Batch width used when the options leave it to the library.
 static u32 default_batch_bits(const tkc_graph *g) {
   if (g->n < 4096) return 64;
-  if (g->n < (1u << 18)) return 256;
-  return 512;
+  return 256;
 }
 
 struct RunSetup {
@@ -245,13 +251,16 @@ static int run_search(tkc_graph *g, const RunSetup &rs, Ctl *hctl) {
   p.B = rs.B;
   p.nocut = rs.nocut;
   const tkc_options &o = ctx->opt;
-  p.bu_num = o.bu_num ? o.bu_num : 1;
-  p.bu_den = o.bu_num ? std::max<u32>(o.bu_den, 1) : 4;
+  // default: a level runs bottom-up when its frontier's arcs exceed 1/8 of all arcs
+  p.bu_num = o.bu_num ? o.bu_num : 8;
+  p.bu_den = o.bu_num ? std::max<u32>(o.bu_den, 1) : 1;
   p.timeout = o.timeout_cycles ? o.timeout_cycles : kDefaultTimeout;
   p.seen = w.seen;
   p.F0 = w.F0;
   p.F1 = w.F1;
   p.N = w.N;
+  p.FB0 = w.FB0;
+  p.FB1 = w.FB1;
   p.L0 = w.L0;
   p.L1 = w.L1;
   p.Loff0 = w.Loff0;
@@ -269,14 +278,39 @@ static int run_search(tkc_graph *g, const RunSetup &rs, Ctl *hctl) {
   p.ctl = w.ctl;
   int maxb = max_coresident_blocks(ctx, rs.W);
   if (maxb <= 0) return TKC_ECUDA;
-  int blocks = o.blocks ? (int)o.blocks : (int)std::max<u64>(2, ((u64)g->n + 4095) / 4096);
+  int blocks = o.blocks ? (int)o.blocks : (int)std::max<u64>(8, ((u64)g->n + 511) / 512);
   blocks = std::min(blocks, maxb);
+  // optional per-step trace for profiling: TKC_TRACE=<csv path>
+  const char *trace_path = getenv("TKC_TRACE");
+  const uint32_t trace_cap = 1u << 20;
+  if (trace_path) {
+    TKC_TRY(cudaMallocAsync(&p.trace, (size_t)trace_cap * 16 * sizeof(u64), st));
+    TKC_TRY(cudaMemsetAsync(p.trace, 0, (size_t)trace_cap * 16 * sizeof(u64), st));
+    p.trace_cap = trace_cap;
+  }
   TKC_TRY(cudaEventRecord(ctx->ev[4], st));
   TKC_RC(run_bfscut(ctx, p, rs.W, blocks));
   TKC_TRY(cudaEventRecord(ctx->ev[5], st));
   TKC_TRY(cudaMemcpyAsync(hctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   TKC_TRY(cudaStreamSynchronize(st));
   w.level_base = hctl->level_id + 1;
+  if (p.trace) {
+    u64 cnt = std::min<u64>(hctl->trace_n, trace_cap);
+    std::vector<u64> tr(cnt * 16);
+    if (cnt) TKC_TRY(cudaMemcpy(tr.data(), p.trace, cnt * 16 * sizeof(u64), cudaMemcpyDeviceToHost));
+    TKC_TRY(cudaFree(p.trace));
+    FILE *f = fopen(trace_path, "a");
+    if (f) {
+      fprintf(f, "# n=%u arcs=%llu B=%u blocks=%d\n", g->n, (unsigned long long)g->arcs, rs.B, blocks);
+      fprintf(f, "t_ns,kind,a,b,c,d,e,f,t_top,t_a_end,t_a_sync,t_b_end,t_flush,t_epi,x,y\n");
+      for (u64 i = 0; i < cnt; ++i) {
+        const u64 *r = &tr[i * 16];
+        for (int j = 0; j < 16; ++j) fprintf(f, j ? ",%llu" : "%llu", r[j]);
+        fprintf(f, "\n");
+      }
+      fclose(f);
+    }
+  }
   if (hctl->err) {
     TKC_RC(reset_rows(ctx));
     TKC_TRY(cudaStreamSynchronize(st));

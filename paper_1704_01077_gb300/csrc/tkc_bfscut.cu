@@ -269,6 +269,25 @@ __device__ __forceinline__ bool row_nonzero(const u64 (&r)[W]) {
   return a != 0;
 }
 
+// Zeroes the frontier rows of the listed vertices and their frontier bits.
+// A long list clears the whole bitmap instead of one bit per vertex.
+template <int W>
+__device__ __forceinline__ void clear_frontier(u64 *F, uint32_t *FB, const uint32_t *list, uint32_t count, uint32_t n,
+                                               uint64_t gthread, uint64_t nthreads) {
+  for (uint64_t i = gthread; i < (uint64_t)count * W; i += nthreads) {
+    uint32_t v = list[i / W];
+    F[(size_t)v * W + (i % W)] = 0;
+  }
+  if (count > n / 32) {
+    for (uint64_t i = gthread; i < n / 32 + 1; i += nthreads) FB[i] = 0;
+  } else {
+    for (uint64_t i = gthread; i < count; i += nthreads) {
+      uint32_t v = list[i];
+      atomicAnd(&FB[v >> 5], ~(1u << (v & 31)));
+    }
+  }
+}
+
 // ------------------------------------------------------------------ shared state
 
 template <int W>
@@ -413,10 +432,22 @@ __device__ __forceinline__ void offer_candidate(const RunParams &p, Smem<W> &sm,
 
 // Epilogue after a level: update every active slot, merge finished searches,
 // apply the cut test, choose the next step.
+__device__ __forceinline__ void trace_stamp(const RunParams &p, int slot) {
+  if (p.trace && threadIdx.x == 0) {
+    u64 idx = ((volatile Ctl *)p.ctl)->trace_n;
+    if (idx < p.trace_cap) {
+      u64 t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      p.trace[idx * 16 + slot] = t;
+    }
+  }
+}
+
 template <int W>
 __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
   Ctl *c = p.ctl;
   const uint32_t B = p.B;
+  trace_stamp(p, 13);
   if (threadIdx.x == 0) {
     sm.ncand = 0;
     sm.nactive = 0;
@@ -510,6 +541,22 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
       else
         bytes = (u64)p.n * rb + c->lvl_scan_v * 8 + c->lvl_scan_a * (4 + rb) + nl * (8 + 2 * rb) + fl * (4 + rb);
       c->alg_bytes += bytes;
+      if (p.trace) {
+        u64 idx = c->trace_n++;
+        if (idx < p.trace_cap) {
+          u64 t;
+          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+          u64 *rec = p.trace + idx * 16;
+          rec[0] = t;
+          rec[1] = (u64)c->dir;
+          rec[2] = fl;
+          rec[3] = fa;
+          rec[4] = nl;
+          rec[5] = c->lvl_scan_v;
+          rec[6] = c->lvl_scan_a;
+          rec[7] = sm.nactive;
+        }
+      }
       c->lvl_scan_v = 0;
       c->lvl_scan_a = 0;
     }
@@ -534,8 +581,10 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
 template <int W>
 __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
   Ctl *c = p.ctl;
+  trace_stamp(p, 13);
   const uint32_t B = p.B;
   u64 *Fcur = c->cur ? p.F1 : p.F0;
+  uint32_t *FBcur = c->cur ? p.FB1 : p.FB0;
   uint32_t *FL = c->cur ? p.L1 : p.L0;
   uint32_t *FLoff = c->cur ? p.Loff1 : p.Loff0;
   uint32_t ntop = c->ntop;
@@ -592,6 +641,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       u64 bit = 1ull << (s & 63);
       p.seen[(size_t)v * W + (s >> 6)] = bit;
       Fcur[(size_t)v * W + (s >> 6)] = bit;
+      atomicOr(&FBcur[v >> 5], 1u << (v & 31));
       FL[s] = v;
       FLoff[s] = (uint32_t)(arcs_total + arcs_pre);
       p.VL[s] = v;
@@ -623,6 +673,22 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     c->vl_count = assigned;
     c->nl_packed = 0;
     c->level_id += 1;
+    if (p.trace) {
+      u64 idx = c->trace_n++;
+      if (idx < p.trace_cap) {
+        u64 t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        u64 *rec = p.trace + idx * 16;
+        rec[0] = t;
+        rec[1] = 2;  // seed step
+        rec[2] = assigned;
+        rec[3] = arcs_total;
+        rec[4] = cursor;
+        rec[5] = cut0;
+        rec[6] = c->vl_count;
+        rec[7] = c->ntop;
+      }
+    }
     c->batches += 1;
     for (int j = 0; j < W; ++j) c->active[j] = sm.active[j];
     if (assigned == 0) {
@@ -656,25 +722,27 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
     const int cur = vc->cur;
     u64 *Fcur = cur ? p.F1 : p.F0;
     u64 *Fnext = cur ? p.F0 : p.F1;
+    uint32_t *FBcur = cur ? p.FB1 : p.FB0;
+    uint32_t *FBnext = cur ? p.FB0 : p.FB1;
     uint32_t *FL = cur ? p.L1 : p.L0;
     uint32_t *FLoff = cur ? p.Loff1 : p.Loff0;
     uint32_t *NL = cur ? p.L0 : p.L1;
     uint32_t *NLoff = cur ? p.Loff0 : p.Loff1;
     const uint32_t fl_count = vc->fl_count;
     if (step == 1) {
+      if (blockIdx.x == 0) trace_stamp(p, 8);
       // ---- clear step: zero the rows touched by the finished batch
       const uint32_t vl = vc->vl_count;
       for (uint64_t i = gthread; i < (uint64_t)vl * W; i += nthreads) {
         uint32_t v = p.VL[i / W];
         p.seen[(size_t)v * W + (i % W)] = 0;
       }
-      for (uint64_t i = gthread; i < (uint64_t)fl_count * W; i += nthreads) {
-        uint32_t v = FL[i / W];
-        Fcur[(size_t)v * W + (i % W)] = 0;
-      }
+      clear_frontier<W>(Fcur, FBcur, FL, fl_count, p.n, gthread, nthreads);
+      if (blockIdx.x == 0) trace_stamp(p, 12);
       if (!grid_sync(c, p.timeout, [&] { epilogue_seed<W>(p, sm); })) break;
       continue;
     }
+    if (blockIdx.x == 0) trace_stamp(p, 8);
     const int dir = vc->dir;
     const uint32_t level_id = vc->level_id;
     const u64 fl_arcs = vc->fl_arcs;
@@ -692,7 +760,12 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
     if (dir == 0) {
       // ---- phase A, top-down: OR each frontier row into its out-neighbours' N rows
       constexpr uint32_t APS = 32 / W;  // arcs per warp step
-      constexpr uint32_t CH = 256;      // arcs per warp task
+      // arcs per warp task: about two tasks per warp, at least one step, so a
+      // small level still spreads over every warp (each step is a chain of
+      // dependent loads)
+      u64 CH = (fl_arcs + 2ull * nwarps - 1) / (2ull * nwarps);
+      CH = (CH + APS - 1) / APS * APS;
+      if (CH < APS) CH = APS;
       const int grp = lane / W, j = lane % W;
       const u64 actj = sm.active[j];
       for (u64 base = (u64)gwarp * CH; base < fl_arcs; base += (u64)nwarps * CH) {
@@ -736,7 +809,9 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
       }
       scanned = 0;
       if (gthread == 0) atomicAdd(&c->edges_scanned, fl_arcs);
+      if (blockIdx.x == 0) trace_stamp(p, 9);
       if (!grid_sync(c, p.timeout, [] {})) break;
+      if (blockIdx.x == 0) trace_stamp(p, 10);
       // ---- phase B: finalize the next level, clear the old frontier rows
       const uint32_t nl_count = (uint32_t)(((volatile Ctl *)c)->nl_packed >> kPackShift);
       for (uint32_t base = gwarp * 32; base < nl_count; base += nwarps * 32) {
@@ -762,14 +837,12 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
           store_row<W>(p.seen, w, sr);
           store_row<W>(Fnext, w, nw);
           store_row<W>(p.N, w, z);
+          atomicOr(&FBnext[w >> 5], 1u << (w & 31));
         }
         warp_count_slots<W>(nw, od, sm.cnt, sm.wsum, lane);
         warp_append_plain(valid && was_empty, w, &c->vl_count, p.VL, lane);
       }
-      for (uint64_t i = gthread; i < (uint64_t)fl_count * W; i += nthreads) {
-        uint32_t v = FL[i / W];
-        Fcur[(size_t)v * W + (i % W)] = 0;
-      }
+      clear_frontier<W>(Fcur, FBcur, FL, fl_count, p.n, gthread, nthreads);
     } else {
       // ---- phase A, bottom-up: each vertex ORs its in-neighbours' frontier rows
       u64 act[W];
@@ -795,6 +868,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
             uint32_t e = p.ioff[w], ee = p.ioff[w + 1];
             for (; e < ee; ++e) {
               uint32_t u = p.icol[e];
+              if (!((FBcur[u >> 5] >> (u & 31)) & 1u)) continue;  // u is not on any frontier
               u64 fr[W];
               load_row<W>(Fcur, u, fr);
               bool full = true;
@@ -820,17 +894,22 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
           store_row<W>(p.seen, w, sr);
           store_row<W>(Fnext, w, nw);
         }
+        {
+          // the warp owns the 32 consecutive vertices of one bitmap word
+          uint32_t word = __ballot_sync(FULL, isnew);
+          if (lane == 0) FBnext[base >> 5] = word;
+        }
         warp_count_slots<W>(nw, od, sm.cnt, sm.wsum, lane);
         warp_append(isnew, w, od, &c->nl_packed, NL, NLoff, lane);
         warp_append_plain(isnew && was_empty, w, &c->vl_count, p.VL, lane);
       }
+      if (blockIdx.x == 0) trace_stamp(p, 9);
       if (!grid_sync(c, p.timeout, [] {})) break;
+      if (blockIdx.x == 0) trace_stamp(p, 10);
       // ---- phase B: only the old frontier rows need clearing
-      for (uint64_t i = gthread; i < (uint64_t)fl_count * W; i += nthreads) {
-        uint32_t v = FL[i / W];
-        Fcur[(size_t)v * W + (i % W)] = 0;
-      }
+      clear_frontier<W>(Fcur, FBcur, FL, fl_count, p.n, gthread, nthreads);
     }
+    if (blockIdx.x == 0) trace_stamp(p, 11);
     // flush the block's per-slot counters
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -851,6 +930,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
       atomicAdd(&c->lvl_scan_a, sm.acc[3]);
     }
     if (threadIdx.x == 0 && sm.acc[2]) atomicAdd(&c->lvl_scan_v, sm.acc[2]);
+    if (blockIdx.x == 0) trace_stamp(p, 12);
     if (!grid_sync(c, p.timeout, [&] { epilogue_level<W>(p, sm); })) break;
   }
 }

@@ -42,9 +42,10 @@ constexpr int kMaxWords = 8;         // 512-bit source batches
 
 // Device-resident state of one persistent BFSCut run (one graph).
 struct Ctl {
-  // grid barrier
+  // grid barrier, alone in its cache line
   unsigned int bar_count;
   unsigned int bar_gen;
+  unsigned int bar_pad[30];
   int err;
   int err_where;
   // loop state
@@ -75,6 +76,7 @@ struct Ctl {
   unsigned long long alg_bytes;
   unsigned long long lvl_scan_v;
   unsigned long long lvl_scan_a;
+  unsigned long long trace_n;  // records written to the optional trace
 };
 
 struct Slot {
@@ -106,6 +108,7 @@ struct RunParams {
   uint64_t timeout;
   // workspace
   unsigned long long *seen, *F0, *F1, *N;
+  uint32_t *FB0, *FB1;      // one bit per vertex: row of F0 / F1 is non-zero
   uint32_t *L0, *L1;        // frontier lists
   uint32_t *Loff0, *Loff1;  // exclusive arc prefix of each list entry
   uint32_t *VL;             // visited list
@@ -118,12 +121,16 @@ struct RunParams {
   unsigned long long *res_S;     // per-vertex S of finished searches
   uint32_t *res_r;               // per-vertex r of finished searches (0 = not finished)
   Ctl *ctl;
+  // optional per-step trace (16 words per record), nullptr when off
+  unsigned long long *trace;
+  uint32_t trace_cap;
 };
 
 struct Workspace {
   uint32_t n_cap = 0;
   int words_cap = 0;
   unsigned long long *seen = nullptr, *F0 = nullptr, *F1 = nullptr, *N = nullptr;
+  uint32_t *FB0 = nullptr, *FB1 = nullptr;
   uint32_t *L0 = nullptr, *L1 = nullptr, *Loff0 = nullptr, *Loff1 = nullptr, *VL = nullptr, *stamp = nullptr;
   unsigned long long *res_S = nullptr;
   uint32_t *res_r = nullptr;
