@@ -146,6 +146,34 @@ int tkc_reach_bounds(tkc_graph *g, uint32_t *alpha, uint32_t *omega);
  * batches of 64 sources (no cutting).  srcs, S, r: host arrays of nsrc. */
 int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_t *S, uint32_t *r);
 
+/* Allocation-free variant of tkc_distance_sums, for callers that cannot
+ * allocate device memory when they need the result: code running inside CUDA
+ * stream capture (cudaMalloc is not permitted there), runtimes that reserve a
+ * fixed device-memory budget at start-up, and latency-critical services that
+ * cannot take the synchronisation an allocation may cause.  The paper has no
+ * counterpart; it exists for those callers only.
+ *
+ * Computes exact S(v) and r(v) of nsrc distinct sources by full BFS (no
+ * cutting), 64 sources at a time, on the CURRENT device and `stream`
+ * (cudaStream_t, NULL = legacy default).  All pointers are DEVICE pointers
+ * owned by the caller: offsets[n+1] and cols[arcs] (CSR of out-arcs, ids < n),
+ * srcs[nsrc] (distinct ids < n), outputs S[nsrc] and r[nsrc].  The call
+ * allocates nothing: its scratch is one fixed array of about 5.5 MB compiled
+ * into the library, which every device that loads the library holds until
+ * the process exits.
+ *  - The first call on a device looks up that array's device address; make
+ *    that first call before any stream capture starts.
+ *  - Every call on a device shares the array and clears what it needs; calls
+ *    whose GPU work overlaps race on it, so serialise them.
+ *  - The call returns after the results are written (it synchronises `stream`).
+ * Errors: TKC_EINVAL (n > TKC_NOALLOC_MAX_N, a null pointer, a source out of
+ * range or repeated), TKC_EGRAPH (offsets not monotone, offsets[0] != 0,
+ * offsets[n] != arcs, a column out of range), TKC_EOVERFLOW, TKC_ECUDA,
+ * TKC_ETIMEOUT.  nsrc = 0 returns TKC_OK without touching the device. */
+#define TKC_NOALLOC_MAX_N 65536
+int tkc_distance_sums_noalloc(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t arcs,
+                              uint32_t nsrc, const uint32_t *srcs, uint64_t *S, uint32_t *r, void *stream);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * contexts), for accounting of device work. */
 uint64_t tkc_kernel_launches(void);

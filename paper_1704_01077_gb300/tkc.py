@@ -32,6 +32,7 @@ TKC_ORDER_DEG = 0
 TKC_ORDER_GIVEN = 1
 TKC_ORDER_LEARNED = 2
 TKC_MAX_K = 1024
+TKC_NOALLOC_MAX_N = 65536
 
 
 class TkcError(RuntimeError):
@@ -61,7 +62,8 @@ class tkc_result(ctypes.Structure):
 
 EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc_free_graph",
             "tkc_topk_closeness", "tkc_topk_closeness_multi", "tkc_source_order", "tkc_set_source_order",
-            "tkc_reach_bounds", "tkc_distance_sums", "tkc_kernel_launches", "tkc_strerror"]
+            "tkc_reach_bounds", "tkc_distance_sums", "tkc_distance_sums_noalloc", "tkc_kernel_launches",
+            "tkc_strerror"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -86,6 +88,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tkc_set_source_order.argtypes = [vp, u32p]
     lib.tkc_reach_bounds.argtypes = [vp, u32p, u32p]
     lib.tkc_distance_sums.argtypes = [vp, ctypes.c_uint32, u32p, u64p, u32p]
+    lib.tkc_distance_sums_noalloc.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, vp, vp, vp,
+                                              vp]
     lib.tkc_kernel_launches.argtypes = []
     lib.tkc_kernel_launches.restype = ctypes.c_uint64
     lib.tkc_strerror.argtypes = [ctypes.c_int]
@@ -283,6 +287,23 @@ def tkc_distance_sums(g, sources) -> tuple[np.ndarray, np.ndarray]:
     r = np.zeros(max(src.size, 1), np.uint32)
     _check(_lib.tkc_distance_sums(g, src.size, _u32p(src), _u64p(S), _u32p(r)), "tkc_distance_sums")
     return S[: src.size], r[: src.size]
+
+
+def tkc_distance_sums_noalloc(offsets, cols, n: int, sources, S, r, stream=None) -> None:
+    """Allocation-free distance sums: every argument is a torch CUDA tensor on
+    the current device (offsets/cols/sources 32-bit, S 64-bit, r 32-bit); the
+    library allocates nothing.  stream defaults to torch's current stream."""
+    for t in (offsets, cols, sources, S, r):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("tkc_distance_sums_noalloc takes contiguous CUDA tensors")
+    if stream is None:
+        stream = current_stream_handle(offsets.device.index)
+    rc = _lib.tkc_distance_sums_noalloc(ctypes.c_void_p(offsets.data_ptr()),
+                                        ctypes.c_void_p(cols.data_ptr() if cols.numel() else 0), n, int(cols.numel()),
+                                        int(sources.numel()), ctypes.c_void_p(sources.data_ptr()),
+                                        ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(r.data_ptr()),
+                                        ctypes.c_void_p(stream))
+    _check(rc, "tkc_distance_sums_noalloc")
 
 
 class Graph:
