@@ -1,12 +1,11 @@
 // Preprocessing for Algorithm 1: CSR validation and in-arc CSR, the
 // computeBoundsDeg source order (Section 4), and the reach bounds alpha/omega
-// (exact component sizes for undirected graphs; Algorithm 6 of Section 8.4 for
-// directed graphs).
+// (exact component sizes for undirected graphs here; Algorithm 6 of Section
+// 8.4 for directed graphs in tkc_scc.cu).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
-#include <vector>
 
 #include "tkc_internal.cuh"
 
@@ -309,6 +308,14 @@ static int radix_sort_pairs(u32 *key, u32 *val, u32 n, int bits, cudaStream_t st
   return TKC_OK;
 }
 
+int scan_exclusive_u32(const u32 *in, u32 *out, u64 len, u32 *tmp, cudaStream_t st) {
+  return scan_exclusive(in, out, len, tmp, st);
+}
+
+int radix_sort_u32_pairs(u32 *key, u32 *val, u32 n, int bits, cudaStream_t st) {
+  return radix_sort_pairs(key, val, n, bits, st);
+}
+
 // ------------------------------------------------------------------ computeBoundsDeg
 
 __global__ void k_maxdeg(const u32 *off, u32 n, u32 *maxd, u32 *nzero) {
@@ -479,147 +486,10 @@ static int reach_undirected(tkc_graph *g) {
   return TKC_OK;
 }
 
-// ------------------------------------------------------------------ reach: directed (Algorithm 6)
+// ------------------------------------------------------------------ reach: directed
 
-// Kosaraju's two passes with explicit stacks.  Components come out in a
-// topological order of the condensation (sources first).
-static u32 host_scc(u32 n, const std::vector<u32> &off, const std::vector<u32> &col, const std::vector<u32> &ioff,
-                    const std::vector<u32> &icol, std::vector<u32> &comp) {
-  std::vector<u32> finish;
-  finish.reserve(n);
-  std::vector<uint8_t> vis(n, 0);
-  std::vector<std::pair<u32, u32>> stk;
-  for (u32 s = 0; s < n; ++s) {
-    if (vis[s]) continue;
-    vis[s] = 1;
-    stk.push_back({s, off[s]});
-    while (!stk.empty()) {
-      auto &top = stk.back();
-      if (top.second < off[top.first + 1]) {
-        u32 w = col[top.second++];
-        if (!vis[w]) {
-          vis[w] = 1;
-          stk.push_back({w, off[w]});
-        }
-      } else {
-        finish.push_back(top.first);
-        stk.pop_back();
-      }
-    }
-  }
-  comp.assign(n, UINT32_MAX);
-  u32 nc = 0;
-  std::vector<u32> st2;
-  for (u32 i = n; i-- > 0;) {
-    u32 s = finish[i];
-    if (comp[s] != UINT32_MAX) continue;
-    comp[s] = nc;
-    st2.push_back(s);
-    while (!st2.empty()) {
-      u32 u = st2.back();
-      st2.pop_back();
-      for (u32 e = ioff[u]; e < ioff[u + 1]; ++e) {
-        u32 w = icol[e];
-        if (comp[w] == UINT32_MAX) {
-          comp[w] = nc;
-          st2.push_back(w);
-        }
-      }
-    }
-    ++nc;
-  }
-  return nc;
-}
-
-// Algorithm 6 on the condensation: the biggest SCC (ties: the one holding the
-// smallest vertex id) gets its exact reach from one BFS; the others, sinks
-// first, get alpha = w + max alpha(succ) and omega = w + sum omega(succ), or
-// w + omega(biggest) + sum of omega(succ) over successors the biggest cannot
-// reach when they reach the biggest; omega is clamped to n.
-static int reach_directed(tkc_graph *g) {
-  cudaStream_t st = g->ctx->stream;
-  const u32 n = g->n;
-  const u64 m = g->arcs;
-  std::vector<u32> off(n + 1), col(m), ioff(n + 1), icol(m);
-  TKC_TRY(cudaMemcpyAsync(off.data(), g->off, (n + 1) * sizeof(u32), cudaMemcpyDeviceToHost, st));
-  TKC_TRY(cudaMemcpyAsync(ioff.data(), g->ioff, (n + 1) * sizeof(u32), cudaMemcpyDeviceToHost, st));
-  if (m) {
-    TKC_TRY(cudaMemcpyAsync(col.data(), g->col, m * sizeof(u32), cudaMemcpyDeviceToHost, st));
-    TKC_TRY(cudaMemcpyAsync(icol.data(), g->icol, m * sizeof(u32), cudaMemcpyDeviceToHost, st));
-  }
-  TKC_TRY(cudaStreamSynchronize(st));
-  std::vector<u32> comp;
-  u32 nc = host_scc(n, off, col, ioff, icol, comp);
-  std::vector<u64> wgt(nc, 0);
-  std::vector<u32> minid(nc, UINT32_MAX);
-  for (u32 v = 0; v < n; ++v) {
-    wgt[comp[v]]++;
-    minid[comp[v]] = std::min(minid[comp[v]], v);
-  }
-  // condensation arcs as sorted unique (c, d) pairs
-  std::vector<u64> carcs;
-  for (u32 v = 0; v < n; ++v)
-    for (u32 e = off[v]; e < off[v + 1]; ++e) {
-      u32 d = comp[col[e]];
-      if (d != comp[v]) carcs.push_back(((u64)comp[v] << 32) | d);
-    }
-  std::sort(carcs.begin(), carcs.end());
-  carcs.erase(std::unique(carcs.begin(), carcs.end()), carcs.end());
-  std::vector<u32> coff(nc + 1, 0), cadj(carcs.size());
-  for (u64 a : carcs) coff[(a >> 32) + 1]++;
-  for (u32 c = 0; c < nc; ++c) coff[c + 1] += coff[c];
-  for (size_t i = 0; i < carcs.size(); ++i) cadj[i] = (u32)carcs[i];  // sorted by source: same slots
-  u32 big = 0;
-  for (u32 c = 1; c < nc; ++c)
-    if (wgt[c] > wgt[big] || (wgt[c] == wgt[big] && minid[c] < minid[big])) big = c;
-  std::vector<uint8_t> from_big(nc, 0), to_big(nc, 0);
-  std::vector<u32> q;
-  q.push_back(big);
-  from_big[big] = 1;
-  u64 reach_big = 0;
-  for (size_t h = 0; h < q.size(); ++h) {
-    u32 c = q[h];
-    reach_big += wgt[c];
-    for (u32 i = coff[c]; i < coff[c + 1]; ++i)
-      if (!from_big[cadj[i]]) {
-        from_big[cadj[i]] = 1;
-        q.push_back(cadj[i]);
-      }
-  }
-  std::vector<u64> A(nc, 0), O(nc, 0);
-  // Kosaraju numbers components sources-first: walk them backwards
-  for (u32 c = nc; c-- > 0;) {
-    if (c == big) {
-      A[c] = O[c] = reach_big;
-      to_big[c] = 1;
-      continue;
-    }
-    u64 a = 0, o = 0, o_not_from_big = 0;
-    bool reaches = false;
-    for (u32 i = coff[c]; i < coff[c + 1]; ++i) {
-      u32 y = cadj[i];
-      a = std::max(a, A[y]);
-      o += O[y];
-      if (!from_big[y]) o_not_from_big += O[y];
-      reaches |= to_big[y] != 0;
-    }
-    if (reaches) {
-      to_big[c] = 1;
-      o = o_not_from_big + O[big];
-    }
-    A[c] = a + wgt[c];
-    O[c] = std::min<u64>(o + wgt[c], n);
-  }
-  std::vector<u32> ha(n), ho(n);
-  for (u32 v = 0; v < n; ++v) {
-    ha[v] = (u32)A[comp[v]];
-    ho[v] = (u32)std::min<u64>(O[comp[v]], n);
-  }
-  TKC_TRY(cudaMemcpyAsync(g->alpha, ha.data(), n * sizeof(u32), cudaMemcpyHostToDevice, st));
-  TKC_TRY(cudaMemcpyAsync(g->omega, ho.data(), n * sizeof(u32), cudaMemcpyHostToDevice, st));
-  TKC_TRY(cudaStreamSynchronize(st));
-  return TKC_OK;
-}
+// SCCs and Algorithm 6 run on the device (tkc_scc.cu).
+int reach_directed_gpu(tkc_graph *g);
 
 int ensure_reach_bounds(tkc_graph *g) {
   if (g->have_reach) return TKC_OK;
@@ -630,7 +500,7 @@ int ensure_reach_bounds(tkc_graph *g) {
   }
   if (!g->alpha) TKC_TRY(cudaMallocAsync(&g->alpha, (size_t)g->n * sizeof(u32), st));
   if (!g->omega) TKC_TRY(cudaMallocAsync(&g->omega, (size_t)g->n * sizeof(u32), st));
-  TKC_RC(g->directed ? reach_directed(g) : reach_undirected(g));
+  TKC_RC(g->directed ? reach_directed_gpu(g) : reach_undirected(g));
   g->have_reach = true;
   return TKC_OK;
 }

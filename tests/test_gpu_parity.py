@@ -124,10 +124,30 @@ def test_degree_order_matches_oracle(gpu_lib, ctx):
             gpu_lib.tkc_free_graph(h)
 
 
+def _cycle_chain(k, size, back_every=0):
+    """k directed cycles of `size` vertices, cycle i -> cycle i+1 (and an arc
+    back to cycle 0 every `back_every` cycles, merging SCCs)."""
+    src, dst = [], []
+    for c in range(k):
+        for j in range(size):
+            src.append(c * size + j)
+            dst.append(c * size + (j + 1) % size)
+        if c + 1 < k:
+            src.append(c * size)
+            dst.append((c + 1) * size + 1 % size)
+        if back_every and c % back_every == back_every - 1:
+            src.append(c * size + size - 1)
+            dst.append((c - back_every + 1) * size)
+    return gg.from_arcs(k * size, src, dst, True, f"cyclechain{k}x{size}")
+
+
 def test_reach_bounds_match_oracle(gpu_lib, ctx):
     cases = [gg.rmat(13, 4, seed=11), gg.random_graph(300, 0.006, 8, True), gg.erdos_renyi(5000, 6000, 2),
              gg.disjoint_union(gg.cycle(5), gg.path(7), gg.star(4)), gg.barabasi_albert(500, 2, 3),
-             gg.reduction_graph(3, [{0}, {1, 2}, {0, 2}])[0]]
+             gg.reduction_graph(3, [{0}, {1, 2}, {0, 2}])[0], gg.rmat(16, 16, seed=gg.workload_seed(1)),
+             gg.random_graph(600, 1.3 / 600, 77, True), gg.erdos_renyi(20000, 26000, 9),
+             _cycle_chain(40, 3), _cycle_chain(30, 4, back_every=3), gg.path(300, directed=True),
+             gg.cycle(50, directed=True), gg.from_arcs(6, [], [], True)]
     for g in cases:
         h = gpu_lib.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
         try:
