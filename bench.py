@@ -34,7 +34,16 @@ WORKLOADS = {
                "directed R-MAT scale 16, edge factor 16, k=10"),
     "ba1m": (lambda gg: gg.barabasi_albert(1_000_000, 5, gg.workload_seed(2)), 10,
              "undirected Barabasi-Albert n=1,000,000, m=5, k=10"),
+    "multi512": (lambda gg: multi_graphs(gg, 512, 1_000, 200_000, gg.workload_seed(3)), 10,
+                 "512 graphs in one launch, n log-uniform in [1k, 200k]; even: undirected Barabasi-Albert m=4, "
+                 "odd: directed Erdos-Renyi with 8n uniform arcs; top-10 of each"),
 }
+
+
+def multi_graphs(gg, count, lo, hi, seed):
+    sizes = gg.log_uniform_sizes(count, lo, hi, seed)
+    return [gg.barabasi_albert(n, 4, gg.splitmix64(seed + i)) if i % 2 == 0
+            else gg.erdos_renyi(n, 8 * n, gg.splitmix64(seed + i), directed=True) for i, n in enumerate(sizes)]
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfscut_traffic.json")
@@ -144,6 +153,8 @@ def run_reference(args, rank, world):
 
     build, k, desc = WORKLOADS[args.workload]
     g = build(gg)
+    if isinstance(g, list):  # several graphs: the sample is taken from the largest
+        g = max(g, key=lambda x: x.arcs)
     for _ in range(args.warmup):
         cpu_oracle_sample(g, k, args.sample)
     vals, times, evs = [], [], []
@@ -153,7 +164,8 @@ def run_reference(args, rank, world):
         times.append(dt)
         evs.append(ev)
     value = sum(evs) / sum(times) / 1e9
-    sample = f"first {args.sample} sources of the degree order (sequential CPU BFSCut, incl. its preprocessing)"
+    sample = (f"first {args.sample} sources of the degree order of {g.name} (sequential CPU BFSCut, incl. its "
+              f"preprocessing)")
     line = {"impl": "reference", "metric": "topk_closeness_gteps", "value": value, "unit": "GTEPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
@@ -196,28 +208,47 @@ def main():
 
         dist.init_process_group("nccl")
     build, k, desc = WORKLOADS[args.workload]
-    g = build(gg)
+    built = build(gg)
+    multi = isinstance(built, list)
+    graphs = built if multi else [built]
+    g = graphs[0]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    off_d = torch.from_numpy(g.offsets.view(np.int32)).to(dev)
-    col_d = torch.from_numpy(g.cols.view(np.int32)).to(dev)
-    off_h = torch.from_numpy(g.offsets.view(np.int32)).pin_memory()
-    col_h = torch.from_numpy(g.cols.view(np.int32)).pin_memory()
+    dev_csr = [(torch.from_numpy(x.offsets.view(np.int32)).to(dev), torch.from_numpy(x.cols.view(np.int32)).to(dev))
+               for x in graphs]
+    host_csr = [(torch.from_numpy(x.offsets.view(np.int32)).pin_memory(),
+                 torch.from_numpy(x.cols.view(np.int32)).pin_memory()) for x in graphs]
     ctx = tkc.tkc_create(tkc.Options(device=local, stream=stream.cuda_stream, batch_bits=args.bits))
 
-    def step_device():
-        h = tkc.tkc_load_csr(ctx, g.n, off_d, col_d, g.directed)
+    class Step:
+        """One step's results summed over the graphs it ran."""
+
+        def __init__(self, results):
+            self.results = results
+            r0 = results[0]
+            self.edges_visited = sum(r.edges_visited for r in results)
+            self.bfs_started = sum(r.bfs_started for r in results)
+            self.bfs_cut = sum(r.bfs_cut for r in results)
+            self.bfs_finished = sum(r.bfs_finished for r in results)
+            for name in ("edges_scanned", "levels", "ms_pre", "ms_bfs", "ms_kernel", "alg_bytes", "batch_bits",
+                         "ids", "dist_sum", "reach"):
+                setattr(self, name, getattr(r0, name))
+
+    def run_step(csr):
+        hs = [tkc.tkc_load_csr(ctx, x.n, o, c, x.directed) for x, (o, c) in zip(graphs, csr)]
         try:
-            return tkc.tkc_topk_closeness(h, k)
+            if multi:
+                return Step(tkc.tkc_topk_closeness_multi(ctx, hs, k))
+            return Step([tkc.tkc_topk_closeness(hs[0], k)])
         finally:
-            tkc.tkc_free_graph(h)
+            for h in hs:
+                tkc.tkc_free_graph(h)
+
+    def step_device():
+        return run_step(dev_csr)
 
     def step_host():
-        h = tkc.tkc_load_csr(ctx, g.n, off_h, col_h, g.directed)
-        try:
-            return tkc.tkc_topk_closeness(h, k)
-        finally:
-            tkc.tkc_free_graph(h)
+        return run_step(host_csr)
 
     for _ in range(args.warmup):
         res = step_device()
@@ -256,8 +287,8 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = sum(r.edges_visited for r in e2e_res) / e2e_s / 1e9 * world
-    h2d = 4 * (g.n + 1) + 4 * g.arcs
-    d2h = k * (4 + 8 + 4 + 8 + 8)
+    h2d = sum(4 * (x.n + 1) + 4 * x.arcs for x in graphs)
+    d2h = len(graphs) * k * (4 + 8 + 4 + 8 + 8)
 
     # roofline of the dominant kernel (the persistent search kernel)
     peak, peak_src = hbm_peak()
@@ -282,9 +313,11 @@ def main():
                        "bfs_finished": results[-1].bfs_finished, "levels": results[-1].levels,
                        "ms_pre": results[-1].ms_pre, "ms_bfs": results[-1].ms_bfs,
                        "ms_kernel": results[-1].ms_kernel,
-                       "textbook_teps_equiv": g.arcs * g.n / (ms_step / 1e3) / 1e9,
+                       "textbook_teps_equiv": sum(x.arcs * x.n for x in graphs) / (ms_step / 1e3) / 1e9,
+                       "graphs": len(graphs), "vertices": sum(x.n for x in graphs),
+                       "arcs": sum(x.arcs for x in graphs),
                        "top_ids": [int(x) for x in results[-1].ids]}}
-    if rank == 0 and args.plain:
+    if rank == 0 and args.plain and not multi:
         tkc.tkc_set_options(ctx, tkc.Options(device=local, stream=stream.cuda_stream, batch_bits=1))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -297,11 +330,12 @@ def main():
     if rank == 0 and not args.no_check:
         import oracle
 
-        top = results[-1]
-        S, r = oracle.bfs_sums(g, top.ids)
-        line["check"] = {"top_k_S_r_match_oracle_bfs": bool(np.array_equal(S, top.dist_sum)
-                                                            and np.array_equal(r, top.reach))}
-    if rank == 0 and not args.no_cpu:
+        ok = True
+        for x, top in zip(graphs, results[-1].results):
+            S, r = oracle.bfs_sums(x, top.ids)
+            ok &= bool(np.array_equal(S, top.dist_sum) and np.array_equal(r, top.reach))
+        line["check"] = {"top_k_S_r_match_oracle_bfs": ok}
+    if rank == 0 and not args.no_cpu and not multi:
         v, dt, ev = cpu_oracle_sample(g, k, args.sample)
         line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                                 "sample": f"first {args.sample} sources of the degree order, sequential CPU "

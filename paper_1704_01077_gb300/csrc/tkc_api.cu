@@ -41,8 +41,7 @@ static int dalloc(T **p, size_t count, cudaStream_t st) {
   return TKC_OK;
 }
 
-int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 kk) {
-  (void)kk;
+int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 top_entries, u32 ng) {
   Workspace &w = ctx->ws;
   cudaStream_t st = ctx->stream;
   if (!w.ctl) {
@@ -50,17 +49,27 @@ int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 kk) {
     TKC_RC(dalloc(&w.slots, 64 * kMaxWords, st));
     TKC_RC(dalloc(&w.cnt, 64 * kMaxWords, st));
     TKC_RC(dalloc(&w.wsum, 64 * kMaxWords, st));
-    TKC_RC(dalloc(&w.top_S, TKC_MAX_K, st));
-    TKC_RC(dalloc(&w.top_r, TKC_MAX_K, st));
-    TKC_RC(dalloc(&w.top_id, TKC_MAX_K, st));
-    TKC_RC(dalloc(&w.out_S, TKC_MAX_K, st));
-    TKC_RC(dalloc(&w.out_r, TKC_MAX_K, st));
-    TKC_RC(dalloc(&w.out_id, TKC_MAX_K, st));
-    TKC_RC(dalloc(&w.out_f, TKC_MAX_K, st));
-    TKC_RC(dalloc(&w.out_c, TKC_MAX_K, st));
-    TKC_RC(dalloc(&w.tied, 1, st));
     TKC_TRY(cudaMemsetAsync(w.cnt, 0, 64 * kMaxWords * sizeof(unsigned), st));
     TKC_TRY(cudaMemsetAsync(w.wsum, 0, 64 * kMaxWords * sizeof(u64), st));
+  }
+  if (top_entries > w.top_cap) {
+    u32 cap = std::max<u32>(top_entries, TKC_MAX_K);
+    TKC_RC(dalloc(&w.top_S, cap, st));
+    TKC_RC(dalloc(&w.top_r, cap, st));
+    TKC_RC(dalloc(&w.top_id, cap, st));
+    TKC_RC(dalloc(&w.out_S, cap, st));
+    TKC_RC(dalloc(&w.out_r, cap, st));
+    TKC_RC(dalloc(&w.out_id, cap, st));
+    TKC_RC(dalloc(&w.out_f, cap, st));
+    TKC_RC(dalloc(&w.out_c, cap, st));
+    w.top_cap = cap;
+  }
+  if (ng > w.ng_cap) {
+    u32 cap = std::max<u32>(ng, 16);
+    TKC_RC(dalloc(&w.tied, cap, st));
+    TKC_RC(dalloc(&w.g_ntop, cap, st));
+    TKC_RC(dalloc(&w.g_ctr, 4 * (size_t)cap, st));
+    w.ng_cap = cap;
   }
   if (n > w.n_cap) {
     u32 cap = std::max<u32>(n, 1024);
@@ -100,7 +109,7 @@ static void free_workspace(tkc_ctx *ctx) {
   Workspace &w = ctx->ws;
   void *ptrs[] = {w.seen, w.F0, w.F1, w.N, w.FB0, w.FB1, w.L0, w.L1, w.Loff0, w.Loff1, w.VL, w.stamp, w.res_S, w.res_r,
                   w.slots, w.cnt, w.wsum, w.top_S, w.top_r, w.top_id, w.ctl, w.out_S, w.out_r, w.out_id,
-                  w.out_f, w.out_c, w.tied};
+                  w.out_f, w.out_c, w.tied, w.g_ntop, w.g_ctr};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -125,75 +134,68 @@ static int reset_rows(tkc_ctx *ctx) {
 
 // ------------------------------------------------------------------ output
 
-// Ties with the k-th entry among finished searches (exact key equality).
-__global__ void k_count_ties(const u64 *res_S, const u32 *res_r, u32 n, const u64 *top_S, const u32 *top_r,
-                             u32 kk, const Ctl *ctl, unsigned *tied) {
-  if (ctl->ntop < kk) return;  // the k-th is a closeness-0 vertex: counted on the host
-  u64 Sx = top_S[kk - 1];
-  u64 rx = top_r[kk - 1];
-  unsigned c = 0;
-  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+// What the output step needs of each graph of a run.
+struct GraphOut {
+  u32 n;          // vertices of the graph
+  u32 base;       // first id of the graph in the run's (union) numbering
+  u32 kk;         // min(k, n)
+  u32 nzero;      // vertices of out-degree 0 (closeness 0)
+  const u32 *zero_ids;  // those vertices in increasing id order (graph-local ids)
+};
+
+// Ties with each graph's k-th entry among finished searches (exact key
+// equality).  A graph whose k-th entry is a closeness-0 vertex is counted on
+// the host (every closeness-0 vertex ties with it).
+__global__ void k_count_ties(const u64 *res_S, const u32 *res_r, const u32 *gid, u32 nv, const u64 *top_S,
+                             const u32 *top_r, const unsigned *g_ntop, u32 kk, const GraphOut *go, unsigned *tied) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
     u32 r = res_r[v];
-    if (r >= 2) {
-      unsigned __int128 a = (unsigned __int128)res_S[v] * (unsigned __int128)((rx - 1) * (rx - 1));
-      unsigned __int128 b = (unsigned __int128)Sx * (unsigned __int128)((u64)(r - 1) * (u64)(r - 1));
-      c += a == b;
-    }
+    if (r < 2) continue;
+    u32 g = gid ? gid[v] : 0;
+    u32 kg = go[g].kk;
+    if (g_ntop[g] < kg) continue;
+    size_t x = (size_t)g * kk + kg - 1;
+    u64 rx = top_r[x];
+    unsigned __int128 a = (unsigned __int128)res_S[v] * (unsigned __int128)((rx - 1) * (rx - 1));
+    unsigned __int128 b = (unsigned __int128)top_S[x] * (unsigned __int128)((u64)(r - 1) * (u64)(r - 1));
+    if (a == b) atomicAdd(&tied[g], 1u);
   }
-  c = __reduce_add_sync(0xffffffffu, c);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(tied, c);
 }
 
-// Final list: the top entries, then (if fewer than k vertices can reach
-// another vertex) closeness-0 vertices in id order from the degree order's
-// tail.  f and c are one IEEE product and one quotient of exact integers.
-__global__ void k_output(const u64 *top_S, const u32 *top_r, const u32 *top_id, const Ctl *ctl, u32 kk, u32 n,
-                         const u32 *zero_deg_ids, u64 *oS, u32 *or_, u32 *oid, double *of, double *oc) {
-  u32 ntop = ctl->ntop;
-  for (u32 i = threadIdx.x; i < kk; i += blockDim.x) {
+// Final list of graph blockIdx.x: its top entries, then (if fewer than k of
+// its vertices reach another vertex) closeness-0 vertices in id order.  f and
+// c are one IEEE product and one quotient of exact integers.
+__global__ void k_output(const u64 *top_S, const u32 *top_r, const u32 *top_id, const unsigned *g_ntop, u32 kk,
+                         const GraphOut *go, u64 *oS, u32 *or_, u32 *oid, double *of, double *oc) {
+  const u32 g = blockIdx.x;
+  const GraphOut G = go[g];
+  const u32 ntop = g_ntop[g];
+  for (u32 i = threadIdx.x; i < G.kk; i += blockDim.x) {
+    size_t src = (size_t)g * kk + i;
     u64 S;
     u32 r, id;
     if (i < ntop) {
-      S = top_S[i];
-      r = top_r[i];
-      id = top_id[i];
+      S = top_S[src];
+      r = top_r[src];
+      id = top_id[src] - G.base;
     } else {
       S = 0;
       r = 1;
-      id = zero_deg_ids[i - ntop];
+      id = G.zero_ids[i - ntop];
     }
-    oS[i] = S;
-    or_[i] = r;
-    oid[i] = id;
+    oS[src] = S;
+    or_[src] = r;
+    oid[src] = id;
     if (r <= 1) {
-      of[i] = __longlong_as_double(0x7ff0000000000000ll);
-      oc[i] = 0.0;
+      of[src] = __longlong_as_double(0x7ff0000000000000ll);
+      oc[src] = 0.0;
     } else {
-      double num = __dmul_rn((double)(n - 1), (double)S);
+      double num = __dmul_rn((double)(G.n - 1), (double)S);
       double den = (double)((u64)(r - 1) * (u64)(r - 1));
-      of[i] = __ddiv_rn(num, den);
-      oc[i] = __ddiv_rn(den, num);
+      of[src] = __ddiv_rn(num, den);
+      oc[src] = __ddiv_rn(den, num);
     }
   }
-}
-
-int finish_topk(tkc_ctx *ctx, tkc_graph *g, u32 kk, tkc_result *out) {
-  Workspace &w = ctx->ws;
-  cudaStream_t st = ctx->stream;
-  TKC_TRY(cudaMemsetAsync(w.tied, 0, sizeof(unsigned), st));
-  unsigned blocks = (unsigned)std::min<u64>((g->n + 255) / 256, (u64)ctx->num_sms * 8);
-  TKC_LAUNCH(k_count_ties<<<std::max(1u, blocks), 256, 0, st>>>(w.res_S, w.res_r, g->n, w.top_S, w.top_r, kk, w.ctl,
-                                                     w.tied));
-  TKC_LAUNCH(k_output<<<1, 256, 0, st>>>(w.top_S, w.top_r, w.top_id, w.ctl, kk, g->n, g->deg_order + g->n_src_deg,
-                              w.out_S, w.out_r, w.out_id, w.out_f, w.out_c));
-  TKC_TRY(cudaGetLastError());
-  if (out->ids) TKC_TRY(cudaMemcpyAsync(out->ids, w.out_id, kk * sizeof(u32), cudaMemcpyDeviceToHost, st));
-  if (out->dist_sum) TKC_TRY(cudaMemcpyAsync(out->dist_sum, w.out_S, kk * sizeof(u64), cudaMemcpyDeviceToHost, st));
-  if (out->reach) TKC_TRY(cudaMemcpyAsync(out->reach, w.out_r, kk * sizeof(u32), cudaMemcpyDeviceToHost, st));
-  if (out->farness) TKC_TRY(cudaMemcpyAsync(out->farness, w.out_f, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
-  if (out->closeness)
-    TKC_TRY(cudaMemcpyAsync(out->closeness, w.out_c, kk * sizeof(double), cudaMemcpyDeviceToHost, st));
-  return TKC_OK;
 }
 
 static int words_for(u32 bits) {
@@ -204,25 +206,30 @@ static int words_for(u32 bits) {
 }
 
 // Batch width used when the options leave it to the library.
-static u32 default_batch_bits(const tkc_graph *g) {
-  if (g->n < 4096) return 64;
+static u32 default_batch_bits(u32 n) {
+  if (n < 4096) return 64;
   return 256;
 }
 
+// One run of the persistent kernel: a graph, or the union of several.
 struct RunSetup {
+  const tkc_graph *g;       // the graph (or the union's stand-in graph)
   const u32 *order;
   u32 norder;
   u32 B;
   int W;
   int nocut;
-  u32 kk;
+  u32 kk;                   // list length per graph
+  u32 ng;
+  const u32 *gid;           // nullptr for one graph
+  const uint8_t *g_directed;
 };
 
-static int run_search(tkc_graph *g, const RunSetup &rs, Ctl *hctl) {
-  tkc_ctx *ctx = g->ctx;
+static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
+  const tkc_graph *g = rs.g;
   Workspace &w = ctx->ws;
   cudaStream_t st = ctx->stream;
-  TKC_RC(ensure_workspace(ctx, g->n, rs.W, rs.kk));
+  TKC_RC(ensure_workspace(ctx, g->n, rs.W, rs.kk * rs.ng, rs.ng));
   if (w.level_base > 0xF0000000u) {
     TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, (size_t)w.n_cap * sizeof(u32), st));
     w.level_base = 0;
@@ -234,6 +241,8 @@ static int run_search(tkc_graph *g, const RunSetup &rs, Ctl *hctl) {
   TKC_TRY(cudaMemcpyAsync(w.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st));
   TKC_TRY(cudaMemsetAsync(w.res_r, 0, (size_t)g->n * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(w.res_S, 0, (size_t)g->n * sizeof(u64), st));
+  TKC_TRY(cudaMemsetAsync(w.g_ntop, 0, (size_t)rs.ng * sizeof(unsigned), st));
+  TKC_TRY(cudaMemsetAsync(w.g_ctr, 0, (size_t)rs.ng * 4 * sizeof(u64), st));
   RunParams p;
   memset(&p, 0, sizeof(p));
   p.n = g->n;
@@ -247,6 +256,11 @@ static int run_search(tkc_graph *g, const RunSetup &rs, Ctl *hctl) {
   p.omega = g->omega;
   p.order = rs.order;
   p.norder = rs.norder;
+  p.ng = rs.ng;
+  p.gid = rs.gid;
+  p.g_directed = rs.g_directed;
+  p.g_ntop = w.g_ntop;
+  p.g_ctr = rs.ng > 1 ? w.g_ctr : nullptr;
   p.kk = rs.kk;
   p.B = rs.B;
   p.nocut = rs.nocut;
@@ -301,7 +315,8 @@ static int run_search(tkc_graph *g, const RunSetup &rs, Ctl *hctl) {
     TKC_TRY(cudaFree(p.trace));
     FILE *f = fopen(trace_path, "a");
     if (f) {
-      fprintf(f, "# n=%u arcs=%llu B=%u blocks=%d\n", g->n, (unsigned long long)g->arcs, rs.B, blocks);
+      fprintf(f, "# n=%u arcs=%llu B=%u blocks=%d graphs=%u\n", g->n, (unsigned long long)g->arcs, rs.B, blocks,
+              rs.ng);
       fprintf(f, "t_ns,kind,a,b,c,d,e,f,t_top,t_a_end,t_a_sync,t_b_end,t_flush,t_epi,x,y\n");
       for (u64 i = 0; i < cnt; ++i) {
         const u64 *r = &tr[i * 16];
@@ -317,6 +332,84 @@ static int run_search(tkc_graph *g, const RunSetup &rs, Ctl *hctl) {
     return hctl->err;
   }
   return TKC_OK;
+}
+
+// Output step of a run: ties, final lists, copies into the callers' results.
+// outs[i] receives graph i.  Returns per-graph g_ntop and counters in the
+// host vectors.
+static int finish_run(tkc_ctx *ctx, const RunSetup &rs, const std::vector<GraphOut> &go_h, tkc_result *outs,
+                      std::vector<unsigned> &ntop, std::vector<unsigned> &tied, std::vector<u64> &gctr) {
+  Workspace &w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  const u32 ng = rs.ng;
+  GraphOut *go = nullptr;
+  TKC_TRY(cudaMallocAsync(&go, ng * sizeof(GraphOut), st));
+  TKC_TRY(cudaMemcpyAsync(go, go_h.data(), ng * sizeof(GraphOut), cudaMemcpyHostToDevice, st));
+  TKC_TRY(cudaMemsetAsync(w.tied, 0, ng * sizeof(unsigned), st));
+  unsigned blocks = (unsigned)std::max<u64>(1, std::min<u64>((rs.g->n + 255) / 256, (u64)ctx->num_sms * 8));
+  TKC_LAUNCH(k_count_ties<<<blocks, 256, 0, st>>>(w.res_S, w.res_r, rs.gid, rs.g->n, w.top_S, w.top_r, w.g_ntop,
+                                                  rs.kk, go, w.tied));
+  TKC_LAUNCH(k_output<<<ng, 256, 0, st>>>(w.top_S, w.top_r, w.top_id, w.g_ntop, rs.kk, go, w.out_S, w.out_r,
+                                          w.out_id, w.out_f, w.out_c));
+  TKC_TRY(cudaGetLastError());
+  ntop.resize(ng);
+  tied.resize(ng);
+  gctr.resize(4 * (size_t)ng);
+  TKC_TRY(cudaMemcpyAsync(ntop.data(), w.g_ntop, ng * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaMemcpyAsync(tied.data(), w.tied, ng * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  if (ng > 1)
+    TKC_TRY(cudaMemcpyAsync(gctr.data(), w.g_ctr, 4 * (size_t)ng * sizeof(u64), cudaMemcpyDeviceToHost, st));
+  for (u32 i = 0; i < ng; ++i) {
+    tkc_result *out = &outs[i];
+    const u32 kg = go_h[i].kk;
+    const size_t src = (size_t)i * rs.kk;
+    if (!kg) continue;
+    if (out->ids) TKC_TRY(cudaMemcpyAsync(out->ids, w.out_id + src, kg * sizeof(u32), cudaMemcpyDeviceToHost, st));
+    if (out->dist_sum)
+      TKC_TRY(cudaMemcpyAsync(out->dist_sum, w.out_S + src, kg * sizeof(u64), cudaMemcpyDeviceToHost, st));
+    if (out->reach) TKC_TRY(cudaMemcpyAsync(out->reach, w.out_r + src, kg * sizeof(u32), cudaMemcpyDeviceToHost, st));
+    if (out->farness)
+      TKC_TRY(cudaMemcpyAsync(out->farness, w.out_f + src, kg * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (out->closeness)
+      TKC_TRY(cudaMemcpyAsync(out->closeness, w.out_c + src, kg * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  TKC_TRY(cudaFreeAsync(go, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  for (u32 i = 0; i < ng; ++i)
+    if (ntop[i] < go_h[i].kk) tied[i] = go_h[i].nzero;  // the k-th is a closeness-0 vertex
+  return TKC_OK;
+}
+
+// Stand-in graph for the disjoint union of several graphs.
+__global__ void k_union_offsets(const u64 *offptr, const u32 *vbase, const u64 *abase, u32 ng, u32 nv, u32 *off_u,
+                                u32 *gid) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i <= nv; i += gridDim.x * blockDim.x) {
+    if (i == nv) {
+      off_u[nv] = (u32)abase[ng];
+      continue;
+    }
+    u32 lo = 0, hi = ng;  // last g with vbase[g] <= i
+    while (hi - lo > 1) {
+      u32 mid = (lo + hi) >> 1;
+      if (vbase[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    const u32 *og = (const u32 *)offptr[lo];
+    off_u[i] = og[i - vbase[lo]] + (u32)abase[lo];
+    gid[i] = lo;
+  }
+}
+
+__global__ void k_union_cols(const u64 *colptr, const u32 *vbase, const u64 *abase, u32 ng, u64 na, u32 *col_u) {
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < na; e += (u64)gridDim.x * blockDim.x) {
+    u32 lo = 0, hi = ng;
+    while (hi - lo > 1) {
+      u32 mid = (lo + hi) >> 1;
+      if (abase[mid] <= e) lo = mid;
+      else hi = mid;
+    }
+    col_u[e] = ((const u32 *)colptr[lo])[e - abase[lo]] + vbase[lo];
+  }
 }
 
 }  // namespace tkc
@@ -505,6 +598,29 @@ int tkc_reach_bounds(tkc_graph *g, uint32_t *alpha, uint32_t *omega) {
   return TKC_OK;
 }
 
+static void reset_result(tkc_result *r, u32 kk) {
+  r->n_returned = kk;
+  r->n_tied_at_kth = 0;
+  r->edges_visited = r->edges_scanned = r->bfs_started = r->bfs_cut = r->bfs_finished = r->levels = 0;
+  r->ms_pre = r->ms_bfs = r->ms_kernel = 0.0;
+  r->alg_bytes = 0;
+  r->batch_bits = 0;
+}
+
+static int source_order_of(tkc_graph *g, const tkc_options &o, const u32 **order, u32 *norder) {
+  if (o.order == TKC_ORDER_GIVEN) {
+    if (!g->given_order) return TKC_EINVAL;
+    *order = g->given_order;
+    *norder = g->n_src_given;
+  } else if (o.order == TKC_ORDER_DEG) {
+    *order = g->deg_order;
+    *norder = g->n_src_deg;
+  } else {
+    return TKC_EINVAL;
+  }
+  return TKC_OK;
+}
+
 int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   if (!g || !out) return TKC_EINVAL;
   if (k > TKC_MAX_K) return TKC_EINVAL;
@@ -513,12 +629,7 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   if (kk > 0 && out->capacity < kk) return TKC_EINVAL;
   TKC_TRY(cudaSetDevice(ctx->device));
   tkc_result r = *out;
-  r.n_returned = kk;
-  r.n_tied_at_kth = 0;
-  r.edges_visited = r.edges_scanned = r.bfs_started = r.bfs_cut = r.bfs_finished = r.levels = 0;
-  r.ms_pre = r.ms_bfs = r.ms_kernel = 0.0;
-  r.alg_bytes = 0;
-  r.batch_bits = 0;
+  reset_result(&r, kk);
   if (kk == 0) {
     *out = r;
     return TKC_OK;
@@ -528,33 +639,32 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   TKC_RC(ensure_degree_order(g));
   TKC_RC(ensure_reach_bounds(g));
   RunSetup rs;
+  memset(&rs, 0, sizeof(rs));
   const tkc_options &o = ctx->opt;
-  if (o.order == TKC_ORDER_GIVEN) {
-    if (!g->given_order) return TKC_EINVAL;
-    rs.order = g->given_order;
-    rs.norder = g->n_src_given;
-  } else if (o.order == TKC_ORDER_DEG) {
-    rs.order = g->deg_order;
-    rs.norder = g->n_src_deg;
-  } else {
-    return TKC_EINVAL;
-  }
+  TKC_RC(source_order_of(g, o, &rs.order, &rs.norder));
   TKC_TRY(cudaEventRecord(ctx->ev[1], st));
-  u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g);
+  u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g->n);
+  rs.g = g;
   rs.B = bits;
   rs.W = words_for(bits);
   rs.nocut = 0;
   rs.kk = kk;
+  rs.ng = 1;
   r.batch_bits = bits;
   Ctl hc;
-  TKC_RC(run_search(g, rs, &hc));
-  TKC_RC(finish_topk(ctx, g, kk, &r));
-  unsigned tied = 0;
-  TKC_TRY(cudaMemcpyAsync(&tied, ctx->ws.tied, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TKC_RC(run_search(ctx, rs, &hc));
+  std::vector<GraphOut> go(1);
+  go[0].n = g->n;
+  go[0].base = 0;
+  go[0].kk = kk;
+  go[0].nzero = g->n - g->n_src_deg;
+  go[0].zero_ids = g->deg_order + g->n_src_deg;
+  std::vector<unsigned> ntop, tied;
+  std::vector<u64> gctr;
+  TKC_RC(finish_run(ctx, rs, go, &r, ntop, tied, gctr));
   TKC_TRY(cudaEventRecord(ctx->ev[2], st));
   TKC_TRY(cudaStreamSynchronize(st));
-  // when the k-th entry is a closeness-0 vertex, every such vertex ties with it
-  r.n_tied_at_kth = hc.ntop < kk ? g->n - g->n_src_deg : tied;
+  r.n_tied_at_kth = tied[0];
   r.edges_visited = hc.edges_visited;
   r.edges_scanned = hc.edges_scanned;
   r.bfs_started = hc.bfs_started;
@@ -590,14 +700,17 @@ int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_
   TKC_TRY(cudaMallocAsync(&dsrc, uniq.size() * sizeof(u32), st));
   TKC_TRY(cudaMemcpyAsync(dsrc, uniq.data(), uniq.size() * sizeof(u32), cudaMemcpyHostToDevice, st));
   RunSetup rs;
+  memset(&rs, 0, sizeof(rs));
+  rs.g = g;
   rs.order = dsrc;
   rs.norder = (u32)uniq.size();
   rs.B = 64;
   rs.W = 1;
   rs.nocut = 1;
   rs.kk = 1;
+  rs.ng = 1;
   Ctl hc;
-  int rc = run_search(g, rs, &hc);
+  int rc = run_search(ctx, rs, &hc);
   std::vector<u64> allS;
   std::vector<u32> allr;
   if (rc == TKC_OK) {
@@ -624,10 +737,152 @@ int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_
 
 int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs) {
   if (!ctx || (ng && (!gs || !outs))) return TKC_EINVAL;
+  if (k > TKC_MAX_K) return TKC_EINVAL;
+  if (ng == 0) return TKC_OK;
+  TKC_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const tkc_options &o = ctx->opt;
+  if (o.order != TKC_ORDER_DEG) return TKC_EINVAL;  // the union is searched in degree order
+  u64 nv64 = 0, na = 0;
+  u32 maxn = 0;
   for (u32 i = 0; i < ng; ++i) {
     if (!gs[i] || gs[i]->ctx != ctx) return TKC_EINVAL;
-    TKC_RC(tkc_topk_closeness(gs[i], k, &outs[i]));
+    u32 kg = std::min<u32>(k, gs[i]->n);
+    if (kg > 0 && outs[i].capacity < kg) return TKC_EINVAL;
+    nv64 += gs[i]->n;
+    na += gs[i]->arcs;
+    maxn = std::max(maxn, gs[i]->n);
   }
+  if (nv64 >= kMaxN || na >= (1ull << 32)) return TKC_EOVERFLOW;
+  const u32 nv = (u32)nv64;
+  const u32 kk = std::min<u32>(k, maxn);
+  for (u32 i = 0; i < ng; ++i) reset_result(&outs[i], std::min<u32>(k, gs[i]->n));
+  if (kk == 0) return TKC_OK;
+  TKC_TRY(cudaEventRecord(ctx->ev[0], st));
+  // per-graph preprocessing (cached in each graph), then the union
+  std::vector<u32> vbase(ng + 1, 0);
+  std::vector<u64> abase(ng + 1, 0), offptr(ng), colptr(ng);
+  std::vector<uint8_t> gdir(ng);
+  for (u32 i = 0; i < ng; ++i) {
+    TKC_RC(ensure_degree_order(gs[i]));
+    TKC_RC(ensure_reach_bounds(gs[i]));
+    vbase[i + 1] = vbase[i] + gs[i]->n;
+    abase[i + 1] = abase[i] + gs[i]->arcs;
+    offptr[i] = (u64)gs[i]->off;
+    colptr[i] = (u64)gs[i]->col;
+    gdir[i] = (uint8_t)gs[i]->directed;
+  }
+  tkc_graph U;
+  U.ctx = ctx;
+  U.n = nv;
+  U.arcs = na;
+  U.directed = 1;
+  u32 *gid = nullptr, *d_vbase = nullptr;
+  u64 *d_abase = nullptr, *d_offptr = nullptr, *d_colptr = nullptr;
+  uint8_t *d_gdir = nullptr;
+  int rc = TKC_OK;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, gid, d_vbase, d_abase, d_offptr,
+                    d_colptr, d_gdir};
+    for (void *q : ptrs)
+      if (q) cudaFree(q);
+  };
+#define MULTI_TRY(expr)                                              \
+  do {                                                               \
+    cudaError_t e_ = (expr);                                         \
+    if (e_ != cudaSuccess) {                                         \
+      tkc_set_last_cuda_error(e_, #expr, __FILE__, __LINE__);        \
+      cleanup();                                                     \
+      return e_ == cudaErrorMemoryAllocation ? TKC_ENOMEM : TKC_ECUDA; \
+    }                                                                \
+  } while (0)
+#define MULTI_RC(expr)  \
+  do {                  \
+    rc = (expr);        \
+    if (rc != TKC_OK) { \
+      cleanup();        \
+      return rc;        \
+    }                   \
+  } while (0)
+  MULTI_TRY(cudaMallocAsync(&U.off, ((size_t)nv + 1) * sizeof(u32), st));
+  MULTI_TRY(cudaMallocAsync(&U.col, std::max<size_t>(na, 1) * sizeof(u32), st));
+  MULTI_TRY(cudaMallocAsync(&U.alpha, std::max<size_t>(nv, 1) * sizeof(u32), st));
+  MULTI_TRY(cudaMallocAsync(&U.omega, std::max<size_t>(nv, 1) * sizeof(u32), st));
+  MULTI_TRY(cudaMallocAsync(&gid, std::max<size_t>(nv, 1) * sizeof(u32), st));
+  MULTI_TRY(cudaMallocAsync(&d_vbase, (ng + 1) * sizeof(u32), st));
+  MULTI_TRY(cudaMallocAsync(&d_abase, (ng + 1) * sizeof(u64), st));
+  MULTI_TRY(cudaMallocAsync(&d_offptr, ng * sizeof(u64), st));
+  MULTI_TRY(cudaMallocAsync(&d_colptr, ng * sizeof(u64), st));
+  MULTI_TRY(cudaMallocAsync(&d_gdir, ng, st));
+  MULTI_TRY(cudaMemcpyAsync(d_vbase, vbase.data(), (ng + 1) * sizeof(u32), cudaMemcpyHostToDevice, st));
+  MULTI_TRY(cudaMemcpyAsync(d_abase, abase.data(), (ng + 1) * sizeof(u64), cudaMemcpyHostToDevice, st));
+  MULTI_TRY(cudaMemcpyAsync(d_offptr, offptr.data(), ng * sizeof(u64), cudaMemcpyHostToDevice, st));
+  MULTI_TRY(cudaMemcpyAsync(d_colptr, colptr.data(), ng * sizeof(u64), cudaMemcpyHostToDevice, st));
+  MULTI_TRY(cudaMemcpyAsync(d_gdir, gdir.data(), ng, cudaMemcpyHostToDevice, st));
+  unsigned gb = (unsigned)std::max<u64>(1, std::min<u64>((nv + 256) / 256, (u64)ctx->num_sms * 16));
+  TKC_LAUNCH(k_union_offsets<<<gb, 256, 0, st>>>(d_offptr, d_vbase, d_abase, ng, nv, U.off, gid));
+  unsigned ga = (unsigned)std::max<u64>(1, std::min<u64>((na + 255) / 256, (u64)ctx->num_sms * 16));
+  if (na) TKC_LAUNCH(k_union_cols<<<ga, 256, 0, st>>>(d_colptr, d_vbase, d_abase, ng, na, U.col));
+  MULTI_TRY(cudaGetLastError());
+  for (u32 i = 0; i < ng; ++i)
+    if (gs[i]->n) {
+      MULTI_TRY(cudaMemcpyAsync(U.alpha + vbase[i], gs[i]->alpha, gs[i]->n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+      MULTI_TRY(cudaMemcpyAsync(U.omega + vbase[i], gs[i]->omega, gs[i]->n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+    }
+  MULTI_RC(build_in_csr(&U));
+  MULTI_RC(ensure_degree_order(&U));
+  TKC_TRY(cudaEventRecord(ctx->ev[1], st));
+  RunSetup rs;
+  memset(&rs, 0, sizeof(rs));
+  u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(nv);
+  rs.g = &U;
+  rs.order = U.deg_order;
+  rs.norder = U.n_src_deg;
+  rs.B = bits;
+  rs.W = words_for(bits);
+  rs.nocut = 0;
+  rs.kk = kk;
+  rs.ng = ng;
+  rs.gid = gid;
+  rs.g_directed = d_gdir;
+  Ctl hc;
+  MULTI_RC(run_search(ctx, rs, &hc));
+  std::vector<GraphOut> go(ng);
+  for (u32 i = 0; i < ng; ++i) {
+    go[i].n = gs[i]->n;
+    go[i].base = vbase[i];
+    go[i].kk = std::min<u32>(k, gs[i]->n);
+    go[i].nzero = gs[i]->n - gs[i]->n_src_deg;
+    go[i].zero_ids = gs[i]->deg_order + gs[i]->n_src_deg;
+  }
+  std::vector<unsigned> ntop, tied;
+  std::vector<u64> gctr;
+  MULTI_RC(finish_run(ctx, rs, go, outs, ntop, tied, gctr));
+  MULTI_TRY(cudaEventRecord(ctx->ev[2], st));
+  MULTI_TRY(cudaStreamSynchronize(st));
+  float ms0 = 0, ms1 = 0, ms2 = 0;
+  cudaEventElapsedTime(&ms0, ctx->ev[0], ctx->ev[1]);
+  cudaEventElapsedTime(&ms1, ctx->ev[1], ctx->ev[2]);
+  cudaEventElapsedTime(&ms2, ctx->ev[4], ctx->ev[5]);
+  for (u32 i = 0; i < ng; ++i) {
+    tkc_result &r = outs[i];
+    r.n_tied_at_kth = tied[i];
+    r.edges_visited = gctr[4 * (size_t)i + 0];
+    r.bfs_started = gctr[4 * (size_t)i + 1];
+    r.bfs_cut = gctr[4 * (size_t)i + 2];
+    r.bfs_finished = gctr[4 * (size_t)i + 3];
+    r.edges_scanned = hc.edges_scanned;  // shared by the run
+    r.levels = hc.levels;
+    r.alg_bytes = hc.alg_bytes;
+    r.batch_bits = bits;
+    r.ms_pre = ms0;
+    r.ms_bfs = ms1;
+    r.ms_kernel = ms2;
+  }
+#undef MULTI_TRY
+#undef MULTI_RC
+  cleanup();
   return TKC_OK;
 }
 

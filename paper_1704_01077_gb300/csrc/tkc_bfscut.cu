@@ -299,7 +299,7 @@ struct Smem {
   u64 tS[kTopMax];
   uint32_t tr[kTopMax], tid[kTopMax];
   u64 cS[64 * W];
-  uint32_t cr[64 * W], cid[64 * W];
+  uint32_t cr[64 * W], cid[64 * W], cg[64 * W];
   unsigned ncand;
   unsigned nactive;
   unsigned scan[kTPB / 32 + 1];
@@ -372,10 +372,9 @@ __device__ u64 block_exscan64(Smem<W> &sm, u64 x, u64 *total) {
 // and the candidates (keys are unique: farness then id), so each position below
 // k gets exactly one writer and the old list is read from a shared copy.
 template <int W>
-__device__ void merge_topk(const RunParams &p, Smem<W> &sm) {
-  Ctl *c = p.ctl;
+__device__ void merge_topk_one(const RunParams &p, Smem<W> &sm) {
   const uint32_t kk = p.kk;
-  uint32_t ntop = c->ntop;
+  uint32_t ntop = p.g_ntop[0];
   uint32_t nc = sm.ncand;
   if (nc == 0) return;
   for (uint32_t i = threadIdx.x; i < ntop; i += kTPB) {
@@ -415,19 +414,83 @@ __device__ void merge_topk(const RunParams &p, Smem<W> &sm) {
   }
   __syncthreads();
   uint32_t nnew = ntop + nc < kk ? ntop + nc : kk;
-  if (threadIdx.x == 0) c->ntop = nnew;
+  if (threadIdx.x == 0) p.g_ntop[0] = nnew;
   __syncthreads();
+}
+
+// Several graphs: the thread holding a graph's first candidate inserts that
+// graph's candidates into its list one by one (each list has one writer).
+template <int W>
+__device__ void merge_topk_many(const RunParams &p, Smem<W> &sm) {
+  const uint32_t kk = p.kk;
+  const uint32_t nc = sm.ncand;
+  for (uint32_t i = threadIdx.x; i < nc; i += kTPB) {
+    const uint32_t g = sm.cg[i];
+    bool first = true;
+    for (uint32_t j = 0; j < i && first; ++j) first = sm.cg[j] != g;
+    if (!first) continue;
+    u64 *tS = p.top_S + (size_t)g * kk;
+    uint32_t *tr = p.top_r + (size_t)g * kk, *ti = p.top_id + (size_t)g * kk;
+    uint32_t cnt = p.g_ntop[g];
+    for (uint32_t j = i; j < nc; ++j) {
+      if (sm.cg[j] != g) continue;
+      u64 S = sm.cS[j];
+      uint32_t r = sm.cr[j], id = sm.cid[j];
+      if (cnt == kk && !entry_less(S, r, id, tS[kk - 1], tr[kk - 1], ti[kk - 1])) continue;
+      uint32_t pos = cnt < kk ? cnt++ : kk - 1;
+      while (pos > 0 && entry_less(S, r, id, tS[pos - 1], tr[pos - 1], ti[pos - 1])) {
+        tS[pos] = tS[pos - 1];
+        tr[pos] = tr[pos - 1];
+        ti[pos] = ti[pos - 1];
+        --pos;
+      }
+      tS[pos] = S;
+      tr[pos] = r;
+      ti[pos] = id;
+    }
+    p.g_ntop[g] = cnt;
+  }
+  __syncthreads();
+}
+
+template <int W>
+__device__ __forceinline__ void merge_topk(const RunParams &p, Smem<W> &sm) {
+  if (p.ng == 1) merge_topk_one(p, sm);
+  else merge_topk_many(p, sm);
+}
+
+// The current k-th entry of graph g's list, if the list is full.
+struct Thresh {
+  bool have;
+  u64 S;
+  uint32_t r, id;
+};
+
+__device__ __forceinline__ Thresh thresh_of(const RunParams &p, uint32_t g) {
+  Thresh t;
+  t.have = p.g_ntop[g] == p.kk;
+  size_t i = (size_t)g * p.kk + p.kk - 1;
+  t.S = t.have ? p.top_S[i] : 0;
+  t.r = t.have ? p.top_r[i] : 0;
+  t.id = t.have ? p.top_id[i] : 0;
+  return t;
+}
+
+__device__ __forceinline__ void graph_count(const RunParams &p, uint32_t g, int which, u64 v) {
+  if (p.g_ctr && v) atomicAdd(&p.g_ctr[(size_t)g * 4 + which], v);
 }
 
 // Adds a finished search to the candidate list if it can enter the top list.
 template <int W>
 __device__ __forceinline__ void offer_candidate(const RunParams &p, Smem<W> &sm, u64 S, uint32_t r, uint32_t v,
-                                                bool have_x, u64 Sx, uint32_t rx, uint32_t idx) {
-  if (have_x && !entry_less(S, r, v, Sx, rx, idx)) return;
+                                                uint32_t g) {
+  Thresh x = thresh_of(p, g);
+  if (x.have && !entry_less(S, r, v, x.S, x.r, x.id)) return;
   unsigned pos = atomicAdd(&sm.ncand, 1u);
   sm.cS[pos] = S;
   sm.cr[pos] = r;
   sm.cid[pos] = v;
+  sm.cg[pos] = g;
 }
 
 // Epilogue after a level: update every active slot, merge finished searches,
@@ -455,10 +518,6 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
   if (threadIdx.x < W) sm.active[threadIdx.x] = 0;
   for (int i = threadIdx.x; i < 4; i += kTPB) sm.acc[i] = 0;
   __syncthreads();
-  uint32_t ntop0 = c->ntop;
-  bool have_x0 = ntop0 == p.kk;
-  u64 Sx0 = have_x0 ? p.top_S[p.kk - 1] : 0;
-  uint32_t rx0 = have_x0 ? p.top_r[p.kk - 1] : 0, ix0 = have_x0 ? p.top_id[p.kk - 1] : 0;
   // 1. per-slot level update
   int cont[(64 * W + kTPB - 1) / kTPB];
   uint32_t finished = 0;
@@ -479,12 +538,14 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
       p.res_S[sl.v] = sl.S;
       p.res_r[sl.v] = (uint32_t)sl.nd;
       ++finished;
-      offer_candidate(p, sm, sl.S, (uint32_t)sl.nd, sl.v, have_x0, Sx0, rx0, ix0);
+      graph_count(p, sl.graph, 3, 1);
+      offer_candidate(p, sm, sl.S, (uint32_t)sl.nd, sl.v, sl.graph);
     } else {
+      const int directed = p.g_directed ? p.g_directed[sl.graph] : p.directed;
       sl.d += 1;
       sl.S += (u64)sl.d * cn;
       sl.nd += cn;
-      sl.g = ws - (p.directed ? 0ull : (u64)cn);
+      sl.g = ws - (directed ? 0ull : (u64)cn);
       sl.arcs = ws;
       cont[t] = 1;
     }
@@ -494,10 +555,6 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
   __syncthreads();
   // 2. top-k merge and the new threshold
   merge_topk(p, sm);
-  uint32_t ntop = c->ntop;
-  bool have_x = ntop == p.kk && !p.nocut;
-  u64 Sx = have_x ? p.top_S[p.kk - 1] : 0;
-  uint32_t rx = have_x ? p.top_r[p.kk - 1] : 0;
   // 3. BFSCut test for the slots that continue
   uint32_t cuts = 0;
   u64 visited = 0;
@@ -506,12 +563,15 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
     uint32_t s = threadIdx.x + t * kTPB;
     if (!cont[t]) continue;
     Slot sl = p.slots[s];
-    if (have_x && cut_exceeds(sl.S, sl.d, sl.nd, sl.g, sl.alpha, sl.omega, Sx, rx)) {
+    Thresh x = thresh_of(p, sl.graph);
+    if (!p.nocut && x.have && cut_exceeds(sl.S, sl.d, sl.nd, sl.g, sl.alpha, sl.omega, x.S, x.r)) {
       sl.state = 2;
       ++cuts;
+      graph_count(p, sl.graph, 2, 1);
       p.slots[s] = sl;
     } else {
       visited += sl.arcs;
+      graph_count(p, sl.graph, 0, sl.arcs);
       atomicOr(&sm.active[s >> 6], 1ull << (s & 63));
       atomicAdd(&sm.nactive, 1u);
     }
@@ -587,10 +647,6 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
   uint32_t *FBcur = c->cur ? p.FB1 : p.FB0;
   uint32_t *FL = c->cur ? p.L1 : p.L0;
   uint32_t *FLoff = c->cur ? p.Loff1 : p.Loff0;
-  uint32_t ntop = c->ntop;
-  bool have_x = ntop == p.kk && !p.nocut;
-  u64 Sx = have_x ? p.top_S[p.kk - 1] : 0;
-  uint32_t rx = have_x ? p.top_r[p.kk - 1] : 0;
   uint32_t cursor = c->cursor;
   uint32_t assigned = 0;
   u64 arcs_total = 0, started = 0, cut0 = 0;
@@ -602,8 +658,13 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     uint32_t v = valid ? p.order[idx] : 0;
     uint32_t od = valid ? p.off[v + 1] - p.off[v] : 0;
     uint32_t a = valid ? p.alpha[v] : 0, o = valid ? p.omega[v] : 0;
+    uint32_t gv = (valid && p.gid) ? p.gid[v] : 0;
     // level 0: S_0 = 0, n_0 = 1, gamma_1 = out-degree
-    bool cut = valid && have_x && cut_exceeds(0, 0, 1, od, a, o, Sx, rx);
+    bool cut = false;
+    if (valid && !p.nocut) {
+      Thresh x = thresh_of(p, gv);
+      cut = x.have && cut_exceeds(0, 0, 1, od, a, o, x.S, x.r);
+    }
     bool keep = valid && !cut;
     uint32_t total;
     uint32_t pre = block_exscan(sm, keep ? 1u : 0u, &total);
@@ -621,6 +682,10 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     }
     bool in = threadIdx.x < consumed;
     bool take = keep && in;
+    if (cut && in) {
+      graph_count(p, gv, 1, 1);
+      graph_count(p, gv, 2, 1);
+    }
     uint32_t s = assigned + pre;
     u64 myarcs = take ? od : 0;
     u64 arcs_pre_total;
@@ -636,8 +701,10 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       sl.alpha = a;
       sl.omega = o;
       sl.state = 1;
-      sl.pad = 0;
+      sl.graph = gv;
       p.slots[s] = sl;
+      graph_count(p, gv, 1, 1);
+      graph_count(p, gv, 0, od);
       u64 bit = 1ull << (s & 63);
       p.seen[(size_t)v * W + (s >> 6)] = bit;
       Fcur[(size_t)v * W + (s >> 6)] = bit;
@@ -686,7 +753,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
         rec[4] = cursor;
         rec[5] = cut0;
         rec[6] = c->vl_count;
-        rec[7] = c->ntop;
+        rec[7] = p.g_ntop[0];
       }
     }
     c->batches += 1;

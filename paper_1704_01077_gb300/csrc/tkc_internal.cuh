@@ -61,9 +61,6 @@ struct Ctl {
   unsigned long long fl_arcs;    // arcs out of the current frontier list
   unsigned long long nl_packed;  // next list: count << 38 | arcs
   unsigned long long active[kMaxWords];
-  // top-k
-  unsigned int ntop;
-  unsigned int pad1;
   // counters
   unsigned long long edges_visited;
   unsigned long long edges_scanned;
@@ -88,7 +85,7 @@ struct Slot {
   unsigned int d;         // deepest discovered level
   unsigned int alpha, omega;
   int state;              // 0 free, 1 active, 2 done (waiting for the clear step)
-  unsigned int pad;
+  unsigned int graph;     // graph of the source (several graphs in one run)
 };
 
 struct RunParams {
@@ -101,6 +98,12 @@ struct RunParams {
   const uint32_t *order;
   uint32_t norder;  // sources in `order` to examine (all have out-degree >= 1)
   // search configuration
+  // several graphs in one run, as their disjoint union (ng = 1: one graph)
+  uint32_t ng;
+  const uint32_t *gid;        // graph of each vertex (nullptr: every vertex in graph 0)
+  const uint8_t *g_directed;  // per graph (nullptr: `directed` for all)
+  unsigned int *g_ntop;       // entries in each graph's top list
+  unsigned long long *g_ctr;  // per graph: edges_visited, bfs_started, bfs_cut, bfs_finished (nullable)
   uint32_t kk;        // min(k, n); 0 never reaches the kernel
   uint32_t B;         // active slots per batch (1..64*W)
   int nocut;          // 1: never cut (exact S, r for every source)
@@ -116,7 +119,7 @@ struct RunParams {
   Slot *slots;
   unsigned int *cnt;             // per-slot level counts
   unsigned long long *wsum;      // per-slot sums of out-degree over the new level
-  unsigned long long *top_S;
+  unsigned long long *top_S;     // graph g's list at [g * kk, (g + 1) * kk)
   uint32_t *top_r, *top_id;
   unsigned long long *res_S;     // per-vertex S of finished searches
   uint32_t *res_r;               // per-vertex r of finished searches (0 = not finished)
@@ -143,7 +146,11 @@ struct Workspace {
   unsigned long long *out_S = nullptr;
   uint32_t *out_r = nullptr, *out_id = nullptr;
   double *out_f = nullptr, *out_c = nullptr;
-  unsigned int *tied = nullptr;
+  unsigned int *tied = nullptr;     // per graph
+  unsigned int *g_ntop = nullptr;   // per graph
+  unsigned long long *g_ctr = nullptr;  // 4 per graph
+  uint32_t top_cap = 0;   // entries of top_* / out_* (graphs x k)
+  uint32_t ng_cap = 0;    // graphs of tied / g_ntop / g_ctr
   unsigned int level_base = 0;  // stamp epoch carried across runs
 };
 
@@ -178,12 +185,12 @@ struct tkc_graph {
 namespace tkc {
 // tkc_prep.cu
 int validate_and_transpose(tkc_graph *g);
+int build_in_csr(tkc_graph *g);
 int ensure_degree_order(tkc_graph *g);
 int ensure_reach_bounds(tkc_graph *g);
 int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
 // tkc_bfscut.cu
-int ensure_workspace(tkc_ctx *ctx, uint32_t n, int words, uint32_t kk);
+int ensure_workspace(tkc_ctx *ctx, uint32_t n, int words, uint32_t top_entries, uint32_t ng);
 int run_bfscut(tkc_ctx *ctx, const RunParams &p, int words, int blocks);
-int finish_topk(tkc_ctx *ctx, tkc_graph *g, uint32_t kk, tkc_result *out);
 int max_coresident_blocks(tkc_ctx *ctx, int words);
 }  // namespace tkc

@@ -63,7 +63,8 @@ struct Layout {
   static constexpr size_t top_S = wsum + align256(sizeof(u64) * kSlots);
   static constexpr size_t top_r = top_S + 256;
   static constexpr size_t top_id = top_r + 256;
-  static constexpr size_t flag = top_id + 256;
+  static constexpr size_t g_ntop = top_id + 256;
+  static constexpr size_t flag = g_ntop + 256;
   static constexpr size_t ctl = flag + 256;
   static constexpr size_t total = ctl + align256(sizeof(Ctl));
 };
@@ -185,6 +186,11 @@ extern "C" int tkc_distance_sums_noalloc(const uint32_t *offsets, const uint32_t
   p.omega = (const u32 *)(base + L::omega);
   p.order = srcs;
   p.norder = nsrc;
+  p.ng = 1;
+  p.gid = nullptr;
+  p.g_directed = nullptr;
+  p.g_ntop = (unsigned *)(base + L::g_ntop);
+  p.g_ctr = nullptr;
   p.kk = 1;
   p.B = kSlots;
   p.nocut = 1;

@@ -206,6 +206,14 @@ int validate_and_transpose(tkc_graph *g) {
     g->icol = g->col;
     return TKC_OK;
   }
+  return build_in_csr(g);
+}
+
+// In-arc CSR of g (rows unsorted: the in-arcs of a vertex in scatter order).
+int build_in_csr(tkc_graph *g) {
+  cudaStream_t st = g->ctx->stream;
+  const u32 n = g->n;
+  if (n == 0) return TKC_OK;
   u32 *tmp = nullptr, *cursor = nullptr;
   TKC_TRY(cudaMallocAsync(&g->ioff, ((size_t)n + 1) * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&g->icol, std::max<size_t>(g->arcs, 1) * sizeof(u32), st));

@@ -223,3 +223,53 @@ def test_device_pointer_input(gpu_lib, ctx):
     finally:
         gpu_lib.tkc_free_graph(h)
     _expect_equal(got, oracle.textbook_topk(g, 10), g, 10)
+
+
+def _mixed_graphs(count, lo, hi, seed):
+    """Half Barabasi-Albert (m=4), half directed Erdos-Renyi (mean out-degree 8),
+    vertex counts log-uniform in [lo, hi]."""
+    sizes = gg.log_uniform_sizes(count, lo, hi, seed)
+    out = []
+    for i, n in enumerate(sizes):
+        if i % 2 == 0:
+            out.append(gg.barabasi_albert(max(n, 6), 4, seed + i))
+        else:
+            out.append(gg.erdos_renyi(n, 8 * n, seed + i, directed=True))
+    return out
+
+
+def test_multi_graph_one_launch(gpu_lib, ctx):
+    t = gpu_lib
+    graphs = _mixed_graphs(24, 20, 3000, 4242) + [
+        gg.from_arcs(0, [], [], True, "empty0"), gg.from_arcs(5, [], [], True, "isolated5"), gg.path(3),
+        gg.cycle(7, directed=True), gg.reduction_graph(3, [{0}, {1, 2}, {0, 2}])[0],
+        gg.disjoint_union(gg.cycle(5), gg.path(4), gg.path(1))]
+    for bits, k in ((64, 10), (256, 10), (512, 3), (128, 40)):
+        t.tkc_set_options(ctx, t.Options(batch_bits=bits))
+        hs = [t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed) for g in graphs]
+        try:
+            res = t.tkc_topk_closeness_multi(ctx, hs, k)
+            for g, h, r in zip(graphs, hs, res):
+                ref = oracle.textbook_topk(g, k)
+                _expect_equal(r, ref, g, k)
+                single = t.tkc_topk_closeness(h, k)
+                assert list(single.ids) == list(r.ids) and single.n_tied_at_kth == r.n_tied_at_kth
+        finally:
+            for h in hs:
+                t.tkc_free_graph(h)
+
+
+def test_multi_graph_counters_add_up(gpu_lib, ctx):
+    t = gpu_lib
+    graphs = _mixed_graphs(10, 200, 2000, 99)
+    t.tkc_set_options(ctx, t.Options(batch_bits=128))
+    hs = [t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed) for g in graphs]
+    try:
+        res = t.tkc_topk_closeness_multi(ctx, hs, 10)
+    finally:
+        for h in hs:
+            t.tkc_free_graph(h)
+    for g, r in zip(graphs, res):
+        src = int((g.outdeg() > 0).sum())
+        assert r.bfs_started == src and r.bfs_cut + r.bfs_finished == src
+        assert 0 < r.edges_visited <= g.arcs * src
