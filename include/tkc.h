@@ -47,7 +47,9 @@ extern "C" {
 
 #define TKC_ORDER_DEG 0     /* computeBoundsDeg: out-degree descending, then id ascending (Section 4) */
 #define TKC_ORDER_GIVEN 1   /* caller's order, set by tkc_set_source_order */
-#define TKC_ORDER_LEARNED 2 /* predicted-farness order from the source-order MLP (tkc_set_mlp) */
+#define TKC_ORDER_LEARNED 2 /* source-order model (tkc_set_source_model): with seed_factor = 0 all sources
+                               by predicted farness; with seed_factor > 0 the seed_factor * k sources
+                               predicted closest first (searched without cutting), then the degree order */
 
 #define TKC_MAX_K 1024      /* largest k accepted by tkc_topk_closeness */
 
@@ -64,8 +66,8 @@ typedef struct {
                               arcs * bu_den (bu_num = 0: library default, 8/1) */
   uint32_t bu_den;
   uint32_t blocks;         /* persistent grid size (0 = library default, clamped to co-residency) */
-  uint32_t seed_factor;    /* learned order: number of leading sources searched without cutting, as a
-                              multiple of k, to seed the threshold (0 = none) */
+  uint32_t seed_factor;    /* the first seed_factor * k sources of the order are searched to the end
+                              without cutting, so x starts from exact farness values (0 = none) */
   uint64_t timeout_cycles; /* budget of every device-side wait, in SM clock cycles (0 = default 2^34) */
 } tkc_options;
 
@@ -177,6 +179,47 @@ int tkc_distance_sums_noalloc(const uint32_t *offsets, const uint32_t *cols, uin
 /* Number of CUDA kernels this library has launched in this process (all
  * contexts), for accounting of device work. */
 uint64_t tkc_kernel_launches(void);
+
+/* ---- learned source order (beyond the paper) ------------------------------
+ * Algorithm 1's result does not depend on the order of Q (Section 4: every
+ * order gives the exact top-k; only pruning changes).  The library can order
+ * sources by the farness a small MLP predicts from per-vertex features, so
+ * that the k-th threshold x tightens sooner; the degree order of Section 4 is
+ * the fallback.  Model: x (TKC_MLP_FEATURES) -> 64 -> 64 -> 1, ReLU, bf16
+ * weights, fp32 accumulation.  Parameters, TKC_MLP_PARAMS floats:
+ * W1[64][5], b1[64], W2[64][64], b2[64], w3[64], b3. */
+#define TKC_MLP_FEATURES 5
+#define TKC_MLP_HIDDEN 64
+#define TKC_MLP_PARAMS 4609
+
+/* Standardized features of every vertex into DEVICE array x[n][5]:
+ * log1p of out-degree, in-degree, the 2-walk count sum of out-degrees of
+ * out-neighbours (Lemma 1's gamma at d = 1, a bound on the 2-hop ball), an
+ * h-index estimate of the core number (4 steps from the degree, out- and
+ * in-neighbours), and the SCC size (component size if undirected); each
+ * feature shifted and scaled to mean 0, variance 1 over the graph. */
+int tkc_vertex_features(tkc_graph *g, float *x);
+
+/* Random He-uniform weights from `seed` (zero biases); resets Adam. */
+int tkc_mlp_init(tkc_ctx *ctx, uint64_t seed);
+
+/* Sets / reads the fp32 master weights (host arrays of TKC_MLP_PARAMS);
+ * setting enables TKC_ORDER_LEARNED and resets Adam. */
+int tkc_set_source_model(tkc_ctx *ctx, const float *params, uint32_t nparams);
+int tkc_get_source_model(tkc_ctx *ctx, float *params, uint32_t nparams);
+
+/* y[i] = model(x[i]) for m samples; x, y DEVICE arrays (m x 5, m). */
+int tkc_mlp_forward(tkc_ctx *ctx, const float *x, uint32_t m, float *y);
+
+/* Gradient of L = (1/m) sum_i (model(x_i) - t_i)^2 with respect to the
+ * parameters (forward pass with the bf16 weights) into DEVICE grad[P]; the
+ * loss into host *loss (may be NULL).  x, t: DEVICE arrays. */
+int tkc_mlp_gradient(tkc_ctx *ctx, const float *x, const float *t, uint32_t m, float *grad, float *loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on that gradient with
+ * learning rate lr; refreshes the bf16 weights; loss before the step into
+ * host *loss (may be NULL). */
+int tkc_mlp_train_step(tkc_ctx *ctx, const float *x, const float *t, uint32_t m, float lr, float *loss);
 
 /* Names a TKC_* return code. */
 const char *tkc_strerror(int code);

@@ -219,6 +219,7 @@ struct RunSetup {
   u32 B;
   int W;
   int nocut;
+  u32 nocut_prefix;
   u32 kk;                   // list length per graph
   u32 ng;
   const u32 *gid;           // nullptr for one graph
@@ -264,6 +265,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.kk = rs.kk;
   p.B = rs.B;
   p.nocut = rs.nocut;
+  p.nocut_prefix = rs.nocut_prefix;
   const tkc_options &o = ctx->opt;
   // default: a level runs bottom-up when its frontier's arcs exceed 1/8 of all arcs
   p.bu_num = o.bu_num ? o.bu_num : 8;
@@ -484,6 +486,7 @@ void tkc_destroy(tkc_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   free_workspace(ctx);
+  free_mlp(ctx);
   for (auto &ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
   delete ctx;
@@ -549,7 +552,8 @@ void tkc_free_graph(tkc_graph *g) {
   cudaStreamSynchronize(g->ctx->stream);
   if (g->ioff && g->ioff != g->off) cudaFree(g->ioff);
   if (g->icol && g->icol != g->col) cudaFree(g->icol);
-  void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega};
+  void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega, g->scc_size, g->features,
+                  g->learned_order, g->seeded_order};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   g->ctx->graphs_alive--;
@@ -607,13 +611,22 @@ static void reset_result(tkc_result *r, u32 kk) {
   r->batch_bits = 0;
 }
 
-static int source_order_of(tkc_graph *g, const tkc_options &o, const u32 **order, u32 *norder) {
+static int source_order_of(tkc_graph *g, const tkc_options &o, u32 kk, const u32 **order, u32 *norder) {
   if (o.order == TKC_ORDER_GIVEN) {
     if (!g->given_order) return TKC_EINVAL;
     *order = g->given_order;
     *norder = g->n_src_given;
   } else if (o.order == TKC_ORDER_DEG) {
     *order = g->deg_order;
+    *norder = g->n_src_deg;
+  } else if (o.order == TKC_ORDER_LEARNED && o.seed_factor == 0) {
+    TKC_RC(ensure_learned_order(g));
+    *order = g->learned_order;
+    *norder = g->n_src_learned;
+  } else if (o.order == TKC_ORDER_LEARNED) {
+    // the model only picks the seeding prefix; the rest keeps the degree order
+    TKC_RC(ensure_seeded_order(g, (u32)std::min<u64>((u64)o.seed_factor * kk, 0xffffffffull)));
+    *order = g->seeded_order;
     *norder = g->n_src_deg;
   } else {
     return TKC_EINVAL;
@@ -641,13 +654,14 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   RunSetup rs;
   memset(&rs, 0, sizeof(rs));
   const tkc_options &o = ctx->opt;
-  TKC_RC(source_order_of(g, o, &rs.order, &rs.norder));
+  TKC_RC(source_order_of(g, o, kk, &rs.order, &rs.norder));
   TKC_TRY(cudaEventRecord(ctx->ev[1], st));
   u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g->n);
   rs.g = g;
   rs.B = bits;
   rs.W = words_for(bits);
   rs.nocut = 0;
+  rs.nocut_prefix = (u32)std::min<u64>((u64)o.seed_factor * kk, 0xffffffffull);
   rs.kk = kk;
   rs.ng = 1;
   r.batch_bits = bits;

@@ -564,7 +564,7 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
     if (!cont[t]) continue;
     Slot sl = p.slots[s];
     Thresh x = thresh_of(p, sl.graph);
-    if (!p.nocut && x.have && cut_exceeds(sl.S, sl.d, sl.nd, sl.g, sl.alpha, sl.omega, x.S, x.r)) {
+    if (!p.nocut && !sl.nocut && x.have && cut_exceeds(sl.S, sl.d, sl.nd, sl.g, sl.alpha, sl.omega, x.S, x.r)) {
       sl.state = 2;
       ++cuts;
       graph_count(p, sl.graph, 2, 1);
@@ -661,7 +661,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     uint32_t gv = (valid && p.gid) ? p.gid[v] : 0;
     // level 0: S_0 = 0, n_0 = 1, gamma_1 = out-degree
     bool cut = false;
-    if (valid && !p.nocut) {
+    if (valid && !p.nocut && idx >= p.nocut_prefix) {
       Thresh x = thresh_of(p, gv);
       cut = x.have && cut_exceeds(0, 0, 1, od, a, o, x.S, x.r);
     }
@@ -702,6 +702,8 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       sl.omega = o;
       sl.state = 1;
       sl.graph = gv;
+      sl.nocut = (cursor + threadIdx.x) < p.nocut_prefix;
+      sl.pad[0] = sl.pad[1] = sl.pad[2] = 0;
       p.slots[s] = sl;
       graph_count(p, gv, 1, 1);
       graph_count(p, gv, 0, od);

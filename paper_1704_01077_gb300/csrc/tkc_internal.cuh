@@ -86,6 +86,8 @@ struct Slot {
   unsigned int alpha, omega;
   int state;              // 0 free, 1 active, 2 done (waiting for the clear step)
   unsigned int graph;     // graph of the source (several graphs in one run)
+  unsigned int nocut;     // 1: searched to the end (threshold seeding)
+  unsigned int pad[3];
 };
 
 struct RunParams {
@@ -107,6 +109,7 @@ struct RunParams {
   uint32_t kk;        // min(k, n); 0 never reaches the kernel
   uint32_t B;         // active slots per batch (1..64*W)
   int nocut;          // 1: never cut (exact S, r for every source)
+  uint32_t nocut_prefix;  // sources at order positions below this are never cut
   uint32_t bu_num, bu_den;
   uint64_t timeout;
   // workspace
@@ -156,8 +159,22 @@ struct Workspace {
 
 }  // namespace tkc
 
+// Source-order model: 5 -> 64 -> 64 -> 1 MLP, fp32 master weights with a
+// bf16 copy for the forward passes, Adam moments.
+struct MlpState {
+  float *w = nullptr;             // TKC_MLP_PARAMS fp32 master weights
+  unsigned short *wb = nullptr;   // bf16 copy used by the forward passes
+  float *m = nullptr, *v = nullptr;  // Adam moments
+  float *grad = nullptr;          // gradient scratch
+  float *loss = nullptr;          // loss accumulator
+  uint64_t step = 0;
+  uint64_t version = 0;           // bumped whenever the weights change
+  bool ready = false;
+};
+
 struct tkc_ctx {
   int device = 0;
+  MlpState mlp;
   cudaStream_t stream = nullptr;
   tkc_options opt{};
   int num_sms = 0;
@@ -178,8 +195,15 @@ struct tkc_graph {
   uint32_t *given_order = nullptr;            // filtered caller order
   uint32_t n_src_given = 0;
   uint32_t *alpha = nullptr, *omega = nullptr;
+  uint32_t *scc_size = nullptr;               // size of the SCC (component, if undirected) of each vertex
   bool have_order = false, have_reach = false;
-  double ms_pre_last = 0.0;
+  float *features = nullptr;                  // standardized vertex features, n x TKC_MLP_FEATURES
+  uint32_t *learned_order = nullptr;          // filtered order by predicted farness
+  uint32_t n_src_learned = 0;
+  uint64_t learned_version = 0;               // model version the learned order was computed with
+  uint32_t *seeded_order = nullptr;           // predicted-closest prefix, then the degree order
+  uint64_t seeded_version = 0;
+  uint32_t seeded_prefix = 0;
 };
 
 namespace tkc {
@@ -189,6 +213,11 @@ int build_in_csr(tkc_graph *g);
 int ensure_degree_order(tkc_graph *g);
 int ensure_reach_bounds(tkc_graph *g);
 int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
+// tkc_mlp.cu
+int ensure_features(tkc_graph *g);
+int ensure_learned_order(tkc_graph *g);
+int ensure_seeded_order(tkc_graph *g, uint32_t prefix);
+void free_mlp(tkc_ctx *ctx);
 // tkc_bfscut.cu
 int ensure_workspace(tkc_ctx *ctx, uint32_t n, int words, uint32_t top_entries, uint32_t ng);
 int run_bfscut(tkc_ctx *ctx, const RunParams &p, int words, int blocks);

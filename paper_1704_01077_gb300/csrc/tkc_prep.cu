@@ -457,11 +457,12 @@ __global__ void k_cc_size(const u32 *parent, u32 n, u32 *size) {
     atomicAdd(&size[parent[v]], 1u);
 }
 
-__global__ void k_cc_out(const u32 *parent, const u32 *size, u32 n, u32 *alpha, u32 *omega) {
+__global__ void k_cc_out(const u32 *parent, const u32 *size, u32 n, u32 *alpha, u32 *omega, u32 *scc_size) {
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     u32 s = size[parent[v]];
     alpha[v] = s;
     omega[v] = s;
+    scc_size[v] = s;
   }
 }
 
@@ -486,7 +487,7 @@ static int reach_undirected(tkc_graph *g) {
   }
   TKC_TRY(cudaMemsetAsync(size, 0, (size_t)n * sizeof(u32), st));
   TKC_LAUNCH(k_cc_size<<<grid_for(n, 256), 256, 0, st>>>(parent, n, size));
-  TKC_LAUNCH(k_cc_out<<<grid_for(n, 256), 256, 0, st>>>(parent, size, n, g->alpha, g->omega));
+  TKC_LAUNCH(k_cc_out<<<grid_for(n, 256), 256, 0, st>>>(parent, size, n, g->alpha, g->omega, g->scc_size));
   TKC_TRY(cudaGetLastError());
   TKC_TRY(cudaFreeAsync(parent, st));
   TKC_TRY(cudaFreeAsync(size, st));
@@ -508,6 +509,7 @@ int ensure_reach_bounds(tkc_graph *g) {
   }
   if (!g->alpha) TKC_TRY(cudaMallocAsync(&g->alpha, (size_t)g->n * sizeof(u32), st));
   if (!g->omega) TKC_TRY(cudaMallocAsync(&g->omega, (size_t)g->n * sizeof(u32), st));
+  if (!g->scc_size) TKC_TRY(cudaMallocAsync(&g->scc_size, (size_t)g->n * sizeof(u32), st));
   TKC_RC(g->directed ? reach_directed_gpu(g) : reach_undirected(g));
   g->have_reach = true;
   return TKC_OK;

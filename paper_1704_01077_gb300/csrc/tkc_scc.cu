@@ -358,11 +358,13 @@ __global__ void k_dp_round(const u32 *list, u32 cnt, const u32 *soff, const u32 
   }
 }
 
-__global__ void k_write_bounds(const u32 *comp, u32 n, const u64 *A, const u64 *O, u32 *alpha, u32 *omega) {
+__global__ void k_write_bounds(const u32 *comp, u32 n, const u64 *A, const u64 *O, const u32 *wgt, u32 *alpha,
+                               u32 *omega, u32 *scc_size) {
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     u32 c = comp[v];
     alpha[v] = (u32)A[c];
     omega[v] = (u32)(O[c] < n ? O[c] : n);
+    scc_size[v] = wgt[c];
   }
 }
 
@@ -537,7 +539,7 @@ int reach_directed_gpu(tkc_graph *g) {
     TKC_RC(rc);
     std::swap(cur_list, nxt_list);
   }
-  TKC_LAUNCH(k_write_bounds<<<grid_of(n), 256, 0, st>>>(comp, n, A, O, g->alpha, g->omega));
+  TKC_LAUNCH(k_write_bounds<<<grid_of(n), 256, 0, st>>>(comp, n, A, O, wgt, g->alpha, g->omega, g->scc_size));
   TKC_TRY(cudaGetLastError());
   TKC_TRY(cudaStreamSynchronize(st));
   return TKC_OK;

@@ -33,6 +33,9 @@ TKC_ORDER_GIVEN = 1
 TKC_ORDER_LEARNED = 2
 TKC_MAX_K = 1024
 TKC_NOALLOC_MAX_N = 65536
+TKC_MLP_FEATURES = 5
+TKC_MLP_HIDDEN = 64
+TKC_MLP_PARAMS = 4609
 
 
 class TkcError(RuntimeError):
@@ -63,7 +66,8 @@ class tkc_result(ctypes.Structure):
 EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc_free_graph",
             "tkc_topk_closeness", "tkc_topk_closeness_multi", "tkc_source_order", "tkc_set_source_order",
             "tkc_reach_bounds", "tkc_distance_sums", "tkc_distance_sums_noalloc", "tkc_kernel_launches",
-            "tkc_strerror"]
+            "tkc_strerror", "tkc_vertex_features", "tkc_mlp_init", "tkc_set_source_model", "tkc_get_source_model",
+            "tkc_mlp_forward", "tkc_mlp_gradient", "tkc_mlp_train_step"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -90,6 +94,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tkc_distance_sums.argtypes = [vp, ctypes.c_uint32, u32p, u64p, u32p]
     lib.tkc_distance_sums_noalloc.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, vp, vp, vp,
                                               vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.tkc_vertex_features.argtypes = [vp, vp]
+    lib.tkc_mlp_init.argtypes = [vp, ctypes.c_uint64]
+    lib.tkc_set_source_model.argtypes = [vp, fp, ctypes.c_uint32]
+    lib.tkc_get_source_model.argtypes = [vp, fp, ctypes.c_uint32]
+    lib.tkc_mlp_forward.argtypes = [vp, vp, ctypes.c_uint32, vp]
+    lib.tkc_mlp_gradient.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, fp]
+    lib.tkc_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_float, fp]
     lib.tkc_kernel_launches.argtypes = []
     lib.tkc_kernel_launches.restype = ctypes.c_uint64
     lib.tkc_strerror.argtypes = [ctypes.c_int]
@@ -304,6 +316,56 @@ def tkc_distance_sums_noalloc(offsets, cols, n: int, sources, S, r, stream=None)
                                         ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(r.data_ptr()),
                                         ctypes.c_void_p(stream))
     _check(rc, "tkc_distance_sums_noalloc")
+
+
+def _dev(t):
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def tkc_vertex_features(g, n: int, device: int = 0):
+    """Standardized vertex features as a float32 CUDA tensor of shape (n, 5)."""
+    import torch
+
+    x = torch.empty((max(n, 1), TKC_MLP_FEATURES), dtype=torch.float32, device=f"cuda:{device}")
+    _check(_lib.tkc_vertex_features(g, _dev(x)), "tkc_vertex_features")
+    return x[:n]
+
+
+def tkc_mlp_init(ctx, seed: int) -> None:
+    _check(_lib.tkc_mlp_init(ctx, seed), "tkc_mlp_init")
+
+
+def tkc_set_source_model(ctx, params) -> None:
+    w = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_lib.tkc_set_source_model(ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size),
+           "tkc_set_source_model")
+
+
+def tkc_get_source_model(ctx) -> np.ndarray:
+    w = np.zeros(TKC_MLP_PARAMS, np.float32)
+    _check(_lib.tkc_get_source_model(ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size),
+           "tkc_get_source_model")
+    return w
+
+
+def tkc_mlp_forward(ctx, x, y) -> None:
+    _check(_lib.tkc_mlp_forward(ctx, _dev(x), x.shape[0], _dev(y)), "tkc_mlp_forward")
+
+
+def tkc_mlp_gradient(ctx, x, t, grad) -> float:
+    loss = ctypes.c_float()
+    _check(_lib.tkc_mlp_gradient(ctx, _dev(x), _dev(t), x.shape[0], _dev(grad), ctypes.byref(loss)),
+           "tkc_mlp_gradient")
+    return loss.value
+
+
+def tkc_mlp_train_step(ctx, x, t, lr: float) -> float:
+    loss = ctypes.c_float()
+    _check(_lib.tkc_mlp_train_step(ctx, _dev(x), _dev(t), x.shape[0], lr, ctypes.byref(loss)),
+           "tkc_mlp_train_step")
+    return loss.value
 
 
 class Graph:

@@ -1,0 +1,117 @@
+"""Learned source order on the GPU: the MLP kernels against the float64
+oracle (oracle/mlp.py), vertex features against oracle/features.py, and the
+learned order's top-k against the textbook oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import features as ofeat
+from oracle import mlp as omlp
+from paper_1704_01077_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(gpu_lib):
+    c = gpu_lib.tkc_create(gpu_lib.Options())
+    yield c
+    gpu_lib.tkc_destroy(c)
+
+
+def _rand_params(seed):
+    rng = np.random.default_rng(seed)
+    return (rng.normal(0, 0.25, omlp.P)).astype(np.float32)
+
+
+def test_forward_and_gradient_match_oracle(gpu_lib, ctx):
+    import torch
+
+    t = gpu_lib
+    for seed, m in ((1, 1000), (2, 64), (3, 5), (4, 4099)):
+        p = _rand_params(seed)
+        t.tkc_set_source_model(ctx, p)
+        pb = omlp.bf16_round(p)
+        rng = np.random.default_rng(10 + seed)
+        x = rng.normal(size=(m, omlp.F)).astype(np.float32)
+        tg = rng.normal(size=m).astype(np.float32)
+        xd = torch.from_numpy(x).cuda()
+        td = torch.from_numpy(tg).cuda()
+        y = torch.empty(m, dtype=torch.float32, device="cuda")
+        t.tkc_mlp_forward(ctx, xd, y)
+        y_ref = omlp.forward(pb, x.astype(np.float64))
+        # fp32 accumulation over 64-term dot products of O(1) values
+        assert np.allclose(y.cpu().numpy(), y_ref, rtol=1e-4, atol=1e-4 * np.abs(y_ref).max())
+        g = torch.empty(omlp.P, dtype=torch.float32, device="cuda")
+        loss = t.tkc_mlp_gradient(ctx, xd, td, g)
+        g_ref = omlp.gradient(pb, x.astype(np.float64), tg.astype(np.float64))
+        scale = np.abs(g_ref).max()
+        assert np.allclose(g.cpu().numpy(), g_ref, rtol=1e-3, atol=2e-5 * scale), seed
+        assert abs(loss - omlp.loss(pb, x.astype(np.float64), tg)) <= 1e-4 * max(1.0, loss)
+
+
+def test_training_reduces_loss(gpu_lib, ctx):
+    import torch
+
+    t = gpu_lib
+    t.tkc_mlp_init(ctx, 7)
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(8192, omlp.F)).astype(np.float32)
+    target = (np.sin(x[:, 0]) + 0.5 * x[:, 1] * x[:, 2] - np.abs(x[:, 3])).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    td = torch.from_numpy(target).cuda()
+    first = None
+    for step in range(400):
+        i = (step * 512) % 8192
+        loss = t.tkc_mlp_train_step(ctx, xd[i:i + 512].contiguous(), td[i:i + 512].contiguous(), 3e-3)
+        first = loss if first is None else first
+    g = torch.empty(omlp.P, dtype=torch.float32, device="cuda")
+    final = t.tkc_mlp_gradient(ctx, xd, td, g)
+    assert final < 0.3 * first, (first, final)
+    w = t.tkc_get_source_model(ctx)
+    assert np.isfinite(w).all()
+
+
+@pytest.mark.parametrize("make", [lambda: gg.rmat(9, 8, seed=3), lambda: gg.barabasi_albert(400, 3, 4),
+                                  lambda: gg.random_graph(150, 0.02, 5, True)])
+def test_features_match_oracle(gpu_lib, ctx, make):
+    g = make()
+    h = gpu_lib.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+    try:
+        x = gpu_lib.tkc_vertex_features(h, g.n).cpu().numpy()
+    finally:
+        gpu_lib.tkc_free_graph(h)
+    ref = ofeat.features(g)
+    assert np.allclose(x, ref, rtol=1e-4, atol=1e-4), np.abs(x - ref).max()
+
+
+def test_learned_order_gives_exact_topk(gpu_lib, ctx):
+    import torch
+
+    t = gpu_lib
+    t.tkc_mlp_init(ctx, 11)
+    for g in (gg.rmat(12, 16, seed=8), gg.barabasi_albert(3000, 4, 9), gg.random_graph(300, 0.01, 3, True)):
+        ref = oracle.textbook_topk(g, 10)
+        h = t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+        try:
+            for bits, seed_factor in ((64, 0), (256, 0), (256, 5), (1, 2)):
+                t.tkc_set_options(ctx, t.Options(batch_bits=bits, order=t.TKC_ORDER_LEARNED,
+                                                 seed_factor=seed_factor))
+                res = t.tkc_topk_closeness(h, 10)
+                assert list(res.ids) == list(ref.ids) and np.array_equal(res.dist_sum, ref.S)
+                assert res.n_tied_at_kth == ref.n_tied
+            # the learned order is the stable sort of all vertices by the model's
+            # prediction: given that order explicitly, the run does the same work
+            x = t.tkc_vertex_features(h, g.n)
+            y = torch.empty(g.n, dtype=torch.float32, device="cuda")
+            t.tkc_mlp_forward(ctx, x.contiguous(), y)
+            order = np.argsort(y.cpu().numpy(), kind="stable").astype(np.uint32)
+            t.tkc_set_source_order(h, order)
+            for bits in (64, 1):
+                t.tkc_set_options(ctx, t.Options(batch_bits=bits, order=t.TKC_ORDER_LEARNED))
+                a = t.tkc_topk_closeness(h, 10)
+                t.tkc_set_options(ctx, t.Options(batch_bits=bits, order=t.TKC_ORDER_GIVEN))
+                b = t.tkc_topk_closeness(h, 10)
+                assert (a.edges_visited, a.bfs_cut, a.levels) == (b.edges_visited, b.bfs_cut, b.levels)
+        finally:
+            t.tkc_free_graph(h)
