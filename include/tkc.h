@@ -69,6 +69,9 @@ typedef struct {
   uint32_t seed_factor;    /* the first seed_factor * k sources of the order are searched to the end
                               without cutting, so x starts from exact farness values (0 = none) */
   uint64_t timeout_cycles; /* budget of every device-side wait, in SM clock cycles (0 = default 2^34) */
+  uint32_t teams;          /* independent groups of SMs, each running its own source batches and sharing
+                              the threshold and the k-lists (0 = library default; plain mode uses 1) */
+  uint32_t pad;
 } tkc_options;
 
 typedef struct {

@@ -41,16 +41,21 @@ static int dalloc(T **p, size_t count, cudaStream_t st) {
   return TKC_OK;
 }
 
-int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 top_entries, u32 ng) {
+int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 top_entries, u32 ng, u32 teams) {
   Workspace &w = ctx->ws;
   cudaStream_t st = ctx->stream;
-  if (!w.ctl) {
-    TKC_RC(dalloc(&w.ctl, 1, st));
-    TKC_RC(dalloc(&w.slots, 64 * kMaxWords, st));
-    TKC_RC(dalloc(&w.cnt, 64 * kMaxWords, st));
-    TKC_RC(dalloc(&w.wsum, 64 * kMaxWords, st));
-    TKC_TRY(cudaMemsetAsync(w.cnt, 0, 64 * kMaxWords * sizeof(unsigned), st));
-    TKC_TRY(cudaMemsetAsync(w.wsum, 0, 64 * kMaxWords * sizeof(u64), st));
+  if (!w.sh) {
+    TKC_RC(dalloc(&w.sh, 1, st));
+  }
+  if (teams > w.teams_cap) {
+    TKC_RC(dalloc(&w.ctl, teams, st));
+    TKC_RC(dalloc(&w.slots, (size_t)teams * 64 * kMaxWords, st));
+    TKC_RC(dalloc(&w.cnt, (size_t)teams * 64 * kMaxWords, st));
+    TKC_RC(dalloc(&w.wsum, (size_t)teams * 64 * kMaxWords, st));
+    TKC_TRY(cudaMemsetAsync(w.cnt, 0, (size_t)teams * 64 * kMaxWords * sizeof(unsigned), st));
+    TKC_TRY(cudaMemsetAsync(w.wsum, 0, (size_t)teams * 64 * kMaxWords * sizeof(u64), st));
+    w.teams_cap = teams;
+    w.n_cap = 0;  // per-team vertex buffers are reallocated for the new team count
   }
   if (top_entries > w.top_cap) {
     u32 cap = std::max<u32>(top_entries, TKC_MAX_K);
@@ -69,29 +74,35 @@ int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 top_entries, u32 ng) {
     TKC_RC(dalloc(&w.tied, cap, st));
     TKC_RC(dalloc(&w.g_ntop, cap, st));
     TKC_RC(dalloc(&w.g_ctr, 4 * (size_t)cap, st));
+    TKC_RC(dalloc(&w.x_seq, cap, st));
+    TKC_RC(dalloc(&w.x_S, cap, st));
+    TKC_RC(dalloc(&w.x_r, cap, st));
+    TKC_RC(dalloc(&w.x_id, cap, st));
     w.ng_cap = cap;
   }
+  const u32 T = w.teams_cap;
   if (n > w.n_cap) {
     u32 cap = std::max<u32>(n, 1024);
-    TKC_RC(dalloc(&w.L0, cap, st));
-    TKC_RC(dalloc(&w.L1, cap, st));
-    TKC_RC(dalloc(&w.Loff0, cap, st));
-    TKC_RC(dalloc(&w.Loff1, cap, st));
-    TKC_RC(dalloc(&w.VL, cap, st));
-    TKC_RC(dalloc(&w.stamp, cap, st));
+    size_t tv = (size_t)T * cap, tfb = (size_t)T * (cap / 32 + 1);
+    TKC_RC(dalloc(&w.L0, tv, st));
+    TKC_RC(dalloc(&w.L1, tv, st));
+    TKC_RC(dalloc(&w.Loff0, tv, st));
+    TKC_RC(dalloc(&w.Loff1, tv, st));
+    TKC_RC(dalloc(&w.VL, tv, st));
+    TKC_RC(dalloc(&w.stamp, tv, st));
     TKC_RC(dalloc(&w.res_S, cap, st));
     TKC_RC(dalloc(&w.res_r, cap, st));
-    TKC_RC(dalloc(&w.FB0, cap / 32 + 1, st));
-    TKC_RC(dalloc(&w.FB1, cap / 32 + 1, st));
-    TKC_TRY(cudaMemsetAsync(w.FB0, 0, ((size_t)cap / 32 + 1) * sizeof(u32), st));
-    TKC_TRY(cudaMemsetAsync(w.FB1, 0, ((size_t)cap / 32 + 1) * sizeof(u32), st));
-    TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, (size_t)cap * sizeof(u32), st));
+    TKC_RC(dalloc(&w.FB0, tfb, st));
+    TKC_RC(dalloc(&w.FB1, tfb, st));
+    TKC_TRY(cudaMemsetAsync(w.FB0, 0, tfb * sizeof(u32), st));
+    TKC_TRY(cudaMemsetAsync(w.FB1, 0, tfb * sizeof(u32), st));
+    TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, tv * sizeof(u32), st));
     w.level_base = 0;
     w.n_cap = cap;
     w.words_cap = 0;  // rows must be reallocated for the new n
   }
   if (words > w.words_cap) {
-    size_t rows = (size_t)w.n_cap * words;
+    size_t rows = (size_t)T * w.n_cap * words;
     TKC_RC(dalloc(&w.seen, rows, st));
     TKC_RC(dalloc(&w.F0, rows, st));
     TKC_RC(dalloc(&w.F1, rows, st));
@@ -109,7 +120,7 @@ static void free_workspace(tkc_ctx *ctx) {
   Workspace &w = ctx->ws;
   void *ptrs[] = {w.seen, w.F0, w.F1, w.N, w.FB0, w.FB1, w.L0, w.L1, w.Loff0, w.Loff1, w.VL, w.stamp, w.res_S, w.res_r,
                   w.slots, w.cnt, w.wsum, w.top_S, w.top_r, w.top_id, w.ctl, w.out_S, w.out_r, w.out_id,
-                  w.out_f, w.out_c, w.tied, w.g_ntop, w.g_ctr};
+                  w.out_f, w.out_c, w.tied, w.g_ntop, w.g_ctr, w.sh, w.x_seq, w.x_S, w.x_r, w.x_id};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -119,16 +130,17 @@ static void free_workspace(tkc_ctx *ctx) {
 // when it ends normally.  After an error they are cleared here.
 static int reset_rows(tkc_ctx *ctx) {
   Workspace &w = ctx->ws;
-  size_t rows = (size_t)w.n_cap * w.words_cap;
+  const size_t T = w.teams_cap;
+  size_t rows = T * w.n_cap * w.words_cap;
   cudaStream_t st = ctx->stream;
   TKC_TRY(cudaMemsetAsync(w.seen, 0, rows * sizeof(u64), st));
   TKC_TRY(cudaMemsetAsync(w.F0, 0, rows * sizeof(u64), st));
   TKC_TRY(cudaMemsetAsync(w.F1, 0, rows * sizeof(u64), st));
   TKC_TRY(cudaMemsetAsync(w.N, 0, rows * sizeof(u64), st));
-  TKC_TRY(cudaMemsetAsync(w.FB0, 0, ((size_t)w.n_cap / 32 + 1) * sizeof(u32), st));
-  TKC_TRY(cudaMemsetAsync(w.FB1, 0, ((size_t)w.n_cap / 32 + 1) * sizeof(u32), st));
-  TKC_TRY(cudaMemsetAsync(w.cnt, 0, 64 * kMaxWords * sizeof(unsigned), st));
-  TKC_TRY(cudaMemsetAsync(w.wsum, 0, 64 * kMaxWords * sizeof(u64), st));
+  TKC_TRY(cudaMemsetAsync(w.FB0, 0, T * ((size_t)w.n_cap / 32 + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(w.FB1, 0, T * ((size_t)w.n_cap / 32 + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(w.cnt, 0, T * 64 * kMaxWords * sizeof(unsigned), st));
+  TKC_TRY(cudaMemsetAsync(w.wsum, 0, T * 64 * kMaxWords * sizeof(u64), st));
   return TKC_OK;
 }
 
@@ -208,7 +220,7 @@ static int words_for(u32 bits) {
 // Batch width used when the options leave it to the library.
 static u32 default_batch_bits(u32 n) {
   if (n < 4096) return 64;
-  return 256;
+  return 128;
 }
 
 // One run of the persistent kernel: a graph, or the union of several.
@@ -226,24 +238,44 @@ struct RunSetup {
   const uint8_t *g_directed;
 };
 
+// Teams used when the options leave it to the library: one team for small
+// graphs (a level is short and the whole GPU serves it), more for large ones
+// so that the latency of one team's level steps overlaps with the others.
+static u32 default_teams(u32 n, u32 B) {
+  if (B <= 1) return 1;
+  if (n < (1u << 14)) return 1;
+  if (n < (1u << 18)) return 4;
+  return 8;
+}
+
 static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   const tkc_graph *g = rs.g;
   Workspace &w = ctx->ws;
   cudaStream_t st = ctx->stream;
-  TKC_RC(ensure_workspace(ctx, g->n, rs.W, rs.kk * rs.ng, rs.ng));
+  const tkc_options &o = ctx->opt;
+  int maxb = max_coresident_blocks(ctx, rs.W);
+  if (maxb <= 0) return TKC_ECUDA;
+  u32 T = rs.B <= 1 ? 1u : (o.teams ? o.teams : default_teams(g->n, rs.B));
+  T = std::max<u32>(1, std::min<u32>(T, (u32)maxb));
+  TKC_RC(ensure_workspace(ctx, g->n, rs.W, rs.kk * rs.ng, rs.ng, T));
   if (w.level_base > 0xF0000000u) {
-    TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, (size_t)w.n_cap * sizeof(u32), st));
+    TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, (size_t)w.teams_cap * w.n_cap * sizeof(u32), st));
     w.level_base = 0;
   }
-  Ctl c;
-  memset(&c, 0, sizeof(c));
-  c.step = 1;  // start with an (empty) clear step whose epilogue seeds the first batch
-  c.level_id = w.level_base;
-  TKC_TRY(cudaMemcpyAsync(w.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  std::vector<Ctl> cs(T);
+  for (u32 t = 0; t < T; ++t) {
+    memset(&cs[t], 0, sizeof(Ctl));
+    cs[t].step = 1;  // start with an (empty) clear step whose epilogue seeds the first batch
+    cs[t].level_id = w.level_base;
+  }
+  TKC_TRY(cudaMemcpyAsync(w.ctl, cs.data(), T * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  TKC_TRY(cudaMemsetAsync(w.sh, 0, sizeof(Shared), st));
   TKC_TRY(cudaMemsetAsync(w.res_r, 0, (size_t)g->n * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(w.res_S, 0, (size_t)g->n * sizeof(u64), st));
   TKC_TRY(cudaMemsetAsync(w.g_ntop, 0, (size_t)rs.ng * sizeof(unsigned), st));
   TKC_TRY(cudaMemsetAsync(w.g_ctr, 0, (size_t)rs.ng * 4 * sizeof(u64), st));
+  TKC_TRY(cudaMemsetAsync(w.x_seq, 0, (size_t)rs.ng * sizeof(unsigned), st));
+  TKC_TRY(cudaMemsetAsync(w.x_r, 0, (size_t)rs.ng * sizeof(u32), st));
   RunParams p;
   memset(&p, 0, sizeof(p));
   p.n = g->n;
@@ -266,7 +298,15 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.B = rs.B;
   p.nocut = rs.nocut;
   p.nocut_prefix = rs.nocut_prefix;
-  const tkc_options &o = ctx->opt;
+  p.teams = T;
+  p.row_stride = (u64)w.n_cap * w.words_cap;
+  p.vtx_stride = w.n_cap;
+  p.fb_stride = w.n_cap / 32 + 1;
+  p.sh = w.sh;
+  p.x_seq = w.x_seq;
+  p.x_S = w.x_S;
+  p.x_r = w.x_r;
+  p.x_id = w.x_id;
   // default: a level runs bottom-up when its frontier's arcs exceed 1/8 of all arcs
   p.bu_num = o.bu_num ? o.bu_num : 8;
   p.bu_den = o.bu_num ? std::max<u32>(o.bu_den, 1) : 1;
@@ -292,10 +332,9 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.res_S = w.res_S;
   p.res_r = w.res_r;
   p.ctl = w.ctl;
-  int maxb = max_coresident_blocks(ctx, rs.W);
-  if (maxb <= 0) return TKC_ECUDA;
   int blocks = o.blocks ? (int)o.blocks : (int)std::max<u64>(8, ((u64)g->n + 511) / 512);
   blocks = std::min(blocks, maxb);
+  blocks = std::max<int>(T, blocks / (int)T * (int)T);  // a multiple of the team count
   // optional per-step trace for profiling: TKC_TRACE=<csv path>
   const char *trace_path = getenv("TKC_TRACE");
   const uint32_t trace_cap = 1u << 20;
@@ -307,24 +346,45 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   TKC_TRY(cudaEventRecord(ctx->ev[4], st));
   TKC_RC(run_bfscut(ctx, p, rs.W, blocks));
   TKC_TRY(cudaEventRecord(ctx->ev[5], st));
-  TKC_TRY(cudaMemcpyAsync(hctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaMemcpyAsync(cs.data(), w.ctl, T * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  Shared hsh;
+  TKC_TRY(cudaMemcpyAsync(&hsh, w.sh, sizeof(Shared), cudaMemcpyDeviceToHost, st));
   TKC_TRY(cudaStreamSynchronize(st));
+  // the teams' counters add up; levels and batches too (they ran side by side)
+  *hctl = cs[0];
+  for (u32 t = 1; t < T; ++t) {
+    const Ctl &x = cs[t];
+    hctl->edges_visited += x.edges_visited;
+    hctl->edges_scanned += x.edges_scanned;
+    hctl->bfs_started += x.bfs_started;
+    hctl->bfs_cut += x.bfs_cut;
+    hctl->bfs_finished += x.bfs_finished;
+    hctl->levels += x.levels;
+    hctl->batches += x.batches;
+    hctl->alg_bytes += x.alg_bytes;
+    hctl->trace_n += x.trace_n;
+    hctl->level_id = std::max(hctl->level_id, x.level_id);
+    if (!hctl->err) hctl->err = x.err;
+  }
+  if (!hctl->err) hctl->err = hsh.err;
   w.level_base = hctl->level_id + 1;
   if (p.trace) {
-    u64 cnt = std::min<u64>(hctl->trace_n, trace_cap);
-    std::vector<u64> tr(cnt * 16);
-    if (cnt) TKC_TRY(cudaMemcpy(tr.data(), p.trace, cnt * 16 * sizeof(u64), cudaMemcpyDeviceToHost));
+    std::vector<u64> tr((size_t)trace_cap * 16);
+    TKC_TRY(cudaMemcpy(tr.data(), p.trace, tr.size() * sizeof(u64), cudaMemcpyDeviceToHost));
     TKC_TRY(cudaFree(p.trace));
     FILE *f = fopen(trace_path, "a");
     if (f) {
-      fprintf(f, "# n=%u arcs=%llu B=%u blocks=%d graphs=%u\n", g->n, (unsigned long long)g->arcs, rs.B, blocks,
-              rs.ng);
-      fprintf(f, "t_ns,kind,a,b,c,d,e,f,t_top,t_a_end,t_a_sync,t_b_end,t_flush,t_epi,x,y\n");
-      for (u64 i = 0; i < cnt; ++i) {
-        const u64 *r = &tr[i * 16];
-        for (int j = 0; j < 16; ++j) fprintf(f, j ? ",%llu" : "%llu", r[j]);
-        fprintf(f, "\n");
-      }
+      fprintf(f, "# n=%u arcs=%llu B=%u blocks=%d graphs=%u teams=%u\n", g->n, (unsigned long long)g->arcs, rs.B,
+              blocks, rs.ng, T);
+      fprintf(f, "t_ns,kind,a,b,c,d,e,f,t_top,t_a_end,t_a_sync,t_b_end,t_flush,t_epi,team,y\n");
+      const u64 per = trace_cap / T;
+      for (u32 t = 0; t < T; ++t)
+        for (u64 i = 0; i < std::min<u64>(cs[t].trace_n, per); ++i) {
+          u64 *r = &tr[((size_t)t * per + i) * 16];
+          r[14] = t;
+          for (int j = 0; j < 16; ++j) fprintf(f, j ? ",%llu" : "%llu", r[j]);
+          fprintf(f, "\n");
+        }
       fclose(f);
     }
   }

@@ -48,11 +48,12 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
 }
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(volatile const int *)p; }
 
-// Grid barrier for a cooperative launch.  The last block to arrive runs
-// `epi` (whole block) before releasing the others.  Returns false when the
-// run must stop (error recorded by any block, including a timed-out wait).
+// Barrier over the `nblocks` blocks of one team (all co-resident: the launch
+// is cooperative).  The last block to arrive runs `epi` (whole block) before
+// releasing the others.  Returns false when the run must stop: an error
+// recorded by this team or any other, including a timed-out wait.
 template <typename Epi>
-__device__ __forceinline__ bool grid_sync(Ctl *ctl, uint64_t timeout, Epi epi) {
+__device__ __forceinline__ bool team_sync(Ctl *ctl, Shared *sh, unsigned nblocks, uint64_t timeout, Epi epi) {
   __shared__ int s_last;
   __shared__ unsigned s_gen;
   __syncthreads();
@@ -61,7 +62,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, uint64_t timeout, Epi epi) {
     s_gen = gen;
     __threadfence();
     unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
-    s_last = (arrived == gridDim.x);
+    s_last = (arrived == nblocks);
   }
   __syncthreads();
   if (s_last) {
@@ -77,9 +78,10 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, uint64_t timeout, Epi epi) {
     long long t0 = clock64();
     unsigned ns = 32;
     while (ld_acquire_u32(&ctl->bar_gen) == s_gen) {
-      if (ld_volatile_i32(&ctl->err) != 0) break;
+      if (ld_volatile_i32(&ctl->err) != 0 || ld_volatile_i32(&sh->err) != 0) break;
       if ((uint64_t)(clock64() - t0) > timeout) {
         atomicCAS(&ctl->err, 0, TKC_ETIMEOUT);
+        atomicCAS(&sh->err, 0, TKC_ETIMEOUT);
         atomicCAS(&ctl->err_where, 0, 1);
         break;
       }
@@ -89,7 +91,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, uint64_t timeout, Epi epi) {
     __threadfence();
   }
   __syncthreads();
-  return ld_volatile_i32(&ctl->err) == 0;
+  return ld_volatile_i32(&ctl->err) == 0 && ld_volatile_i32(&sh->err) == 0;
 }
 
 // ------------------------------------------------------------------ exact arithmetic
@@ -367,6 +369,85 @@ __device__ u64 block_exscan64(Smem<W> &sm, u64 x, u64 *total) {
 
 // ------------------------------------------------------------------ epilogues
 
+// The k-th entry of graph g's list as last published (seqlock: the writer
+// makes the sequence odd, writes, makes it even).  A read that keeps seeing
+// a write in progress reports no threshold, which only means no cut.
+struct Thresh {
+  bool have;
+  u64 S;
+  uint32_t r, id;
+};
+
+__device__ __forceinline__ Thresh thresh_of(const RunParams &p, uint32_t g) {
+  Thresh t;
+  t.have = false;
+  t.S = 0;
+  t.r = t.id = 0;
+  for (int tries = 0; tries < 64; ++tries) {
+    unsigned s1 = ld_acquire_u32(&p.x_seq[g]);
+    if (s1 & 1u) continue;
+    u64 S = *(volatile const u64 *)&p.x_S[g];
+    uint32_t r = *(volatile const uint32_t *)&p.x_r[g];
+    uint32_t id = *(volatile const uint32_t *)&p.x_id[g];
+    __threadfence();
+    unsigned s2 = *(volatile const unsigned *)&p.x_seq[g];
+    if (s1 == s2) {
+      t.have = r != 0;
+      t.S = S;
+      t.r = r;
+      t.id = id;
+      return t;
+    }
+  }
+  return t;
+}
+
+// Publishes graph g's current k-th entry (caller holds the merge lock).
+__device__ __forceinline__ void publish_thresh(const RunParams &p, uint32_t g) {
+  if (p.g_ntop[g] != p.kk) return;
+  size_t i = (size_t)g * p.kk + p.kk - 1;
+  unsigned s = p.x_seq[g];
+  *(volatile unsigned *)&p.x_seq[g] = s + 1u;
+  __threadfence();
+  *(volatile u64 *)&p.x_S[g] = p.top_S[i];
+  *(volatile uint32_t *)&p.x_id[g] = p.top_id[i];
+  *(volatile uint32_t *)&p.x_r[g] = p.top_r[i];
+  __threadfence();
+  st_release_u32(&p.x_seq[g], s + 2u);
+}
+
+// Merge lock shared by the teams; a wait beyond the budget is an error.
+__device__ __forceinline__ bool lock_lists(const RunParams &p) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    long long t0 = clock64();
+    unsigned ns = 32;
+    int ok = 1;
+    while (atomicCAS(&p.sh->lock, 0, 1) != 0) {
+      if (ld_volatile_i32(&p.sh->err) != 0 || (uint64_t)(clock64() - t0) > p.timeout) {
+        atomicCAS(&p.sh->err, 0, TKC_ETIMEOUT);
+        atomicCAS(&p.ctl->err, 0, TKC_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ void unlock_lists(const RunParams &p) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(&p.sh->lock, 0);
+  }
+}
+
 // Merges the block's candidate list (sm.cS/cr/cid, sm.ncand entries) into the
 // global top list.  Every entry's new position is its rank among the old list
 // and the candidates (keys are unique: farness then id), so each position below
@@ -449,31 +530,23 @@ __device__ void merge_topk_many(const RunParams &p, Smem<W> &sm) {
       ti[pos] = id;
     }
     p.g_ntop[g] = cnt;
+    publish_thresh(p, g);
   }
   __syncthreads();
 }
 
 template <int W>
 __device__ __forceinline__ void merge_topk(const RunParams &p, Smem<W> &sm) {
-  if (p.ng == 1) merge_topk_one(p, sm);
-  else merge_topk_many(p, sm);
-}
-
-// The current k-th entry of graph g's list, if the list is full.
-struct Thresh {
-  bool have;
-  u64 S;
-  uint32_t r, id;
-};
-
-__device__ __forceinline__ Thresh thresh_of(const RunParams &p, uint32_t g) {
-  Thresh t;
-  t.have = p.g_ntop[g] == p.kk;
-  size_t i = (size_t)g * p.kk + p.kk - 1;
-  t.S = t.have ? p.top_S[i] : 0;
-  t.r = t.have ? p.top_r[i] : 0;
-  t.id = t.have ? p.top_id[i] : 0;
-  return t;
+  if (sm.ncand == 0) return;
+  if (!lock_lists(p)) return;
+  __threadfence();
+  if (p.ng == 1) {
+    merge_topk_one(p, sm);
+    if (threadIdx.x == 0) publish_thresh(p, 0);
+  } else {
+    merge_topk_many(p, sm);
+  }
+  unlock_lists(p);
 }
 
 __device__ __forceinline__ void graph_count(const RunParams &p, uint32_t g, int which, u64 v) {
@@ -647,14 +720,24 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
   uint32_t *FBcur = c->cur ? p.FB1 : p.FB0;
   uint32_t *FL = c->cur ? p.L1 : p.L0;
   uint32_t *FLoff = c->cur ? p.Loff1 : p.Loff0;
-  uint32_t cursor = c->cursor;
-  uint32_t assigned = 0;
+  uint32_t assigned = 0, last_base = 0;
   u64 arcs_total = 0, started = 0, cut0 = 0;
+  __shared__ uint32_t s_base;
   if (threadIdx.x < W) sm.active[threadIdx.x] = 0;
   __syncthreads();
-  while (assigned < B && cursor < p.norder) {
-    uint32_t idx = cursor + threadIdx.x;
-    bool valid = idx < p.norder;
+  // take sources from the shared cursor, `room` positions at a time, so that
+  // every position taken is either abandoned at level 0 or gets a slot
+  while (assigned < B) {
+    const uint32_t room = B - assigned;
+    if (threadIdx.x == 0) s_base = atomicAdd(&p.sh->cursor, room);
+    __syncthreads();
+    const uint32_t base = s_base;
+    __syncthreads();
+    if (base >= p.norder) break;
+    last_base = base;
+    const uint32_t cnt = room < p.norder - base ? room : p.norder - base;
+    const uint32_t idx = base + threadIdx.x;
+    const bool valid = threadIdx.x < cnt;
     uint32_t v = valid ? p.order[idx] : 0;
     uint32_t od = valid ? p.off[v + 1] - p.off[v] : 0;
     uint32_t a = valid ? p.alpha[v] : 0, o = valid ? p.omega[v] : 0;
@@ -665,24 +748,10 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       Thresh x = thresh_of(p, gv);
       cut = x.have && cut_exceeds(0, 0, 1, od, a, o, x.S, x.r);
     }
-    bool keep = valid && !cut;
+    const bool take = valid && !cut;
     uint32_t total;
-    uint32_t pre = block_exscan(sm, keep ? 1u : 0u, &total);
-    uint32_t room = B - assigned;
-    // the chunk is consumed up to the room-th kept source
-    uint32_t consumed;
-    if (total <= room) {
-      consumed = (cursor + kTPB <= p.norder) ? kTPB : p.norder - cursor;
-    } else {
-      __shared__ uint32_t s_cons;
-      if (keep && pre == room - 1) s_cons = threadIdx.x + 1;
-      __syncthreads();
-      consumed = s_cons;
-      __syncthreads();
-    }
-    bool in = threadIdx.x < consumed;
-    bool take = keep && in;
-    if (cut && in) {
+    uint32_t pre = block_exscan(sm, take ? 1u : 0u, &total);
+    if (cut) {
       graph_count(p, gv, 1, 1);
       graph_count(p, gv, 2, 1);
     }
@@ -702,7 +771,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       sl.omega = o;
       sl.state = 1;
       sl.graph = gv;
-      sl.nocut = (cursor + threadIdx.x) < p.nocut_prefix;
+      sl.nocut = idx < p.nocut_prefix;
       sl.pad[0] = sl.pad[1] = sl.pad[2] = 0;
       p.slots[s] = sl;
       graph_count(p, gv, 1, 1);
@@ -716,24 +785,18 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       p.VL[s] = v;
       atomicOr(&sm.active[s >> 6], bit);
     }
-    uint32_t taken = total < room ? total : room;
-    assigned += taken;
+    uint32_t ncut;
+    block_exscan(sm, cut ? 1u : 0u, &ncut);
+    assigned += total;
     arcs_total += arcs_pre_total;
-    uint32_t ncut_chunk = 0;
-    {
-      uint32_t t2;
-      block_exscan(sm, (cut && in) ? 1u : 0u, &t2);
-      ncut_chunk = t2;
-    }
-    started += taken + ncut_chunk;
-    cut0 += ncut_chunk;
-    cursor += consumed;
+    started += total + ncut;
+    cut0 += ncut;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     // the clear step just zeroed these rows
     c->alg_bytes += (u64)(c->vl_count + c->fl_count) * (4 + 8ull * W);
-    c->cursor = cursor;
+    c->cursor = last_base;
     c->bfs_started += started;
     c->bfs_cut += cut0;
     c->edges_visited += arcs_total;
@@ -752,7 +815,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
         rec[1] = 2;  // seed step
         rec[2] = assigned;
         rec[3] = arcs_total;
-        rec[4] = cursor;
+        rec[4] = last_base;
         rec[5] = cut0;
         rec[6] = c->vl_count;
         rec[7] = p.g_ntop[0];
@@ -775,14 +838,43 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
 // ------------------------------------------------------------------ the kernel
 
 template <int W>
-__global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
+__global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
   __shared__ Smem<W> sm;
+  // this block's team: its own control block, slots, rows, lists and stamps
+  __shared__ RunParams p;
+  const uint32_t bpt = gridDim.x / p0.teams;  // blocks per team
+  const uint32_t team = blockIdx.x / bpt;
+  const uint32_t tb = blockIdx.x % bpt;
+  if (threadIdx.x == 0) {
+    p = p0;
+    p.ctl = p0.ctl + team;
+    p.slots = p0.slots + (size_t)team * 64 * kMaxWords;
+    p.cnt = p0.cnt + (size_t)team * 64 * kMaxWords;
+    p.wsum = p0.wsum + (size_t)team * 64 * kMaxWords;
+    p.seen = p0.seen + team * p0.row_stride;
+    p.F0 = p0.F0 + team * p0.row_stride;
+    p.F1 = p0.F1 + team * p0.row_stride;
+    p.N = p0.N + team * p0.row_stride;
+    p.FB0 = p0.FB0 + team * p0.fb_stride;
+    p.FB1 = p0.FB1 + team * p0.fb_stride;
+    p.L0 = p0.L0 + team * p0.vtx_stride;
+    p.L1 = p0.L1 + team * p0.vtx_stride;
+    p.Loff0 = p0.Loff0 + team * p0.vtx_stride;
+    p.Loff1 = p0.Loff1 + team * p0.vtx_stride;
+    p.VL = p0.VL + team * p0.vtx_stride;
+    p.stamp = p0.stamp + team * p0.vtx_stride;
+    if (p0.trace) {
+      p.trace_cap = p0.trace_cap / p0.teams;
+      p.trace = p0.trace + (size_t)team * p.trace_cap * 16;
+    }
+  }
+  __syncthreads();
   Ctl *c = p.ctl;
   const int lane = threadIdx.x & 31;
-  const uint32_t gwarp = (blockIdx.x * kTPB + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * kTPB) >> 5;
-  const uint32_t gthread = blockIdx.x * kTPB + threadIdx.x;
-  const uint32_t nthreads = gridDim.x * kTPB;
+  const uint32_t gwarp = (tb * kTPB + threadIdx.x) >> 5;
+  const uint32_t nwarps = (bpt * kTPB) >> 5;
+  const uint32_t gthread = tb * kTPB + threadIdx.x;
+  const uint32_t nthreads = bpt * kTPB;
 
   while (true) {
     const int step = ld_volatile_i32(&c->step);
@@ -799,7 +891,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
     uint32_t *NLoff = cur ? p.Loff0 : p.Loff1;
     const uint32_t fl_count = vc->fl_count;
     if (step == 1) {
-      if (blockIdx.x == 0) trace_stamp(p, 8);
+      if (tb == 0) trace_stamp(p, 8);
       // ---- clear step: zero the rows touched by the finished batch
       const uint32_t vl = vc->vl_count;
       for (uint64_t i = gthread; i < (uint64_t)vl * W; i += nthreads) {
@@ -807,11 +899,11 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
         p.seen[(size_t)v * W + (i % W)] = 0;
       }
       clear_frontier<W>(Fcur, FBcur, FL, fl_count, p.n, gthread, nthreads);
-      if (blockIdx.x == 0) trace_stamp(p, 12);
-      if (!grid_sync(c, p.timeout, [&] { epilogue_seed<W>(p, sm); })) break;
+      if (tb == 0) trace_stamp(p, 12);
+      if (!team_sync(c, p.sh, bpt, p.timeout, [&] { epilogue_seed<W>(p, sm); })) break;
       continue;
     }
-    if (blockIdx.x == 0) trace_stamp(p, 8);
+    if (tb == 0) trace_stamp(p, 8);
     const int dir = vc->dir;
     const uint32_t level_id = vc->level_id;
     const u64 fl_arcs = vc->fl_arcs;
@@ -878,9 +970,9 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
       }
       scanned = 0;
       if (gthread == 0) atomicAdd(&c->edges_scanned, fl_arcs);
-      if (blockIdx.x == 0) trace_stamp(p, 9);
-      if (!grid_sync(c, p.timeout, [] {})) break;
-      if (blockIdx.x == 0) trace_stamp(p, 10);
+      if (tb == 0) trace_stamp(p, 9);
+      if (!team_sync(c, p.sh, bpt, p.timeout, [] {})) break;
+      if (tb == 0) trace_stamp(p, 10);
       // ---- phase B: finalize the next level, clear the old frontier rows
       const uint32_t nl_count = (uint32_t)(((volatile Ctl *)c)->nl_packed >> kPackShift);
       for (uint32_t base = gwarp * 32; base < nl_count; base += nwarps * 32) {
@@ -972,13 +1064,13 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
         warp_append(isnew, w, od, &c->nl_packed, NL, NLoff, lane);
         warp_append_plain(isnew && was_empty, w, &c->vl_count, p.VL, lane);
       }
-      if (blockIdx.x == 0) trace_stamp(p, 9);
-      if (!grid_sync(c, p.timeout, [] {})) break;
-      if (blockIdx.x == 0) trace_stamp(p, 10);
+      if (tb == 0) trace_stamp(p, 9);
+      if (!team_sync(c, p.sh, bpt, p.timeout, [] {})) break;
+      if (tb == 0) trace_stamp(p, 10);
       // ---- phase B: only the old frontier rows need clearing
       clear_frontier<W>(Fcur, FBcur, FL, fl_count, p.n, gthread, nthreads);
     }
-    if (blockIdx.x == 0) trace_stamp(p, 11);
+    if (tb == 0) trace_stamp(p, 11);
     // flush the block's per-slot counters
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -999,8 +1091,8 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p) {
       atomicAdd(&c->lvl_scan_a, sm.acc[3]);
     }
     if (threadIdx.x == 0 && sm.acc[2]) atomicAdd(&c->lvl_scan_v, sm.acc[2]);
-    if (blockIdx.x == 0) trace_stamp(p, 12);
-    if (!grid_sync(c, p.timeout, [&] { epilogue_level<W>(p, sm); })) break;
+    if (tb == 0) trace_stamp(p, 12);
+    if (!team_sync(c, p.sh, bpt, p.timeout, [&] { epilogue_level<W>(p, sm); })) break;
   }
 }
 

@@ -76,6 +76,14 @@ struct Ctl {
   unsigned long long trace_n;  // records written to the optional trace
 };
 
+// State shared by all teams of one run.
+struct Shared {
+  unsigned int cursor;   // next position in the source order (teams take chunks)
+  int lock;              // guards the k-lists while a team merges
+  int err;               // first error of any team
+  unsigned int pad;
+};
+
 struct Slot {
   unsigned long long S;   // sum of distances of the discovered levels
   unsigned long long nd;  // size of the discovered ball
@@ -100,6 +108,17 @@ struct RunParams {
   const uint32_t *order;
   uint32_t norder;  // sources in `order` to examine (all have out-degree >= 1)
   // search configuration
+  // teams: independent groups of `gridDim.x / teams` blocks, each running its
+  // own batches; per-team buffers sit at team * stride from the base pointers
+  uint32_t teams;
+  uint64_t row_stride;   // 64-bit words between the teams' seen/F0/F1/N rows
+  uint64_t vtx_stride;   // 32-bit words between the teams' lists and stamps
+  uint64_t fb_stride;    // 32-bit words between the teams' frontier bitmaps
+  Shared *sh;
+  // published k-th entry of each graph's list (seqlock: odd = being written)
+  unsigned int *x_seq;
+  unsigned long long *x_S;
+  uint32_t *x_r, *x_id;
   // several graphs in one run, as their disjoint union (ng = 1: one graph)
   uint32_t ng;
   const uint32_t *gid;        // graph of each vertex (nullptr: every vertex in graph 0)
@@ -152,8 +171,13 @@ struct Workspace {
   unsigned int *tied = nullptr;     // per graph
   unsigned int *g_ntop = nullptr;   // per graph
   unsigned long long *g_ctr = nullptr;  // 4 per graph
+  Shared *sh = nullptr;
+  unsigned int *x_seq = nullptr;
+  unsigned long long *x_S = nullptr;
+  uint32_t *x_r = nullptr, *x_id = nullptr;
   uint32_t top_cap = 0;   // entries of top_* / out_* (graphs x k)
-  uint32_t ng_cap = 0;    // graphs of tied / g_ntop / g_ctr
+  uint32_t ng_cap = 0;    // graphs of tied / g_ntop / g_ctr / x_*
+  uint32_t teams_cap = 0; // teams the per-team buffers are sized for
   unsigned int level_base = 0;  // stamp epoch carried across runs
 };
 
@@ -219,7 +243,7 @@ int ensure_learned_order(tkc_graph *g);
 int ensure_seeded_order(tkc_graph *g, uint32_t prefix);
 void free_mlp(tkc_ctx *ctx);
 // tkc_bfscut.cu
-int ensure_workspace(tkc_ctx *ctx, uint32_t n, int words, uint32_t top_entries, uint32_t ng);
-int run_bfscut(tkc_ctx *ctx, const RunParams &p, int words, int blocks);
+int ensure_workspace(tkc_ctx *ctx, uint32_t n, int words, uint32_t top_entries, uint32_t ng, uint32_t teams);
+int run_bfscut(tkc_ctx *ctx, const RunParams &p, int words, int blocks);  // blocks: a multiple of p.teams
 int max_coresident_blocks(tkc_ctx *ctx, int words);
 }  // namespace tkc

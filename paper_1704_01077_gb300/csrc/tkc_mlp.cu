@@ -138,30 +138,36 @@ __device__ __forceinline__ void load_weights(const unsigned short *wb, float *ws
   __syncthreads();
 }
 
-// y[i] for m samples, one thread per sample.
-__global__ void k_mlp_forward(const float *x, u32 m, const unsigned short *wb, float *y) {
+constexpr int FT = 64;  // samples per forward block
+
+// y[i] for m samples, one thread per sample; the first hidden layer of the
+// block's samples is kept in shared memory, unit-major so that the threads
+// of a warp read consecutive words.
+__global__ void __launch_bounds__(FT) k_mlp_forward(const float *x, u32 m, const unsigned short *wb, float *y) {
   __shared__ float ws[P];
+  __shared__ float h1[H][FT];
   load_weights(wb, ws);
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+  const int t = threadIdx.x;
+  for (u32 i0 = blockIdx.x * FT; i0 < m; i0 += gridDim.x * FT) {
+    const u32 i = i0 + t;
+    const bool valid = i < m;
     float xi[F];
 #pragma unroll
-    for (int f = 0; f < F; ++f) xi[f] = x[(size_t)i * F + f];
-    float h1[H];
-#pragma unroll
+    for (int f = 0; f < F; ++f) xi[f] = valid ? x[(size_t)i * F + f] : 0.f;
     for (int o = 0; o < H; ++o) {
       float a = ws[oB1 + o];
 #pragma unroll
       for (int f = 0; f < F; ++f) a = fmaf(ws[oW1 + o * F + f], xi[f], a);
-      h1[o] = a > 0.f ? a : 0.f;
+      h1[o][t] = a > 0.f ? a : 0.f;
     }
     float out = ws[oB3];
     for (int o = 0; o < H; ++o) {
       float a = ws[oB2 + o];
-#pragma unroll
-      for (int j = 0; j < H; ++j) a = fmaf(ws[oW2 + o * H + j], h1[j], a);
+#pragma unroll 16
+      for (int j = 0; j < H; ++j) a = fmaf(ws[oW2 + o * H + j], h1[j][t], a);
       out = fmaf(ws[oW3 + o], a > 0.f ? a : 0.f, out);
     }
-    y[i] = out;
+    if (valid) y[i] = out;
   }
 }
 
@@ -362,7 +368,7 @@ int ensure_features(tkc_graph *g) {
 
 static int forward(tkc_ctx *ctx, const float *x, u32 m, float *y) {
   if (m == 0) return TKC_OK;
-  TKC_LAUNCH(k_mlp_forward<<<grid_of(m, 128), 128, 0, ctx->stream>>>(x, m, ctx->mlp.wb, y));
+  TKC_LAUNCH(k_mlp_forward<<<grid_of(m, FT), FT, 0, ctx->stream>>>(x, m, ctx->mlp.wb, y));
   TKC_TRY(cudaGetLastError());
   return TKC_OK;
 }

@@ -64,7 +64,12 @@ struct Layout {
   static constexpr size_t top_r = top_S + 256;
   static constexpr size_t top_id = top_r + 256;
   static constexpr size_t g_ntop = top_id + 256;
-  static constexpr size_t flag = g_ntop + 256;
+  static constexpr size_t shared = g_ntop + 256;
+  static constexpr size_t x_seq = shared + 256;
+  static constexpr size_t x_S = x_seq + 256;
+  static constexpr size_t x_r = x_S + 256;
+  static constexpr size_t x_id = x_r + 256;
+  static constexpr size_t flag = x_id + 256;
   static constexpr size_t ctl = flag + 256;
   static constexpr size_t total = ctl + align256(sizeof(Ctl));
 };
@@ -186,6 +191,15 @@ extern "C" int tkc_distance_sums_noalloc(const uint32_t *offsets, const uint32_t
   p.omega = (const u32 *)(base + L::omega);
   p.order = srcs;
   p.norder = nsrc;
+  p.teams = 1;
+  p.row_stride = 0;
+  p.vtx_stride = 0;
+  p.fb_stride = 0;
+  p.sh = (Shared *)(base + L::shared);
+  p.x_seq = (unsigned *)(base + L::x_seq);
+  p.x_S = (u64 *)(base + L::x_S);
+  p.x_r = (u32 *)(base + L::x_r);
+  p.x_id = (u32 *)(base + L::x_id);
   p.ng = 1;
   p.gid = nullptr;
   p.g_directed = nullptr;

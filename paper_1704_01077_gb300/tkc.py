@@ -48,7 +48,7 @@ class tkc_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("order", ctypes.c_uint32),
                 ("batch_bits", ctypes.c_uint32), ("bu_num", ctypes.c_uint32), ("bu_den", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("seed_factor", ctypes.c_uint32),
-                ("timeout_cycles", ctypes.c_uint64)]
+                ("timeout_cycles", ctypes.c_uint64), ("teams", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class tkc_result(ctypes.Structure):
@@ -159,10 +159,11 @@ class Options:
     blocks: int = 0
     seed_factor: int = 0
     timeout_cycles: int = 0
+    teams: int = 0
 
     def to_c(self) -> tkc_options:
         return tkc_options(self.device, self.stream, self.order, self.batch_bits, self.bu_num, self.bu_den,
-                           self.blocks, self.seed_factor, self.timeout_cycles)
+                           self.blocks, self.seed_factor, self.timeout_cycles, self.teams, 0)
 
 
 @dataclass

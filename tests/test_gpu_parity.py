@@ -273,3 +273,31 @@ def test_multi_graph_counters_add_up(gpu_lib, ctx):
         src = int((g.outdeg() > 0).sum())
         assert r.bfs_started == src and r.bfs_cut + r.bfs_finished == src
         assert 0 < r.edges_visited <= g.arcs * src
+
+
+@pytest.mark.parametrize("teams,bits", [(2, 64), (3, 128), (4, 256), (8, 512)])
+def test_teams_give_exact_results(gpu_lib, ctx, teams, bits):
+    """Several teams share the threshold and the k-lists; results stay exact."""
+    t = gpu_lib
+    cases = [gg.rmat(14, 16, seed=gg.workload_seed(1) + teams), gg.barabasi_albert(20000, 4, teams),
+             gg.random_graph(400, 0.01, 31 + teams, True), gg.path(50)]
+    for g in cases:
+        ref = oracle.bfscut(g, 10) if g.n > 5000 else oracle.textbook_topk(g, 10)
+        t.tkc_set_options(ctx, t.Options(batch_bits=bits, teams=teams))
+        h = t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+        try:
+            res = t.tkc_topk_closeness(h, 10)
+        finally:
+            t.tkc_free_graph(h)
+        _expect_equal(res, ref, g, 10)
+        src = int((g.outdeg() > 0).sum())
+        assert res.bfs_started == src and res.bfs_cut + res.bfs_finished == src
+    graphs = _mixed_graphs(12, 50, 4000, 77 + teams)
+    hs = [t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed) for g in graphs]
+    try:
+        res = t.tkc_topk_closeness_multi(ctx, hs, 10)
+    finally:
+        for h in hs:
+            t.tkc_free_graph(h)
+    for g, r in zip(graphs, res):
+        _expect_equal(r, oracle.textbook_topk(g, 10), g, 10)
