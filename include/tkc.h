@@ -134,6 +134,18 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out);
  * tkc_topk_closeness would (counters per graph, ms_* shared).  Same errors. */
 int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
 
+/* Autotuner (no paper counterpart: it only picks launch parameters).
+ * Times candidate batch widths (64..512), team counts (1..16) and bottom-up
+ * thresholds on a sample of g's degree order (its first 1 024 sources, then
+ * every s-th source, about a tenth of all), keeps the fastest in the
+ * context's cache under g's class (directed, log2 n, log2 of the mean degree)
+ * and writes it to *best (other fields copied from the context's options).
+ * Later calls with options.batch_bits = 0 on a graph of the same class use
+ * the cached choice.  With the environment variable TKC_TUNE_CACHE naming a
+ * file, the cache is loaded at tkc_create and saved after each tuning.
+ * Results never depend on these parameters. */
+int tkc_autotune(tkc_graph *g, uint32_t k, tkc_options *best);
+
 /* computeBoundsDeg (Section 4): writes the degree order (out-degree
  * descending, id ascending) to host array order[n]. */
 int tkc_source_order(tkc_graph *g, uint32_t *order);

@@ -497,6 +497,8 @@ const char *tkc_strerror(int code) {
   }
 }
 
+static void tune_cache_load(tkc_ctx *ctx);
+
 int tkc_create(tkc_ctx **out, const tkc_options *opt) {
   if (!out) return TKC_EINVAL;
   *out = nullptr;
@@ -518,6 +520,7 @@ int tkc_create(tkc_ctx **out, const tkc_options *opt) {
     delete ctx;
     return TKC_ECUDA;
   }
+  tune_cache_load(ctx);
   for (auto &ev : ctx->ev) {
     e = cudaEventCreate(&ev);
     if (e != cudaSuccess) {
@@ -694,6 +697,74 @@ static int source_order_of(tkc_graph *g, const tkc_options &o, u32 kk, const u32
   return TKC_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+
+static std::string graph_class(const tkc_graph *g) {
+  int ln = 0;
+  while (ln < 40 && (1ull << (ln + 1)) <= g->n) ++ln;
+  double deg = g->n ? (double)g->arcs / g->n : 0.0;
+  int ld = 0;
+  while (ld < 40 && (1ull << (ld + 1)) <= (unsigned long long)(deg + 0.5)) ++ld;
+  char buf[64];
+  snprintf(buf, sizeof(buf), "%s_n%d_d%d", g->directed ? "dir" : "und", ln, ld);
+  return buf;
+}
+
+static void tune_cache_load(tkc_ctx *ctx) {
+  const char *path = getenv("TKC_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  char key[128];
+  TuneEntry e;
+  while (fscanf(f, " %127[^=]=%u,%u,%u,%u,%lf", key, &e.batch_bits, &e.teams, &e.bu_num, &e.bu_den, &e.ms) == 6)
+    ctx->tune[key] = e;
+  fclose(f);
+}
+
+static void tune_cache_save(tkc_ctx *ctx) {
+  const char *path = getenv("TKC_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "w");
+  if (!f) return;
+  for (auto &kv : ctx->tune)
+    fprintf(f, "%s=%u,%u,%u,%u,%.3f\n", kv.first.c_str(), kv.second.batch_bits, kv.second.teams, kv.second.bu_num,
+            kv.second.bu_den, kv.second.ms);
+  fclose(f);
+}
+
+// Sample of the degree order: its first `head` sources (they set x), then
+// every stride-th of the rest.
+__global__ void k_sample_order(const u32 *order, u32 norder, u32 head, u32 stride, u32 count, u32 *out) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    out[i] = i < head ? order[i] : order[head + (u64)(i - head) * stride];
+}
+
+static int time_config(tkc_graph *g, const u32 *order, u32 norder, u32 kk, u32 bits, u32 teams, u32 bu, double *ms) {
+  tkc_ctx *ctx = g->ctx;
+  tkc_options saved = ctx->opt;
+  ctx->opt.teams = teams;
+  ctx->opt.bu_num = bu;
+  ctx->opt.bu_den = 1;
+  RunSetup rs;
+  memset(&rs, 0, sizeof(rs));
+  rs.g = g;
+  rs.order = order;
+  rs.norder = norder;
+  rs.B = bits;
+  rs.W = words_for(bits);
+  rs.kk = kk;
+  rs.ng = 1;
+  Ctl hc;
+  int rc = run_search(ctx, rs, &hc);
+  ctx->opt = saved;
+  if (rc != TKC_OK) return rc;
+  float t = 0;
+  cudaEventElapsedTime(&t, ctx->ev[4], ctx->ev[5]);
+  *ms = t;
+  return TKC_OK;
+}
+
 int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   if (!g || !out) return TKC_EINVAL;
   if (k > TKC_MAX_K) return TKC_EINVAL;
@@ -717,6 +788,18 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   TKC_RC(source_order_of(g, o, kk, &rs.order, &rs.norder));
   TKC_TRY(cudaEventRecord(ctx->ev[1], st));
   u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g->n);
+  tkc_options saved = ctx->opt;
+  if (!o.batch_bits) {
+    auto it = ctx->tune.find(graph_class(g));
+    if (it != ctx->tune.end()) {
+      bits = it->second.batch_bits;
+      if (!ctx->opt.teams) ctx->opt.teams = it->second.teams;
+      if (!ctx->opt.bu_num) {
+        ctx->opt.bu_num = it->second.bu_num;
+        ctx->opt.bu_den = it->second.bu_den;
+      }
+    }
+  }
   rs.g = g;
   rs.B = bits;
   rs.W = words_for(bits);
@@ -726,7 +809,9 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   rs.ng = 1;
   r.batch_bits = bits;
   Ctl hc;
-  TKC_RC(run_search(ctx, rs, &hc));
+  int rc_run = run_search(ctx, rs, &hc);
+  ctx->opt = saved;
+  TKC_RC(rc_run);
   std::vector<GraphOut> go(1);
   go[0].n = g->n;
   go[0].base = 0;
@@ -754,6 +839,65 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   r.ms_bfs = ms1;
   r.ms_kernel = ms2;
   *out = r;
+  return TKC_OK;
+}
+
+int tkc_autotune(tkc_graph *g, uint32_t k, tkc_options *best) {
+  if (!g || !best) return TKC_EINVAL;
+  if (k > TKC_MAX_K) return TKC_EINVAL;
+  tkc_ctx *ctx = g->ctx;
+  TKC_TRY(cudaSetDevice(ctx->device));
+  *best = ctx->opt;
+  u32 kk = std::min<u32>(k, g->n);
+  if (kk == 0) return TKC_OK;
+  TKC_RC(ensure_degree_order(g));
+  TKC_RC(ensure_reach_bounds(g));
+  cudaStream_t st = ctx->stream;
+  const u32 ns = g->n_src_deg;
+  const u32 head = std::min<u32>(ns, 1024);
+  const u32 want = std::max<u32>(ns / 10, std::min<u32>(ns, 32768));
+  const u32 stride = std::max<u32>(1, (ns - head) / std::max<u32>(1, want - head));
+  const u32 count = head + (ns > head ? (ns - head + stride - 1) / stride : 0);
+  u32 *order = nullptr;
+  TKC_TRY(cudaMallocAsync(&order, std::max<u32>(count, 1) * sizeof(u32), st));
+  TKC_LAUNCH(k_sample_order<<<(count + 255) / 256 > 0 ? std::min<u32>((count + 255) / 256, 4096) : 1, 256, 0, st>>>(
+      g->deg_order, ns, head, stride, count, order));
+  TKC_TRY(cudaGetLastError());
+  const u32 bits_c[] = {64, 128, 256, 512};
+  const u32 teams_c[] = {1, 2, 4, 8, 16};
+  double best_ms = 1e300;
+  u32 bb = default_batch_bits(g->n), bt = 1, bu = 8;
+  int rc = TKC_OK;
+  for (u32 b : bits_c)
+    for (u32 t : teams_c) {
+      double ms = 0;
+      rc = time_config(g, order, count, kk, b, t, 8, &ms);
+      if (rc != TKC_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        bb = b;
+        bt = t;
+      }
+    }
+  for (u32 u : {4u, 16u, 32u}) {
+    if (rc != TKC_OK) break;
+    double ms = 0;
+    rc = time_config(g, order, count, kk, bb, bt, u, &ms);
+    if (rc == TKC_OK && ms < best_ms) {
+      best_ms = ms;
+      bu = u;
+    }
+  }
+  cudaFreeAsync(order, st);
+  cudaStreamSynchronize(st);
+  if (rc != TKC_OK) return rc;
+  TuneEntry e{bb, bt, bu, 1, best_ms};
+  ctx->tune[graph_class(g)] = e;
+  tune_cache_save(ctx);
+  best->batch_bits = bb;
+  best->teams = bt;
+  best->bu_num = bu;
+  best->bu_den = 1;
   return TKC_OK;
 }
 

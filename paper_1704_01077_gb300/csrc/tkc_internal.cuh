@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -196,9 +197,16 @@ struct MlpState {
   bool ready = false;
 };
 
+// Autotuner choice for one graph class.
+struct TuneEntry {
+  uint32_t batch_bits, teams, bu_num, bu_den;
+  double ms;
+};
+
 struct tkc_ctx {
   int device = 0;
   MlpState mlp;
+  std::map<std::string, TuneEntry> tune;  // graph class -> fastest parameters
   cudaStream_t stream = nullptr;
   tkc_options opt{};
   int num_sms = 0;

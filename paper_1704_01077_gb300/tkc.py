@@ -67,7 +67,7 @@ EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc
             "tkc_topk_closeness", "tkc_topk_closeness_multi", "tkc_source_order", "tkc_set_source_order",
             "tkc_reach_bounds", "tkc_distance_sums", "tkc_distance_sums_noalloc", "tkc_kernel_launches",
             "tkc_strerror", "tkc_vertex_features", "tkc_mlp_init", "tkc_set_source_model", "tkc_get_source_model",
-            "tkc_mlp_forward", "tkc_mlp_gradient", "tkc_mlp_train_step"]
+            "tkc_mlp_forward", "tkc_mlp_gradient", "tkc_mlp_train_step", "tkc_autotune"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tkc_mlp_forward.argtypes = [vp, vp, ctypes.c_uint32, vp]
     lib.tkc_mlp_gradient.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, fp]
     lib.tkc_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_float, fp]
+    lib.tkc_autotune.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(tkc_options)]
     lib.tkc_kernel_launches.argtypes = []
     lib.tkc_kernel_launches.restype = ctypes.c_uint64
     lib.tkc_strerror.argtypes = [ctypes.c_int]
@@ -317,6 +318,15 @@ def tkc_distance_sums_noalloc(offsets, cols, n: int, sources, S, r, stream=None)
                                         ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(r.data_ptr()),
                                         ctypes.c_void_p(stream))
     _check(rc, "tkc_distance_sums_noalloc")
+
+
+def tkc_autotune(g, k: int) -> Options:
+    """Tunes the launch parameters on g; returns them as Options (stream left to the caller)."""
+    o = tkc_options()
+    _check(_lib.tkc_autotune(g, k, ctypes.byref(o)), "tkc_autotune")
+    return Options(device=o.device, stream=o.stream, order=o.order, batch_bits=o.batch_bits, bu_num=o.bu_num,
+                   bu_den=o.bu_den, blocks=o.blocks, seed_factor=o.seed_factor, timeout_cycles=o.timeout_cycles,
+                   teams=o.teams)
 
 
 def _dev(t):

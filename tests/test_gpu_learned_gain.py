@@ -36,7 +36,7 @@ def test_learned_order_gain_on_held_out_graphs(gpu_lib, tmp_path):
                 row = {"scale": scale}
                 for name, order, sf in (("degree", t.TKC_ORDER_DEG, 0), ("learned", t.TKC_ORDER_LEARNED, 0),
                                         ("learned_seed5", t.TKC_ORDER_LEARNED, 5)):
-                    t.tkc_set_options(ctx, t.Options(batch_bits=64, order=order, seed_factor=sf))
+                    t.tkc_set_options(ctx, t.Options(batch_bits=64, order=order, seed_factor=sf, teams=1))
                     r = t.tkc_topk_closeness(h, 10)
                     assert list(r.ids) == list(ref.ids) and np.array_equal(r.dist_sum, ref.S)
                     row[name] = r.edges_visited

@@ -301,3 +301,20 @@ def test_teams_give_exact_results(gpu_lib, ctx, teams, bits):
             t.tkc_free_graph(h)
     for g, r in zip(graphs, res):
         _expect_equal(r, oracle.textbook_topk(g, 10), g, 10)
+
+
+def test_autotune_picks_valid_parameters_and_keeps_results(gpu_lib, ctx):
+    t = gpu_lib
+    g = gg.rmat(14, 16, seed=gg.workload_seed(1) + 5)
+    ref = oracle.bfscut(g, 10)
+    t.tkc_set_options(ctx, t.Options())
+    h = t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+    try:
+        best = t.tkc_autotune(h, 10)
+        assert best.batch_bits in (64, 128, 256, 512) and best.teams in (1, 2, 4, 8, 16)
+        assert best.bu_num in (4, 8, 16, 32) and best.bu_den == 1
+        res = t.tkc_topk_closeness(h, 10)  # batch_bits = 0: the cached choice applies
+        assert res.batch_bits == best.batch_bits
+        _expect_equal(res, ref, g, 10)
+    finally:
+        t.tkc_free_graph(h)
