@@ -32,6 +32,8 @@ WORKLOADS = {
                "self-loops and duplicates removed, k=10"),
     "rmat16": (lambda gg: gg.rmat(16, 16, seed=gg.workload_seed(1)), 10,
                "directed R-MAT scale 16, edge factor 16, k=10"),
+    "rmat20": (lambda gg: gg.rmat(20, 16, seed=gg.workload_seed(1)), 10,
+               "directed R-MAT scale 20, edge factor 16, k=10 (profiling size: inputs above L2, a few GB)"),
     "ba1m": (lambda gg: gg.barabasi_albert(1_000_000, 5, gg.workload_seed(2)), 10,
              "undirected Barabasi-Albert n=1,000,000, m=5, k=10"),
     "multi512": (lambda gg: multi_graphs(gg, 512, 1_000, 200_000, gg.workload_seed(3)), 10,

@@ -325,36 +325,63 @@ __global__ void k_sinks(const u32 *wgt, const u32 *soff, u32 n, u32 *rem, u32 *l
   }
 }
 
-// Evaluates alpha/omega of the ready SCCs (all successors done) and releases
-// predecessors whose last successor this was.
-__global__ void k_dp_round(const u32 *list, u32 cnt, const u32 *soff, const u32 *succ, const u32 *poff,
-                           const u32 *pred, const u32 *wgt, const u32 *dist_from_big, const u32 *dist_to_big,
-                           u32 big, u64 reach_big, u32 n, u64 *A, u64 *O, u32 *rem, u32 *next, u32 *next_cnt) {
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+// Evaluates alpha/omega of the ready SCCs (all successors done), one warp
+// per SCC reducing over its successors.
+__global__ void k_dp_eval(const u32 *list, u32 cnt, const u32 *soff, const u32 *succ, const u32 *wgt,
+                          const u32 *dist_from_big, const u32 *dist_to_big, u32 big, u64 reach_big, u32 n, u64 *A,
+                          u64 *O, u32 *npred, const u32 *poff) {
+  const int lane = threadIdx.x & 31;
+  for (u32 i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < cnt; i += (gridDim.x * blockDim.x) >> 5) {
     u32 c = list[i];
-    u64 a, o;
-    if (c == big) {
-      a = o = reach_big;
-    } else {
-      u64 amax = 0, osum = 0, onot = 0;
-      for (u32 e = soff[c]; e < soff[c + 1]; ++e) {
+    u64 amax = 0, osum = 0, onot = 0;
+    if (c != big) {
+      for (u32 e = soff[c] + lane; e < soff[c + 1]; e += 32) {
         u32 y = succ[e];
         amax = A[y] > amax ? A[y] : amax;
         osum += O[y];
         if (dist_from_big[y] == INF) onot += O[y];
       }
-      if (dist_to_big[c] != INF) osum = onot + O[big];
-      a = amax + wgt[c];
-      o = osum + wgt[c];
-      if (o > n) o = n;
+      for (int o = 16; o; o >>= 1) {
+        u64 t = __shfl_down_sync(FULL, amax, o);
+        amax = t > amax ? t : amax;
+        osum += __shfl_down_sync(FULL, osum, o);
+        onot += __shfl_down_sync(FULL, onot, o);
+      }
     }
-    A[c] = a;
-    O[c] = o;
-    __threadfence();
-    for (u32 e = poff[c]; e < poff[c + 1]; ++e) {
-      u32 p = pred[e];
-      if (atomicSub(&rem[p], 1u) == 1u) next[atomicAdd(next_cnt, 1u)] = p;
+    if (lane == 0) {
+      u64 a, o;
+      if (c == big) {
+        a = o = reach_big;
+      } else {
+        if (dist_to_big[c] != INF) osum = onot + O[big];
+        a = amax + wgt[c];
+        o = osum + wgt[c];
+        if (o > n) o = n;
+      }
+      A[c] = a;
+      O[c] = o;
+      npred[i] = poff[c + 1] - poff[c];
     }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) npred[cnt] = 0;
+}
+
+// Releases the predecessors of the SCCs just evaluated, one thread per
+// predecessor arc (pos: exclusive prefix of the predecessor counts); an SCC
+// whose last successor this was joins the next ready list.
+__global__ void k_dp_release(const u32 *list, u32 cnt, const u32 *pos, const u32 *poff, const u32 *pred, u32 *rem,
+                             u32 *next, u32 *next_cnt) {
+  const u32 total = pos[cnt];
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    u32 lo = 0, hi = cnt;  // last j with pos[j] <= i
+    while (hi - lo > 1) {
+      u32 mid = (lo + hi) >> 1;
+      if (pos[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    u32 c = list[lo];
+    u32 p = pred[poff[c] + (i - pos[lo])];
+    if (atomicSub(&rem[p], 1u) == 1u) next[atomicAdd(next_cnt, 1u)] = p;
   }
 }
 
@@ -529,12 +556,18 @@ int reach_directed_gpu(tkc_graph *g) {
   TKC_LAUNCH(k_sinks<<<grid_of(n), 256, 0, st>>>(wgt, soff, n, rem, listA, flag));
   u32 cnt = read_u32(flag, st, &rc);
   TKC_RC(rc);
-  u32 *cur_list = listA, *nxt_list = listB;
+  u32 *cur_list = listA, *nxt_list = listB, *ppos = nullptr, *ptmp = nullptr;
+  TKC_TRY(b.get(&ppos, (size_t)n + 1));
+  TKC_TRY(b.get(&ptmp, ((size_t)n + 1) / 4096 + 2));
   for (u32 round = 0; cnt > 0; ++round) {
     if (round > n) return TKC_ETIMEOUT;
     TKC_TRY(cudaMemsetAsync(flag + 1, 0, sizeof(u32), st));
-    TKC_LAUNCH(k_dp_round<<<grid_of(cnt), 256, 0, st>>>(cur_list, cnt, soff, sv, poff, pred, wgt, fw, bw, big,
-                                                         reach_big, n, A, O, rem, nxt_list, flag + 1));
+    TKC_LAUNCH(k_dp_eval<<<grid_of((u64)cnt * 32), 256, 0, st>>>(cur_list, cnt, soff, sv, wgt, fw, bw, big,
+                                                                    reach_big, n, A, O, ppos, poff));
+    TKC_RC(scan_exclusive_u32(ppos, ppos, (u64)cnt + 1, ptmp, st));
+    TKC_LAUNCH(k_dp_release<<<grid_of((u64)cnt * 8), 256, 0, st>>>(cur_list, cnt, ppos, poff, pred, rem, nxt_list,
+                                                                     flag + 1));
+    TKC_TRY(cudaGetLastError());
     cnt = read_u32(flag + 1, st, &rc);
     TKC_RC(rc);
     std::swap(cur_list, nxt_list);
