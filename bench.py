@@ -27,6 +27,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     # name: (builder, k, description)
+    "ba2000": (lambda gg: gg.barabasi_albert(2000, 4, gg.workload_seed(0)), 10,
+               "undirected Barabasi-Albert n=2,000, m=4 (7,990 edges), k=10"),
     "rmat22": (lambda gg: gg.rmat(22, 16, seed=gg.workload_seed(4)), 10,
                "directed R-MAT scale 22 (4,194,304 vertices), edge factor 16, a/b/c/d=0.57/0.19/0.19/0.05, "
                "self-loops and duplicates removed, k=10"),
@@ -191,6 +193,10 @@ def main():
     ap.add_argument("--sample", type=int, default=96, help="CPU oracle sample: number of sources")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--k", type=int, default=0, help="top-k (0 = the workload's k)")
+    ap.add_argument("--order", default="degree", choices=["degree", "learned", "learned-seed"],
+                    help="source order: degree bound, learned model, or learned seeding prefix + degree")
+    ap.add_argument("--teams", type=int, default=0, help="teams of SMs (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "tkc":
         args.warmup = 3
@@ -210,6 +216,7 @@ def main():
 
         dist.init_process_group("nccl")
     build, k, desc = WORKLOADS[args.workload]
+    k = args.k or k
     built = build(gg)
     multi = isinstance(built, list)
     graphs = built if multi else [built]
@@ -220,7 +227,15 @@ def main():
                for x in graphs]
     host_csr = [(torch.from_numpy(x.offsets.view(np.int32)).pin_memory(),
                  torch.from_numpy(x.cols.view(np.int32)).pin_memory()) for x in graphs]
-    ctx = tkc.tkc_create(tkc.Options(device=local, stream=stream.cuda_stream, batch_bits=args.bits))
+    order = {"degree": tkc.TKC_ORDER_DEG, "learned": tkc.TKC_ORDER_LEARNED,
+             "learned-seed": tkc.TKC_ORDER_LEARNED}[args.order]
+    base_opt = dict(device=local, stream=stream.cuda_stream, batch_bits=args.bits, order=order, teams=args.teams,
+                    seed_factor=5 if args.order == "learned-seed" else 0)
+    ctx = tkc.tkc_create(tkc.Options(**base_opt))
+    if args.order != "degree":
+        from paper_1704_01077_gb300.train_order import load_weights
+
+        tkc.tkc_set_source_model(ctx, load_weights())
 
     class Step:
         """One step's results summed over the graphs it ran."""
@@ -306,7 +321,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "k": k, "batch_bits": res.batch_bits,
-                       "order": "degree", "l2": "inputs larger than L2 (CSR 280 MB + 1 GiB bit rows)",
+                       "order": args.order, "teams": args.teams or "library default",
+                       "l2": "inputs larger than L2 (CSR 280 MB + bit rows)" if args.workload in
+                       ("rmat22", "multi512", "ba1m") else "small graph: may be L2-resident",
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary(),
@@ -320,7 +337,7 @@ def main():
                        "arcs": sum(x.arcs for x in graphs),
                        "top_ids": [int(x) for x in results[-1].ids]}}
     if rank == 0 and args.plain and not multi:
-        tkc.tkc_set_options(ctx, tkc.Options(device=local, stream=stream.cuda_stream, batch_bits=1))
+        tkc.tkc_set_options(ctx, tkc.Options(**dict(base_opt, batch_bits=1, teams=1)))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pr = step_device()
