@@ -70,7 +70,8 @@ typedef struct {
                               without cutting, so x starts from exact farness values (0 = none) */
   uint64_t timeout_cycles; /* budget of every device-side wait, in SM clock cycles (0 = default 2^34) */
   uint32_t teams;          /* independent groups of SMs, each running its own source batches and sharing
-                              the threshold and the k-lists (0 = library default; plain mode uses 1) */
+                              the threshold and the k-lists (0 = library default: one team of 8 SMs per
+                              8 SMs for n >= 2^16; plain mode uses 1) */
   uint32_t pad;
 } tkc_options;
 
@@ -135,7 +136,8 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out);
 int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
 
 /* Autotuner (no paper counterpart: it only picks launch parameters).
- * Times candidate batch widths (64..512), team counts (1..16) and bottom-up
+ * Times candidate batch widths (64..512), team counts (1, 4, and SMs/16,
+ * SMs/8, SMs/4, i.e. 16, 8 and 4 blocks per team) and bottom-up
  * thresholds on a sample of g's degree order (its first 1 024 sources, then
  * every s-th source, about a tenth of all), keeps the fastest in the
  * context's cache under g's class (directed, log2 n, log2 of the mean degree)

@@ -219,7 +219,7 @@ static int words_for(u32 bits) {
 
 // Batch width used when the options leave it to the library.
 static u32 default_batch_bits(u32 n) {
-  if (n < 4096) return 64;
+  if (n < 4096 || n >= (1u << 16)) return 64;
   return 128;
 }
 
@@ -241,11 +241,10 @@ struct RunSetup {
 // Teams used when the options leave it to the library: one team for small
 // graphs (a level is short and the whole GPU serves it), more for large ones
 // so that the latency of one team's level steps overlaps with the others.
-static u32 default_teams(u32 n, u32 B) {
-  if (B <= 1) return 1;
-  if (n < (1u << 14)) return 1;
-  if (n < (1u << 18)) return 4;
-  return 8;
+static u32 default_teams(u32 n, u32 B, u32 maxb) {
+  if (B <= 1 || n < (1u << 14)) return 1;
+  if (n < (1u << 16)) return std::max<u32>(1, maxb / 16);
+  return std::max<u32>(1, maxb / 8);  // eight blocks (SMs) per team, every SM used
 }
 
 static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
@@ -255,7 +254,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   const tkc_options &o = ctx->opt;
   int maxb = max_coresident_blocks(ctx, rs.W);
   if (maxb <= 0) return TKC_ECUDA;
-  u32 T = rs.B <= 1 ? 1u : (o.teams ? o.teams : default_teams(g->n, rs.B));
+  u32 T = rs.B <= 1 ? 1u : (o.teams ? o.teams : default_teams(g->n, rs.B, (u32)maxb));
   T = std::max<u32>(1, std::min<u32>(T, (u32)maxb));
   TKC_RC(ensure_workspace(ctx, g->n, rs.W, rs.kk * rs.ng, rs.ng, T));
   if (w.level_base > 0xF0000000u) {
@@ -864,7 +863,9 @@ int tkc_autotune(tkc_graph *g, uint32_t k, tkc_options *best) {
       g->deg_order, ns, head, stride, count, order));
   TKC_TRY(cudaGetLastError());
   const u32 bits_c[] = {64, 128, 256, 512};
-  const u32 teams_c[] = {1, 2, 4, 8, 16};
+  const int maxb_t = std::max(1, max_coresident_blocks(ctx, 1));
+  const u32 teams_c[] = {1, 4, (u32)std::max(1, maxb_t / 16), (u32)std::max(1, maxb_t / 8),
+                         (u32)std::max(1, maxb_t / 4)};
   double best_ms = 1e300;
   u32 bb = default_batch_bits(g->n), bt = 1, bu = 8;
   int rc = TKC_OK;

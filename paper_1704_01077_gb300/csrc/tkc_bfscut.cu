@@ -924,9 +924,10 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
       // arcs per warp task: about two tasks per warp, at least one step, so a
       // small level still spreads over every warp (each step is a chain of
       // dependent loads)
+      constexpr int TU = W <= 2 ? 4 : 2;  // warp steps unrolled per iteration
       u64 CH = (fl_arcs + 2ull * nwarps - 1) / (2ull * nwarps);
-      CH = (CH + APS - 1) / APS * APS;
-      if (CH < APS) CH = APS;
+      CH = (CH + TU * APS - 1) / (TU * APS) * (TU * APS);
+      if (CH < TU * APS) CH = TU * APS;
       const int grp = lane / W, j = lane % W;
       const u64 actj = sm.active[j];
       for (u64 base = (u64)gwarp * CH; base < fl_arcs; base += (u64)nwarps * CH) {
@@ -939,32 +940,40 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
           else hi = mid;
         }
         uint32_t ent = lo;
-        for (u64 e0 = base; e0 < end; e0 += APS) {
-          u64 e = e0 + grp;
-          bool valid = e < end;
+        // TU warp steps per iteration: every arc's loads are issued before
+        // any arc's atomic
+        for (u64 e0 = base; e0 < end; e0 += TU * APS) {
+          u64 ew[TU];
+          uint32_t iw[TU], uw[TU], ww[TU];
+          u64 fw[TU], bw[TU], cw[TU];
           uint32_t ii = ent;
-          if (valid)
-            while (ii + 1 < fl_count && FLoff[ii + 1] <= e) ++ii;
-          bool app = false;
-          uint32_t w = 0;
-          if (valid) {
-            uint32_t u = FL[ii];
-            u64 f = Fcur[(size_t)u * W + j] & actj;
-            if (f) {
-              w = p.col[p.off[u] + (uint32_t)(e - FLoff[ii])];
-              u64 bits = f & ~p.seen[(size_t)w * W + j];
-              if (bits) {
-                u64 *np = p.N + (size_t)w * W + j;
-                u64 curv = *(volatile u64 *)np;
-                if (bits & ~curv) {
-                  u64 old = atomicOr(np, bits);
-                  if (old == 0) app = atomicExch(&p.stamp[w], level_id) != level_id;
-                }
-              }
-            }
+#pragma unroll
+          for (int t = 0; t < TU; ++t) {
+            ew[t] = e0 + (u64)t * APS + grp;
+            if (ew[t] < end)
+              while (ii + 1 < fl_count && FLoff[ii + 1] <= ew[t]) ++ii;
+            iw[t] = ii;
           }
-          uint32_t od = app ? p.off[w + 1] - p.off[w] : 0;
-          warp_append(app, w, od, &c->nl_packed, NL, NLoff, lane);
+#pragma unroll
+          for (int t = 0; t < TU; ++t) uw[t] = ew[t] < end ? FL[iw[t]] : 0;
+#pragma unroll
+          for (int t = 0; t < TU; ++t) fw[t] = ew[t] < end ? Fcur[(size_t)uw[t] * W + j] & actj : 0;
+#pragma unroll
+          for (int t = 0; t < TU; ++t) ww[t] = fw[t] ? p.col[p.off[uw[t]] + (uint32_t)(ew[t] - FLoff[iw[t]])] : 0;
+#pragma unroll
+          for (int t = 0; t < TU; ++t) bw[t] = fw[t] ? fw[t] & ~p.seen[(size_t)ww[t] * W + j] : 0;
+#pragma unroll
+          for (int t = 0; t < TU; ++t) cw[t] = bw[t] ? *(volatile u64 *)(p.N + (size_t)ww[t] * W + j) : 0;
+#pragma unroll
+          for (int t = 0; t < TU; ++t) {
+            bool app = false;
+            if (bw[t] & ~cw[t]) {
+              u64 old = atomicOr(p.N + (size_t)ww[t] * W + j, bw[t]);
+              if (old == 0) app = atomicExch(&p.stamp[ww[t]], level_id) != level_id;
+            }
+            uint32_t od = app ? p.off[ww[t] + 1] - p.off[ww[t]] : 0;
+            warp_append(app, ww[t], od, &c->nl_packed, NL, NLoff, lane);
+          }
           ent = __reduce_max_sync(FULL, ii);
         }
       }
@@ -1026,24 +1035,37 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
             any |= miss[q] != 0;
           }
           if (any) {
-            uint32_t e = p.ioff[w], ee = p.ioff[w + 1];
-            for (; e < ee; ++e) {
-              uint32_t u = p.icol[e];
-              if (!((FBcur[u >> 5] >> (u & 31)) & 1u)) continue;  // u is not on any frontier
-              u64 fr[W];
-              load_row<W>(Fcur, u, fr);
+            // U in-arcs per step: their columns and frontier bits are loaded
+            // together, then the rows of those on a frontier; the early exit
+            // is tested once per step (extra rows only repeat found bits)
+            constexpr int U = W >= 8 ? 2 : W >= 4 ? 4 : 8;
+            const uint32_t e0 = p.ioff[w], ee = p.ioff[w + 1];
+            uint32_t e = e0;
+            for (; e < ee; e += U) {
+              uint32_t uu[U], fb[U];
+#pragma unroll
+              for (int j = 0; j < U; ++j) uu[j] = e + j < ee ? p.icol[e + j] : 0xffffffffu;
+#pragma unroll
+              for (int j = 0; j < U; ++j)
+                fb[j] = uu[j] != 0xffffffffu ? (FBcur[uu[j] >> 5] >> (uu[j] & 31)) & 1u : 0u;
+#pragma unroll
+              for (int j = 0; j < U; ++j) {
+                if (fb[j]) {
+                  u64 fr[W];
+                  load_row<W>(Fcur, uu[j], fr);
+#pragma unroll
+                  for (int q = 0; q < W; ++q) nw[q] |= fr[q] & miss[q];
+                }
+              }
               bool full = true;
 #pragma unroll
-              for (int q = 0; q < W; ++q) {
-                nw[q] |= fr[q] & miss[q];
-                full &= nw[q] == miss[q];
-              }
+              for (int q = 0; q < W; ++q) full &= nw[q] == miss[q];
               if (full) {
-                ++e;
+                e += U;
                 break;
               }
             }
-            scanned += e - p.ioff[w];
+            scanned += (e < ee ? e : ee) - e0;
             scanned_v += 1;
           }
         }

@@ -311,7 +311,7 @@ def test_autotune_picks_valid_parameters_and_keeps_results(gpu_lib, ctx):
     h = t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
     try:
         best = t.tkc_autotune(h, 10)
-        assert best.batch_bits in (64, 128, 256, 512) and best.teams in (1, 2, 4, 8, 16)
+        assert best.batch_bits in (64, 128, 256, 512) and 1 <= best.teams <= 64
         assert best.bu_num in (4, 8, 16, 32) and best.bu_den == 1
         res = t.tkc_topk_closeness(h, 10)  # batch_bits = 0: the cached choice applies
         assert res.batch_bits == best.batch_bits
