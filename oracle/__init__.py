@@ -15,6 +15,9 @@ Functions and what pins them (see ``tests/test_oracle.py``):
   tree_sums       Algorithm 2                    BFS on random trees
   cut_bounds      Lemma 1 per level              invariants: <= S, non-decreasing, ends at S
   bfscut          Algorithm 1 + Algorithm 4      textbook top-k on thousands of graphs
+  nb_bounds       Algorithm 3, Eq. 3, Eq. 6      brute-force walk counts, exact on trees and
+                                                 cycles, hand-computed hypercube, <= S/(r-1)^2,
+                                                 minimum over every r in [alpha, omega]
 """
 from __future__ import annotations
 
@@ -71,7 +74,10 @@ def _bind(lib):
     lib.orc_cut_bounds.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u64p,
                                    ctypes.c_int]
     lib.orc_bfscut.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p, _u32p,
-                               _u64p, _u32p, _u32p, ctypes.POINTER(Counters), _u64p, _u32p, ctypes.c_uint32]
+                               _u64p, _u32p, _u32p, ctypes.POINTER(Counters), _u64p, _u32p, ctypes.c_uint32,
+                               _u64p]
+    lib.orc_nb_bounds.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, _u32p, _u32p, ctypes.c_uint32,
+                                  _u64p, _u32p, _u64p, _u64p, ctypes.c_uint32]
     return lib
 
 
@@ -201,9 +207,11 @@ class TopK:
     all_r: np.ndarray | None = None
 
 
-def bfscut(g, k, order=None, want_all=False, max_sources=0) -> TopK:
+def bfscut(g, k, order=None, want_all=False, max_sources=0, lb_key=None) -> TopK:
     """Algorithm 1 + BFSCut, one source at a time, in degree order (or `order`).
-    max_sources > 0 examines only that prefix of the order (for timing samples)."""
+    max_sources > 0 examines only that prefix of the order (for timing samples).
+    lb_key (with `order` sorted by it): NBCut's stop at the first source whose
+    neighbourhood bound exceeds the k-th farness."""
     off, col = _csr(g)
     kk = min(k, g.n)
     ids = np.zeros(max(kk, 1), np.uint32)
@@ -214,10 +222,11 @@ def bfscut(g, k, order=None, want_all=False, max_sources=0) -> TopK:
     order_a = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
     allS = np.zeros(max(g.n, 1), np.uint64) if want_all else None
     allr = np.zeros(max(g.n, 1), np.uint32) if want_all else None
+    key_a = None if lb_key is None else np.ascontiguousarray(lb_key, dtype=np.uint64)
     cnt = _check(_load().orc_bfscut(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), k,
                                     _p(order_a, _u32p), _p(ids, _u32p), _p(S, _u64p), _p(r, _u32p),
                                     ctypes.byref(tied), ctypes.byref(ctr), _p(allS, _u64p), _p(allr, _u32p),
-                                    max_sources))
+                                    max_sources, _p(key_a, _u64p)))
     return TopK(ids[:cnt], S[:cnt], r[:cnt], int(tied.value), ctr,
                 None if allS is None else allS[: g.n], None if allr is None else allr[: g.n])
 
@@ -227,3 +236,45 @@ def textbook_topk(g, k, threads: int = 0) -> TopK:
     S, r = bfs_sums(g, threads=threads)
     ids, tied = topk(S, r, k)
     return TopK(ids, S[ids], r[ids], tied)
+
+
+NB_FRAC = 46          # fixed-point bits of the neighbourhood-bound order key
+NB_DEFAULT_LEVELS = 256
+
+
+@dataclass
+class NBBounds:
+    S: np.ndarray       # S~ at the minimising candidate reach
+    r: np.ndarray       # that reach (1: out-degree 0, closeness 0)
+    key: np.ndarray     # floor(S * 2^46 / (r-1)^2); UINT64_MAX when r = 1
+    levels: int         # sweeps run
+    counts: np.ndarray | None = None  # counts[k][v] = N~_k(v)
+
+
+def nb_bounds(g, max_levels=NB_DEFAULT_LEVELS, counts_levels=0, alpha=None, omega=None) -> NBBounds:
+    """computeBoundsNB (Algorithm 3; Eq. 3 for directed graphs; Eq. 6 with the
+    Algorithm 6 reach bounds).  alpha/omega default to this oracle's own."""
+    off, col = _csr(g)
+    if alpha is None or omega is None:
+        alpha, omega = alpha_omega(g)
+    a = np.ascontiguousarray(alpha, dtype=np.uint32)
+    o = np.ascontiguousarray(omega, dtype=np.uint32)
+    n1 = max(g.n, 1)
+    S = np.zeros(n1, np.uint64)
+    r = np.zeros(n1, np.uint32)
+    key = np.zeros(n1, np.uint64)
+    counts = np.zeros((max(counts_levels, 1), n1), np.uint64) if counts_levels else None
+    lev = _check(_load().orc_nb_bounds(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), _p(a, _u32p),
+                                       _p(o, _u32p), max_levels, _p(S, _u64p), _p(r, _u32p), _p(key, _u64p),
+                                       _p(counts, _u64p), counts_levels))
+    return NBBounds(S[: g.n], r[: g.n], key[: g.n], int(lev),
+                    None if counts is None else counts[:, : g.n])
+
+
+def nb_order(g, key):
+    """Sources of out-degree >= 1 by increasing key, ties by increasing id
+    (computeBoundsNB's queue Q)."""
+    deg = np.diff(np.asarray(g.offsets, dtype=np.int64))
+    ids = np.nonzero(deg > 0)[0].astype(np.uint32)
+    key = np.asarray(key, dtype=np.uint64)[ids]
+    return ids[np.lexsort((ids, key))]

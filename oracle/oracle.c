@@ -461,6 +461,172 @@ int orc_tree_sums(uint32_t n, const uint32_t *off, const uint32_t *col, uint64_t
 }
 
 /* ---------------------------------------------------------------------- */
+/* computeBoundsNB: neighbourhood-based lower bound (Section 5, Algorithm 3; */
+/* directed graphs Eq. 3; unknown reach Section 8.1, Eq. 6)                  */
+/* ---------------------------------------------------------------------- */
+
+/* Counts are exact until they reach this value; any count >= n may stand for
+ * "at least n" and every count at or above it is stored as exactly this. */
+#define ORC_NB_CAP ((uint64_t)1 << 32)
+/* Bits below the binary point of the order key floor(L' * 2^46), L' = S~/(r-1)^2. */
+#define ORC_NB_FRAC 46
+
+/* One candidate reach r of Eq. 6 with its sum bound S~(r); keeps the smallest
+ * ratio S~/(r-1)^2 (the first one on ties: candidates come in increasing r). */
+static void nb_candidate(uint64_t S, uint64_t r, int *have, uint64_t *bS, uint64_t *br) {
+  if (!*have) { *have = 1; *bS = S; *br = r; return; }
+  u128 lhs = (u128)S * (u128)((*br - 1) * (*br - 1));
+  u128 rhs = (u128)*bS * (u128)((r - 1) * (r - 1));
+  if (lhs < rhs) { *bS = S; *br = r; }
+}
+
+/*
+ * Upper bounds N~_k(s) on the number of vertices at distance k from s, all
+ * vertices advancing one level per sweep:
+ *   N~_0(s) = 1, N~_1(s) = outdeg(s);
+ *   undirected (Eq. 2, Algorithm 3): N~_2(s) = sum_{w in N(s)} N~_1(w) - deg(s),
+ *     N~_k(s) = sum_{w in N(s)} N~_{k-1}(w) - N~_{k-2}(s) (deg(s) - 1) for k > 2
+ *     (the count of non-backtracking walks of length k, exact on trees);
+ *   directed (Eq. 3): N~_k(s) = sum_{w in Gamma(s)} N~_{k-1}(w) (walks).
+ * A count that would reach ORC_NB_CAP, or that is computed from a capped
+ * count, is stored as ORC_NB_CAP (it still bounds the level size, < n).
+ *
+ * Section 5's proposition on level-size upper bounds: with
+ * c_k = sum_{i<=k} N~_i, the function
+ *   S~(r) = sum_{k>=1} k * min(N~_k, max(r - c_{k-1}, 0))
+ * is a lower bound on S(s) at r = r(s).  It is linear with slope k on
+ * (c_{k-1}, c_k], so by the Section 8 lemma on bounds of the form
+ * (n-1) S~(r)/(r-1)^2 the minimum over r in [alpha(s), omega(s)] lies at alpha,
+ * at omega or at some c_l strictly between them (Eq. 6); Algorithm 3's
+ * nVisited is c_k and its S~ is the running sum.  For undirected graphs
+ * alpha = omega = r(s) (Algorithm 3 itself).
+ *
+ * Readings (where the paper is silent or its listing garbled):
+ *  - Every vertex's counts advance at every level, finished or not: later
+ *    levels of its neighbours need them (Algorithm 3 skips finished vertices
+ *    and names s as v there).
+ *  - A vertex finishes when omega(s) <= c_k (Eq. 6's third case), or when
+ *    N~_k(s) = 0: no walk continues, so r(s) <= c_{k-1} and no larger r is a
+ *    candidate (omega can exceed the walk count: Algorithm 6 counts the
+ *    biggest SCC's reach again for every path to it).  A vertex of
+ *    out-degree 0 has r = 1 (closeness 0) and gets (S, r) = (0, 1).
+ *  - At most max_levels sweeps run.  A vertex still unfinished after level K
+ *    takes N~_{K+1} as unbounded: S~ continues with slope K+1 from c_K, which
+ *    adds the candidates alpha (if above c_K) and omega.  This is the same
+ *    proposition with a weaker (still valid) count.
+ *
+ * Writes for every vertex the minimising candidate (S_lb, r_lb): the farness
+ * bound is (n-1) S_lb / (r_lb - 1)^2, and the order key
+ * floor(S_lb * 2^46 / (r_lb - 1)^2) (UINT64_MAX when r_lb = 1).  counts, if
+ * not NULL, receives N~_k(v) at counts[k * n + v] for k < counts_levels
+ * (sweeps continue until then even if all vertices have finished).  Returns
+ * the number of sweeps run, or a negative code.  alpha/omega: Algorithm 6
+ * bounds (exact component size if undirected).
+ */
+int orc_nb_bounds(uint32_t n, const uint32_t *off, const uint32_t *col, int directed,
+                  const uint32_t *alpha, const uint32_t *omega, uint32_t max_levels,
+                  uint64_t *S_lb, uint32_t *r_lb, uint64_t *key, uint64_t *counts, uint32_t counts_levels) {
+  if (n == 0) return 0;
+  if (max_levels == 0 || max_levels > 65535) return ORC_EINVAL;
+  uint64_t *Nk2 = (uint64_t *)malloc((size_t)n * sizeof(uint64_t)); /* N~_{k-2} */
+  uint64_t *Nk1 = (uint64_t *)malloc((size_t)n * sizeof(uint64_t)); /* N~_{k-1} */
+  uint64_t *Nk = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));  /* N~_k */
+  uint64_t *nVisited = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  uint64_t *Ssum = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  uint64_t *bS = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  uint64_t *br = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  int *have = (int *)calloc(n, sizeof(int));
+  char *finished = (char *)calloc(n, 1);
+  int rc = ORC_OK;
+  if (!Nk2 || !Nk1 || !Nk || !nVisited || !Ssum || !bS || !br || !have || !finished) { rc = ORC_ENOMEM; goto out; }
+  uint32_t nFinished = 0;
+  for (uint32_t s = 0; s < n; ++s) {
+    Nk2[s] = 0;
+    Nk1[s] = 1; /* N~_0 */
+    nVisited[s] = 1;
+    Ssum[s] = 0;
+    if (counts && counts_levels > 0) counts[s] = 1;
+  }
+  uint32_t k;
+  for (k = 1; k <= max_levels && (nFinished < n || k < counts_levels); ++k) {
+    for (uint32_t s = 0; s < n; ++s) {
+      uint64_t deg = off[s + 1] - off[s];
+      if (k == 1) { Nk[s] = deg; continue; }
+      uint64_t sum = 0;
+      int capped = 0;
+      for (uint32_t e = off[s]; e < off[s + 1]; ++e) {
+        sum += Nk1[col[e]]; /* each term <= 2^32, at most 2^32 terms */
+        if (sum >= ORC_NB_CAP) capped = 1;
+      }
+      if (directed) {
+        Nk[s] = capped ? ORC_NB_CAP : sum;
+      } else {
+        uint64_t back = (k == 2) ? deg : deg - 1; /* N~_0 = 1 at k = 2 */
+        if (capped || Nk2[s] >= ORC_NB_CAP) {
+          Nk[s] = ORC_NB_CAP;
+        } else {
+          u128 sub = (u128)Nk2[s] * back;
+          if (sub > sum) { rc = ORC_EINVAL; goto out; } /* impossible for a simple graph */
+          Nk[s] = sum - (uint64_t)sub;
+        }
+      }
+    }
+    if (counts && k < counts_levels) memcpy(counts + (size_t)k * n, Nk, (size_t)n * sizeof(uint64_t));
+    for (uint32_t s = 0; s < n; ++s) {
+      Nk2[s] = Nk1[s];
+      Nk1[s] = Nk[s];
+      if (finished[s]) continue;
+      const uint64_t a = alpha[s], o = omega[s], Nks = Nk[s];
+      const uint64_t c0 = nVisited[s], c1 = c0 + Nks, P0 = Ssum[s];
+      if (Nks == 0) {
+        /* no walk continues: r(s) <= c0, nothing above c0 is a candidate */
+        finished[s] = 1;
+        ++nFinished;
+        if (!have[s]) {
+          if (c0 != 1) { rc = ORC_EINVAL; goto out; } /* alpha above every possible reach */
+          bS[s] = 0; br[s] = 1; have[s] = 1;         /* out-degree 0: r = 1 */
+        }
+        continue;
+      }
+      if (a > c0 && a <= c1) nb_candidate(P0 + (uint64_t)k * (a - c0), a, &have[s], &bS[s], &br[s]);
+      if (c1 > a && c1 < o) nb_candidate(P0 + (uint64_t)k * Nks, c1, &have[s], &bS[s], &br[s]);
+      if (o <= c1) {
+        nb_candidate(P0 + (uint64_t)k * (o - c0), o, &have[s], &bS[s], &br[s]);
+        finished[s] = 1;
+        ++nFinished;
+        continue;
+      }
+      nVisited[s] = c1;
+      Ssum[s] = P0 + (uint64_t)k * Nks;
+      if (k == max_levels) {
+        /* level K+1 unbounded: slope K+1 from c_K up to omega */
+        const uint64_t P1 = Ssum[s];
+        if (a > c1) nb_candidate(P1 + (uint64_t)(k + 1) * (a - c1), a, &have[s], &bS[s], &br[s]);
+        nb_candidate(P1 + (uint64_t)(k + 1) * (o - c1), o, &have[s], &bS[s], &br[s]);
+        finished[s] = 1;
+        ++nFinished;
+      }
+    }
+  }
+  for (uint32_t s = 0; s < n; ++s) {
+    S_lb[s] = bS[s];
+    r_lb[s] = (uint32_t)br[s];
+    if (key) {
+      if (br[s] <= 1) {
+        key[s] = UINT64_MAX;
+      } else {
+        u128 num = (u128)bS[s] << ORC_NB_FRAC;
+        key[s] = (uint64_t)(num / (u128)((br[s] - 1) * (br[s] - 1)));
+      }
+    }
+  }
+  rc = (int)(k - 1);
+out:
+  free(Nk2); free(Nk1); free(Nk); free(nVisited); free(Ssum); free(bS); free(br); free(have); free(finished);
+  return rc;
+}
+
+/* ---------------------------------------------------------------------- */
 /* BFSCut lower bound (Section 6, Lemma 1 with the Section 8.2 reading)     */
 /* ---------------------------------------------------------------------- */
 
@@ -616,10 +782,17 @@ static void top_insert(entry_t *top, uint32_t *cnt, uint32_t k, uint64_t S, uint
  * optionally per-vertex S/r of every finished BFS (r = 0 if not finished).
  * max_sources > 0 stops after that many searches (a timing sample only: the
  * returned list is then the top of the examined prefix, not the answer).
+ *
+ * lb_key (NULL = none) turns this into NBCut: lb_key[v] is the order key of
+ * orc_nb_bounds, floor(2^46 L'(v)) with L'(v) a lower bound on S(v)/(r(v)-1)^2,
+ * and order_in must list vertices by increasing key.  Algorithm 1 then stops
+ * at the first source whose key exceeds x strictly (key / 2^46 > S_x/(r_x-1)^2):
+ * every later source has a bound at least as large, hence farness > x.
  */
 int orc_bfscut(uint32_t n, const uint32_t *off, const uint32_t *col, int directed, uint32_t k,
                const uint32_t *order_in, uint32_t *ids, uint64_t *S_out, uint32_t *r_out,
-               uint32_t *n_tied, orc_counters *ctr, uint64_t *allS, uint32_t *allr, uint32_t max_sources) {
+               uint32_t *n_tied, orc_counters *ctr, uint64_t *allS, uint32_t *allr, uint32_t max_sources,
+               const uint64_t *lb_key) {
   if (k == 0 || n == 0) { if (n_tied) *n_tied = 0; return 0; }
   int rc = ORC_OK;
   uint32_t *order = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
@@ -647,6 +820,11 @@ int orc_bfscut(uint32_t n, const uint32_t *off, const uint32_t *col, int directe
     int have_x = ntop == kk;
     uint64_t Sx = have_x ? top[kk - 1].S : 0;
     uint32_t rx = have_x ? top[kk - 1].r : 0;
+    if (lb_key && have_x) {
+      u128 lhs = (u128)lb_key[v] * (u128)((uint64_t)(rx - 1) * (uint64_t)(rx - 1));
+      u128 rhs = (u128)Sx << ORC_NB_FRAC;
+      if (lhs > rhs) break; /* Algorithm 1: the head of Q is bounded above x */
+    }
     c.bfs_started++;
     uint32_t head = 0, tail = 0;
     dist[v] = 0;

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import test_oracle as pins
+import test_oracle_nb as nbpins
 
 MUTANTS = {
     "bfs_dropped_distance": ("S += dist[w];", "S += dist[w] - (dist[w] > 1);",
@@ -44,6 +45,23 @@ MUTANTS = {
                             [pins.test_alpha_omega_hand_built_dag]),
     "tree_level2_off": ("cur[s] = sum - deg;", "cur[s] = sum - deg + 1;",
                         [lambda: pins.test_tree_algorithm_matches_bfs(3)]),
+    "nb_level2_subtracts_deg_minus_one": ("uint64_t back = (k == 2) ? deg : deg - 1;",
+                                          "uint64_t back = deg - 1;",
+                                          [lambda: nbpins.test_counts_equal_enumerated_walks(False)]),
+    "nb_dropped_backtrack_term": ("Nk[s] = sum - (uint64_t)sub;", "Nk[s] = sum;",
+                                  [lambda: nbpins.test_exact_on_trees(0)]),
+    "nb_missing_kink": ("if (c1 > a && c1 < o) nb_candidate(", "if (0) nb_candidate(",
+                        [lambda: nbpins.test_candidate_minimum_equals_minimum_over_every_reach(40)]),
+    "nb_omega_slope_off": ("nb_candidate(P0 + (uint64_t)k * (o - c0), o,", "nb_candidate(P0 + (uint64_t)(k + 1) * (o - c0), o,",
+                           [nbpins.test_bound_below_farness_random]),
+    "nb_tail_slope_off": ("nb_candidate(P1 + (uint64_t)(k + 1) * (o - c1), o,", "nb_candidate(P1 + (uint64_t)(k + 2) * (o - c1), o,",
+                          [lambda: nbpins.test_candidate_minimum_equals_minimum_over_every_reach(2)]),
+    "nb_stop_non_strict": ("if (lhs > rhs) break; /* Algorithm 1", "if (lhs >= rhs) break; /* Algorithm 1",
+                           [nbpins.test_nbcut_equals_textbook_with_ties]),
+    "nb_walks_stop_ignored": ("      if (Nks == 0) {\n        /* no walk", "      if (Nks == 0 && c0 == 1) {\n        /* no walk",
+                              [nbpins.test_walks_that_stop_bound_the_reach]),
+    "nb_sink_gets_reach_two": ("bS[s] = 0; br[s] = 1; have[s] = 1;", "bS[s] = 0; br[s] = 2; have[s] = 1;",
+                               [nbpins.test_out_degree_zero_has_closeness_zero]),
     "degree_order_unstable": ("for (uint32_t v = 0; v < n; ++v) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               "for (uint32_t v = n; v-- > 0;) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               [pins.test_degree_order_matches_lexsort]),
@@ -67,7 +85,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
         for check in checks:
             try:
                 check()
-            except AssertionError:
+            except (AssertionError, RuntimeError):  # a failed pin or an oracle that reports an error
                 caught = True
         assert caught, f"planted mistake {name} passed every pin"
     finally:
