@@ -194,8 +194,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--k", type=int, default=0, help="top-k (0 = the workload's k)")
-    ap.add_argument("--order", default="degree", choices=["degree", "learned", "learned-seed"],
-                    help="source order: degree bound, learned model, or learned seeding prefix + degree")
+    ap.add_argument("--order", default="degree", choices=["degree", "nb", "learned", "learned-seed"],
+                    help="source order: degree bound (DegCut), neighbourhood bound with its stop (NBCut), "
+                         "learned model, or learned seeding prefix + degree")
+    ap.add_argument("--nb-levels", type=int, default=0, help="NBCut: most sweeps of the bound (0 = 256)")
     ap.add_argument("--teams", type=int, default=0, help="teams of SMs (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "tkc":
@@ -227,12 +229,12 @@ def main():
                for x in graphs]
     host_csr = [(torch.from_numpy(x.offsets.view(np.int32)).pin_memory(),
                  torch.from_numpy(x.cols.view(np.int32)).pin_memory()) for x in graphs]
-    order = {"degree": tkc.TKC_ORDER_DEG, "learned": tkc.TKC_ORDER_LEARNED,
+    order = {"degree": tkc.TKC_ORDER_DEG, "nb": tkc.TKC_ORDER_NB, "learned": tkc.TKC_ORDER_LEARNED,
              "learned-seed": tkc.TKC_ORDER_LEARNED}[args.order]
     base_opt = dict(device=local, stream=stream.cuda_stream, batch_bits=args.bits, order=order, teams=args.teams,
-                    seed_factor=5 if args.order == "learned-seed" else 0)
+                    seed_factor=5 if args.order == "learned-seed" else 0, nb_levels=args.nb_levels)
     ctx = tkc.tkc_create(tkc.Options(**base_opt))
-    if args.order != "degree":
+    if args.order.startswith("learned"):
         from paper_1704_01077_gb300.train_order import load_weights
 
         tkc.tkc_set_source_model(ctx, load_weights())

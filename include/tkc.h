@@ -1,12 +1,14 @@
 /*
  * tkc -- exact top-k closeness centrality on one GB300 GPU.
  *
- * C ABI of the CUDA library (libtkc.so).  The method is DegCut from
- * Bergamini, Borassi, Crescenzi, Marino, Meyerhenke, "Computing top-k
+ * C ABI of the CUDA library (libtkc.so).  The method is DegCut and NBCut
+ * from Bergamini, Borassi, Crescenzi, Marino, Meyerhenke, "Computing top-k
  * Closeness Centrality Faster in Unweighted Graphs" (arXiv 1704.01077):
- * Algorithm 1 with computeBoundsDeg (Section 4) and updateBoundsBFSCut
- * (Section 6, Algorithm 4, Lemma 1), reach bounds alpha/omega for directed
- * graphs (Section 8, Lemma 2, Algorithm 6).
+ * Algorithm 1 with computeBoundsDeg (Section 4) or computeBoundsNB (Section 5,
+ * Algorithm 3) and updateBoundsBFSCut (Section 6, Algorithm 4 and its lemma
+ * bounding S from a partial BFS), reach bounds alpha/omega for directed graphs
+ * (Section 8: its lemma on bounds of the form (n-1) L(r)/(r-1)^2, Eq. 6,
+ * Algorithm 6).
  *
  * Definitions (Section 2): R(v) = vertices reachable from v, v included;
  * r(v) = |R(v)|; S(v) = sum of d(v,w) over R(v);
@@ -50,6 +52,9 @@ extern "C" {
 #define TKC_ORDER_LEARNED 2 /* source-order model (tkc_set_source_model): with seed_factor = 0 all sources
                                by predicted farness; with seed_factor > 0 the seed_factor * k sources
                                predicted closest first (searched without cutting), then the degree order */
+#define TKC_ORDER_NB 3      /* computeBoundsNB (NBCut): sources by increasing neighbourhood-based farness
+                               bound (tkc_nb_bounds), ties by id; the search stops at the first source
+                               whose bound exceeds the k-th farness found (Algorithm 1's stop) */
 
 #define TKC_MAX_K 1024      /* largest k accepted by tkc_topk_closeness */
 
@@ -72,7 +77,7 @@ typedef struct {
   uint32_t teams;          /* independent groups of SMs, each running its own source batches and sharing
                               the threshold and the k-lists (0 = library default: one team of 8 SMs per
                               8 SMs for n >= 2^16; plain mode uses 1) */
-  uint32_t pad;
+  uint32_t nb_levels;      /* TKC_ORDER_NB: most level sweeps of computeBoundsNB, 1..65535 (0 = 256) */
 } tkc_options;
 
 typedef struct {
@@ -123,7 +128,8 @@ int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offset
 /* Frees a graph and everything derived from it. */
 void tkc_free_graph(tkc_graph *g);
 
-/* Exact top-k closeness (Algorithm 1, DegCut; Sections 4, 6, 8).  Writes
+/* Exact top-k closeness (Algorithm 1, DegCut or NBCut by options.order;
+ * Sections 4, 5, 6, 8).  Writes
  * min(k, n) entries of out->ids/dist_sum/reach/farness/closeness (those not
  * NULL; out->capacity must be >= min(k, n)) and the counters.  k = 0 or n = 0
  * return no entries.  Errors: TKC_EINVAL (k > TKC_MAX_K, capacity too small),
@@ -160,6 +166,28 @@ int tkc_set_source_order(tkc_graph *g, const uint32_t *order);
 /* Reach bounds alpha(v) <= r(v) <= omega(v) (Section 8.4, Algorithm 6; exact
  * component size for undirected graphs) into host arrays alpha[n], omega[n]. */
 int tkc_reach_bounds(tkc_graph *g, uint32_t *alpha, uint32_t *omega);
+
+/* computeBoundsNB (Section 5, Algorithm 3; Eq. 3 for directed graphs; Eq. 6
+ * with the Algorithm 6 reach bounds).  N~_k(v), an upper bound on the number
+ * of vertices at distance k from v, counts the non-backtracking walks of
+ * length k (undirected, Eq. 2) or the walks of length k (directed, Eq. 3);
+ * all vertices advance one level per device sweep, at most max_levels sweeps
+ * (0 = 256, at most 65535; a vertex unfinished after the last sweep takes the
+ * next level as unbounded, which keeps the bound valid).  With
+ * c_k = N~_0 + ... + N~_k, S~(r) = sum_k k min(N~_k, max(r - c_{k-1}, 0)) is a
+ * lower bound on S(v) when r = r(v), and the bound on the farness is the least
+ * (n-1) S~(r)/(r-1)^2 over r = alpha(v), omega(v) and the c_k between them.
+ * Counts are exact below 2^32 and stored as 2^32 above (any value >= n bounds
+ * a level).  Outputs (host arrays, any may be NULL):
+ *   S_lb[n], r_lb[n]: the minimising (S~, r); r_lb = 1 for out-degree 0
+ *                     (closeness 0); farness >= (n-1) S_lb / (r_lb - 1)^2;
+ *   key[n]:           floor(S_lb * 2^46 / (r_lb - 1)^2) (UINT64_MAX if r_lb = 1);
+ *   order[n]:         the vertices of out-degree >= 1 by (key, id), *n_order of them;
+ *   *levels:          sweeps run.
+ * Results are cached on g per max_levels.  Errors: TKC_EINVAL (max_levels >
+ * 65535), TKC_ENOMEM, TKC_ECUDA. */
+int tkc_nb_bounds(tkc_graph *g, uint32_t max_levels, uint64_t *S_lb, uint32_t *r_lb, uint64_t *key,
+                  uint32_t *order, uint32_t *n_order, uint32_t *levels);
 
 /* Exact S(v) and r(v) of the listed sources by full BFS on the device, in
  * batches of 64 sources (no cutting).  srcs, S, r: host arrays of nsrc. */
@@ -211,7 +239,7 @@ uint64_t tkc_kernel_launches(void);
 
 /* Standardized features of every vertex into DEVICE array x[n][5]:
  * log1p of out-degree, in-degree, the 2-walk count sum of out-degrees of
- * out-neighbours (Lemma 1's gamma at d = 1, a bound on the 2-hop ball), an
+ * out-neighbours (the Section 6 lemma's gamma at d = 1, a bound on the 2-hop ball), an
  * h-index estimate of the core number (4 steps from the degree, out- and
  * in-neighbours), and the SCC size (component size if undirected); each
  * feature shifted and scaled to mean 0, variance 1 over the graph. */

@@ -13,7 +13,7 @@ Functions and what pins them (see ``tests/test_oracle.py``):
   scc             Tarjan                         mutual reachability by brute force
   alpha_omega     Algorithm 6                    alpha <= r <= omega, exact hand-built DAGs
   tree_sums       Algorithm 2                    BFS on random trees
-  cut_bounds      Lemma 1 per level              invariants: <= S, non-decreasing, ends at S
+  cut_bounds      Sec. 6 lemma / level           invariants: <= S, non-decreasing, ends at S
   bfscut          Algorithm 1 + Algorithm 4      textbook top-k on thousands of graphs
   nb_bounds       Algorithm 3, Eq. 3, Eq. 6      brute-force walk counts, exact on trees and
                                                  cycles, hand-computed hypercube, <= S/(r-1)^2,
@@ -189,7 +189,7 @@ def cut_bounds(g, v, maxlev=256):
 
 
 def cut_min(Sd, d, nd, g, lo, hi):
-    """(L, r): the r in [max(lo, nd), hi] minimising the Lemma 1 farness bound."""
+    """(L, r): the r in [max(lo, nd), hi] minimising the Section 6 lemma's farness bound."""
     L = ctypes.c_uint64()
     r = ctypes.c_uint64()
     _load().orc_cut_min(Sd, d, nd, g, lo, hi, ctypes.byref(L), ctypes.byref(r))

@@ -627,7 +627,7 @@ out:
 }
 
 /* ---------------------------------------------------------------------- */
-/* BFSCut lower bound (Section 6, Lemma 1 with the Section 8.2 reading)     */
+/* BFSCut lower bound (Section 6's lemma, with the Section 8.2 reading)     */
 /* ---------------------------------------------------------------------- */
 
 /*
@@ -636,13 +636,13 @@ out:
  *   g    = upper bound on |Gamma_{d+1}(v)|: the sum of outdeg(w) over
  *          Gamma_d(v) for directed graphs, of deg(w)-1 for undirected graphs
  *          at d >= 1, and deg(v) at d = 0.
- * Lemma 1 gives S(v) >= S_d - |Gamma_{d+1}| + (d+2)(r - n_d) for the true
+ * Section 6's lemma gives S(v) >= S_d - |Gamma_{d+1}| + (d+2)(r - n_d) for the true
  * r = r(v), with |Gamma_{d+1}| <= g.  Because also |Gamma_{d+1}| <= r - n_d,
  *   L_d(r) = S_d + (d+1)(r - n_d) + max(0, r - n_d - g)
  * is a lower bound on S(v) at r = r(v).  r(v) lies in [max(alpha, n_d), omega];
  * L_d(r)/(r-1)^2 is minimised over that interval at an end point or at the
  * kink r = n_d + g (it is linear on each side of the kink, and a linear L makes
- * the ratio's minimum fall at an end point of the piece, Lemma 2).
+ * the ratio's minimum fall at an end point of the piece, Section 8's lemma).
  *
  * Returns 1 if the farness bound exceeds the threshold (Sx, rx) strictly at
  * every candidate r, i.e. the vertex can be abandoned.  have_x = 0 means fewer

@@ -232,6 +232,7 @@ struct RunSetup {
   int W;
   int nocut;
   u32 nocut_prefix;
+  const u64 *lb_key;        // NBCut order keys (nullptr: no stop test)
   u32 kk;                   // list length per graph
   u32 ng;
   const u32 *gid;           // nullptr for one graph
@@ -297,6 +298,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.B = rs.B;
   p.nocut = rs.nocut;
   p.nocut_prefix = rs.nocut_prefix;
+  p.lb_key = rs.lb_key;
   p.teams = T;
   p.row_stride = (u64)w.n_cap * w.words_cap;
   p.vtx_stride = w.n_cap;
@@ -498,9 +500,16 @@ const char *tkc_strerror(int code) {
 
 static void tune_cache_load(tkc_ctx *ctx);
 
+static bool options_valid(const tkc_options *opt) {
+  const u32 b = opt->batch_bits;
+  if (!(b == 0 || b == 1 || b == 64 || b == 128 || b == 256 || b == 512)) return false;
+  return opt->order <= TKC_ORDER_NB && opt->nb_levels <= 65535;
+}
+
 int tkc_create(tkc_ctx **out, const tkc_options *opt) {
   if (!out) return TKC_EINVAL;
   *out = nullptr;
+  if (opt && !options_valid(opt)) return TKC_EINVAL;
   tkc_ctx *ctx = new (std::nothrow) tkc_ctx();
   if (!ctx) return TKC_ENOMEM;
   if (opt) ctx->opt = *opt;
@@ -535,9 +544,7 @@ int tkc_create(tkc_ctx **out, const tkc_options *opt) {
 int tkc_set_options(tkc_ctx *ctx, const tkc_options *opt) {
   if (!ctx || !opt) return TKC_EINVAL;
   if (opt->device != ctx->device) return TKC_EINVAL;
-  u32 b = opt->batch_bits;
-  if (!(b == 0 || b == 1 || b == 64 || b == 128 || b == 256 || b == 512)) return TKC_EINVAL;
-  if (opt->order > TKC_ORDER_LEARNED) return TKC_EINVAL;
+  if (!options_valid(opt)) return TKC_EINVAL;
   ctx->opt = *opt;
   ctx->stream = (cudaStream_t)opt->stream;
   return TKC_OK;
@@ -615,7 +622,7 @@ void tkc_free_graph(tkc_graph *g) {
   if (g->ioff && g->ioff != g->off) cudaFree(g->ioff);
   if (g->icol && g->icol != g->col) cudaFree(g->icol);
   void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega, g->scc_size, g->features,
-                  g->learned_order, g->seeded_order};
+                  g->learned_order, g->seeded_order, g->nb_order, g->nb_S, g->nb_r, g->nb_key};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   g->ctx->graphs_alive--;
@@ -673,8 +680,17 @@ static void reset_result(tkc_result *r, u32 kk) {
   r->batch_bits = 0;
 }
 
-static int source_order_of(tkc_graph *g, const tkc_options &o, u32 kk, const u32 **order, u32 *norder) {
-  if (o.order == TKC_ORDER_GIVEN) {
+static u32 nb_levels_of(const tkc_options &o) { return o.nb_levels ? o.nb_levels : 256u; }
+
+static int source_order_of(tkc_graph *g, const tkc_options &o, u32 kk, const u32 **order, u32 *norder,
+                           const u64 **lb_key) {
+  *lb_key = nullptr;
+  if (o.order == TKC_ORDER_NB) {
+    TKC_RC(ensure_nb_bounds(g, nb_levels_of(o)));
+    *order = g->nb_order;
+    *norder = g->n_src_nb;
+    *lb_key = g->nb_key;
+  } else if (o.order == TKC_ORDER_GIVEN) {
     if (!g->given_order) return TKC_EINVAL;
     *order = g->given_order;
     *norder = g->n_src_given;
@@ -784,7 +800,7 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   RunSetup rs;
   memset(&rs, 0, sizeof(rs));
   const tkc_options &o = ctx->opt;
-  TKC_RC(source_order_of(g, o, kk, &rs.order, &rs.norder));
+  TKC_RC(source_order_of(g, o, kk, &rs.order, &rs.norder, &rs.lb_key));
   TKC_TRY(cudaEventRecord(ctx->ev[1], st));
   u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g->n);
   tkc_options saved = ctx->opt;

@@ -12,7 +12,7 @@
 //            out-degree sums by warp bit-transpose + popcount; old F rows cleared;
 //   epilogue (last block to reach the grid barrier): per-slot S, n_d, gamma,
 //            merge of finished searches into the top-k, x = k-th farness, the
-//            BFSCut test of Lemma 1 at r in [alpha', omega] (Section 8.2), and
+//            BFSCut test of the Section 6 lemma at r in [alpha', omega] (Section 8.2), and
 //            the next step's direction.
 // When every slot of a batch is done, a clear step zeroes the rows the batch
 // touched and the epilogue seeds the next batch from the source order,
@@ -96,7 +96,7 @@ __device__ __forceinline__ bool team_sync(Ctl *ctl, Shared *sh, unsigned nblocks
 
 // ------------------------------------------------------------------ exact arithmetic
 
-// Lemma 1 at radius d, evaluated at reach r >= nd:
+// The Section 6 lemma at radius d, evaluated at reach r >= nd:
 //   L = S_d + (d+1)(r - n_d) + max(0, r - n_d - g)
 __device__ __forceinline__ u64 cut_sum(u64 Sd, u64 d, u64 nd, u64 g, u64 r) {
   u64 rem = r - nd;
@@ -110,8 +110,8 @@ __device__ __forceinline__ bool ratio_less(u64 a, u64 ra, u64 b, u64 rb) {
 
 // True when the farness lower bound exceeds x = (Sx, rx) strictly for every
 // r in [max(lo, nd), hi].  The bound divided by (r-1)^2 is linear-over-square
-// on [lo', kink] and on [kink, hi] (kink = nd + g), so by Lemma 2 its minimum
-// over the interval is at lo', hi or the kink.
+// on [lo', kink] and on [kink, hi] (kink = nd + g), so by the Section 8 lemma
+// on such bounds its minimum over the interval is at lo', hi or the kink.
 __device__ bool cut_exceeds(u64 Sd, u64 d, u64 nd, u64 g, u64 lo, u64 hi, u64 Sx, u64 rx) {
   if (lo < nd) lo = nd;
   if (hi < lo) hi = lo;
@@ -126,6 +126,13 @@ __device__ bool cut_exceeds(u64 Sd, u64 d, u64 nd, u64 g, u64 lo, u64 hi, u64 Sx
     if (!ratio_less(Sx, rx, L, r)) return false;
   }
   return true;
+}
+
+// NBCut's stop (Algorithm 1 with computeBoundsNB): the source's order key
+// floor(2^46 L') with L' <= S/(r-1)^2 exceeds x = Sx/(rx-1)^2 strictly.  The
+// order is sorted by key, so every later source of the graph exceeds x too.
+__device__ __forceinline__ bool nb_exceeds(u64 key, u64 Sx, u64 rx) {
+  return (u128)key * (u128)((rx - 1) * (rx - 1)) > ((u128)Sx << 46);
 }
 
 // (S, r, id) order: farness ascending, then id ascending.  r >= 2 here.
@@ -743,12 +750,15 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     uint32_t a = valid ? p.alpha[v] : 0, o = valid ? p.omega[v] : 0;
     uint32_t gv = (valid && p.gid) ? p.gid[v] : 0;
     // level 0: S_0 = 0, n_0 = 1, gamma_1 = out-degree
-    bool cut = false;
+    bool cut = false, stop = false;
     if (valid && !p.nocut && idx >= p.nocut_prefix) {
       Thresh x = thresh_of(p, gv);
-      cut = x.have && cut_exceeds(0, 0, 1, od, a, o, x.S, x.r);
+      stop = x.have && p.lb_key && nb_exceeds(p.lb_key[v], x.S, x.r);
+      cut = !stop && x.have && cut_exceeds(0, 0, 1, od, a, o, x.S, x.r);
     }
-    const bool take = valid && !cut;
+    // one graph: nothing after a stopped position is searched, by any team
+    if (stop && !p.gid) atomicMax(&p.sh->cursor, p.norder);
+    const bool take = valid && !cut && !stop;
     uint32_t total;
     uint32_t pre = block_exscan(sm, take ? 1u : 0u, &total);
     if (cut) {

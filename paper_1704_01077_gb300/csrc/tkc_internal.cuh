@@ -130,6 +130,10 @@ struct RunParams {
   uint32_t B;         // active slots per batch (1..64*W)
   int nocut;          // 1: never cut (exact S, r for every source)
   uint32_t nocut_prefix;  // sources at order positions below this are never cut
+  // NBCut (nullptr: off): per-vertex floor(2^46 * bound on S/(r-1)^2), the
+  // order sorted by it; seeding stops at the first source whose key exceeds
+  // its graph's k-th farness strictly
+  const unsigned long long *lb_key;
   uint32_t bu_num, bu_den;
   uint64_t timeout;
   // workspace
@@ -236,6 +240,13 @@ struct tkc_graph {
   uint32_t *seeded_order = nullptr;           // predicted-closest prefix, then the degree order
   uint64_t seeded_version = 0;
   uint32_t seeded_prefix = 0;
+  uint32_t *nb_order = nullptr;               // NBCut order: out-degree >= 1, by (nb_key, id)
+  uint32_t n_src_nb = 0;
+  uint32_t nb_cap = 0;                        // level cap the bounds were computed with (0 = none yet)
+  uint32_t nb_levels = 0;                     // sweeps run
+  unsigned long long *nb_S = nullptr;         // neighbourhood bound: S~ at the minimising reach
+  uint32_t *nb_r = nullptr;                   //   that reach (1: out-degree 0)
+  unsigned long long *nb_key = nullptr;       //   floor(S~ * 2^46 / (r-1)^2)
 };
 
 namespace tkc {
@@ -245,6 +256,8 @@ int build_in_csr(tkc_graph *g);
 int ensure_degree_order(tkc_graph *g);
 int ensure_reach_bounds(tkc_graph *g);
 int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
+// tkc_nb.cu
+int ensure_nb_bounds(tkc_graph *g, uint32_t max_levels);
 // tkc_mlp.cu
 int ensure_features(tkc_graph *g);
 int ensure_learned_order(tkc_graph *g);

@@ -44,7 +44,7 @@ unsigned grid_of(u64 work, unsigned tpb = 256, unsigned cap = 152 * 16) {
 // ---------------------------------------------------------------- features
 
 // 2-walk count: sum of out-degrees of the out-neighbours (the gamma bound of
-// Lemma 1 at d = 1, an upper bound on the 2-hop ball), one warp per vertex.
+// the Section 6 lemma at d = 1, an upper bound on the 2-hop ball), one warp per vertex.
 __global__ void k_two_walks(const u32 *off, const u32 *col, u32 n, float *w2) {
   const int lane = threadIdx.x & 31;
   for (u32 v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {

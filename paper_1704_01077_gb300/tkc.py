@@ -31,6 +31,7 @@ TKC_EOVERFLOW = -6
 TKC_ORDER_DEG = 0
 TKC_ORDER_GIVEN = 1
 TKC_ORDER_LEARNED = 2
+TKC_ORDER_NB = 3
 TKC_MAX_K = 1024
 TKC_NOALLOC_MAX_N = 65536
 TKC_MLP_FEATURES = 5
@@ -48,7 +49,7 @@ class tkc_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("order", ctypes.c_uint32),
                 ("batch_bits", ctypes.c_uint32), ("bu_num", ctypes.c_uint32), ("bu_den", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("seed_factor", ctypes.c_uint32),
-                ("timeout_cycles", ctypes.c_uint64), ("teams", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("timeout_cycles", ctypes.c_uint64), ("teams", ctypes.c_uint32), ("nb_levels", ctypes.c_uint32)]
 
 
 class tkc_result(ctypes.Structure):
@@ -67,7 +68,7 @@ EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc
             "tkc_topk_closeness", "tkc_topk_closeness_multi", "tkc_source_order", "tkc_set_source_order",
             "tkc_reach_bounds", "tkc_distance_sums", "tkc_distance_sums_noalloc", "tkc_kernel_launches",
             "tkc_strerror", "tkc_vertex_features", "tkc_mlp_init", "tkc_set_source_model", "tkc_get_source_model",
-            "tkc_mlp_forward", "tkc_mlp_gradient", "tkc_mlp_train_step", "tkc_autotune"]
+            "tkc_mlp_forward", "tkc_mlp_gradient", "tkc_mlp_train_step", "tkc_autotune", "tkc_nb_bounds"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -103,6 +104,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tkc_mlp_gradient.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, fp]
     lib.tkc_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_float, fp]
     lib.tkc_autotune.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(tkc_options)]
+    lib.tkc_nb_bounds.argtypes = [vp, ctypes.c_uint32, u64p, u32p, u64p, u32p, u32p, u32p]
     lib.tkc_kernel_launches.argtypes = []
     lib.tkc_kernel_launches.restype = ctypes.c_uint64
     lib.tkc_strerror.argtypes = [ctypes.c_int]
@@ -161,10 +163,11 @@ class Options:
     seed_factor: int = 0
     timeout_cycles: int = 0
     teams: int = 0
+    nb_levels: int = 0
 
     def to_c(self) -> tkc_options:
         return tkc_options(self.device, self.stream, self.order, self.batch_bits, self.bu_num, self.bu_den,
-                           self.blocks, self.seed_factor, self.timeout_cycles, self.teams, 0)
+                           self.blocks, self.seed_factor, self.timeout_cycles, self.teams, self.nb_levels)
 
 
 @dataclass
@@ -293,6 +296,27 @@ def tkc_reach_bounds(g, n: int) -> tuple[np.ndarray, np.ndarray]:
     o = np.zeros(max(n, 1), np.uint32)
     _check(_lib.tkc_reach_bounds(g, _u32p(a), _u32p(o)), "tkc_reach_bounds")
     return a[:n], o[:n]
+
+
+@dataclass
+class NBBounds:
+    S: np.ndarray       # S~ at the minimising reach
+    r: np.ndarray       # that reach (1: out-degree 0)
+    key: np.ndarray     # floor(S * 2^46 / (r-1)^2)
+    order: np.ndarray   # out-degree >= 1 vertices by (key, id)
+    levels: int
+
+
+def tkc_nb_bounds(g, n: int, max_levels: int = 0) -> NBBounds:
+    S = np.zeros(max(n, 1), np.uint64)
+    r = np.zeros(max(n, 1), np.uint32)
+    key = np.zeros(max(n, 1), np.uint64)
+    order = np.zeros(max(n, 1), np.uint32)
+    cnt = ctypes.c_uint32(0)
+    lev = ctypes.c_uint32(0)
+    _check(_lib.tkc_nb_bounds(g, max_levels, _u64p(S), _u32p(r), _u64p(key), _u32p(order), ctypes.byref(cnt),
+                              ctypes.byref(lev)), "tkc_nb_bounds")
+    return NBBounds(S[:n], r[:n], key[:n], order[: cnt.value], int(lev.value))
 
 
 def tkc_distance_sums(g, sources) -> tuple[np.ndarray, np.ndarray]:

@@ -62,7 +62,7 @@ def test_constants_match_header():
 
     text = open(HEADER).read()
     for name in ("TKC_OK", "TKC_EINVAL", "TKC_EGRAPH", "TKC_ENOMEM", "TKC_ECUDA", "TKC_ETIMEOUT",
-                 "TKC_EOVERFLOW", "TKC_ORDER_DEG", "TKC_ORDER_GIVEN", "TKC_ORDER_LEARNED", "TKC_MAX_K",
+                 "TKC_EOVERFLOW", "TKC_ORDER_DEG", "TKC_ORDER_GIVEN", "TKC_ORDER_LEARNED", "TKC_ORDER_NB", "TKC_MAX_K",
                  "TKC_NOALLOC_MAX_N", "TKC_MLP_FEATURES", "TKC_MLP_HIDDEN", "TKC_MLP_PARAMS"):
         m = re.search(rf"#define {name} (-?\d+)", text)
         assert m and int(m.group(1)) == getattr(tkc, name), name

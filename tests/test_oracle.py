@@ -300,7 +300,7 @@ def test_cut_bound_invariants():
 
 
 def test_cut_min_is_minimum_over_whole_interval():
-    """Lemma 2: the bound's minimum over [alpha', omega] is at a candidate point;
+    """Section 8's lemma: the bound's minimum over [alpha', omega] is at a candidate point;
     brute force over every integer r with exact rationals."""
     rng = np.random.default_rng(17)
     for _ in range(3000):
