@@ -2,6 +2,7 @@
 
 One step = one full pass of the method through the C ABI: load the CSR
 (validate, in-arc CSR), degree order, reach bounds (SCC / Algorithm 6), the
+source order (by default computeBoundsNB: NBCut; --order degree: DegCut), the
 persistent batched BFSCut kernel, and the output.  The metric is GTEPS =
 edges_visited (the paper's m_vis: arcs of every expanded BFS level) per second
 of step wall time, with the exact top-10 checked against a CPU-oracle sample.
@@ -66,13 +67,13 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(workload: str, bits: int):
+def ncu_traffic(workload: str, order: str, bits: int):
     """Per-launch DRAM bytes of the search kernel from a committed ncu summary,
     only if it was taken on the current kernel source."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
-        e = d.get(f"{workload}_b{bits}")
+        e = d.get(f"{workload}_{order}_b{bits}")
         if e and e.get("kernel_sha") == kernel_hash():
             return e["dram_bytes_per_launch"], e
     except Exception:
@@ -194,7 +195,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--k", type=int, default=0, help="top-k (0 = the workload's k)")
-    ap.add_argument("--order", default="degree", choices=["degree", "nb", "learned", "learned-seed"],
+    ap.add_argument("--order", default="nb", choices=["degree", "nb", "learned", "learned-seed"],
                     help="source order: degree bound (DegCut), neighbourhood bound with its stop (NBCut), "
                          "learned model, or learned seeding prefix + degree")
     ap.add_argument("--nb-levels", type=int, default=0, help="NBCut: most sweeps of the bound (0 = 256)")
@@ -314,7 +315,7 @@ def main():
     kern_ms = statistics.mean(r.ms_kernel for r in results)
     alg = statistics.mean(r.alg_bytes for r in results)
     achieved = alg / (kern_ms / 1e3) / 1e9
-    traffic, traffic_entry = ncu_traffic(args.workload, res.batch_bits)
+    traffic, traffic_entry = ncu_traffic(args.workload, args.order, res.batch_bits)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_src,
                 "alg_bytes_per_launch": alg, "kernel_ms": kern_ms}

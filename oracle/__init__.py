@@ -77,7 +77,13 @@ def _bind(lib):
                                _u64p, _u32p, _u32p, ctypes.POINTER(Counters), _u64p, _u32p, ctypes.c_uint32,
                                _u64p]
     lib.orc_nb_bounds.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, _u32p, _u32p, ctypes.c_uint32,
-                                  _u64p, _u32p, _u64p, _u64p, ctypes.c_uint32]
+                                  _u64p, _u32p, _u64p, _u64p, ctypes.c_uint32, _dp]
+    lib.orc_harmonic_sums.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u32p, _dp, _u32p,
+                                      ctypes.c_int]
+    lib.orc_harmonic_topk.argtypes = [ctypes.c_uint32, _dp, ctypes.c_uint32, _u32p, _u32p]
+    lib.orc_bfscut_harmonic.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p, _dp,
+                                        _u32p, _dp, _u32p, _u32p, ctypes.POINTER(Counters), _dp, _u32p,
+                                        ctypes.c_uint32]
     return lib
 
 
@@ -249,6 +255,7 @@ class NBBounds:
     key: np.ndarray     # floor(S * 2^46 / (r-1)^2); UINT64_MAX when r = 1
     levels: int         # sweeps run
     counts: np.ndarray | None = None  # counts[k][v] = N~_k(v)
+    h_ub: np.ndarray | None = None    # harmonic-centrality upper bound
 
 
 def nb_bounds(g, max_levels=NB_DEFAULT_LEVELS, counts_levels=0, alpha=None, omega=None) -> NBBounds:
@@ -264,11 +271,12 @@ def nb_bounds(g, max_levels=NB_DEFAULT_LEVELS, counts_levels=0, alpha=None, omeg
     r = np.zeros(n1, np.uint32)
     key = np.zeros(n1, np.uint64)
     counts = np.zeros((max(counts_levels, 1), n1), np.uint64) if counts_levels else None
+    hub = np.zeros(n1, np.float64)
     lev = _check(_load().orc_nb_bounds(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), _p(a, _u32p),
                                        _p(o, _u32p), max_levels, _p(S, _u64p), _p(r, _u32p), _p(key, _u64p),
-                                       _p(counts, _u64p), counts_levels))
+                                       _p(counts, _u64p), counts_levels, _p(hub, _dp)))
     return NBBounds(S[: g.n], r[: g.n], key[: g.n], int(lev),
-                    None if counts is None else counts[:, : g.n])
+                    None if counts is None else counts[:, : g.n], hub[: g.n])
 
 
 def nb_order(g, key):
@@ -278,3 +286,73 @@ def nb_order(g, key):
     ids = np.nonzero(deg > 0)[0].astype(np.uint32)
     key = np.asarray(key, dtype=np.uint64)[ids]
     return ids[np.lexsort((ids, key))]
+
+
+# ---------------------------------------------------------------- harmonic centrality
+
+def harmonic_sums(g, sources=None, threads: int = 0):
+    """Textbook h(v) = sum over w != v of 1/d(v,w) (per-level FP64 sums) and r(v)."""
+    off, col = _csr(g)
+    srcs = None if sources is None else np.ascontiguousarray(sources, dtype=np.uint32)
+    cnt = g.n if srcs is None else len(srcs)
+    H = np.zeros(max(cnt, 1), np.float64)
+    r = np.zeros(max(cnt, 1), np.uint32)
+    _check(_load().orc_harmonic_sums(g.n, _p(off, _u32p), _p(col, _u32p), cnt, _p(srcs, _u32p), _p(H, _dp),
+                                     _p(r, _u32p), threads))
+    return H[:cnt], r[:cnt]
+
+
+def harmonic_topk(H, k):
+    n = len(H)
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    ids = np.zeros(max(min(k, n), 1), np.uint32)
+    tied = ctypes.c_uint32(0)
+    cnt = _check(_load().orc_harmonic_topk(n, _p(H, _dp), k, _p(ids, _u32p), ctypes.byref(tied)))
+    return ids[:cnt], int(tied.value)
+
+
+@dataclass
+class HarmonicTopK:
+    ids: np.ndarray
+    H: np.ndarray
+    r: np.ndarray
+    n_tied: int
+    counters: Counters | None = None
+    all_H: np.ndarray | None = None
+    all_r: np.ndarray | None = None
+
+
+def textbook_harmonic_topk(g, k, threads: int = 0) -> HarmonicTopK:
+    H, r = harmonic_sums(g, threads=threads)
+    ids, tied = harmonic_topk(H, k)
+    return HarmonicTopK(ids, H[ids], r[ids], tied)
+
+
+def bfscut_harmonic(g, k, order=None, ub=None, want_all=False, max_sources=0) -> HarmonicTopK:
+    """Algorithm 1 + BFSCut for harmonic centrality (degree order or `order`);
+    ub with `order` sorted by decreasing ub gives the NBCut stop."""
+    off, col = _csr(g)
+    kk = min(k, g.n)
+    ids = np.zeros(max(kk, 1), np.uint32)
+    H = np.zeros(max(kk, 1), np.float64)
+    r = np.zeros(max(kk, 1), np.uint32)
+    tied = ctypes.c_uint32(0)
+    ctr = Counters()
+    order_a = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
+    ub_a = None if ub is None else np.ascontiguousarray(ub, dtype=np.float64)
+    allH = np.zeros(max(g.n, 1), np.float64) if want_all else None
+    allr = np.zeros(max(g.n, 1), np.uint32) if want_all else None
+    cnt = _check(_load().orc_bfscut_harmonic(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), k,
+                                             _p(order_a, _u32p), _p(ub_a, _dp), _p(ids, _u32p), _p(H, _dp),
+                                             _p(r, _u32p), ctypes.byref(tied), ctypes.byref(ctr), _p(allH, _dp),
+                                             _p(allr, _u32p), max_sources))
+    return HarmonicTopK(ids[:cnt], H[:cnt], r[:cnt], int(tied.value), ctr,
+                        None if allH is None else allH[: g.n], None if allr is None else allr[: g.n])
+
+
+def nb_harmonic_order(g, h_ub):
+    """Sources of out-degree >= 1 by decreasing harmonic upper bound, ties by id."""
+    deg = np.diff(np.asarray(g.offsets, dtype=np.int64))
+    ids = np.nonzero(deg > 0)[0].astype(np.uint32)
+    h = np.asarray(h_ub, dtype=np.float64)[ids]
+    return ids[np.lexsort((ids, -h))]

@@ -521,11 +521,15 @@ static void nb_candidate(uint64_t S, uint64_t r, int *have, uint64_t *bS, uint64
  * not NULL, receives N~_k(v) at counts[k * n + v] for k < counts_levels
  * (sweeps continue until then even if all vertices have finished).  Returns
  * the number of sweeps run, or a negative code.  alpha/omega: Algorithm 6
- * bounds (exact component size if undirected).
+ * bounds (exact component size if undirected).  h_ub, if not NULL, receives
+ * the harmonic-centrality counterpart (see the harmonic section below):
+ * the sum over k of min(N~_k, max(omega - c_{k-1}, 0)) / k in increasing k, plus
+ * (omega - c_K) / (K+1) for a vertex unfinished at the level cap.
  */
 int orc_nb_bounds(uint32_t n, const uint32_t *off, const uint32_t *col, int directed,
                   const uint32_t *alpha, const uint32_t *omega, uint32_t max_levels,
-                  uint64_t *S_lb, uint32_t *r_lb, uint64_t *key, uint64_t *counts, uint32_t counts_levels) {
+                  uint64_t *S_lb, uint32_t *r_lb, uint64_t *key, uint64_t *counts, uint32_t counts_levels,
+                  double *h_ub) {
   if (n == 0) return 0;
   if (max_levels == 0 || max_levels > 65535) return ORC_EINVAL;
   uint64_t *Nk2 = (uint64_t *)malloc((size_t)n * sizeof(uint64_t)); /* N~_{k-2} */
@@ -545,6 +549,7 @@ int orc_nb_bounds(uint32_t n, const uint32_t *off, const uint32_t *col, int dire
     Nk1[s] = 1; /* N~_0 */
     nVisited[s] = 1;
     Ssum[s] = 0;
+    if (h_ub) h_ub[s] = 0.0;
     if (counts && counts_levels > 0) counts[s] = 1;
   }
   uint32_t k;
@@ -592,17 +597,20 @@ int orc_nb_bounds(uint32_t n, const uint32_t *off, const uint32_t *col, int dire
       if (c1 > a && c1 < o) nb_candidate(P0 + (uint64_t)k * Nks, c1, &have[s], &bS[s], &br[s]);
       if (o <= c1) {
         nb_candidate(P0 + (uint64_t)k * (o - c0), o, &have[s], &bS[s], &br[s]);
+        if (h_ub) h_ub[s] = h_ub[s] + (double)(o - c0) / (double)k;
         finished[s] = 1;
         ++nFinished;
         continue;
       }
       nVisited[s] = c1;
       Ssum[s] = P0 + (uint64_t)k * Nks;
+      if (h_ub) h_ub[s] = h_ub[s] + (double)Nks / (double)k;
       if (k == max_levels) {
         /* level K+1 unbounded: slope K+1 from c_K up to omega */
         const uint64_t P1 = Ssum[s];
         if (a > c1) nb_candidate(P1 + (uint64_t)(k + 1) * (a - c1), a, &have[s], &bS[s], &br[s]);
         nb_candidate(P1 + (uint64_t)(k + 1) * (o - c1), o, &have[s], &bS[s], &br[s]);
+        if (h_ub) h_ub[s] = h_ub[s] + (double)(o - c1) / (double)(k + 1);
         finished[s] = 1;
         ++nFinished;
       }
@@ -891,5 +899,258 @@ int orc_bfscut(uint32_t n, const uint32_t *off, const uint32_t *col, int directe
   rc = (int)kk;
 done:
   free(order); free(alpha); free(omega); free(dist); free(queue); free(fS); free(fr); free(top);
+  return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Harmonic centrality (Section 9, "Harmonic Centrality"): the same method  */
+/* for h(v) = sum over w != v of 1/d(v,w), largest first                    */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Readings (the paper states only that its bounds carry over to measures
+ * sum_w f(d(v,w)) with f decreasing and f(inf) = 0):
+ *  - The FP64 value of h(v) is formed per BFS level: the count c_d of vertices
+ *    at distance d divided by d, these quotients added in increasing d, every
+ *    operation rounded to nearest with no contraction.  The oracle and the
+ *    library form it the same way, so the same counts give the same bits; the
+ *    top-k is ranked by that value, ties by smaller id.
+ *  - BFSCut's bound after level d (the Section 6 lemma with f = 1/d): the
+ *    vertices not yet found lie at distance >= d+1, at most g of them (the same
+ *    gamma as for closeness) at d+1, and there are at most omega - n_d of them,
+ *    so h(v) <= U_d = H_d + min(g, w)/(d+1) + max(0, w - g)/(d+2), w = omega - n_d.
+ *    U_d grows with the reach, so omega alone bounds it (alpha is not needed).
+ *  - Rounding: the FP64 h may exceed the exact h by (D+1) units in the last
+ *    place and the computed U_d fall short of the exact bound by (d+3); a
+ *    search is abandoned only when fl(U_d * (1 + 2^-20)) < x, which implies
+ *    h_fp64(v) < x for every depth below 2^32.  Strict: a vertex tied with the
+ *    k-th is never abandoned.
+ *  - computeBoundsNB for h: with the same level-size bounds N~_k, assigning as
+ *    many vertices as possible to the nearest levels maximises sum 1/d, so
+ *    h(v) <= sum_k min(N~_k, max(omega - c_{k-1}, 0)) / k (quotients added in
+ *    increasing k; after a level cap K the remaining omega - c_K vertices count
+ *    at distance K+1).  Sources go in decreasing order of this bound, ties by
+ *    id, and Algorithm 1 stops at the first one whose bound (times 1 + 2^-20)
+ *    is below x.
+ */
+#define ORC_H_MARGIN (1.0 + 1.0 / 1048576.0)
+
+/* BFS from s counting each level; returns h(v) as defined above, r(v) and the
+ * arcs scanned. */
+static double bfs_harmonic_one(const uint32_t *off, const uint32_t *col, uint32_t s, uint32_t *dist,
+                               uint32_t *queue, uint32_t *r_out) {
+  uint32_t head = 0, tail = 0, d = 0;
+  double h = 0.0;
+  dist[s] = 0;
+  queue[tail++] = s;
+  while (head < tail) {
+    uint32_t end = tail;
+    uint64_t cnt = 0;
+    while (head < end) {
+      uint32_t u = queue[head++];
+      for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+        uint32_t w = col[e];
+        if (dist[w] == UINT32_MAX) {
+          dist[w] = d + 1;
+          queue[tail++] = w;
+          ++cnt;
+        }
+      }
+    }
+    if (cnt == 0) break;
+    ++d;
+    h = h + (double)cnt / (double)d;
+  }
+  for (uint32_t i = 0; i < tail; ++i) dist[queue[i]] = UINT32_MAX;
+  *r_out = tail;
+  return h;
+}
+
+/* Textbook harmonic centrality: h(v) and r(v) for the listed sources (all
+ * vertices if srcs == NULL).  Pinned by exact rationals from Floyd-Warshall
+ * distances (within the rounding bound), closed forms and networkx. */
+int orc_harmonic_sums(uint32_t n, const uint32_t *off, const uint32_t *col, uint32_t nsrc,
+                      const uint32_t *srcs, double *H, uint32_t *r, int nthreads) {
+  if (n == 0) return ORC_OK;
+  int rc = ORC_OK;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+  {
+    uint32_t *dist = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    uint32_t *queue = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    if (!dist || !queue) {
+      rc = ORC_ENOMEM;
+    } else {
+      for (uint32_t i = 0; i < n; ++i) dist[i] = UINT32_MAX;
+      int64_t cnt = srcs ? (int64_t)nsrc : (int64_t)n;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+      for (int64_t i = 0; i < cnt; ++i) {
+        uint32_t s = srcs ? srcs[i] : (uint32_t)i;
+        H[i] = bfs_harmonic_one(off, col, s, dist, queue, &r[i]);
+      }
+    }
+    free(dist);
+    free(queue);
+  }
+  (void)nthreads;
+  return rc;
+}
+
+typedef struct {
+  double h;
+  uint32_t r;
+  uint32_t id;
+} hentry_t;
+
+/* larger h first, then smaller id */
+static int hentry_before(const hentry_t *a, const hentry_t *b) {
+  if (a->h != b->h) return a->h > b->h;
+  return a->id < b->id;
+}
+
+static int cmp_hentry(const void *pa, const void *pb) {
+  const hentry_t *a = (const hentry_t *)pa, *b = (const hentry_t *)pb;
+  if (hentry_before(a, b)) return -1;
+  if (hentry_before(b, a)) return 1;
+  return 0;
+}
+
+/* Top-k by harmonic centrality (largest h, ties by id) and the number of
+ * vertices whose h equals the k-th's.  Returns min(k, n). */
+int orc_harmonic_topk(uint32_t n, const double *H, uint32_t k, uint32_t *ids, uint32_t *n_tied) {
+  uint32_t kk = k < n ? k : n;
+  if (kk == 0) { if (n_tied) *n_tied = 0; return 0; }
+  hentry_t *e = (hentry_t *)malloc((size_t)n * sizeof(hentry_t));
+  if (!e) return ORC_ENOMEM;
+  for (uint32_t v = 0; v < n; ++v) { e[v].h = H[v]; e[v].r = 0; e[v].id = v; }
+  qsort(e, n, sizeof(hentry_t), cmp_hentry);
+  uint32_t t = 0;
+  for (uint32_t v = 0; v < n; ++v) t += H[v] == e[kk - 1].h;
+  for (uint32_t i = 0; i < kk; ++i) ids[i] = e[i].id;
+  if (n_tied) *n_tied = t;
+  free(e);
+  return (int)kk;
+}
+
+static void htop_insert(hentry_t *top, uint32_t *cnt, uint32_t k, double h, uint32_t r, uint32_t id) {
+  hentry_t e = {h, r, id};
+  if (*cnt == k && !hentry_before(&e, &top[k - 1])) return;
+  uint32_t i = *cnt < k ? (*cnt)++ : k - 1;
+  while (i > 0 && hentry_before(&e, &top[i - 1])) { top[i] = top[i - 1]; --i; }
+  top[i] = e;
+}
+
+/* U_d of the reading above, in this operation order. */
+static double harmonic_cut_bound(double Hd, uint32_t d, uint64_t nd, uint64_t g, uint64_t omega) {
+  uint64_t w = omega > nd ? omega - nd : 0;
+  uint64_t near = g < w ? g : w;
+  uint64_t far = w > g ? w - g : 0;
+  double t1 = (double)near / (double)(d + 1);
+  double t2 = (double)far / (double)(d + 2);
+  return (Hd + t1) + t2;
+}
+
+/*
+ * Algorithm 1 + BFSCut for harmonic centrality, one source at a time, in the
+ * degree order (or order_in).  ub (NULL = none) is computeBoundsNB's upper bound
+ * per vertex, with order_in sorted by decreasing ub: the loop stops at the first
+ * source with fl(ub * (1 + 2^-20)) < x.  Vertices of out-degree 0 have h = 0 and
+ * are not searched.  Outputs as orc_bfscut, with H in place of S.
+ */
+int orc_bfscut_harmonic(uint32_t n, const uint32_t *off, const uint32_t *col, int directed, uint32_t k,
+                        const uint32_t *order_in, const double *ub, uint32_t *ids, double *H_out, uint32_t *r_out,
+                        uint32_t *n_tied, orc_counters *ctr, double *allH, uint32_t *allr, uint32_t max_sources) {
+  if (k == 0 || n == 0) { if (n_tied) *n_tied = 0; return 0; }
+  int rc = ORC_OK;
+  uint32_t *order = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *alpha = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *omega = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *dist = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *queue = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  double *fH = (double *)calloc(n, sizeof(double));
+  uint32_t *fr = (uint32_t *)calloc(n, sizeof(uint32_t));
+  uint32_t kk = k < n ? k : n;
+  hentry_t *top = (hentry_t *)malloc((size_t)kk * sizeof(hentry_t));
+  if (!order || !alpha || !omega || !dist || !queue || !fH || !fr || !top) { rc = ORC_ENOMEM; goto done; }
+  if (order_in)
+    memcpy(order, order_in, (size_t)n * sizeof(uint32_t));
+  else if ((rc = orc_degree_order(n, off, order)) != ORC_OK)
+    goto done;
+  if ((rc = orc_alpha_omega(n, off, col, directed, alpha, omega)) != ORC_OK) goto done;
+  for (uint32_t i = 0; i < n; ++i) dist[i] = UINT32_MAX;
+  orc_counters c = {0, 0, 0, 0};
+  uint32_t ntop = 0;
+  for (uint32_t oi = 0; oi < n; ++oi) {
+    uint32_t v = order[oi];
+    if (off[v + 1] == off[v]) continue; /* h(v) = 0 */
+    if (max_sources && c.bfs_started >= max_sources) break;
+    int have_x = ntop == kk;
+    double xH = have_x ? top[kk - 1].h : 0.0;
+    if (ub && have_x && ub[v] * ORC_H_MARGIN < xH) break; /* Algorithm 1: the head of Q is bounded below x */
+    c.bfs_started++;
+    uint32_t head = 0, tail = 0;
+    dist[v] = 0;
+    queue[tail++] = v;
+    uint64_t nd = 1, g = off[v + 1] - off[v];
+    uint32_t d = 0;
+    double Hd = 0.0;
+    int cut = 0;
+    while (1) {
+      if (have_x && harmonic_cut_bound(Hd, d, nd, g, omega[v]) * ORC_H_MARGIN < xH) { cut = 1; break; }
+      uint32_t level_end = tail;
+      uint64_t cnt = 0, gs = 0;
+      while (head < level_end) {
+        uint32_t u = queue[head++];
+        c.edges_visited += off[u + 1] - off[u];
+        for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+          uint32_t w = col[e];
+          if (dist[w] == UINT32_MAX) {
+            dist[w] = d + 1;
+            queue[tail++] = w;
+            ++cnt;
+            gs += (off[w + 1] - off[w]) - (directed ? 0u : 1u);
+          }
+        }
+      }
+      if (cnt == 0) break;
+      ++d;
+      Hd = Hd + (double)cnt / (double)d;
+      nd += cnt;
+      g = gs;
+    }
+    for (uint32_t i = 0; i < tail; ++i) dist[queue[i]] = UINT32_MAX;
+    if (cut) { c.bfs_cut++; continue; }
+    c.bfs_finished++;
+    fH[v] = Hd;
+    fr[v] = (uint32_t)nd;
+    htop_insert(top, &ntop, kk, Hd, (uint32_t)nd, v);
+  }
+  /* fewer than kk searched: out-degree-0 vertices (h = 0) in id order */
+  for (uint32_t v = 0; v < n && ntop < kk; ++v)
+    if (off[v + 1] == off[v]) htop_insert(top, &ntop, kk, 0.0, 1, v);
+  for (uint32_t i = 0; i < kk; ++i) {
+    ids[i] = top[i].id;
+    if (H_out) H_out[i] = top[i].h;
+    if (r_out) r_out[i] = top[i].r;
+  }
+  if (n_tied) {
+    uint32_t t = 0;
+    const double last = top[kk - 1].h;
+    for (uint32_t v = 0; v < n; ++v) {
+      if (off[v + 1] == off[v]) t += last == 0.0;
+      else if (fr[v] && fH[v] == last) ++t;
+    }
+    *n_tied = t;
+  }
+  if (allH) memcpy(allH, fH, (size_t)n * sizeof(double));
+  if (allr) memcpy(allr, fr, (size_t)n * sizeof(uint32_t));
+  if (ctr) *ctr = c;
+  rc = (int)kk;
+done:
+  free(order); free(alpha); free(omega); free(dist); free(queue); free(fH); free(fr); free(top);
   return rc;
 }

@@ -73,6 +73,7 @@ int ensure_workspace(tkc_ctx *ctx, u32 n, int words, u32 top_entries, u32 ng, u3
     u32 cap = std::max<u32>(ng, 16);
     TKC_RC(dalloc(&w.tied, cap, st));
     TKC_RC(dalloc(&w.g_ntop, cap, st));
+    TKC_RC(dalloc(&w.g_stop, cap, st));
     TKC_RC(dalloc(&w.g_ctr, 4 * (size_t)cap, st));
     TKC_RC(dalloc(&w.x_seq, cap, st));
     TKC_RC(dalloc(&w.x_S, cap, st));
@@ -120,7 +121,7 @@ static void free_workspace(tkc_ctx *ctx) {
   Workspace &w = ctx->ws;
   void *ptrs[] = {w.seen, w.F0, w.F1, w.N, w.FB0, w.FB1, w.L0, w.L1, w.Loff0, w.Loff1, w.VL, w.stamp, w.res_S, w.res_r,
                   w.slots, w.cnt, w.wsum, w.top_S, w.top_r, w.top_id, w.ctl, w.out_S, w.out_r, w.out_id,
-                  w.out_f, w.out_c, w.tied, w.g_ntop, w.g_ctr, w.sh, w.x_seq, w.x_S, w.x_r, w.x_id};
+                  w.out_f, w.out_c, w.tied, w.g_ntop, w.g_stop, w.g_ctr, w.sh, w.x_seq, w.x_S, w.x_r, w.x_id};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -273,6 +274,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   TKC_TRY(cudaMemsetAsync(w.res_r, 0, (size_t)g->n * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(w.res_S, 0, (size_t)g->n * sizeof(u64), st));
   TKC_TRY(cudaMemsetAsync(w.g_ntop, 0, (size_t)rs.ng * sizeof(unsigned), st));
+  TKC_TRY(cudaMemsetAsync(w.g_stop, 0, (size_t)rs.ng * sizeof(unsigned), st));
   TKC_TRY(cudaMemsetAsync(w.g_ctr, 0, (size_t)rs.ng * 4 * sizeof(u64), st));
   TKC_TRY(cudaMemsetAsync(w.x_seq, 0, (size_t)rs.ng * sizeof(unsigned), st));
   TKC_TRY(cudaMemsetAsync(w.x_r, 0, (size_t)rs.ng * sizeof(u32), st));
@@ -299,6 +301,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.nocut = rs.nocut;
   p.nocut_prefix = rs.nocut_prefix;
   p.lb_key = rs.lb_key;
+  p.g_stop = w.g_stop;
   p.teams = T;
   p.row_stride = (u64)w.n_cap * w.words_cap;
   p.vtx_stride = w.n_cap;
@@ -977,7 +980,9 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
   TKC_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   const tkc_options &o = ctx->opt;
-  if (o.order != TKC_ORDER_DEG) return TKC_EINVAL;  // the union is searched in degree order
+  // the union is searched in degree order, or in NBCut order (each graph stops on its own)
+  if (o.order != TKC_ORDER_DEG && o.order != TKC_ORDER_NB) return TKC_EINVAL;
+  const bool nb = o.order == TKC_ORDER_NB;
   u64 nv64 = 0, na = 0;
   u32 maxn = 0;
   for (u32 i = 0; i < ng; ++i) {
@@ -1001,6 +1006,7 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
   for (u32 i = 0; i < ng; ++i) {
     TKC_RC(ensure_degree_order(gs[i]));
     TKC_RC(ensure_reach_bounds(gs[i]));
+    if (nb) TKC_RC(ensure_nb_bounds(gs[i], nb_levels_of(o)));
     vbase[i + 1] = vbase[i] + gs[i]->n;
     abase[i + 1] = abase[i] + gs[i]->arcs;
     offptr[i] = (u64)gs[i]->off;
@@ -1018,8 +1024,8 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
   int rc = TKC_OK;
   auto cleanup = [&]() {
     cudaStreamSynchronize(st);
-    void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, gid, d_vbase, d_abase, d_offptr,
-                    d_colptr, d_gdir};
+    void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.nb_key, U.nb_order, gid, d_vbase,
+                    d_abase, d_offptr, d_colptr, d_gdir};
     for (void *q : ptrs)
       if (q) cudaFree(q);
   };
@@ -1066,14 +1072,26 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
       MULTI_TRY(cudaMemcpyAsync(U.omega + vbase[i], gs[i]->omega, gs[i]->n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
     }
   MULTI_RC(build_in_csr(&U));
-  MULTI_RC(ensure_degree_order(&U));
+  if (nb) {
+    // every graph's keys side by side, then all sources by (key, union id)
+    MULTI_TRY(cudaMallocAsync(&U.nb_key, std::max<size_t>(nv, 1) * sizeof(u64), st));
+    MULTI_TRY(cudaMallocAsync(&U.nb_order, std::max<size_t>(nv, 1) * sizeof(u32), st));
+    for (u32 i = 0; i < ng; ++i)
+      if (gs[i]->n)
+        MULTI_TRY(cudaMemcpyAsync(U.nb_key + vbase[i], gs[i]->nb_key, gs[i]->n * sizeof(u64), cudaMemcpyDeviceToDevice,
+                                  st));
+    MULTI_RC(nb_sort_sources(&U, U.nb_key, U.nb_order, &U.n_src_nb));
+  } else {
+    MULTI_RC(ensure_degree_order(&U));
+  }
   TKC_TRY(cudaEventRecord(ctx->ev[1], st));
   RunSetup rs;
   memset(&rs, 0, sizeof(rs));
   u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(nv);
   rs.g = &U;
-  rs.order = U.deg_order;
-  rs.norder = U.n_src_deg;
+  rs.order = nb ? U.nb_order : U.deg_order;
+  rs.norder = nb ? U.n_src_nb : U.n_src_deg;
+  rs.lb_key = nb ? U.nb_key : nullptr;
   rs.B = bits;
   rs.W = words_for(bits);
   rs.nocut = 0;

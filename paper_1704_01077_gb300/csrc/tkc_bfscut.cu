@@ -751,14 +751,21 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     uint32_t gv = (valid && p.gid) ? p.gid[v] : 0;
     // level 0: S_0 = 0, n_0 = 1, gamma_1 = out-degree
     bool cut = false, stop = false;
-    if (valid && !p.nocut && idx >= p.nocut_prefix) {
+    // several graphs: a graph whose search stopped skips its later sources
+    const bool stopped = valid && p.lb_key && p.gid && *(volatile unsigned *)&p.g_stop[gv];
+    if (valid && !stopped && !p.nocut && idx >= p.nocut_prefix) {
       Thresh x = thresh_of(p, gv);
       stop = x.have && p.lb_key && nb_exceeds(p.lb_key[v], x.S, x.r);
       cut = !stop && x.have && cut_exceeds(0, 0, 1, od, a, o, x.S, x.r);
     }
-    // one graph: nothing after a stopped position is searched, by any team
-    if (stop && !p.gid) atomicMax(&p.sh->cursor, p.norder);
-    const bool take = valid && !cut && !stop;
+    // nothing after a stopped position of its graph is searched, by any team
+    if (stop) {
+      if (!p.gid)
+        atomicMax(&p.sh->cursor, p.norder);
+      else
+        *(volatile unsigned *)&p.g_stop[gv] = 1u;
+    }
+    const bool take = valid && !cut && !stop && !stopped;
     uint32_t total;
     uint32_t pre = block_exscan(sm, take ? 1u : 0u, &total);
     if (cut) {

@@ -134,6 +134,7 @@ struct RunParams {
   // order sorted by it; seeding stops at the first source whose key exceeds
   // its graph's k-th farness strictly
   const unsigned long long *lb_key;
+  unsigned int *g_stop;  // several graphs: graph g's search has stopped (its later sources are skipped)
   uint32_t bu_num, bu_den;
   uint64_t timeout;
   // workspace
@@ -175,6 +176,7 @@ struct Workspace {
   double *out_f = nullptr, *out_c = nullptr;
   unsigned int *tied = nullptr;     // per graph
   unsigned int *g_ntop = nullptr;   // per graph
+  unsigned int *g_stop = nullptr;   // per graph: NBCut stop reached
   unsigned long long *g_ctr = nullptr;  // 4 per graph
   Shared *sh = nullptr;
   unsigned int *x_seq = nullptr;
@@ -258,6 +260,7 @@ int ensure_reach_bounds(tkc_graph *g);
 int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
 // tkc_nb.cu
 int ensure_nb_bounds(tkc_graph *g, uint32_t max_levels);
+int nb_sort_sources(tkc_graph *g, const unsigned long long *key, uint32_t *order, uint32_t *count);
 // tkc_mlp.cu
 int ensure_features(tkc_graph *g);
 int ensure_learned_order(tkc_graph *g);

@@ -291,6 +291,45 @@ __global__ void k_key_hi(u32 ns, const u32 *val, const u64 *key, u32 *hi) {
 
 }  // namespace
 
+// The vertices of g with out-degree >= 1, sorted by (key, id): stable LSD radix
+// passes over the low and then the high 32 key bits, ids starting ascending.
+// Writes *count of them to order (device); synchronises the stream.
+int nb_sort_sources(tkc_graph *g, const u64 *key, u32 *order, u32 *count) {
+  cudaStream_t st = g->ctx->stream;
+  const u32 n = g->n;
+  *count = 0;
+  if (n == 0) return TKC_OK;
+  u32 *ids = nullptr, *lo = nullptr;
+  u64 *maxkey = nullptr;
+  TKC_TRY(cudaMallocAsync(&ids, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&lo, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&maxkey, sizeof(u64), st));
+  TKC_TRY(cudaMemsetAsync(maxkey, 0, sizeof(u64), st));
+  TKC_LAUNCH(k_iota<<<grid_of(n), 256, 0, st>>>(n, ids));
+  TKC_RC(filter_order(g, ids, order, count));  // synchronises
+  const u32 ns = *count;
+  if (ns) {
+    TKC_LAUNCH(k_key_parts<<<grid_of(ns), 256, 0, st>>>(ns, order, key, lo, maxkey));
+    u64 mk = 0;
+    TKC_TRY(cudaMemcpyAsync(&mk, maxkey, sizeof(u64), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaStreamSynchronize(st));
+    int bits = 0;
+    while (bits < 64 && (mk >> bits) != 0) ++bits;
+    if (bits <= 32) {
+      TKC_RC(radix_sort_u32_pairs(lo, order, ns, bits, st));
+    } else {
+      TKC_RC(radix_sort_u32_pairs(lo, order, ns, 32, st));
+      TKC_LAUNCH(k_key_hi<<<grid_of(ns), 256, 0, st>>>(ns, order, key, lo));
+      TKC_RC(radix_sort_u32_pairs(lo, order, ns, bits - 32, st));
+    }
+  }
+  TKC_TRY(cudaFreeAsync(ids, st));
+  TKC_TRY(cudaFreeAsync(lo, st));
+  TKC_TRY(cudaFreeAsync(maxkey, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  return TKC_OK;
+}
+
 // Computes the bound, the order keys and the NBCut order of g (cached until the
 // level cap changes).
 int ensure_nb_bounds(tkc_graph *g, u32 K) {
@@ -363,36 +402,12 @@ int ensure_nb_bounds(tkc_graph *g, u32 K) {
     if (h_left == 0) break;
   }
   TKC_LAUNCH(k_nb_keys<<<grid_of(n), 256, 0, st>>>(n, s, g->nb_S, g->nb_r, g->nb_key, err));
-  // NBCut order: sources of out-degree >= 1 by (key, id), stable LSD passes
-  u32 *ids = nullptr, *lo = nullptr;
-  u64 *maxkey = nullptr;
-  TKC_TRY(cudaMallocAsync(&ids, n1 * sizeof(u32), st));
-  TKC_TRY(cudaMallocAsync(&lo, n1 * sizeof(u32), st));
-  TKC_TRY(cudaMallocAsync(&maxkey, sizeof(u64), st));
-  TKC_TRY(cudaMemsetAsync(maxkey, 0, sizeof(u64), st));
-  TKC_LAUNCH(k_iota<<<grid_of(n), 256, 0, st>>>(n, ids));
-  TKC_RC(filter_order(g, ids, g->nb_order, &g->n_src_nb));  // synchronises
-  const u32 ns = g->n_src_nb;
   int h_err = 0;
   TKC_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  if (ns) {
-    TKC_LAUNCH(k_key_parts<<<grid_of(ns), 256, 0, st>>>(ns, g->nb_order, g->nb_key, lo, maxkey));
-    u64 mk = 0;
-    TKC_TRY(cudaMemcpyAsync(&mk, maxkey, sizeof(u64), cudaMemcpyDeviceToHost, st));
-    TKC_TRY(cudaStreamSynchronize(st));
-    int bits = 0;
-    while (bits < 64 && (mk >> bits) != 0) ++bits;
-    if (bits <= 32) {
-      TKC_RC(radix_sort_u32_pairs(lo, g->nb_order, ns, bits, st));
-    } else {
-      TKC_RC(radix_sort_u32_pairs(lo, g->nb_order, ns, 32, st));
-      TKC_LAUNCH(k_key_hi<<<grid_of(ns), 256, 0, st>>>(ns, g->nb_order, g->nb_key, lo));
-      TKC_RC(radix_sort_u32_pairs(lo, g->nb_order, ns, bits - 32, st));
-    }
-  }
+  TKC_RC(nb_sort_sources(g, g->nb_key, g->nb_order, &g->n_src_nb));
   TKC_TRY(cudaStreamSynchronize(st));
   for (int i = 0; i < 3; ++i) TKC_TRY(cudaFreeAsync(N[i], st));
-  void *frees[] = {s.c, s.P, s.bS, s.bR, s.flag, segpos, seg_row, seg_begin, tmp, left, err, ids, lo, maxkey};
+  void *frees[] = {s.c, s.P, s.bS, s.bR, s.flag, segpos, seg_row, seg_begin, tmp, left, err};
   for (void *p : frees)
     if (p) TKC_TRY(cudaFreeAsync(p, st));
   if (h_err) return TKC_EGRAPH;

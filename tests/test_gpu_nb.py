@@ -183,3 +183,24 @@ def test_nb_degenerate_and_options(gpu_lib, ctx):
             tkc.tkc_nb_bounds(h, 5, 70000)
     finally:
         tkc.tkc_free_graph(h)
+
+
+def test_nbcut_many_graphs_in_one_launch(gpu_lib, ctx):
+    """Several graphs, NBCut order over their union: each graph stops on its own."""
+    tkc = gpu_lib
+    gs = [gg.barabasi_albert(900, 3, 41), gg.rmat(11, 16, seed=42), gg.cycle(30), gg.path(12, directed=True),
+          gg.erdos_renyi(1500, 12000, 43, directed=True), gg.from_arcs(5, [], [], True, "empty5"),
+          gg.random_tree(400, 44), gg.hypercube(5)]
+    for bits, teams in ((1, 1), (64, 0), (256, 3)):
+        tkc.tkc_set_options(ctx, tkc.Options(batch_bits=bits, order=tkc.TKC_ORDER_NB, teams=teams))
+        hs = [tkc.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed) for g in gs]
+        try:
+            res = tkc.tkc_topk_closeness_multi(ctx, hs, 7)
+        finally:
+            for h in hs:
+                tkc.tkc_free_graph(h)
+            tkc.tkc_set_options(ctx, tkc.Options())
+        for g, got in zip(gs, res):
+            _expect_equal(got, oracle.textbook_topk(g, 7), g, 7)
+        big = res[1]
+        assert big.bfs_started < int((gs[1].outdeg() > 0).sum())
