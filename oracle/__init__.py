@@ -18,6 +18,9 @@ Functions and what pins them (see ``tests/test_oracle.py``):
   nb_bounds       Algorithm 3, Eq. 3, Eq. 6      brute-force walk counts, exact on trees and
                                                  cycles, hand-computed hypercube, <= S/(r-1)^2,
                                                  minimum over every r in [alpha, omega]
+  harmonic_*      Section 9 (harmonic centrality) exact rationals from Floyd-Warshall within
+                                                 the rounding bound, networkx, closed forms;
+                                                 BFSCut/NBCut equal to the textbook top-k
 """
 from __future__ import annotations
 
@@ -84,6 +87,8 @@ def _bind(lib):
     lib.orc_bfscut_harmonic.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p, _dp,
                                         _u32p, _dp, _u32p, _u32p, ctypes.POINTER(Counters), _dp, _u32p,
                                         ctypes.c_uint32]
+    lib.orc_harmonic_cut_bounds.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32,
+                                            ctypes.c_uint32, _dp, ctypes.c_int]
     return lib
 
 
@@ -348,6 +353,18 @@ def bfscut_harmonic(g, k, order=None, ub=None, want_all=False, max_sources=0) ->
                                              _p(allr, _u32p), max_sources))
     return HarmonicTopK(ids[:cnt], H[:cnt], r[:cnt], int(tied.value), ctr,
                         None if allH is None else allH[: g.n], None if allr is None else allr[: g.n])
+
+
+H_MARGIN = 1.0 + 2.0 ** -20   # a search is abandoned only when bound * H_MARGIN < x
+
+
+def harmonic_cut_bounds(g, v, omega_v, maxlev=256):
+    """U_0, U_1, ...: BFSCut's upper bounds on h(v) after each level, at reach omega_v."""
+    off, col = _csr(g)
+    U = np.zeros(maxlev, np.float64)
+    cnt = _check(_load().orc_harmonic_cut_bounds(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), v,
+                                                 omega_v, _p(U, _dp), maxlev))
+    return U[:cnt]
 
 
 def nb_harmonic_order(g, h_ub):

@@ -1154,3 +1154,46 @@ done:
   free(order); free(alpha); free(omega); free(dist); free(queue); free(fH); free(fr); free(top);
   return rc;
 }
+
+/* The bound sequence U_0, U_1, ... of one source for a given omega (>= r(v)),
+ * for the invariant tests: every U_d * (1 + 2^-20) >= h(v), non-increasing in
+ * exact arithmetic, and the last equals h(v) when omega = r(v).  Returns the
+ * number of levels written (at most maxlev). */
+int orc_harmonic_cut_bounds(uint32_t n, const uint32_t *off, const uint32_t *col, int directed, uint32_t v,
+                            uint32_t omega_v, double *U, int maxlev) {
+  uint32_t *dist = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *queue = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  if (!dist || !queue) { free(dist); free(queue); return ORC_ENOMEM; }
+  for (uint32_t i = 0; i < n; ++i) dist[i] = UINT32_MAX;
+  uint32_t head = 0, tail = 0, d = 0;
+  dist[v] = 0;
+  queue[tail++] = v;
+  uint64_t nd = 1, g = off[v + 1] - off[v];
+  double Hd = 0.0;
+  int nl = 0;
+  while (1) {
+    if (nl < maxlev) U[nl] = harmonic_cut_bound(Hd, d, nd, g, omega_v);
+    ++nl;
+    uint32_t level_end = tail;
+    uint64_t cnt = 0, gs = 0;
+    while (head < level_end) {
+      uint32_t u = queue[head++];
+      for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+        uint32_t w = col[e];
+        if (dist[w] == UINT32_MAX) {
+          dist[w] = d + 1;
+          queue[tail++] = w;
+          ++cnt;
+          gs += (off[w + 1] - off[w]) - (directed ? 0u : 1u);
+        }
+      }
+    }
+    if (cnt == 0) break;
+    ++d;
+    Hd = Hd + (double)cnt / (double)d;
+    nd += cnt;
+    g = gs;
+  }
+  free(dist); free(queue);
+  return nl < maxlev ? nl : maxlev;
+}

@@ -14,6 +14,7 @@ import pytest
 import oracle
 import test_oracle as pins
 import test_oracle_nb as nbpins
+import test_oracle_harmonic as hpins
 
 MUTANTS = {
     "bfs_dropped_distance": ("S += dist[w];", "S += dist[w] - (dist[w] > 1);",
@@ -62,6 +63,18 @@ MUTANTS = {
                               [nbpins.test_walks_that_stop_bound_the_reach]),
     "nb_sink_gets_reach_two": ("bS[s] = 0; br[s] = 1; have[s] = 1;", "bS[s] = 0; br[s] = 2; have[s] = 1;",
                                [nbpins.test_out_degree_zero_has_closeness_zero]),
+    "harmonic_level_off_by_one": ("    h = h + (double)cnt / (double)d;\n", "    h = h + (double)cnt / (double)(d + (d > 2));\n",
+                                  [hpins.test_textbook_within_rounding_of_exact_and_per_level_definition]),
+    "harmonic_near_term_too_small": ("double t1 = (double)near / (double)(d + 1);",
+                                     "double t1 = (double)near / (double)(d + 2);",
+                                     [hpins.test_cut_bounds_hold_and_tighten]),
+    "harmonic_ties_by_larger_id": ("  return a->id < b->id;\n}\n\nstatic int cmp_hentry", "  return a->id > b->id;\n}\n\nstatic int cmp_hentry",
+                                   [hpins.test_topk_order_and_ties]),
+    "harmonic_nb_tail_too_small": ("h_ub[s] = h_ub[s] + (double)(o - c1) / (double)(k + 1);",
+                                   "h_ub[s] = h_ub[s] + (double)(o - c1) / (double)(k + 3);",
+                                   [hpins.test_nb_upper_bound_holds]),
+    "harmonic_nb_last_piece_dropped": ("if (h_ub) h_ub[s] = h_ub[s] + (double)(o - c0) / (double)k;", "(void)0;",
+                                       [hpins.test_nb_upper_bound_holds]),
     "degree_order_unstable": ("for (uint32_t v = 0; v < n; ++v) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               "for (uint32_t v = n; v-- > 0;) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               [pins.test_degree_order_matches_lexsort]),
