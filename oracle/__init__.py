@@ -18,6 +18,9 @@ Functions and what pins them (see ``tests/test_oracle.py``):
   nb_bounds       Algorithm 3, Eq. 3, Eq. 6      brute-force walk counts, exact on trees and
                                                  cycles, hand-computed hypercube, <= S/(r-1)^2,
                                                  minimum over every r in [alpha, omega]
+  lb_level_bounds Section 7, Eq. 4, Eq. 5         <= S on the reach class, per-vertex form of the
+                                                 equation, the Section 7 difference lemma
+  bfsbound        Algorithm 1 + Algorithm 5      textbook top-k, DegBound and NBBound
   harmonic_*      Section 9 (harmonic centrality) exact rationals from Floyd-Warshall within
                                                  the rounding bound, networkx, closed forms;
                                                  BFSCut/NBCut equal to the textbook top-k
@@ -87,6 +90,9 @@ def _bind(lib):
     lib.orc_bfscut_harmonic.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p, _dp,
                                         _u32p, _dp, _u32p, _u32p, ctypes.POINTER(Counters), _dp, _u32p,
                                         ctypes.c_uint32]
+    lib.orc_lb_level_bounds.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p, _u64p]
+    lib.orc_bfsbound.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p, _u64p, _u32p,
+                                 _u32p, _u64p, _u32p, _u32p, ctypes.POINTER(Counters), ctypes.c_uint32]
     lib.orc_harmonic_cut_bounds.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32,
                                             ctypes.c_uint32, _dp, ctypes.c_int]
     return lib
@@ -373,3 +379,34 @@ def nb_harmonic_order(g, h_ub):
     ids = np.nonzero(deg > 0)[0].astype(np.uint32)
     h = np.asarray(h_ub, dtype=np.float64)[ids]
     return ids[np.lexsort((ids, -h))]
+
+
+# ---------------------------------------------------------------- updateBoundsLB (DegBound / NBBound)
+
+def lb_level_bounds(g, s):
+    """BFS from s: (level per vertex, UINT32_MAX if unreachable; level bound L(i) per level)."""
+    off, col = _csr(g)
+    level = np.zeros(max(g.n, 1), np.uint32)
+    L = np.zeros(max(g.n, 1) + 1, np.uint64)
+    nl = _check(_load().orc_lb_level_bounds(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), s,
+                                            _p(level, _u32p), _p(L, _u64p)))
+    return level[: g.n], L[:nl]
+
+
+def bfsbound(g, k, order=None, nb=None, max_sources=0) -> TopK:
+    """Algorithm 1 with updateBoundsLB: DegBound (nb None, degree order unless
+    `order`) or NBBound (nb = nb_bounds(g), order = its NB order)."""
+    off, col = _csr(g)
+    kk = min(k, g.n)
+    ids = np.zeros(max(kk, 1), np.uint32)
+    S = np.zeros(max(kk, 1), np.uint64)
+    r = np.zeros(max(kk, 1), np.uint32)
+    tied = ctypes.c_uint32(0)
+    ctr = Counters()
+    order_a = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
+    iS = None if nb is None else np.ascontiguousarray(nb.S, dtype=np.uint64)
+    ir = None if nb is None else np.ascontiguousarray(nb.r, dtype=np.uint32)
+    cnt = _check(_load().orc_bfsbound(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), k, _p(order_a, _u32p),
+                                      _p(iS, _u64p), _p(ir, _u32p), _p(ids, _u32p), _p(S, _u64p), _p(r, _u32p),
+                                      ctypes.byref(tied), ctypes.byref(ctr), max_sources))
+    return TopK(ids[:cnt], S[:cnt], r[:cnt], int(tied.value), ctr)

@@ -1197,3 +1197,193 @@ int orc_harmonic_cut_bounds(uint32_t n, const uint32_t *off, const uint32_t *col
   free(dist); free(queue);
   return nl < maxlev ? nl : maxlev;
 }
+
+/* ---------------------------------------------------------------------- */
+/* updateBoundsLB (Section 7, Algorithm 5; Eq. 4 undirected, Eq. 5         */
+/* directed): a full BFS from s bounds the farness of every vertex whose    */
+/* reach equals s's (its component; its SCC if directed)                    */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Level bound of level i of a BFS from s with level sizes g[0..D] (g[0] = 1,
+ * the source itself):
+ *   undirected (Eq. 4): L(i) = 2 sum_{|j-i| <= 1} g_j + sum_{|j-i| > 1} g_j |j-i| - 2
+ *   directed   (Eq. 5): L(i) = 2 sum_{j - i <= 1} g_j + sum_{j - i > 1} g_j (j-i) - 2
+ * and S(w) >= L(l(w)) - outdeg(w) for every w at level l(w) whose reach is
+ * s's.  Readings: the sums run over all of R(s) including s at level 0 (the
+ * set the bound is derived from; Section 7's lemma sets g_j = 0 for j <= 0,
+ * which only weakens it), and L(i) is evaluated from its definition for
+ * every level (Algorithm 5's first line, L(1) = g_1 + g_2 + sum_{>2} - 2,
+ * does not match the definition, so the recurrence is not used).
+ */
+static uint64_t lb_level(const uint64_t *g, uint32_t D, uint32_t i, int directed) {
+  uint64_t s = 0;
+  for (uint32_t j = 0; j <= D; ++j) {
+    int64_t diff = (int64_t)j - (int64_t)i;
+    int64_t ad = diff < 0 ? -diff : diff;
+    if (directed) {
+      if (diff <= 1) s += 2 * g[j];
+      else s += g[j] * (uint64_t)diff;
+    } else {
+      if (ad <= 1) s += 2 * g[j];
+      else s += g[j] * (uint64_t)ad;
+    }
+  }
+  return s - 2;
+}
+
+/* BFS from s; writes level[v] (UINT32_MAX if unreachable) and the level
+ * bound of each level to L[0..D] (L must hold n entries).  Returns D + 1. */
+int orc_lb_level_bounds(uint32_t n, const uint32_t *off, const uint32_t *col, int directed, uint32_t s,
+                        uint32_t *level, uint64_t *L) {
+  uint32_t *queue = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint64_t *g = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+  if (!queue || !g) { free(queue); free(g); return ORC_ENOMEM; }
+  for (uint32_t i = 0; i < n; ++i) level[i] = UINT32_MAX;
+  uint32_t head = 0, tail = 0, D = 0;
+  level[s] = 0;
+  queue[tail++] = s;
+  while (head < tail) {
+    uint32_t u = queue[head++];
+    for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+      uint32_t w = col[e];
+      if (level[w] == UINT32_MAX) {
+        level[w] = level[u] + 1;
+        if (level[w] > D) D = level[w];
+        queue[tail++] = w;
+      }
+    }
+  }
+  for (uint32_t i = 0; i < tail; ++i) g[level[queue[i]]]++;
+  for (uint32_t i = 0; i <= D; ++i) L[i] = lb_level(g, D, i, directed);
+  free(queue); free(g);
+  return (int)(D + 1);
+}
+
+static uint64_t nb_key_of(uint64_t S, uint64_t r) {
+  if (r <= 1) return UINT64_MAX;
+  u128 num = (u128)S << ORC_NB_FRAC;
+  return (uint64_t)(num / (u128)((r - 1) * (r - 1)));
+}
+
+/*
+ * Algorithm 1 with updateBoundsLB (DegBound with init_S == NULL: every bound
+ * 0; NBBound with init_S/init_r = computeBoundsNB's (S~, r)), one source at a
+ * time.  Q holds the unvisited vertices of out-degree >= 1 ordered by
+ * (key, position in order0), key = floor(2^46 S_lb / (r_lb - 1)^2) of the
+ * vertex's current bound (the reading of the NBCut order: an exact integer
+ * order whose key never exceeds the bound).  The head v of Q is searched
+ * completely (no cut) unless the k-list is full and key(v) / 2^46 > x
+ * strictly, which ends the loop.  After each search from s, every w with
+ * comp[w] == comp[s] (its component, or its SCC if directed: then r(w) =
+ * r(s)) gets bound (L(l(w)) - outdeg(w), r(s)) if that ratio is larger than
+ * its current one.  Outputs as orc_bfscut (counters: edges_visited counts
+ * the arcs of every search, all complete; bfs_cut stays 0).
+ */
+int orc_bfsbound(uint32_t n, const uint32_t *off, const uint32_t *col, int directed, uint32_t k,
+                 const uint32_t *order0, const uint64_t *init_S, const uint32_t *init_r, uint32_t *ids,
+                 uint64_t *S_out, uint32_t *r_out, uint32_t *n_tied, orc_counters *ctr, uint32_t max_sources) {
+  if (k == 0 || n == 0) { if (n_tied) *n_tied = 0; return 0; }
+  int rc = ORC_OK;
+  uint32_t kk = k < n ? k : n;
+  uint32_t *order = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *rank0 = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *comp = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *level = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint64_t *L = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+  uint64_t *bS = (uint64_t *)calloc(n, sizeof(uint64_t));
+  uint64_t *br = (uint64_t *)calloc(n, sizeof(uint64_t));
+  uint64_t *key = (uint64_t *)calloc(n, sizeof(uint64_t));
+  uint64_t *fS = (uint64_t *)calloc(n, sizeof(uint64_t));
+  uint32_t *fr = (uint32_t *)calloc(n, sizeof(uint32_t));
+  char *done = (char *)calloc(n, 1);
+  entry_t *top = (entry_t *)malloc((size_t)kk * sizeof(entry_t));
+  if (!order || !rank0 || !comp || !level || !L || !bS || !br || !key || !fS || !fr || !done || !top) {
+    rc = ORC_ENOMEM;
+    goto out;
+  }
+  if (order0) memcpy(order, order0, (size_t)n * sizeof(uint32_t));
+  else if ((rc = orc_degree_order(n, off, order)) != ORC_OK) goto out;
+  for (uint32_t i = 0; i < n; ++i) rank0[order[i]] = i;
+  if (directed) {
+    int64_t nc = orc_scc(n, off, col, comp);
+    if (nc < 0) { rc = (int)nc; goto out; }
+  } else {
+    /* components: the SCCs of the symmetric graph */
+    int64_t nc = orc_scc(n, off, col, comp);
+    if (nc < 0) { rc = (int)nc; goto out; }
+  }
+  for (uint32_t v = 0; v < n; ++v) {
+    bS[v] = init_S ? init_S[v] : 0;
+    br[v] = init_S ? init_r[v] : 2; /* bound 0 */
+    key[v] = nb_key_of(bS[v], br[v]);
+  }
+  orc_counters c = {0, 0, 0, 0};
+  uint32_t ntop = 0;
+  while (1) {
+    /* head of Q: smallest (key, rank0) among unvisited vertices of out-degree >= 1 */
+    uint32_t v = UINT32_MAX;
+    for (uint32_t w = 0; w < n; ++w) {
+      if (done[w] || off[w + 1] == off[w]) continue;
+      if (v == UINT32_MAX || key[w] < key[v] || (key[w] == key[v] && rank0[w] < rank0[v])) v = w;
+    }
+    if (v == UINT32_MAX) break;
+    if (max_sources && c.bfs_started >= max_sources) break;
+    if (ntop == kk) {
+      uint64_t Sx = top[kk - 1].S, rx = top[kk - 1].r;
+      u128 lhs = (u128)key[v] * (u128)((rx - 1) * (rx - 1));
+      if (lhs > ((u128)Sx << ORC_NB_FRAC)) break; /* Algorithm 1: the head of Q exceeds x */
+    }
+    done[v] = 1;
+    c.bfs_started++;
+    c.bfs_finished++;
+    int nl = orc_lb_level_bounds(n, off, col, directed, v, level, L);
+    if (nl < 0) { rc = nl; goto out; }
+    uint64_t S = 0, r = 0;
+    for (uint32_t w = 0; w < n; ++w)
+      if (level[w] != UINT32_MAX) {
+        S += level[w];
+        ++r;
+        c.edges_visited += off[w + 1] - off[w];
+      }
+    fS[v] = S;
+    fr[v] = (uint32_t)r;
+    top_insert(top, &ntop, kk, S, (uint32_t)r, v);
+    if (r <= 1) continue;
+    /* updateBoundsLB: vertices whose reach is R(v) */
+    for (uint32_t w = 0; w < n; ++w) {
+      if (level[w] == UINT32_MAX || comp[w] != comp[v] || w == v) continue;
+      uint64_t lbS = L[level[w]] - (uint64_t)(off[w + 1] - off[w]);
+      /* keep the larger of lbS/(r-1)^2 and the current bound */
+      u128 lhs = (u128)lbS * (u128)((br[w] - 1) * (br[w] - 1));
+      u128 rhs = (u128)bS[w] * (u128)((r - 1) * (r - 1));
+      if (br[w] <= 1 || lhs > rhs) {
+        bS[w] = lbS;
+        br[w] = r;
+        key[w] = nb_key_of(lbS, r);
+      }
+    }
+  }
+  for (uint32_t v = 0; v < n && ntop < kk; ++v)
+    if (off[v + 1] == off[v]) top_insert(top, &ntop, kk, 0, 1, v);
+  for (uint32_t i = 0; i < kk; ++i) {
+    ids[i] = top[i].id;
+    if (S_out) S_out[i] = top[i].S;
+    if (r_out) r_out[i] = top[i].r;
+  }
+  if (n_tied) {
+    uint32_t t = 0;
+    const entry_t *last = &top[kk - 1];
+    for (uint32_t v = 0; v < n; ++v) {
+      if (off[v + 1] == off[v]) t += last->r <= 1;
+      else if (fr[v] && cmp_farness(fS[v], fr[v], last->S, last->r) == 0) ++t;
+    }
+    *n_tied = t;
+  }
+  if (ctr) *ctr = c;
+  rc = (int)kk;
+out:
+  free(order); free(rank0); free(comp); free(level); free(L); free(bS); free(br); free(key); free(fS); free(fr);
+  free(done); free(top);
+  return rc;
+}

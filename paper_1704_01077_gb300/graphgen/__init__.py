@@ -178,6 +178,26 @@ def hypercube(d: int) -> Graph:
     return from_arcs(n, src, dst, False, f"Q{d}")
 
 
+def grid(rows: int, cols: int, directed: bool = False, seed: int | None = None, drop: float = 0.0) -> Graph:
+    """rows x cols 4-neighbour grid, a street-network stand-in.  With a seed,
+    each undirected edge is dropped with probability `drop`; directed grids
+    keep each direction of an edge independently with probability 1 - drop
+    (one-way streets)."""
+    v = np.arange(rows * cols).reshape(rows, cols)
+    a = np.concatenate([v[:, :-1].ravel(), v[:-1, :].ravel()])
+    b = np.concatenate([v[:, 1:].ravel(), v[1:, :].ravel()])
+    if directed:
+        src, dst = np.concatenate([a, b]), np.concatenate([b, a])
+        if seed is not None and drop > 0:
+            keep = np.random.default_rng(seed).random(src.size) >= drop
+            src, dst = src[keep], dst[keep]
+        return from_arcs(rows * cols, src, dst, True, f"grid{rows}x{cols}d")
+    if seed is not None and drop > 0:
+        keep = np.random.default_rng(seed).random(a.size) >= drop
+        a, b = a[keep], b[keep]
+    return from_arcs(rows * cols, a, b, False, f"grid{rows}x{cols}")
+
+
 def disjoint_union(*gs: Graph) -> Graph:
     src, dst, base = [], [], 0
     directed = any(g.directed for g in gs)

@@ -15,6 +15,7 @@ import oracle
 import test_oracle as pins
 import test_oracle_nb as nbpins
 import test_oracle_harmonic as hpins
+import test_oracle_lb as lbpins
 
 MUTANTS = {
     "bfs_dropped_distance": ("S += dist[w];", "S += dist[w] - (dist[w] > 1);",
@@ -75,6 +76,19 @@ MUTANTS = {
                                    [hpins.test_nb_upper_bound_holds]),
     "harmonic_nb_last_piece_dropped": ("if (h_ub) h_ub[s] = h_ub[s] + (double)(o - c0) / (double)k;", "(void)0;",
                                        [hpins.test_nb_upper_bound_holds]),
+    "lb_drops_source_level": ("  for (uint32_t j = 0; j <= D; ++j) {\n    int64_t diff", "  for (uint32_t j = 1; j <= D; ++j) {\n    int64_t diff",
+                              [lbpins.test_level_bound_definition_and_difference_lemma]),
+    "lb_directed_uses_both_sides": ("      if (diff <= 1) s += 2 * g[j];\n      else s += g[j] * (uint64_t)diff;",
+                                    "      if (ad <= 1) s += 2 * g[j];\n      else s += g[j] * (uint64_t)ad;",
+                                    [lbpins.test_vertex_bounds_below_distance_sums]),
+    "lb_offset_off_by_one": ("  return s - 2;\n}", "  return s - 1;\n}", [lbpins.test_grid_level_bound_by_hand]),
+    "lb_outside_reach_class": ("if (level[w] == UINT32_MAX || comp[w] != comp[v] || w == v) continue;",
+                               "if (level[w] == UINT32_MAX || w == v) continue;",
+                               [lbpins.test_bfsbound_bounds_only_the_reach_class]),
+    "lb_stop_non_strict": ("if (lhs > ((u128)Sx << ORC_NB_FRAC)) break; /* Algorithm 1: the head of Q exceeds x */",
+                           "if (lhs >= ((u128)Sx << ORC_NB_FRAC)) break; /* Algorithm 1: the head of Q exceeds x */",
+                           [lambda: lbpins.test_bfsbound_equals_textbook_random(False),
+                            lambda: lbpins.test_bfsbound_equals_textbook_families(0, False)]),
     "degree_order_unstable": ("for (uint32_t v = 0; v < n; ++v) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               "for (uint32_t v = n; v-- > 0;) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               [pins.test_degree_order_matches_lexsort]),
