@@ -39,6 +39,8 @@ WORKLOADS = {
                "directed R-MAT scale 20, edge factor 16, k=10 (profiling size: inputs above L2, a few GB)"),
     "ba1m": (lambda gg: gg.barabasi_albert(1_000_000, 5, gg.workload_seed(2)), 10,
              "undirected Barabasi-Albert n=1,000,000, m=5, k=10"),
+    "grid1k": (lambda gg: gg.grid(1000, 1000, seed=gg.workload_seed(5), drop=0.1), 10,
+               "undirected 1000 x 1000 grid, 10% of edges dropped (street-network stand-in), k=10"),
     "multi512": (lambda gg: multi_graphs(gg, 512, 1_000, 200_000, gg.workload_seed(3)), 10,
                  "512 graphs in one launch, n log-uniform in [1k, 200k]; even: undirected Barabasi-Albert m=4, "
                  "odd: directed Erdos-Renyi with 8n uniform arcs; top-10 of each"),
@@ -199,6 +201,10 @@ def main():
                     help="source order: degree bound (DegCut), neighbourhood bound with its stop (NBCut), "
                          "learned model, or learned seeding prefix + degree")
     ap.add_argument("--nb-levels", type=int, default=0, help="NBCut: most sweeps of the bound (0 = 256)")
+    ap.add_argument("--measure", default="closeness", choices=["closeness", "harmonic"],
+                    help="rank by closeness (the paper's main measure) or harmonic centrality")
+    ap.add_argument("--bound", default="cut", choices=["cut", "lb"],
+                    help="updateBounds: BFSCut (cut) or updateBoundsLB (lb: DegBound / NBBound)")
     ap.add_argument("--teams", type=int, default=0, help="teams of SMs (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "tkc":
@@ -251,12 +257,20 @@ def main():
             self.bfs_cut = sum(r.bfs_cut for r in results)
             self.bfs_finished = sum(r.bfs_finished for r in results)
             for name in ("edges_scanned", "levels", "ms_pre", "ms_bfs", "ms_kernel", "alg_bytes", "batch_bits",
-                         "ids", "dist_sum", "reach"):
+                         "ids", "dist_sum", "reach", "closeness"):
                 setattr(self, name, getattr(r0, name))
 
     def run_step(csr):
         hs = [tkc.tkc_load_csr(ctx, x.n, o, c, x.directed) for x, (o, c) in zip(graphs, csr)]
         try:
+            if args.bound == "lb":
+                if multi or args.measure != "closeness":
+                    raise SystemExit("--bound lb runs closeness on one graph")
+                return Step([tkc.tkc_topk_closeness_bound(hs[0], k)])
+            if args.measure == "harmonic":
+                if multi:
+                    return Step(tkc.tkc_topk_harmonic_multi(ctx, hs, k))
+                return Step([tkc.tkc_topk_harmonic(hs[0], k)])
             if multi:
                 return Step(tkc.tkc_topk_closeness_multi(ctx, hs, k))
             return Step([tkc.tkc_topk_closeness(hs[0], k)])
@@ -315,7 +329,8 @@ def main():
     kern_ms = statistics.mean(r.ms_kernel for r in results)
     alg = statistics.mean(r.alg_bytes for r in results)
     achieved = alg / (kern_ms / 1e3) / 1e9
-    traffic, traffic_entry = ncu_traffic(args.workload, args.order, res.batch_bits)
+    traffic, traffic_entry = (ncu_traffic(args.workload, args.order, res.batch_bits)
+                              if args.measure == "closeness" and args.bound == "cut" else (None, None))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_src,
                 "alg_bytes_per_launch": alg, "kernel_ms": kern_ms}
@@ -324,7 +339,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "k": k, "batch_bits": res.batch_bits,
-                       "order": args.order, "teams": args.teams or "library default",
+                       "order": args.order, "measure": args.measure, "bound": args.bound, "teams": args.teams or "library default",
                        "l2": "inputs larger than L2 (CSR 280 MB + bit rows)" if args.workload in
                        ("rmat22", "multi512", "ba1m") else "small graph: may be L2-resident",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -354,9 +369,14 @@ def main():
 
         ok = True
         for x, top in zip(graphs, results[-1].results):
-            S, r = oracle.bfs_sums(x, top.ids)
-            ok &= bool(np.array_equal(S, top.dist_sum) and np.array_equal(r, top.reach))
-        line["check"] = {"top_k_S_r_match_oracle_bfs": ok}
+            if args.measure == "harmonic":
+                H, r = oracle.harmonic_sums(x, top.ids)
+                ok &= bool(H.tobytes() == top.closeness.tobytes() and np.array_equal(r, top.reach))
+            else:
+                S, r = oracle.bfs_sums(x, top.ids)
+                ok &= bool(np.array_equal(S, top.dist_sum) and np.array_equal(r, top.reach))
+        key = "top_k_h_r_match_oracle_bfs" if args.measure == "harmonic" else "top_k_S_r_match_oracle_bfs"
+        line["check"] = {key: ok}
     if rank == 0 and not args.no_cpu and not multi:
         v, dt, ev = cpu_oracle_sample(g, k, args.sample)
         line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",

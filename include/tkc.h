@@ -141,6 +141,41 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out);
  * tkc_topk_closeness would (counters per graph, ms_* shared).  Same errors. */
 int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
 
+/* Top-k harmonic centrality h(v) = sum over w != v of 1/d(v,w) (the paper's
+ * closing generalisation of its method to sums of f(d(v,w)) with f decreasing,
+ * Section 9): Algorithm 1 with the degree or NB order (options.order) and
+ * BFSCut's upper bound on h.  h is formed per BFS level in FP64: the count of
+ * vertices at distance d divided by d, added in increasing d, each operation
+ * rounded to nearest; vertices are ranked by that value, largest first, ties
+ * by id; n_tied_at_kth counts the vertices with the same FP64 value.  A search
+ * is abandoned only when its bound times (1 + 2^-20) is below the k-th h (the
+ * margin covers rounding), so the result is the exact top-k of that ranking.
+ * Writes ids, reach (r), closeness[] = h(v), farness[] = 1/h(v) (+inf when
+ * h = 0, i.e. out-degree 0) and dist_sum[] = 0 (S is not kept); counters as
+ * tkc_topk_closeness.  Same errors. */
+int tkc_topk_harmonic(tkc_graph *g, uint32_t k, tkc_result *out);
+
+/* tkc_topk_harmonic for ng graphs in one persistent launch (as
+ * tkc_topk_closeness_multi). */
+int tkc_topk_harmonic_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
+
+/* Exact top-k closeness by Algorithm 1 with updateBoundsLB (Section 7,
+ * Algorithm 5; Eq. 4 undirected, Eq. 5 directed): DegBound with
+ * options.order = TKC_ORDER_DEG, NBBound with TKC_ORDER_NB (the paper's best
+ * variant on street networks).  Every search is complete; after a search from
+ * s each vertex w whose reach equals s's (its component, or its SCC if
+ * directed) gets the bound S(w) >= L(d(s,w)) - outdeg(w), L(i) = 2 x (vertices
+ * within one level of i; directed: at most one level deeper) + the level
+ * distance of all other vertices - 2, over R(s) including s.  The search runs
+ * in rounds of options.batch_bits sources (0 = 64; 1 = one source per round):
+ * the unsearched vertices of smallest bound key floor(2^46 S_lb/(r-1)^2), ties
+ * by their position in the initial order, and stops when that key exceeds the
+ * k-th farness strictly.  Results as tkc_topk_closeness (bfs_cut = 0).  Errors:
+ * TKC_EINVAL (order not DEG or NB, k > TKC_MAX_K, capacity too small),
+ * TKC_EOVERFLOW (a search deeper than 65 534 levels), TKC_ENOMEM, TKC_ECUDA,
+ * TKC_ETIMEOUT.  Device memory: about 2 x batch_bits bytes per vertex. */
+int tkc_topk_closeness_bound(tkc_graph *g, uint32_t k, tkc_result *out);
+
 /* Autotuner (no paper counterpart: it only picks launch parameters).
  * Times candidate batch widths (64..512), team counts (1, 4, and SMs/16,
  * SMs/8, SMs/4, i.e. 16, 8 and 4 blocks per team) and bottom-up
@@ -188,6 +223,14 @@ int tkc_reach_bounds(tkc_graph *g, uint32_t *alpha, uint32_t *omega);
  * 65535), TKC_ENOMEM, TKC_ECUDA. */
 int tkc_nb_bounds(tkc_graph *g, uint32_t max_levels, uint64_t *S_lb, uint32_t *r_lb, uint64_t *key,
                   uint32_t *order, uint32_t *n_order, uint32_t *levels);
+
+/* The harmonic counterpart of tkc_nb_bounds (same sweeps): h_ub[n] receives
+ * an upper bound on h(v), the sum over k of min(N~_k, max(omega(v) - c_{k-1}, 0)) / k
+ * (quotients added in increasing k, FP64 rounded to nearest; a vertex unfinished
+ * after the last sweep adds (omega - c_K) / (K+1)), and order[] the vertices of
+ * out-degree >= 1 by decreasing h_ub, ties by id (*n_order of them).  Host
+ * arrays, any may be NULL.  Errors as tkc_nb_bounds. */
+int tkc_nb_harmonic_bounds(tkc_graph *g, uint32_t max_levels, double *h_ub, uint32_t *order, uint32_t *n_order);
 
 /* Exact S(v) and r(v) of the listed sources by full BFS on the device, in
  * batches of 64 sources (no cutting).  srcs, S, r: host arrays of nsrc. */

@@ -160,7 +160,8 @@ struct GraphOut {
 // equality).  A graph whose k-th entry is a closeness-0 vertex is counted on
 // the host (every closeness-0 vertex ties with it).
 __global__ void k_count_ties(const u64 *res_S, const u32 *res_r, const u32 *gid, u32 nv, const u64 *top_S,
-                             const u32 *top_r, const unsigned *g_ntop, u32 kk, const GraphOut *go, unsigned *tied) {
+                             const u32 *top_r, const unsigned *g_ntop, u32 kk, const GraphOut *go, int harmonic,
+                             unsigned *tied) {
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
     u32 r = res_r[v];
     if (r < 2) continue;
@@ -168,6 +169,11 @@ __global__ void k_count_ties(const u64 *res_S, const u32 *res_r, const u32 *gid,
     u32 kg = go[g].kk;
     if (g_ntop[g] < kg) continue;
     size_t x = (size_t)g * kk + kg - 1;
+    if (harmonic) {
+      // the same FP64 h, bit for bit
+      if (res_S[v] == top_S[x]) atomicAdd(&tied[g], 1u);
+      continue;
+    }
     u64 rx = top_r[x];
     unsigned __int128 a = (unsigned __int128)res_S[v] * (unsigned __int128)((rx - 1) * (rx - 1));
     unsigned __int128 b = (unsigned __int128)top_S[x] * (unsigned __int128)((u64)(r - 1) * (u64)(r - 1));
@@ -177,9 +183,10 @@ __global__ void k_count_ties(const u64 *res_S, const u32 *res_r, const u32 *gid,
 
 // Final list of graph blockIdx.x: its top entries, then (if fewer than k of
 // its vertices reach another vertex) closeness-0 vertices in id order.  f and
-// c are one IEEE product and one quotient of exact integers.
+// c are one IEEE product and one quotient of exact integers.  Harmonic runs:
+// c = h (the list key's FP64 value), f = 1/h, S not kept (0).
 __global__ void k_output(const u64 *top_S, const u32 *top_r, const u32 *top_id, const unsigned *g_ntop, u32 kk,
-                         const GraphOut *go, u64 *oS, u32 *or_, u32 *oid, double *of, double *oc) {
+                         const GraphOut *go, int harmonic, u64 *oS, u32 *or_, u32 *oid, double *of, double *oc) {
   const u32 g = blockIdx.x;
   const GraphOut G = go[g];
   const u32 ntop = g_ntop[g];
@@ -196,10 +203,14 @@ __global__ void k_output(const u64 *top_S, const u32 *top_r, const u32 *top_id, 
       r = 1;
       id = G.zero_ids[i - ntop];
     }
-    oS[src] = S;
+    oS[src] = harmonic ? 0 : S;
     or_[src] = r;
     oid[src] = id;
-    if (r <= 1) {
+    if (harmonic) {
+      const double h = r <= 1 ? 0.0 : __longlong_as_double((long long)S);
+      oc[src] = h;
+      of[src] = h > 0.0 ? __ddiv_rn(1.0, h) : __longlong_as_double(0x7ff0000000000000ll);
+    } else if (r <= 1) {
       of[src] = __longlong_as_double(0x7ff0000000000000ll);
       oc[src] = 0.0;
     } else {
@@ -219,8 +230,9 @@ static int words_for(u32 bits) {
 }
 
 // Batch width used when the options leave it to the library.
-static u32 default_batch_bits(u32 n) {
-  if (n < 4096 || n >= (1u << 16)) return 64;
+static u32 default_batch_bits(u32 n, bool nb = false) {
+  if (n < 4096) return 64;
+  if (n >= (1u << 16)) return nb ? 128 : 64;
   return 128;
 }
 
@@ -232,19 +244,29 @@ struct RunSetup {
   u32 B;
   int W;
   int nocut;
+  int harmonic;             // rank by harmonic centrality instead of closeness
   u32 nocut_prefix;
   const u64 *lb_key;        // NBCut order keys (nullptr: no stop test)
   u32 kk;                   // list length per graph
   u32 ng;
   const u32 *gid;           // nullptr for one graph
   const uint8_t *g_directed;
+  // updateBoundsLB rounds: level recording, one team, lists kept across rounds
+  uint16_t *lvl;
+  u32 *hist;
+  u32 hist_cap;
+  int keep_lists;
+  u32 force_teams;
 };
 
 // Teams used when the options leave it to the library: one team for small
 // graphs (a level is short and the whole GPU serves it), more for large ones
 // so that the latency of one team's level steps overlaps with the others.
-static u32 default_teams(u32 n, u32 B, u32 maxb) {
+// NBCut on one graph examines few sources, each batch deeper: fewer, larger
+// teams (measured on R-MAT 22: 4 teams 357 ms, 9 teams 372 ms, 19 teams 411 ms).
+static u32 default_teams(u32 n, u32 B, u32 maxb, bool nb) {
   if (B <= 1 || n < (1u << 14)) return 1;
+  if (nb) return std::max<u32>(1, maxb / 32);
   if (n < (1u << 16)) return std::max<u32>(1, maxb / 16);
   return std::max<u32>(1, maxb / 8);  // eight blocks (SMs) per team, every SM used
 }
@@ -256,28 +278,24 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   const tkc_options &o = ctx->opt;
   int maxb = max_coresident_blocks(ctx, rs.W);
   if (maxb <= 0) return TKC_ECUDA;
-  u32 T = rs.B <= 1 ? 1u : (o.teams ? o.teams : default_teams(g->n, rs.B, (u32)maxb));
+  const bool nb_one = rs.lb_key != nullptr && rs.ng == 1;
+  u32 T = rs.B <= 1 ? 1u : (o.teams ? o.teams : default_teams(g->n, rs.B, (u32)maxb, nb_one));
+  if (rs.force_teams) T = rs.force_teams;
   T = std::max<u32>(1, std::min<u32>(T, (u32)maxb));
   TKC_RC(ensure_workspace(ctx, g->n, rs.W, rs.kk * rs.ng, rs.ng, T));
   if (w.level_base > 0xF0000000u) {
     TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, (size_t)w.teams_cap * w.n_cap * sizeof(u32), st));
     w.level_base = 0;
   }
-  std::vector<Ctl> cs(T);
-  for (u32 t = 0; t < T; ++t) {
-    memset(&cs[t], 0, sizeof(Ctl));
-    cs[t].step = 1;  // start with an (empty) clear step whose epilogue seeds the first batch
-    cs[t].level_id = w.level_base;
+  if (!rs.keep_lists) {
+    TKC_TRY(cudaMemsetAsync(w.res_r, 0, (size_t)g->n * sizeof(u32), st));
+    TKC_TRY(cudaMemsetAsync(w.res_S, 0, (size_t)g->n * sizeof(u64), st));
+    TKC_TRY(cudaMemsetAsync(w.g_ntop, 0, (size_t)rs.ng * sizeof(unsigned), st));
+    TKC_TRY(cudaMemsetAsync(w.g_stop, 0, (size_t)rs.ng * sizeof(unsigned), st));
+    TKC_TRY(cudaMemsetAsync(w.g_ctr, 0, (size_t)rs.ng * 4 * sizeof(u64), st));
+    TKC_TRY(cudaMemsetAsync(w.x_seq, 0, (size_t)rs.ng * sizeof(unsigned), st));
+    TKC_TRY(cudaMemsetAsync(w.x_r, 0, (size_t)rs.ng * sizeof(u32), st));
   }
-  TKC_TRY(cudaMemcpyAsync(w.ctl, cs.data(), T * sizeof(Ctl), cudaMemcpyHostToDevice, st));
-  TKC_TRY(cudaMemsetAsync(w.sh, 0, sizeof(Shared), st));
-  TKC_TRY(cudaMemsetAsync(w.res_r, 0, (size_t)g->n * sizeof(u32), st));
-  TKC_TRY(cudaMemsetAsync(w.res_S, 0, (size_t)g->n * sizeof(u64), st));
-  TKC_TRY(cudaMemsetAsync(w.g_ntop, 0, (size_t)rs.ng * sizeof(unsigned), st));
-  TKC_TRY(cudaMemsetAsync(w.g_stop, 0, (size_t)rs.ng * sizeof(unsigned), st));
-  TKC_TRY(cudaMemsetAsync(w.g_ctr, 0, (size_t)rs.ng * 4 * sizeof(u64), st));
-  TKC_TRY(cudaMemsetAsync(w.x_seq, 0, (size_t)rs.ng * sizeof(unsigned), st));
-  TKC_TRY(cudaMemsetAsync(w.x_r, 0, (size_t)rs.ng * sizeof(u32), st));
   RunParams p;
   memset(&p, 0, sizeof(p));
   p.n = g->n;
@@ -302,6 +320,10 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.nocut_prefix = rs.nocut_prefix;
   p.lb_key = rs.lb_key;
   p.g_stop = w.g_stop;
+  p.harmonic = rs.harmonic;
+  p.lvl = rs.lvl;
+  p.hist = rs.hist;
+  p.hist_cap = rs.hist_cap;
   p.teams = T;
   p.row_stride = (u64)w.n_cap * w.words_cap;
   p.vtx_stride = w.n_cap;
@@ -347,51 +369,84 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
     TKC_TRY(cudaMemsetAsync(p.trace, 0, (size_t)trace_cap * 16 * sizeof(u64), st));
     p.trace_cap = trace_cap;
   }
+  // Opening: with several teams on one graph, the first batch runs alone on
+  // the whole grid (one team), so that a threshold exists before the teams
+  // start and the batch that sets it gets every SM; the teams then take the
+  // rest of the order.  The k-lists and thresholds carry over.
+  const bool opening = T > 1 && rs.ng == 1 && !rs.nocut && rs.norder > rs.B;
+  struct Phase {
+    u32 teams, begin, count;
+  };
+  std::vector<Phase> phases;
+  if (opening) {
+    phases.push_back({1u, 0u, rs.B});
+    phases.push_back({T, rs.B, rs.norder - rs.B});
+  } else {
+    phases.push_back({T, 0u, rs.norder});
+  }
+  memset(hctl, 0, sizeof(Ctl));
+  std::vector<Ctl> cs(T);
   TKC_TRY(cudaEventRecord(ctx->ev[4], st));
-  TKC_RC(run_bfscut(ctx, p, rs.W, blocks));
-  TKC_TRY(cudaEventRecord(ctx->ev[5], st));
-  TKC_TRY(cudaMemcpyAsync(cs.data(), w.ctl, T * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-  Shared hsh;
-  TKC_TRY(cudaMemcpyAsync(&hsh, w.sh, sizeof(Shared), cudaMemcpyDeviceToHost, st));
-  TKC_TRY(cudaStreamSynchronize(st));
-  // the teams' counters add up; levels and batches too (they ran side by side)
-  *hctl = cs[0];
-  for (u32 t = 1; t < T; ++t) {
-    const Ctl &x = cs[t];
-    hctl->edges_visited += x.edges_visited;
-    hctl->edges_scanned += x.edges_scanned;
-    hctl->bfs_started += x.bfs_started;
-    hctl->bfs_cut += x.bfs_cut;
-    hctl->bfs_finished += x.bfs_finished;
-    hctl->levels += x.levels;
-    hctl->batches += x.batches;
-    hctl->alg_bytes += x.alg_bytes;
-    hctl->trace_n += x.trace_n;
-    hctl->level_id = std::max(hctl->level_id, x.level_id);
-    if (!hctl->err) hctl->err = x.err;
-  }
-  if (!hctl->err) hctl->err = hsh.err;
-  w.level_base = hctl->level_id + 1;
-  if (p.trace) {
-    std::vector<u64> tr((size_t)trace_cap * 16);
-    TKC_TRY(cudaMemcpy(tr.data(), p.trace, tr.size() * sizeof(u64), cudaMemcpyDeviceToHost));
-    TKC_TRY(cudaFree(p.trace));
-    FILE *f = fopen(trace_path, "a");
-    if (f) {
-      fprintf(f, "# n=%u arcs=%llu B=%u blocks=%d graphs=%u teams=%u\n", g->n, (unsigned long long)g->arcs, rs.B,
-              blocks, rs.ng, T);
-      fprintf(f, "t_ns,kind,a,b,c,d,e,f,t_top,t_a_end,t_a_sync,t_b_end,t_flush,t_epi,team,y\n");
-      const u64 per = trace_cap / T;
-      for (u32 t = 0; t < T; ++t)
-        for (u64 i = 0; i < std::min<u64>(cs[t].trace_n, per); ++i) {
-          u64 *r = &tr[((size_t)t * per + i) * 16];
-          r[14] = t;
-          for (int j = 0; j < 16; ++j) fprintf(f, j ? ",%llu" : "%llu", r[j]);
-          fprintf(f, "\n");
-        }
-      fclose(f);
+  for (const Phase &ph : phases) {
+    for (u32 t = 0; t < ph.teams; ++t) {
+      memset(&cs[t], 0, sizeof(Ctl));
+      cs[t].step = 1;  // start with an (empty) clear step whose epilogue seeds the first batch
+      cs[t].level_id = w.level_base;
     }
+    TKC_TRY(cudaMemcpyAsync(w.ctl, cs.data(), ph.teams * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    TKC_TRY(cudaMemsetAsync(w.sh, 0, sizeof(Shared), st));
+    p.teams = ph.teams;
+    p.order = rs.order + ph.begin;
+    p.norder = ph.count;
+    p.nocut_prefix = rs.nocut_prefix > ph.begin ? rs.nocut_prefix - ph.begin : 0;
+    const int pblocks = std::max<int>((int)ph.teams, blocks / (int)ph.teams * (int)ph.teams);
+    TKC_RC(run_bfscut(ctx, p, rs.W, pblocks));
+    TKC_TRY(cudaMemcpyAsync(cs.data(), w.ctl, ph.teams * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    Shared hsh;
+    TKC_TRY(cudaMemcpyAsync(&hsh, w.sh, sizeof(Shared), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaStreamSynchronize(st));
+    // the teams' counters add up; levels and batches too (they ran side by side)
+    for (u32 t = 0; t < ph.teams; ++t) {
+      const Ctl &x = cs[t];
+      hctl->edges_visited += x.edges_visited;
+      hctl->edges_scanned += x.edges_scanned;
+      hctl->bfs_started += x.bfs_started;
+      hctl->bfs_cut += x.bfs_cut;
+      hctl->bfs_finished += x.bfs_finished;
+      hctl->levels += x.levels;
+      hctl->batches += x.batches;
+      hctl->alg_bytes += x.alg_bytes;
+      hctl->trace_n += x.trace_n;
+      hctl->level_id = std::max(hctl->level_id, x.level_id);
+      if (!hctl->err) hctl->err = x.err;
+    }
+    if (!hctl->err) hctl->err = hsh.err;
+    w.level_base = hctl->level_id + 1;
+    if (p.trace) {
+      std::vector<u64> tr((size_t)trace_cap * 16);
+      TKC_TRY(cudaMemcpy(tr.data(), p.trace, tr.size() * sizeof(u64), cudaMemcpyDeviceToHost));
+      TKC_TRY(cudaMemset(p.trace, 0, tr.size() * sizeof(u64)));
+      FILE *f = fopen(trace_path, "a");
+      if (f) {
+        fprintf(f, "# n=%u arcs=%llu B=%u blocks=%d graphs=%u teams=%u\n", g->n, (unsigned long long)g->arcs, rs.B,
+                pblocks, rs.ng, ph.teams);
+        fprintf(f, "t_ns,kind,a,b,c,d,e,f,t_top,t_a_end,t_a_sync,t_b_end,t_flush,t_epi,team,y\n");
+        const u64 per = trace_cap / ph.teams;
+        for (u32 t = 0; t < ph.teams; ++t)
+          for (u64 i = 0; i < std::min<u64>(cs[t].trace_n, per); ++i) {
+            u64 *r = &tr[((size_t)t * per + i) * 16];
+            r[14] = t;
+            for (int j = 0; j < 16; ++j) fprintf(f, j ? ",%llu" : "%llu", r[j]);
+            fprintf(f, "\n");
+          }
+        fclose(f);
+      }
+      for (u32 t = 0; t < ph.teams; ++t) cs[t].trace_n = 0;
+    }
+    if (hctl->err) break;
   }
+  TKC_TRY(cudaEventRecord(ctx->ev[5], st));
+  if (p.trace) TKC_TRY(cudaFree(p.trace));
   if (hctl->err) {
     TKC_RC(reset_rows(ctx));
     TKC_TRY(cudaStreamSynchronize(st));
@@ -414,9 +469,9 @@ static int finish_run(tkc_ctx *ctx, const RunSetup &rs, const std::vector<GraphO
   TKC_TRY(cudaMemsetAsync(w.tied, 0, ng * sizeof(unsigned), st));
   unsigned blocks = (unsigned)std::max<u64>(1, std::min<u64>((rs.g->n + 255) / 256, (u64)ctx->num_sms * 8));
   TKC_LAUNCH(k_count_ties<<<blocks, 256, 0, st>>>(w.res_S, w.res_r, rs.gid, rs.g->n, w.top_S, w.top_r, w.g_ntop,
-                                                  rs.kk, go, w.tied));
-  TKC_LAUNCH(k_output<<<ng, 256, 0, st>>>(w.top_S, w.top_r, w.top_id, w.g_ntop, rs.kk, go, w.out_S, w.out_r,
-                                          w.out_id, w.out_f, w.out_c));
+                                                  rs.kk, go, rs.harmonic, w.tied));
+  TKC_LAUNCH(k_output<<<ng, 256, 0, st>>>(w.top_S, w.top_r, w.top_id, w.g_ntop, rs.kk, go, rs.harmonic, w.out_S,
+                                          w.out_r, w.out_id, w.out_f, w.out_c));
   TKC_TRY(cudaGetLastError());
   ntop.resize(ng);
   tied.resize(ng);
@@ -625,7 +680,8 @@ void tkc_free_graph(tkc_graph *g) {
   if (g->ioff && g->ioff != g->off) cudaFree(g->ioff);
   if (g->icol && g->icol != g->col) cudaFree(g->icol);
   void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega, g->scc_size, g->features,
-                  g->learned_order, g->seeded_order, g->nb_order, g->nb_S, g->nb_r, g->nb_key};
+                  g->learned_order, g->seeded_order, g->nb_order, g->nb_S, g->nb_r, g->nb_key, g->nb_hkey,
+                  g->nb_horder, g->comp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   g->ctx->graphs_alive--;
@@ -685,14 +741,14 @@ static void reset_result(tkc_result *r, u32 kk) {
 
 static u32 nb_levels_of(const tkc_options &o) { return o.nb_levels ? o.nb_levels : 256u; }
 
-static int source_order_of(tkc_graph *g, const tkc_options &o, u32 kk, const u32 **order, u32 *norder,
-                           const u64 **lb_key) {
+static int source_order_of(tkc_graph *g, const tkc_options &o, u32 kk, int harmonic, const u32 **order,
+                           u32 *norder, const u64 **lb_key) {
   *lb_key = nullptr;
   if (o.order == TKC_ORDER_NB) {
     TKC_RC(ensure_nb_bounds(g, nb_levels_of(o)));
-    *order = g->nb_order;
+    *order = harmonic ? g->nb_horder : g->nb_order;
     *norder = g->n_src_nb;
-    *lb_key = g->nb_key;
+    *lb_key = harmonic ? g->nb_hkey : g->nb_key;
   } else if (o.order == TKC_ORDER_GIVEN) {
     if (!g->given_order) return TKC_EINVAL;
     *order = g->given_order;
@@ -783,7 +839,7 @@ static int time_config(tkc_graph *g, const u32 *order, u32 norder, u32 kk, u32 b
   return TKC_OK;
 }
 
-int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
+static int topk_one(tkc_graph *g, uint32_t k, tkc_result *out, int harmonic) {
   if (!g || !out) return TKC_EINVAL;
   if (k > TKC_MAX_K) return TKC_EINVAL;
   tkc_ctx *ctx = g->ctx;
@@ -803,9 +859,9 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   RunSetup rs;
   memset(&rs, 0, sizeof(rs));
   const tkc_options &o = ctx->opt;
-  TKC_RC(source_order_of(g, o, kk, &rs.order, &rs.norder, &rs.lb_key));
+  TKC_RC(source_order_of(g, o, kk, harmonic, &rs.order, &rs.norder, &rs.lb_key));
   TKC_TRY(cudaEventRecord(ctx->ev[1], st));
-  u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g->n);
+  u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g->n, rs.lb_key != nullptr);
   tkc_options saved = ctx->opt;
   if (!o.batch_bits) {
     auto it = ctx->tune.find(graph_class(g));
@@ -822,6 +878,7 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) {
   rs.B = bits;
   rs.W = words_for(bits);
   rs.nocut = 0;
+  rs.harmonic = harmonic;
   rs.nocut_prefix = (u32)std::min<u64>((u64)o.seed_factor * kk, 0xffffffffull);
   rs.kk = kk;
   rs.ng = 1;
@@ -973,7 +1030,193 @@ int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_
   return TKC_OK;
 }
 
-int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs) {
+// Algorithm 1 with updateBoundsLB (DegBound with the degree order, NBBound
+// with options.order = TKC_ORDER_NB): rounds of up to B complete searches from
+// the unsearched vertices of smallest bound, each round raising the bounds of
+// the vertices whose reach equals a searched source's.
+static int topk_bound(tkc_graph *g, uint32_t k, tkc_result *out) {
+  if (!g || !out) return TKC_EINVAL;
+  if (k > TKC_MAX_K) return TKC_EINVAL;
+  tkc_ctx *ctx = g->ctx;
+  const tkc_options &o = ctx->opt;
+  if (o.order != TKC_ORDER_DEG && o.order != TKC_ORDER_NB) return TKC_EINVAL;
+  u32 kk = std::min<u32>(k, g->n);
+  if (kk > 0 && out->capacity < kk) return TKC_EINVAL;
+  TKC_TRY(cudaSetDevice(ctx->device));
+  tkc_result r = *out;
+  reset_result(&r, kk);
+  if (kk == 0) {
+    *out = r;
+    return TKC_OK;
+  }
+  cudaStream_t st = ctx->stream;
+  const u32 n = g->n;
+  TKC_TRY(cudaEventRecord(ctx->ev[0], st));
+  TKC_RC(ensure_degree_order(g));
+  TKC_RC(ensure_reach_bounds(g));
+  const bool nb = o.order == TKC_ORDER_NB;
+  if (nb) TKC_RC(ensure_nb_bounds(g, nb_levels_of(o)));
+  const u32 *order0 = nb ? g->nb_order : g->deg_order;
+  const u32 n0 = nb ? g->n_src_nb : g->n_src_deg;
+  const u32 B = o.batch_bits ? o.batch_bits : 64;
+  const u32 cap = std::min<u32>(n + 1, 65535u);  // levels per search (depth < n)
+  TKC_RC(ensure_workspace(ctx, n, words_for(B), kk, 1, 1));
+  u64 *bS = nullptr, *key = nullptr, *Ltab = nullptr, *smax = nullptr, *bkeys = nullptr;
+  u32 *bR = nullptr, *cand = nullptr, *pos = nullptr, *tmp = nullptr, *lo = nullptr, *hist = nullptr, *depth = nullptr;
+  uint8_t *done = nullptr;
+  uint16_t *lvl = nullptr;
+  int rc = TKC_OK;
+  auto cleanup = [&]() {
+    void *ptrs[] = {bS, key, Ltab, smax, bkeys, bR, cand, pos, tmp, lo, hist, depth, done, lvl};
+    for (void *q : ptrs)
+      if (q) cudaFreeAsync(q, st);
+    cudaStreamSynchronize(st);
+  };
+#define LB_TRY(expr)                                                  \
+  do {                                                                \
+    cudaError_t e_ = (expr);                                          \
+    if (e_ != cudaSuccess) {                                          \
+      tkc_set_last_cuda_error(e_, #expr, __FILE__, __LINE__);         \
+      cleanup();                                                      \
+      return e_ == cudaErrorMemoryAllocation ? TKC_ENOMEM : TKC_ECUDA; \
+    }                                                                 \
+  } while (0)
+#define LB_RC(expr)     \
+  do {                  \
+    rc = (expr);        \
+    if (rc != TKC_OK) { \
+      cleanup();        \
+      return rc;        \
+    }                   \
+  } while (0)
+  const size_t n1 = std::max<size_t>(n, 1);
+  LB_TRY(cudaMallocAsync(&bS, n1 * sizeof(u64), st));
+  LB_TRY(cudaMallocAsync(&key, n1 * sizeof(u64), st));
+  LB_TRY(cudaMallocAsync(&bR, n1 * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&done, n1, st));
+  LB_TRY(cudaMallocAsync(&cand, n1 * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&pos, (n1 + 1) * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&tmp, ((n1 + 1) / 4096 + 16) * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&lo, n1 * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&smax, sizeof(u64), st));
+  LB_TRY(cudaMallocAsync(&hist, (size_t)B * cap * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&Ltab, (size_t)B * cap * sizeof(u64), st));
+  LB_TRY(cudaMallocAsync(&depth, (size_t)B * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&bkeys, (size_t)B * sizeof(u64), st));
+  LB_TRY(cudaMallocAsync(&lvl, n1 * B * sizeof(uint16_t), st));
+  LB_TRY(cudaMemsetAsync(lvl, 0xff, n1 * B * sizeof(uint16_t), st));
+  LB_RC(lb_init(g, nb ? g->nb_S : nullptr, nb ? g->nb_r : nullptr, nb ? g->nb_key : nullptr, bS, bR, key, done));
+  TKC_TRY(cudaEventRecord(ctx->ev[1], st));
+  Ctl total;
+  memset(&total, 0, sizeof(total));
+  double ms_kernel = 0;
+  u32 nround = 0;
+  std::vector<u64> h_key(B);
+  while (true) {
+    u32 m = 0;
+    LB_RC(lb_sorted_candidates(g, order0, n0, done, key, cand, &m, pos, tmp, lo, smax));
+    if (m == 0) break;
+    const u32 take = std::min<u32>(B, m);
+    // the batch's keys and the current k-th entry decide the stop
+    LB_RC(lb_gather_keys(g, take, cand, key, bkeys));
+    LB_TRY(cudaMemcpyAsync(h_key.data(), bkeys, take * sizeof(u64), cudaMemcpyDeviceToHost, st));
+    unsigned ntop = 0;
+    u64 xS = 0;
+    u32 xr = 0;
+    Workspace &w = ctx->ws;
+    if (nround > 0) {
+      LB_TRY(cudaMemcpyAsync(&ntop, w.g_ntop, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      LB_TRY(cudaMemcpyAsync(&xS, w.top_S + kk - 1, sizeof(u64), cudaMemcpyDeviceToHost, st));
+      LB_TRY(cudaMemcpyAsync(&xr, w.top_r + kk - 1, sizeof(u32), cudaMemcpyDeviceToHost, st));
+    }
+    LB_TRY(cudaStreamSynchronize(st));
+    // Algorithm 1: stop at the first candidate whose key exceeds x strictly
+    u32 cnt = take;
+    if (ntop == kk) {
+      for (u32 i = 0; i < take; ++i) {
+        const unsigned __int128 lhs = (unsigned __int128)h_key[i] * ((u64)(xr - 1) * (u64)(xr - 1));
+        if (lhs > ((unsigned __int128)xS << 46)) {
+          cnt = i;
+          break;
+        }
+      }
+    }
+    if (cnt == 0) break;
+    LB_TRY(cudaMemsetAsync(hist, 0, (size_t)B * cap * sizeof(u32), st));
+    RunSetup rs;
+    memset(&rs, 0, sizeof(rs));
+    rs.g = g;
+    rs.order = cand;
+    rs.norder = cnt;
+    rs.B = B;
+    rs.W = words_for(B);
+    rs.nocut = 1;
+    rs.kk = kk;
+    rs.ng = 1;
+    rs.lvl = lvl;
+    rs.hist = hist;
+    rs.hist_cap = cap;
+    rs.keep_lists = nround > 0;
+    rs.force_teams = 1;
+    Ctl hc;
+    LB_RC(run_search(ctx, rs, &hc));
+    float ms = 0;
+    LB_TRY(cudaEventSynchronize(ctx->ev[5]));
+    LB_TRY(cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]));
+    ms_kernel += ms;
+    total.edges_visited += hc.edges_visited;
+    total.edges_scanned += hc.edges_scanned;
+    total.bfs_started += hc.bfs_started;
+    total.bfs_finished += hc.bfs_finished;
+    total.levels += hc.levels;
+    total.alg_bytes += hc.alg_bytes;
+    LB_RC(lb_update(g, B, cnt, cand, lvl, hist, cap, depth, Ltab, w.res_r, bS, bR, key, done));
+    ++nround;
+  }
+  RunSetup rs;
+  memset(&rs, 0, sizeof(rs));
+  rs.g = g;
+  rs.kk = kk;
+  rs.ng = 1;
+  r.batch_bits = B;
+  if (nround == 0) {
+    // nothing searched (no vertex reaches another): the list is empty
+    LB_TRY(cudaMemsetAsync(ctx->ws.g_ntop, 0, sizeof(unsigned), st));
+    LB_TRY(cudaMemsetAsync(ctx->ws.res_r, 0, n1 * sizeof(u32), st));
+  }
+  std::vector<GraphOut> go(1);
+  go[0].n = n;
+  go[0].base = 0;
+  go[0].kk = kk;
+  go[0].nzero = n - g->n_src_deg;
+  go[0].zero_ids = g->deg_order + g->n_src_deg;
+  std::vector<unsigned> ntop, tied;
+  std::vector<u64> gctr;
+  LB_RC(finish_run(ctx, rs, go, &r, ntop, tied, gctr));
+  LB_TRY(cudaEventRecord(ctx->ev[2], st));
+  LB_TRY(cudaStreamSynchronize(st));
+  cleanup();
+#undef LB_TRY
+#undef LB_RC
+  r.n_tied_at_kth = tied[0];
+  r.edges_visited = total.edges_visited;
+  r.edges_scanned = total.edges_scanned;
+  r.bfs_started = total.bfs_started;
+  r.bfs_cut = 0;
+  r.bfs_finished = total.bfs_finished;
+  r.levels = total.levels;
+  r.alg_bytes = total.alg_bytes;
+  float ms0 = 0, ms1 = 0;
+  cudaEventElapsedTime(&ms0, ctx->ev[0], ctx->ev[1]);
+  cudaEventElapsedTime(&ms1, ctx->ev[1], ctx->ev[2]);
+  r.ms_pre = ms0;
+  r.ms_bfs = ms1;
+  r.ms_kernel = ms_kernel;
+  *out = r;
+  return TKC_OK;
+}
+
+static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs, int harmonic) {
   if (!ctx || (ng && (!gs || !outs))) return TKC_EINVAL;
   if (k > TKC_MAX_K) return TKC_EINVAL;
   if (ng == 0) return TKC_OK;
@@ -1006,7 +1249,6 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
   for (u32 i = 0; i < ng; ++i) {
     TKC_RC(ensure_degree_order(gs[i]));
     TKC_RC(ensure_reach_bounds(gs[i]));
-    if (nb) TKC_RC(ensure_nb_bounds(gs[i], nb_levels_of(o)));
     vbase[i + 1] = vbase[i] + gs[i]->n;
     abase[i + 1] = abase[i] + gs[i]->arcs;
     offptr[i] = (u64)gs[i]->off;
@@ -1024,8 +1266,8 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
   int rc = TKC_OK;
   auto cleanup = [&]() {
     cudaStreamSynchronize(st);
-    void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.nb_key, U.nb_order, gid, d_vbase,
-                    d_abase, d_offptr, d_colptr, d_gdir};
+    void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.nb_S, U.nb_r, U.nb_key, U.nb_hkey,
+                    U.nb_order, U.nb_horder, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir};
     for (void *q : ptrs)
       if (q) cudaFree(q);
   };
@@ -1073,14 +1315,11 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
     }
   MULTI_RC(build_in_csr(&U));
   if (nb) {
-    // every graph's keys side by side, then all sources by (key, union id)
-    MULTI_TRY(cudaMallocAsync(&U.nb_key, std::max<size_t>(nv, 1) * sizeof(u64), st));
-    MULTI_TRY(cudaMallocAsync(&U.nb_order, std::max<size_t>(nv, 1) * sizeof(u32), st));
-    for (u32 i = 0; i < ng; ++i)
-      if (gs[i]->n)
-        MULTI_TRY(cudaMemcpyAsync(U.nb_key + vbase[i], gs[i]->nb_key, gs[i]->n * sizeof(u64), cudaMemcpyDeviceToDevice,
-                                  st));
-    MULTI_RC(nb_sort_sources(&U, U.nb_key, U.nb_order, &U.n_src_nb));
+    // the sweeps run once over the union (each vertex's counts involve only its
+    // own graph, so they equal the per-graph values); all sources of all graphs
+    // are then ordered by (key, union id)
+    U.have_reach = true;
+    MULTI_RC(ensure_nb_bounds(&U, nb_levels_of(o), gid, d_gdir));
   } else {
     MULTI_RC(ensure_degree_order(&U));
   }
@@ -1089,12 +1328,13 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
   memset(&rs, 0, sizeof(rs));
   u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(nv);
   rs.g = &U;
-  rs.order = nb ? U.nb_order : U.deg_order;
+  rs.order = nb ? (harmonic ? U.nb_horder : U.nb_order) : U.deg_order;
   rs.norder = nb ? U.n_src_nb : U.n_src_deg;
-  rs.lb_key = nb ? U.nb_key : nullptr;
+  rs.lb_key = nb ? (harmonic ? U.nb_hkey : U.nb_key) : nullptr;
   rs.B = bits;
   rs.W = words_for(bits);
   rs.nocut = 0;
+  rs.harmonic = harmonic;
   rs.kk = kk;
   rs.ng = ng;
   rs.gid = gid;
@@ -1137,6 +1377,20 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
 #undef MULTI_RC
   cleanup();
   return TKC_OK;
+}
+
+int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) { return topk_one(g, k, out, 0); }
+
+int tkc_topk_harmonic(tkc_graph *g, uint32_t k, tkc_result *out) { return topk_one(g, k, out, 1); }
+
+int tkc_topk_closeness_bound(tkc_graph *g, uint32_t k, tkc_result *out) { return topk_bound(g, k, out); }
+
+int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs) {
+  return topk_many(ctx, gs, ng, k, outs, 0);
+}
+
+int tkc_topk_harmonic_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs) {
+  return topk_many(ctx, gs, ng, k, outs, 1);
 }
 
 }  // extern "C"

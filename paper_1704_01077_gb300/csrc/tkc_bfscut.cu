@@ -135,12 +135,32 @@ __device__ __forceinline__ bool nb_exceeds(u64 key, u64 Sx, u64 rx) {
   return (u128)key * (u128)((rx - 1) * (rx - 1)) > ((u128)Sx << 46);
 }
 
-// (S, r, id) order: farness ascending, then id ascending.  r >= 2 here.
-__device__ __forceinline__ bool entry_less(u64 Sa, u32 ra, u32 ia, u64 Sb, u32 rb, u32 ib) {
+// List order.  Closeness: (S, r, id) by farness ascending, then id ascending
+// (r >= 2 here).  Harmonic: the key is the FP64 bit pattern of h >= 0, which
+// orders like the value; larger h first, then smaller id.
+__device__ __forceinline__ bool entry_less(bool harmonic, u64 Sa, u32 ra, u32 ia, u64 Sb, u32 rb, u32 ib) {
+  if (harmonic) return Sa != Sb ? Sa > Sb : ia < ib;
   u128 lhs = (u128)Sa * (u128)((u64)(rb - 1) * (u64)(rb - 1));
   u128 rhs = (u128)Sb * (u128)((u64)(ra - 1) * (u64)(ra - 1));
   if (lhs != rhs) return lhs < rhs;
   return ia < ib;
+}
+
+// Harmonic centrality (the paper's closing generalisation to sums of f(d) with
+// f = 1/d): after level d, the vertices not yet found lie at distance >= d+1,
+// at most g of them at d+1, and there are at most omega - n_d of them, so
+//   h <= U = H_d + min(g, w)/(d+1) + max(0, w - g)/(d+2),  w = omega - n_d.
+// The search is abandoned when fl(U * (1 + 2^-20)) < x: the margin covers the
+// rounding of H_d and U and of the FP64 h it is compared with (depths < 2^32).
+constexpr double kHMargin = 1.0 + 1.0 / 1048576.0;
+
+__device__ __forceinline__ bool harmonic_below(double Hd, u64 d, u64 nd, u64 g, u64 omega, u64 xbits) {
+  const u64 w = omega > nd ? omega - nd : 0;
+  const u64 near_ = g < w ? g : w, far_ = w > g ? w - g : 0;
+  const double t1 = __ddiv_rn((double)near_, (double)(d + 1));
+  const double t2 = __ddiv_rn((double)far_, (double)(d + 2));
+  const double U = __dadd_rn(__dadd_rn(Hd, t1), t2);
+  return __dmul_rn(U, kHMargin) < __longlong_as_double((long long)xbits);
 }
 
 // ------------------------------------------------------------------ warp helpers
@@ -293,6 +313,22 @@ __device__ __forceinline__ void clear_frontier(u64 *F, uint32_t *FB, const uint3
     for (uint64_t i = gthread; i < count; i += nthreads) {
       uint32_t v = list[i];
       atomicAnd(&FB[v >> 5], ~(1u << (v & 31)));
+    }
+  }
+}
+
+// updateBoundsLB: the slots whose bits are new in this vertex's row found it at
+// this depth.
+template <int W>
+__device__ __forceinline__ void record_levels(const RunParams &p, uint32_t v, const u64 (&nw)[W], uint32_t depth) {
+  uint16_t *row = p.lvl + (size_t)v * p.B;
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    u64 b = nw[q];
+    while (b) {
+      const int j = __ffsll((long long)b) - 1;
+      b &= b - 1;
+      row[64 * q + j] = (uint16_t)depth;
     }
   }
 }
@@ -478,12 +514,12 @@ __device__ void merge_topk_one(const RunParams &p, Smem<W> &sm) {
     uint32_t lo = 0, hi = ntop;  // first existing entry not less than the candidate
     while (lo < hi) {
       uint32_t mid = (lo + hi) >> 1;
-      if (entry_less(sm.tS[mid], sm.tr[mid], sm.tid[mid], S, r, id)) lo = mid + 1;
+      if (entry_less(p.harmonic, sm.tS[mid], sm.tr[mid], sm.tid[mid], S, r, id)) lo = mid + 1;
       else hi = mid;
     }
     uint32_t rank = lo;
     for (uint32_t j = 0; j < nc; ++j)
-      if (j != i && entry_less(sm.cS[j], sm.cr[j], sm.cid[j], S, r, id)) ++rank;
+      if (j != i && entry_less(p.harmonic, sm.cS[j], sm.cr[j], sm.cid[j], S, r, id)) ++rank;
     if (rank < kk) {
       p.top_S[rank] = S;
       p.top_r[rank] = r;
@@ -493,7 +529,7 @@ __device__ void merge_topk_one(const RunParams &p, Smem<W> &sm) {
   for (uint32_t i = threadIdx.x; i < ntop; i += kTPB) {
     uint32_t rank = i;
     for (uint32_t j = 0; j < nc; ++j)
-      if (entry_less(sm.cS[j], sm.cr[j], sm.cid[j], sm.tS[i], sm.tr[i], sm.tid[i])) ++rank;
+      if (entry_less(p.harmonic, sm.cS[j], sm.cr[j], sm.cid[j], sm.tS[i], sm.tr[i], sm.tid[i])) ++rank;
     if (rank < kk) {
       p.top_S[rank] = sm.tS[i];
       p.top_r[rank] = sm.tr[i];
@@ -524,9 +560,9 @@ __device__ void merge_topk_many(const RunParams &p, Smem<W> &sm) {
       if (sm.cg[j] != g) continue;
       u64 S = sm.cS[j];
       uint32_t r = sm.cr[j], id = sm.cid[j];
-      if (cnt == kk && !entry_less(S, r, id, tS[kk - 1], tr[kk - 1], ti[kk - 1])) continue;
+      if (cnt == kk && !entry_less(p.harmonic, S, r, id, tS[kk - 1], tr[kk - 1], ti[kk - 1])) continue;
       uint32_t pos = cnt < kk ? cnt++ : kk - 1;
-      while (pos > 0 && entry_less(S, r, id, tS[pos - 1], tr[pos - 1], ti[pos - 1])) {
+      while (pos > 0 && entry_less(p.harmonic, S, r, id, tS[pos - 1], tr[pos - 1], ti[pos - 1])) {
         tS[pos] = tS[pos - 1];
         tr[pos] = tr[pos - 1];
         ti[pos] = ti[pos - 1];
@@ -565,7 +601,7 @@ template <int W>
 __device__ __forceinline__ void offer_candidate(const RunParams &p, Smem<W> &sm, u64 S, uint32_t r, uint32_t v,
                                                 uint32_t g) {
   Thresh x = thresh_of(p, g);
-  if (x.have && !entry_less(S, r, v, x.S, x.r, x.id)) return;
+  if (x.have && !entry_less(p.harmonic, S, r, v, x.S, x.r, x.id)) return;
   unsigned pos = atomicAdd(&sm.ncand, 1u);
   sm.cS[pos] = S;
   sm.cr[pos] = r;
@@ -615,15 +651,23 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
     if (cn == 0) {
       // the BFS from sl.v is complete: S and r = n_d are exact
       sl.state = 2;
-      p.res_S[sl.v] = sl.S;
+      const u64 key = p.harmonic ? (u64)__double_as_longlong(sl.H) : sl.S;
+      p.res_S[sl.v] = key;
       p.res_r[sl.v] = (uint32_t)sl.nd;
       ++finished;
       graph_count(p, sl.graph, 3, 1);
-      offer_candidate(p, sm, sl.S, (uint32_t)sl.nd, sl.v, sl.graph);
+      offer_candidate(p, sm, key, (uint32_t)sl.nd, sl.v, sl.graph);
     } else {
       const int directed = p.g_directed ? p.g_directed[sl.graph] : p.directed;
       sl.d += 1;
+      if (p.hist) {
+        if (sl.d < p.hist_cap)
+          p.hist[(size_t)s * p.hist_cap + sl.d] = cn;
+        else
+          atomicCAS(&c->err, 0, TKC_EOVERFLOW);
+      }
       sl.S += (u64)sl.d * cn;
+      sl.H = __dadd_rn(sl.H, __ddiv_rn((double)cn, (double)sl.d));
       sl.nd += cn;
       sl.g = ws - (directed ? 0ull : (u64)cn);
       sl.arcs = ws;
@@ -644,7 +688,9 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
     if (!cont[t]) continue;
     Slot sl = p.slots[s];
     Thresh x = thresh_of(p, sl.graph);
-    if (!p.nocut && !sl.nocut && x.have && cut_exceeds(sl.S, sl.d, sl.nd, sl.g, sl.alpha, sl.omega, x.S, x.r)) {
+    const bool below = x.have && (p.harmonic ? harmonic_below(sl.H, sl.d, sl.nd, sl.g, sl.omega, x.S)
+                                             : cut_exceeds(sl.S, sl.d, sl.nd, sl.g, sl.alpha, sl.omega, x.S, x.r));
+    if (!p.nocut && !sl.nocut && below) {
       sl.state = 2;
       ++cuts;
       graph_count(p, sl.graph, 2, 1);
@@ -702,6 +748,7 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
     }
     c->nl_packed = 0;
     c->cur ^= 1;
+    c->bdepth += 1;
     c->fl_count = (uint32_t)(packed >> kPackShift);
     c->fl_arcs = packed & kArcMask;
     c->level_id += 1;
@@ -730,8 +777,33 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
   uint32_t assigned = 0, last_base = 0;
   u64 arcs_total = 0, started = 0, cut0 = 0;
   __shared__ uint32_t s_base;
+  __shared__ int s_gate;
   if (threadIdx.x < W) sm.active[threadIdx.x] = 0;
+  // One graph and several teams, no threshold yet: the other teams start only
+  // after team 0's first batch.  Until then every source they took would be
+  // searched to the end; afterwards most are abandoned at once.
+  if (threadIdx.x == 0) {
+    volatile Shared *vsh = p.sh;
+    if (p.team == 0 && c->batches >= 1) vsh->first_done = 1u;
+    s_gate = p.teams > 1 && p.team != 0 && p.ng == 1 && !p.nocut && vsh->first_done == 0u &&
+             vsh->cursor < p.norder && vsh->err == 0 && !thresh_of(p, 0).have;
+  }
   __syncthreads();
+  if (s_gate) {
+    if (threadIdx.x == 0) {
+      __nanosleep(2000);
+      c->fl_count = 0;
+      c->fl_arcs = 0;
+      c->vl_count = 0;
+      c->nl_packed = 0;
+      c->level_id += 1;
+      for (int j = 0; j < W; ++j) c->active[j] = 0;
+      c->step = 1;  // another empty clear step, then this check again
+    }
+    for (uint32_t s = threadIdx.x; s < B; s += kTPB) p.slots[s].state = 0;
+    __syncthreads();
+    return;
+  }
   // take sources from the shared cursor, `room` positions at a time, so that
   // every position taken is either abandoned at level 0 or gets a slot
   while (assigned < B) {
@@ -755,8 +827,15 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     const bool stopped = valid && p.lb_key && p.gid && *(volatile unsigned *)&p.g_stop[gv];
     if (valid && !stopped && !p.nocut && idx >= p.nocut_prefix) {
       Thresh x = thresh_of(p, gv);
-      stop = x.have && p.lb_key && nb_exceeds(p.lb_key[v], x.S, x.r);
-      cut = !stop && x.have && cut_exceeds(0, 0, 1, od, a, o, x.S, x.r);
+      if (p.harmonic) {
+        stop = x.have && p.lb_key &&
+               __dmul_rn(__longlong_as_double((long long)~p.lb_key[v]), kHMargin) <
+                   __longlong_as_double((long long)x.S);
+        cut = !stop && x.have && harmonic_below(0.0, 0, 1, od, o, x.S);
+      } else {
+        stop = x.have && p.lb_key && nb_exceeds(p.lb_key[v], x.S, x.r);
+        cut = !stop && x.have && cut_exceeds(0, 0, 1, od, a, o, x.S, x.r);
+      }
     }
     // nothing after a stopped position of its graph is searched, by any team
     if (stop) {
@@ -789,7 +868,8 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       sl.state = 1;
       sl.graph = gv;
       sl.nocut = idx < p.nocut_prefix;
-      sl.pad[0] = sl.pad[1] = sl.pad[2] = 0;
+      sl.pad = 0;
+      sl.H = 0.0;
       p.slots[s] = sl;
       graph_count(p, gv, 1, 1);
       graph_count(p, gv, 0, od);
@@ -820,6 +900,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     c->fl_count = assigned;
     c->fl_arcs = arcs_total;
     c->vl_count = assigned;
+    c->bdepth = 0;
     c->nl_packed = 0;
     c->level_id += 1;
     if (p.trace) {
@@ -842,6 +923,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     for (int j = 0; j < W; ++j) c->active[j] = sm.active[j];
     if (assigned == 0) {
       c->done = 1;
+      if (p.team == 0) ((volatile Shared *)p.sh)->first_done = 1u;
     } else {
       c->step = 0;
       c->dir = ((u128)arcs_total * p.bu_num > (u128)p.arcs * p.bu_den) ? 1 : 0;
@@ -864,6 +946,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
   const uint32_t tb = blockIdx.x % bpt;
   if (threadIdx.x == 0) {
     p = p0;
+    p.team = team;
     p.ctl = p0.ctl + team;
     p.slots = p0.slots + (size_t)team * 64 * kMaxWords;
     p.cnt = p0.cnt + (size_t)team * 64 * kMaxWords;
@@ -923,6 +1006,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
     if (tb == 0) trace_stamp(p, 8);
     const int dir = vc->dir;
     const uint32_t level_id = vc->level_id;
+    const uint32_t depth = vc->bdepth + 1;  // depth of the level being discovered
     const u64 fl_arcs = vc->fl_arcs;
     if (threadIdx.x < W) sm.active[threadIdx.x] = vc->active[threadIdx.x];
     for (int i = threadIdx.x; i < 64 * W; i += kTPB) {
@@ -1025,6 +1109,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
           store_row<W>(Fnext, w, nw);
           store_row<W>(p.N, w, z);
           atomicOr(&FBnext[w >> 5], 1u << (w & 31));
+          if (p.lvl) record_levels<W>(p, w, nw, depth);
         }
         warp_count_slots<W>(nw, od, sm.cnt, sm.wsum, lane);
         warp_append_plain(valid && was_empty, w, &c->vl_count, p.VL, lane);
@@ -1093,6 +1178,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
           for (int q = 0; q < W; ++q) sr[q] |= nw[q];
           store_row<W>(p.seen, w, sr);
           store_row<W>(Fnext, w, nw);
+          if (p.lvl) record_levels<W>(p, w, nw, depth);
         }
         {
           // the warp owns the 32 consecutive vertices of one bitmap word

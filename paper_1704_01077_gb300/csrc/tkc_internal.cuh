@@ -75,6 +75,8 @@ struct Ctl {
   unsigned long long lvl_scan_v;
   unsigned long long lvl_scan_a;
   unsigned long long trace_n;  // records written to the optional trace
+  unsigned int bdepth;         // depth reached by the current batch (0 after seeding)
+  unsigned int pad1;
 };
 
 // State shared by all teams of one run.
@@ -82,7 +84,7 @@ struct Shared {
   unsigned int cursor;   // next position in the source order (teams take chunks)
   int lock;              // guards the k-lists while a team merges
   int err;               // first error of any team
-  unsigned int pad;
+  unsigned int first_done;  // team 0 has finished its first batch (other teams may start)
 };
 
 struct Slot {
@@ -96,7 +98,8 @@ struct Slot {
   int state;              // 0 free, 1 active, 2 done (waiting for the clear step)
   unsigned int graph;     // graph of the source (several graphs in one run)
   unsigned int nocut;     // 1: searched to the end (threshold seeding)
-  unsigned int pad[3];
+  unsigned int pad;
+  double H;               // harmonic runs: sum over discovered levels of |level| / level
 };
 
 struct RunParams {
@@ -112,6 +115,7 @@ struct RunParams {
   // teams: independent groups of `gridDim.x / teams` blocks, each running its
   // own batches; per-team buffers sit at team * stride from the base pointers
   uint32_t teams;
+  uint32_t team;         // this block's team (set by the kernel)
   uint64_t row_stride;   // 64-bit words between the teams' seen/F0/F1/N rows
   uint64_t vtx_stride;   // 32-bit words between the teams' lists and stamps
   uint64_t fb_stride;    // 32-bit words between the teams' frontier bitmaps
@@ -129,12 +133,20 @@ struct RunParams {
   uint32_t kk;        // min(k, n); 0 never reaches the kernel
   uint32_t B;         // active slots per batch (1..64*W)
   int nocut;          // 1: never cut (exact S, r for every source)
+  int harmonic;       // 1: rank by harmonic centrality (list keys are the FP64 bits of h, largest first)
   uint32_t nocut_prefix;  // sources at order positions below this are never cut
   // NBCut (nullptr: off): per-vertex floor(2^46 * bound on S/(r-1)^2), the
   // order sorted by it; seeding stops at the first source whose key exceeds
-  // its graph's k-th farness strictly
+  // its graph's k-th farness strictly.  Harmonic runs: ~(FP64 bits of the
+  // upper bound on h), stop when the bound is below the k-th h.
   const unsigned long long *lb_key;
   unsigned int *g_stop;  // several graphs: graph g's search has stopped (its later sources are skipped)
+  // updateBoundsLB (nullptr: off; one team, every search complete): the level
+  // at which each vertex is found by each slot, lvl[v * B + slot] (0xffff: not
+  // found), and each slot's level sizes hist[slot * hist_cap + level]
+  uint16_t *lvl;
+  uint32_t *hist;
+  uint32_t hist_cap;
   uint32_t bu_num, bu_den;
   uint64_t timeout;
   // workspace
@@ -234,6 +246,7 @@ struct tkc_graph {
   uint32_t n_src_given = 0;
   uint32_t *alpha = nullptr, *omega = nullptr;
   uint32_t *scc_size = nullptr;               // size of the SCC (component, if undirected) of each vertex
+  uint32_t *comp = nullptr;                   // SCC (component, if undirected) id of each vertex
   bool have_order = false, have_reach = false;
   float *features = nullptr;                  // standardized vertex features, n x TKC_MLP_FEATURES
   uint32_t *learned_order = nullptr;          // filtered order by predicted farness
@@ -249,6 +262,8 @@ struct tkc_graph {
   unsigned long long *nb_S = nullptr;         // neighbourhood bound: S~ at the minimising reach
   uint32_t *nb_r = nullptr;                   //   that reach (1: out-degree 0)
   unsigned long long *nb_key = nullptr;       //   floor(S~ * 2^46 / (r-1)^2)
+  unsigned long long *nb_hkey = nullptr;      // harmonic: ~(FP64 bits of the upper bound on h)
+  uint32_t *nb_horder = nullptr;              // harmonic NBCut order: by (nb_hkey, id)
 };
 
 namespace tkc {
@@ -259,8 +274,21 @@ int ensure_degree_order(tkc_graph *g);
 int ensure_reach_bounds(tkc_graph *g);
 int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
 // tkc_nb.cu
-int ensure_nb_bounds(tkc_graph *g, uint32_t max_levels);
+// gid/g_directed (several graphs as one union): per-vertex directedness
+int ensure_nb_bounds(tkc_graph *g, uint32_t max_levels, const uint32_t *gid = nullptr,
+                     const uint8_t *g_directed = nullptr);
 int nb_sort_sources(tkc_graph *g, const unsigned long long *key, uint32_t *order, uint32_t *count);
+// tkc_lb.cu
+int lb_init(tkc_graph *g, const unsigned long long *S0, const uint32_t *r0, const unsigned long long *key0,
+            unsigned long long *bS, uint32_t *bR, unsigned long long *key, uint8_t *done);
+int lb_sorted_candidates(tkc_graph *g, const uint32_t *order0, uint32_t n0, const uint8_t *done,
+                         const unsigned long long *key, uint32_t *cand, uint32_t *count, uint32_t *scratch_pos,
+                         uint32_t *scratch_tmp, uint32_t *scratch_lo, unsigned long long *scratch_max);
+int lb_gather_keys(tkc_graph *g, uint32_t cnt, const uint32_t *cand, const unsigned long long *key,
+                   unsigned long long *out);
+int lb_update(tkc_graph *g, uint32_t B, uint32_t nsrc, const uint32_t *srcs, uint16_t *lvl, uint32_t *hist,
+              uint32_t cap, uint32_t *depth, unsigned long long *Ltab, const uint32_t *res_r, unsigned long long *bS,
+              uint32_t *bR, unsigned long long *key, uint8_t *done);
 // tkc_mlp.cu
 int ensure_features(tkc_graph *g);
 int ensure_learned_order(tkc_graph *g);

@@ -25,7 +25,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <vector>
 
 #include "tkc_internal.cuh"
 
@@ -147,6 +150,7 @@ struct NbState {
   u64 *bS;      // best candidate's sum bound
   u32 *bR;      // best candidate's reach
   uint8_t *flag;
+  double *hU;   // harmonic centrality: running upper bound on h
 };
 
 __device__ __forceinline__ void candidate(u64 S, u64 r, bool &have, u64 &bS, u64 &br) {
@@ -167,7 +171,8 @@ __device__ __forceinline__ void candidate(u64 S, u64 r, bool &have, u64 &bS, u64
 // Level k: cur holds the gathered sums (k >= 2) and receives N~_k; prev2 holds
 // N~_{k-2}.  Unfinished vertices are counted into *left; an impossible
 // subtraction or an empty candidate set raises *err.
-__global__ void k_nb_level(u32 n, u32 k, u32 K, int directed, const u32 *__restrict__ off,
+__global__ void k_nb_level(u32 n, u32 k, u32 K, int directed, const u32 *__restrict__ gid,
+                           const uint8_t *__restrict__ gdir, const u32 *__restrict__ off,
                            const u32 *__restrict__ alpha, const u32 *__restrict__ omega,
                            const u64 *__restrict__ prev2, u64 *__restrict__ cur, NbState st, u32 *left,
                            int *err) {
@@ -179,7 +184,7 @@ __global__ void k_nb_level(u32 n, u32 k, u32 K, int directed, const u32 *__restr
       x = deg;
     } else {
       const u64 sum = cur[v] < kCap ? cur[v] : kCap;
-      if (directed) {
+      if (gdir ? gdir[gid[v]] : directed) {
         x = sum;
       } else {
         const u64 p2 = prev2[v];
@@ -202,6 +207,7 @@ __global__ void k_nb_level(u32 n, u32 k, u32 K, int directed, const u32 *__restr
     bool have = f & kHave;
     u64 bS = have ? st.bS[v] : 0, br = have ? st.bR[v] : 0;
     const u64 a = alpha[v], o = omega[v], c0 = st.c[v], P0 = st.P[v];
+    double hU = st.hU[v];
     bool fin = false;
     if (x == 0) {
       // no walk continues: r(v) <= c0, nothing above c0 is a candidate
@@ -218,18 +224,22 @@ __global__ void k_nb_level(u32 n, u32 k, u32 K, int directed, const u32 *__restr
       if (c1 > a && c1 < o) candidate(P0 + (u64)k * x, c1, have, bS, br);
       if (o <= c1) {
         candidate(P0 + (u64)k * (o - c0), o, have, bS, br);
+        hU = __dadd_rn(hU, __ddiv_rn((double)(o - c0), (double)k));
         fin = true;
       } else {
         const u64 P1 = P0 + (u64)k * x;
         st.c[v] = c1;
         st.P[v] = P1;
+        hU = __dadd_rn(hU, __ddiv_rn((double)x, (double)k));
         if (k == K) {
           // level K+1 unbounded: slope K+1 from c_K up to omega
           if (a > c1) candidate(P1 + (u64)(k + 1) * (a - c1), a, have, bS, br);
           candidate(P1 + (u64)(k + 1) * (o - c1), o, have, bS, br);
+          hU = __dadd_rn(hU, __ddiv_rn((double)(o - c1), (double)(k + 1)));
           fin = true;
         }
       }
+      st.hU[v] = hU;
     }
     if (have) {
       st.bS[v] = bS;
@@ -247,18 +257,22 @@ __global__ void k_nb_init(u32 n, NbState st, u64 *prev1, u64 *prev2) {
     st.c[v] = 1;
     st.P[v] = 0;
     st.flag[v] = 0;
+    st.hU[v] = 0.0;
     prev1[v] = 1;  // N~_0
     prev2[v] = 0;
   }
 }
 
-// order key of every vertex, and its bound in the graph's arrays
-__global__ void k_nb_keys(u32 n, NbState st, u64 *S_out, u32 *r_out, u64 *key, int *err) {
+// order keys of every vertex, and its bounds in the graph's arrays; the
+// harmonic key is the complement of the bound's FP64 bits (h >= 0), so that an
+// ascending sort puts the largest bound first
+__global__ void k_nb_keys(u32 n, NbState st, u64 *S_out, u32 *r_out, u64 *key, u64 *hkey, int *err) {
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     if (!(st.flag[v] & kHave)) {
       atomicOr(err, 4);  // every vertex finishes with a candidate
       continue;
     }
+    hkey[v] = ~(u64)__double_as_longlong(st.hU[v]);
     const u64 S = st.bS[v];
     const u64 r = st.bR[v];
     S_out[v] = S;
@@ -332,7 +346,7 @@ int nb_sort_sources(tkc_graph *g, const u64 *key, u32 *order, u32 *count) {
 
 // Computes the bound, the order keys and the NBCut order of g (cached until the
 // level cap changes).
-int ensure_nb_bounds(tkc_graph *g, u32 K) {
+int ensure_nb_bounds(tkc_graph *g, u32 K, const u32 *gid, const uint8_t *gdir) {
   if (K == 0 || K > 65535) return TKC_EINVAL;
   if (g->nb_order && g->nb_cap == K) return TKC_OK;
   TKC_RC(ensure_reach_bounds(g));
@@ -345,6 +359,8 @@ int ensure_nb_bounds(tkc_graph *g, u32 K) {
     TKC_TRY(cudaMallocAsync(&g->nb_S, n1 * sizeof(u64), st));
     TKC_TRY(cudaMallocAsync(&g->nb_r, n1 * sizeof(u32), st));
     TKC_TRY(cudaMallocAsync(&g->nb_key, n1 * sizeof(u64), st));
+    TKC_TRY(cudaMallocAsync(&g->nb_hkey, n1 * sizeof(u64), st));
+    TKC_TRY(cudaMallocAsync(&g->nb_horder, n1 * sizeof(u32), st));
   }
   if (n == 0) {
     g->n_src_nb = 0;
@@ -364,6 +380,7 @@ int ensure_nb_bounds(tkc_graph *g, u32 K) {
   TKC_TRY(cudaMallocAsync(&s.bS, n1 * sizeof(u64), st));
   TKC_TRY(cudaMallocAsync(&s.bR, n1 * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&s.flag, n1, st));
+  TKC_TRY(cudaMallocAsync(&s.hU, n1 * sizeof(double), st));
   TKC_TRY(cudaMallocAsync(&segpos, (n1 + 1) * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&tmp, ((n1 + 1) / 4096 + 16) * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&left, 2 * sizeof(u32), st));
@@ -392,8 +409,8 @@ int ensure_nb_bounds(tkc_graph *g, u32 K) {
                     nseg, seg_row, seg_begin, g->off, g->col, prev1, cur));
     }
     TKC_TRY(cudaMemsetAsync(left, 0, sizeof(u32), st));
-    TKC_LAUNCH(k_nb_level<<<grid_of(n), 256, 0, st>>>(n, k, K, g->directed, g->off, g->alpha, g->omega, prev2, cur,
-                                                      s, left, err));
+    TKC_LAUNCH(k_nb_level<<<grid_of(n), 256, 0, st>>>(n, k, K, g->directed, gid, gdir, g->off, g->alpha, g->omega,
+                                                      prev2, cur, s, left, err));
     TKC_TRY(cudaGetLastError());
     u32 h_left = 0;
     TKC_TRY(cudaMemcpyAsync(&h_left, left, sizeof(u32), cudaMemcpyDeviceToHost, st));
@@ -401,13 +418,15 @@ int ensure_nb_bounds(tkc_graph *g, u32 K) {
     levels = k;
     if (h_left == 0) break;
   }
-  TKC_LAUNCH(k_nb_keys<<<grid_of(n), 256, 0, st>>>(n, s, g->nb_S, g->nb_r, g->nb_key, err));
+  TKC_LAUNCH(k_nb_keys<<<grid_of(n), 256, 0, st>>>(n, s, g->nb_S, g->nb_r, g->nb_key, g->nb_hkey, err));
   int h_err = 0;
   TKC_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TKC_RC(nb_sort_sources(g, g->nb_key, g->nb_order, &g->n_src_nb));
+  u32 nh = 0;
+  TKC_RC(nb_sort_sources(g, g->nb_hkey, g->nb_horder, &nh));
   TKC_TRY(cudaStreamSynchronize(st));
   for (int i = 0; i < 3; ++i) TKC_TRY(cudaFreeAsync(N[i], st));
-  void *frees[] = {s.c, s.P, s.bS, s.bR, s.flag, segpos, seg_row, seg_begin, tmp, left, err};
+  void *frees[] = {s.c, s.P, s.bS, s.bR, s.flag, s.hU, segpos, seg_row, seg_begin, tmp, left, err};
   for (void *p : frees)
     if (p) TKC_TRY(cudaFreeAsync(p, st));
   if (h_err) return TKC_EGRAPH;
@@ -439,6 +458,28 @@ int tkc_nb_bounds(tkc_graph *g, uint32_t max_levels, uint64_t *S_lb, uint32_t *r
   TKC_TRY(cudaStreamSynchronize(st));
   if (n_order) *n_order = g->n_src_nb;
   if (levels) *levels = g->nb_levels;
+  return TKC_OK;
+}
+
+int tkc_nb_harmonic_bounds(tkc_graph *g, uint32_t max_levels, double *h_ub, uint32_t *order, uint32_t *n_order) {
+  if (!g || max_levels > 65535) return TKC_EINVAL;
+  TKC_TRY(cudaSetDevice(g->ctx->device));
+  TKC_RC(ensure_nb_bounds(g, max_levels ? max_levels : 256u));
+  cudaStream_t st = g->ctx->stream;
+  const size_t n = g->n;
+  if (n && h_ub) {
+    std::vector<u64> keys(n);
+    TKC_TRY(cudaMemcpyAsync(keys.data(), g->nb_hkey, n * sizeof(u64), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < n; ++i) {
+      const u64 b = ~keys[i];
+      memcpy(&h_ub[i], &b, sizeof(double));
+    }
+  }
+  if (n && order && g->n_src_nb)
+    TKC_TRY(cudaMemcpyAsync(order, g->nb_horder, (size_t)g->n_src_nb * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  if (n_order) *n_order = g->n_src_nb;
   return TKC_OK;
 }
 

@@ -489,6 +489,7 @@ static int reach_undirected(tkc_graph *g) {
   TKC_LAUNCH(k_cc_size<<<grid_for(n, 256), 256, 0, st>>>(parent, n, size));
   TKC_LAUNCH(k_cc_out<<<grid_for(n, 256), 256, 0, st>>>(parent, size, n, g->alpha, g->omega, g->scc_size));
   TKC_TRY(cudaGetLastError());
+  TKC_TRY(cudaMemcpyAsync(g->comp, parent, (size_t)n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
   TKC_TRY(cudaFreeAsync(parent, st));
   TKC_TRY(cudaFreeAsync(size, st));
   TKC_TRY(cudaFreeAsync(changed, st));
@@ -510,6 +511,7 @@ int ensure_reach_bounds(tkc_graph *g) {
   if (!g->alpha) TKC_TRY(cudaMallocAsync(&g->alpha, (size_t)g->n * sizeof(u32), st));
   if (!g->omega) TKC_TRY(cudaMallocAsync(&g->omega, (size_t)g->n * sizeof(u32), st));
   if (!g->scc_size) TKC_TRY(cudaMallocAsync(&g->scc_size, (size_t)g->n * sizeof(u32), st));
+  if (!g->comp) TKC_TRY(cudaMallocAsync(&g->comp, (size_t)g->n * sizeof(u32), st));
   TKC_RC(g->directed ? reach_directed_gpu(g) : reach_undirected(g));
   g->have_reach = true;
   return TKC_OK;

@@ -489,6 +489,7 @@ int reach_directed_gpu(tkc_graph *g) {
     TKC_RC(rc);
     TKC_LAUNCH(k_color_assign<<<grid_of(n), 256, 0, st>>>(n, active, color, found, comp));
   }
+  TKC_TRY(cudaMemcpyAsync(g->comp, comp, (size_t)n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
   // component sizes and the biggest SCC
   TKC_TRY(b.get(&wgt, n));
   TKC_TRY(b.get(&minid, n));

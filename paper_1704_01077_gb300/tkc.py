@@ -68,7 +68,8 @@ EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc
             "tkc_topk_closeness", "tkc_topk_closeness_multi", "tkc_source_order", "tkc_set_source_order",
             "tkc_reach_bounds", "tkc_distance_sums", "tkc_distance_sums_noalloc", "tkc_kernel_launches",
             "tkc_strerror", "tkc_vertex_features", "tkc_mlp_init", "tkc_set_source_model", "tkc_get_source_model",
-            "tkc_mlp_forward", "tkc_mlp_gradient", "tkc_mlp_train_step", "tkc_autotune", "tkc_nb_bounds"]
+            "tkc_mlp_forward", "tkc_mlp_gradient", "tkc_mlp_train_step", "tkc_autotune", "tkc_nb_bounds",
+            "tkc_topk_harmonic", "tkc_topk_harmonic_multi", "tkc_nb_harmonic_bounds", "tkc_topk_closeness_bound"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -105,6 +106,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tkc_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_float, fp]
     lib.tkc_autotune.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(tkc_options)]
     lib.tkc_nb_bounds.argtypes = [vp, ctypes.c_uint32, u64p, u32p, u64p, u32p, u32p, u32p]
+    lib.tkc_topk_harmonic.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(tkc_result)]
+    lib.tkc_topk_closeness_bound.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(tkc_result)]
+    lib.tkc_topk_harmonic_multi.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.POINTER(tkc_result)]
+    lib.tkc_nb_harmonic_bounds.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double), u32p, u32p]
     lib.tkc_kernel_launches.argtypes = []
     lib.tkc_kernel_launches.restype = ctypes.c_uint64
     lib.tkc_strerror.argtypes = [ctypes.c_int]
@@ -278,6 +284,45 @@ def tkc_topk_closeness_multi(ctx, graphs, k: int) -> list[Result]:
         keep.append(arrays)
     _check(_lib.tkc_topk_closeness_multi(ctx, arr, ng, k, results), "tkc_topk_closeness_multi")
     return [_to_result(results[i], keep[i]) for i in range(ng)]
+
+
+def tkc_topk_harmonic(g, k: int, capacity: int | None = None) -> Result:
+    """Top-k harmonic centrality: closeness[] holds h(v), farness[] 1/h(v)."""
+    cap = k if capacity is None else capacity
+    res, arrays = _new_result(cap)
+    _check(_lib.tkc_topk_harmonic(g, k, ctypes.byref(res)), "tkc_topk_harmonic")
+    return _to_result(res, arrays)
+
+
+def tkc_topk_closeness_bound(g, k: int, capacity: int | None = None) -> Result:
+    """Top-k closeness by DegBound / NBBound (Algorithm 1 with updateBoundsLB)."""
+    cap = k if capacity is None else capacity
+    res, arrays = _new_result(cap)
+    _check(_lib.tkc_topk_closeness_bound(g, k, ctypes.byref(res)), "tkc_topk_closeness_bound")
+    return _to_result(res, arrays)
+
+
+def tkc_topk_harmonic_multi(ctx, graphs, k: int) -> list[Result]:
+    ng = len(graphs)
+    arr = (ctypes.c_void_p * max(ng, 1))(*[g.value if isinstance(g, ctypes.c_void_p) else g for g in graphs])
+    results = (tkc_result * max(ng, 1))()
+    keep = []
+    for i in range(ng):
+        res, arrays = _new_result(k)
+        results[i] = res
+        keep.append(arrays)
+    _check(_lib.tkc_topk_harmonic_multi(ctx, arr, ng, k, results), "tkc_topk_harmonic_multi")
+    return [_to_result(results[i], keep[i]) for i in range(ng)]
+
+
+def tkc_nb_harmonic_bounds(g, n: int, max_levels: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """(h_ub, order): the upper bound on h per vertex and the sources by decreasing bound."""
+    h = np.zeros(max(n, 1), np.float64)
+    order = np.zeros(max(n, 1), np.uint32)
+    cnt = ctypes.c_uint32(0)
+    _check(_lib.tkc_nb_harmonic_bounds(g, max_levels, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       _u32p(order), ctypes.byref(cnt)), "tkc_nb_harmonic_bounds")
+    return h[:n], order[: cnt.value]
 
 
 def tkc_source_order(g, n: int) -> np.ndarray:
