@@ -154,6 +154,9 @@ __device__ __forceinline__ bool entry_less(bool harmonic, u64 Sa, u32 ra, u32 ia
 // rounding of H_d and U and of the FP64 h it is compared with (depths < 2^32).
 constexpr double kHMargin = 1.0 + 1.0 / 1048576.0;
 
+// bottom-up: in-degrees above this are walked by the whole warp
+constexpr uint32_t kHeavyIn = 256;
+
 __device__ __forceinline__ bool harmonic_below(double Hd, u64 d, u64 nd, u64 g, u64 omega, u64 xbits) {
   const u64 w = omega > nd ? omega - nd : 0;
   const u64 near_ = g < w ? g : w, far_ = w > g ? w - g : 0;
@@ -175,6 +178,12 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
     x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y & m) << j));
     m ^= m << (j >> 1);
   }
+  return x;
+}
+
+__device__ __forceinline__ u64 warp_or(u64 x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(FULL, x, o);
   return x;
 }
 
@@ -1124,10 +1133,13 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
         uint32_t w = base + lane;
         bool valid = w < p.n;
         u64 nw[W], sr[W], miss[W];
-        uint32_t od = 0;
-        bool was_empty = false, any = false;
+        uint32_t od = 0, e0 = 0, ee = 0;
+        bool was_empty = false, any = false, heavy = false;
 #pragma unroll
-        for (int q = 0; q < W; ++q) nw[q] = 0;
+        for (int q = 0; q < W; ++q) {
+          nw[q] = 0;
+          miss[q] = 0;
+        }
         if (valid) {
           load_row<W>(p.seen, w, sr);
           was_empty = !row_nonzero<W>(sr);
@@ -1136,12 +1148,14 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
             miss[q] = act[q] & ~sr[q];
             any |= miss[q] != 0;
           }
-          if (any) {
+          e0 = p.ioff[w];
+          ee = p.ioff[w + 1];
+          heavy = any && ee - e0 > kHeavyIn;
+          if (any && !heavy) {
             // U in-arcs per step: their columns and frontier bits are loaded
             // together, then the rows of those on a frontier; the early exit
             // is tested once per step (extra rows only repeat found bits)
             constexpr int U = W >= 8 ? 2 : W >= 4 ? 4 : 8;
-            const uint32_t e0 = p.ioff[w], ee = p.ioff[w + 1];
             uint32_t e = e0;
             for (; e < ee; e += U) {
               uint32_t uu[U], fb[U];
@@ -1168,6 +1182,57 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
               }
             }
             scanned += (e < ee ? e : ee) - e0;
+            scanned_v += 1;
+          }
+        }
+        // vertices of high in-degree: the whole warp walks their in-arcs
+        // (coalesced column reads, HU per lane per step) so that one lane does
+        // not hold the level up; same result as the lane loop (the OR of the
+        // frontier rows of in-neighbours, or every missing bit found)
+        for (unsigned hv = __ballot_sync(FULL, heavy); hv; hv &= hv - 1) {
+          const int src = __ffs(hv) - 1;
+          const uint32_t hb = __shfl_sync(FULL, e0, src), he = __shfl_sync(FULL, ee, src);
+          u64 hm[W], acc[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            hm[q] = __shfl_sync(FULL, miss[q], src);
+            acc[q] = 0;
+          }
+          constexpr int HU = W >= 8 ? 1 : W >= 4 ? 2 : 4;
+          uint32_t e = hb;
+          for (; e < he; e += 32 * HU) {
+            uint32_t uu[HU], fb[HU];
+#pragma unroll
+            for (int j = 0; j < HU; ++j) {
+              const uint32_t i = e + 32 * j + lane;
+              uu[j] = i < he ? p.icol[i] : 0xffffffffu;
+            }
+#pragma unroll
+            for (int j = 0; j < HU; ++j)
+              fb[j] = uu[j] != 0xffffffffu ? (FBcur[uu[j] >> 5] >> (uu[j] & 31)) & 1u : 0u;
+#pragma unroll
+            for (int j = 0; j < HU; ++j) {
+              if (fb[j]) {
+                u64 fr[W];
+                load_row<W>(Fcur, uu[j], fr);
+#pragma unroll
+                for (int q = 0; q < W; ++q) acc[q] |= fr[q] & hm[q];
+              }
+            }
+            bool full = true;
+#pragma unroll
+            for (int q = 0; q < W; ++q) full &= warp_or(acc[q]) == hm[q];
+            if (full) {
+              e += 32 * HU;
+              break;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < W; ++q) acc[q] = warp_or(acc[q]);
+          if (lane == src) {
+#pragma unroll
+            for (int q = 0; q < W; ++q) nw[q] = acc[q];
+            scanned += (e < he ? e : he) - hb;
             scanned_v += 1;
           }
         }
