@@ -155,7 +155,7 @@ __device__ __forceinline__ bool entry_less(bool harmonic, u64 Sa, u32 ra, u32 ia
 constexpr double kHMargin = 1.0 + 1.0 / 1048576.0;
 
 // bottom-up: in-degrees above this are walked by the whole warp
-constexpr uint32_t kHeavyIn = 256;
+constexpr uint32_t kHeavyIn = 24;
 
 __device__ __forceinline__ bool harmonic_below(double Hd, u64 d, u64 nd, u64 g, u64 omega, u64 xbits) {
   const u64 w = omega > nd ? omega - nd : 0;
