@@ -85,8 +85,14 @@ __global__ void k_trim_round(const u32 *off, const u32 *col, const u32 *ioff, co
 // One level of a BFS restricted to `active` (nullable): vertices at `level`
 // label their unlabelled neighbours with level + 1.  Warps collect the
 // frontier vertices of 32 consecutive ids and expand each with all lanes.
+// Frontier vertices of out-degree above this are expanded by the whole grid.
+constexpr u32 kBfsHeavy = 2048;
+
+// One BFS level: the vertices at `level` relax their arcs (a warp per vertex);
+// those of degree above kBfsHeavy are listed for k_bfs_heavy instead, so that
+// a hub does not keep one warp busy while the rest of the grid waits.
 __global__ void k_bfs_sweep(const u32 *off, const u32 *col, u32 n, const uint8_t *active, u32 *dist, u32 level,
-                            u32 *changed) {
+                            u32 *changed, u32 *heavy, u32 *nheavy) {
   const int lane = threadIdx.x & 31;
   for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
     u32 v = base + lane;
@@ -96,7 +102,12 @@ __global__ void k_bfs_sweep(const u32 *off, const u32 *col, u32 n, const uint8_t
       int src = __ffs(mask) - 1;
       mask &= mask - 1;
       u32 x = base + src;
-      for (u32 i = off[x] + lane; i < off[x + 1]; i += 32) {
+      const u32 b = off[x], e = off[x + 1];
+      if (e - b > kBfsHeavy) {
+        if (lane == 0) heavy[atomicAdd(nheavy, 1u)] = x;
+        continue;
+      }
+      for (u32 i = b + lane; i < e; i += 32) {
         u32 w = col[i];
         if ((!active || active[w]) && dist[w] == INF) {
           dist[w] = level + 1;
@@ -108,19 +119,43 @@ __global__ void k_bfs_sweep(const u32 *off, const u32 *col, u32 n, const uint8_t
   }
 }
 
-int bfs_levels(const u32 *off, const u32 *col, u32 n, const uint8_t *active, u32 *dist, u32 src, u32 *d_changed,
-               cudaStream_t st) {
+// The listed heavy vertices of the level, each expanded by every thread.
+__global__ void k_bfs_heavy(const u32 *off, const u32 *col, const uint8_t *active, u32 *dist, u32 level,
+                            u32 *changed, const u32 *heavy, const u32 *nheavy) {
+  const u32 nh = *nheavy;
+  u32 ch = 0;
+  for (u32 h = 0; h < nh; ++h) {
+    const u32 x = heavy[h];
+    for (u32 i = off[x] + blockIdx.x * blockDim.x + threadIdx.x; i < off[x + 1]; i += gridDim.x * blockDim.x) {
+      u32 w = col[i];
+      if ((!active || active[w]) && dist[w] == INF) {
+        dist[w] = level + 1;
+        ch = 1;
+      }
+    }
+  }
+  if (__any_sync(FULL, ch) && (threadIdx.x & 31) == 0) *changed = 1;
+}
+
+// BFS levels from src over the arcs (off, col), restricted to active vertices
+// (nullptr: all); flag must hold 2 words.
+int bfs_levels(const u32 *off, const u32 *col, u32 n, u64 arcs, const uint8_t *active, u32 *dist, u32 src,
+               u32 *flag, cudaStream_t st) {
+  u32 *heavy = nullptr;
+  TKC_TRY(cudaMallocAsync(&heavy, (size_t)(arcs / kBfsHeavy + 1) * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(dist, 0xff, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(dist + src, 0, sizeof(u32), st));
   for (u32 level = 0;; ++level) {
     if (level > n) return TKC_ETIMEOUT;
-    TKC_TRY(cudaMemsetAsync(d_changed, 0, sizeof(u32), st));
-    TKC_LAUNCH(k_bfs_sweep<<<grid_of(n), 256, 0, st>>>(off, col, n, active, dist, level, d_changed));
+    TKC_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(u32), st));
+    TKC_LAUNCH(k_bfs_sweep<<<grid_of(n), 256, 0, st>>>(off, col, n, active, dist, level, flag, heavy, flag + 1));
+    TKC_LAUNCH(k_bfs_heavy<<<grid_of(arcs / 8 + 1), 256, 0, st>>>(off, col, active, dist, level, flag, heavy, flag + 1));
     u32 h = 0;
-    TKC_TRY(cudaMemcpyAsync(&h, d_changed, sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaMemcpyAsync(&h, flag, sizeof(u32), cudaMemcpyDeviceToHost, st));
     TKC_TRY(cudaStreamSynchronize(st));
     if (!h) break;
   }
+  TKC_TRY(cudaFreeAsync(heavy, st));
   return TKC_OK;
 }
 
@@ -462,8 +497,8 @@ int reach_directed_gpu(tkc_graph *g) {
     if (hb == 0) break;  // nothing left
     if (round == 0) {
       u32 pivot = 0xffffffffu - (u32)(hb & 0xffffffffu);
-      TKC_RC(bfs_levels(g->off, g->col, n, active, fw, pivot, flag, st));
-      TKC_RC(bfs_levels(g->ioff, g->icol, n, active, bw, pivot, flag, st));
+      TKC_RC(bfs_levels(g->off, g->col, n, g->arcs, active, fw, pivot, flag, st));
+      TKC_RC(bfs_levels(g->ioff, g->icol, n, g->arcs, active, bw, pivot, flag, st));
       TKC_LAUNCH(k_fwbw_mark<<<grid_of(n), 256, 0, st>>>(fw, bw, n, active, comp, pivot));
       continue;  // trim again, then colour
     }
@@ -506,8 +541,8 @@ int reach_directed_gpu(tkc_graph *g) {
   TKC_TRY(cudaMemcpyAsync(&big, comp + big_min, sizeof(u32), cudaMemcpyDeviceToHost, st));
   TKC_TRY(cudaStreamSynchronize(st));
   // exact reach of the biggest SCC (forward), and the SCCs that reach it (backward)
-  TKC_RC(bfs_levels(g->off, g->col, n, nullptr, fw, big, flag, st));
-  TKC_RC(bfs_levels(g->ioff, g->icol, n, nullptr, bw, big, flag, st));
+  TKC_RC(bfs_levels(g->off, g->col, n, g->arcs, nullptr, fw, big, flag, st));
+  TKC_RC(bfs_levels(g->ioff, g->icol, n, g->arcs, nullptr, bw, big, flag, st));
   TKC_TRY(cudaMemsetAsync(flag, 0, sizeof(u32), st));
   TKC_LAUNCH(k_count_reached<<<grid_of(n), 256, 0, st>>>(fw, n, flag));
   const u64 reach_big = read_u32(flag, st, &rc);
