@@ -1058,7 +1058,7 @@ static int topk_bound(tkc_graph *g, uint32_t k, tkc_result *out) {
   if (nb) TKC_RC(ensure_nb_bounds(g, nb_levels_of(o)));
   const u32 *order0 = nb ? g->nb_order : g->deg_order;
   const u32 n0 = nb ? g->n_src_nb : g->n_src_deg;
-  const u32 B = o.batch_bits ? o.batch_bits : 64;
+  const u32 B = o.batch_bits ? o.batch_bits : 256;  // measured on 1000 x 1000 grids: 64: 6.8 s, 256: 5.1 s
   const u32 cap = std::min<u32>(n + 1, 65535u);  // levels per search (depth < n)
   TKC_RC(ensure_workspace(ctx, n, words_for(B), kk, 1, 1));
   u64 *bS = nullptr, *key = nullptr, *Ltab = nullptr, *smax = nullptr, *bkeys = nullptr;
