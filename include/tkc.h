@@ -167,13 +167,14 @@ int tkc_topk_harmonic_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uin
  * directed) gets the bound S(w) >= L(d(s,w)) - outdeg(w), L(i) = 2 x (vertices
  * within one level of i; directed: at most one level deeper) + the level
  * distance of all other vertices - 2, over R(s) including s.  The search runs
- * in rounds of options.batch_bits sources (0 = 256; 1 = one source per round):
+ * in rounds of options.teams batches of options.batch_bits sources (defaults: 8 x 64 from 2^16 vertices up,
+ * else 1 x 256; batch_bits 1 = one source per round):
  * the unsearched vertices of smallest bound key floor(2^46 S_lb/(r-1)^2), ties
  * by their position in the initial order, and stops when that key exceeds the
  * k-th farness strictly.  Results as tkc_topk_closeness (bfs_cut = 0).  Errors:
  * TKC_EINVAL (order not DEG or NB, k > TKC_MAX_K, capacity too small),
  * TKC_EOVERFLOW (a search deeper than 65 534 levels), TKC_ENOMEM, TKC_ECUDA,
- * TKC_ETIMEOUT.  Device memory: about 2 x batch_bits bytes per vertex. */
+ * TKC_ETIMEOUT.  Device memory: about 2 x teams x batch_bits bytes per vertex. */
 int tkc_topk_closeness_bound(tkc_graph *g, uint32_t k, tkc_result *out);
 
 /* Autotuner (no paper counterpart: it only picks launch parameters).

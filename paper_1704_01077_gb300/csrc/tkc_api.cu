@@ -254,7 +254,9 @@ struct RunSetup {
   // updateBoundsLB rounds: level recording, one team, lists kept across rounds
   uint16_t *lvl;
   u32 *hist;
+  u32 *lvl_src;
   u32 hist_cap;
+  u32 lvl_stride;
   int keep_lists;
   u32 force_teams;
 };
@@ -323,7 +325,9 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.harmonic = rs.harmonic;
   p.lvl = rs.lvl;
   p.hist = rs.hist;
+  p.lvl_src = rs.lvl_src;
   p.hist_cap = rs.hist_cap;
+  p.lvl_stride = rs.lvl_stride;
   p.teams = T;
   p.row_stride = (u64)w.n_cap * w.words_cap;
   p.vtx_stride = w.n_cap;
@@ -1058,16 +1062,25 @@ static int topk_bound(tkc_graph *g, uint32_t k, tkc_result *out) {
   if (nb) TKC_RC(ensure_nb_bounds(g, nb_levels_of(o)));
   const u32 *order0 = nb ? g->nb_order : g->deg_order;
   const u32 n0 = nb ? g->n_src_nb : g->n_src_deg;
-  const u32 B = o.batch_bits ? o.batch_bits : 256;  // measured on 1000 x 1000 grids: 64: 6.8 s, 256: 5.1 s
+  // defaults measured with NBBound on a 1000 x 1000 grid: 256 sources x 1 team 4.55 s, 256 x 2 4.16 s,
+  // 128 x 4 4.03 s, 64 x 8 3.48 s, 64 x 16 3.99 s (more sources per round refresh the bounds less often)
+  const bool large = n >= (1u << 16);
+  const u32 B = o.batch_bits ? o.batch_bits : (large ? 64u : 256u);
   const u32 cap = std::min<u32>(n + 1, 65535u);  // levels per search (depth < n)
-  TKC_RC(ensure_workspace(ctx, n, words_for(B), kk, 1, 1));
+  // teams run one batch each per round (0: one team below 2^16 vertices, else 8)
+  int maxb = max_coresident_blocks(ctx, words_for(B));
+  if (maxb <= 0) return TKC_ECUDA;
+  const u32 T = std::max<u32>(1, std::min<u32>(B <= 1 ? 1u : (o.teams ? o.teams : (large ? 8u : 1u)), (u32)maxb));
+  const u32 TB = T * B;  // sources per round
+  TKC_RC(ensure_workspace(ctx, n, words_for(B), kk, 1, T));
   u64 *bS = nullptr, *key = nullptr, *Ltab = nullptr, *smax = nullptr, *bkeys = nullptr;
   u32 *bR = nullptr, *cand = nullptr, *pos = nullptr, *tmp = nullptr, *lo = nullptr, *hist = nullptr, *depth = nullptr;
+  u32 *srcs = nullptr;
   uint8_t *done = nullptr;
   uint16_t *lvl = nullptr;
   int rc = TKC_OK;
   auto cleanup = [&]() {
-    void *ptrs[] = {bS, key, Ltab, smax, bkeys, bR, cand, pos, tmp, lo, hist, depth, done, lvl};
+    void *ptrs[] = {bS, key, Ltab, smax, bkeys, bR, cand, pos, tmp, lo, hist, depth, done, lvl, srcs};
     for (void *q : ptrs)
       if (q) cudaFreeAsync(q, st);
     cudaStreamSynchronize(st);
@@ -1099,24 +1112,25 @@ static int topk_bound(tkc_graph *g, uint32_t k, tkc_result *out) {
   LB_TRY(cudaMallocAsync(&tmp, ((n1 + 1) / 4096 + 16) * sizeof(u32), st));
   LB_TRY(cudaMallocAsync(&lo, n1 * sizeof(u32), st));
   LB_TRY(cudaMallocAsync(&smax, sizeof(u64), st));
-  LB_TRY(cudaMallocAsync(&hist, (size_t)B * cap * sizeof(u32), st));
-  LB_TRY(cudaMallocAsync(&Ltab, (size_t)B * cap * sizeof(u64), st));
-  LB_TRY(cudaMallocAsync(&depth, (size_t)B * sizeof(u32), st));
-  LB_TRY(cudaMallocAsync(&bkeys, (size_t)B * sizeof(u64), st));
-  LB_TRY(cudaMallocAsync(&lvl, n1 * B * sizeof(uint16_t), st));
-  LB_TRY(cudaMemsetAsync(lvl, 0xff, n1 * B * sizeof(uint16_t), st));
+  LB_TRY(cudaMallocAsync(&hist, (size_t)TB * cap * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&Ltab, (size_t)TB * cap * sizeof(u64), st));
+  LB_TRY(cudaMallocAsync(&depth, (size_t)TB * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&bkeys, (size_t)TB * sizeof(u64), st));
+  LB_TRY(cudaMallocAsync(&srcs, (size_t)TB * sizeof(u32), st));
+  LB_TRY(cudaMallocAsync(&lvl, n1 * TB * sizeof(uint16_t), st));
+  LB_TRY(cudaMemsetAsync(lvl, 0xff, n1 * TB * sizeof(uint16_t), st));
   LB_RC(lb_init(g, nb ? g->nb_S : nullptr, nb ? g->nb_r : nullptr, nb ? g->nb_key : nullptr, bS, bR, key, done));
   TKC_TRY(cudaEventRecord(ctx->ev[1], st));
   Ctl total;
   memset(&total, 0, sizeof(total));
   double ms_kernel = 0;
   u32 nround = 0;
-  std::vector<u64> h_key(B);
+  std::vector<u64> h_key(TB);
   while (true) {
     u32 m = 0;
     LB_RC(lb_sorted_candidates(g, order0, n0, done, key, cand, &m, pos, tmp, lo, smax));
     if (m == 0) break;
-    const u32 take = std::min<u32>(B, m);
+    const u32 take = std::min<u32>(TB, m);
     // the batch's keys and the current k-th entry decide the stop
     LB_RC(lb_gather_keys(g, take, cand, key, bkeys));
     LB_TRY(cudaMemcpyAsync(h_key.data(), bkeys, take * sizeof(u64), cudaMemcpyDeviceToHost, st));
@@ -1142,7 +1156,8 @@ static int topk_bound(tkc_graph *g, uint32_t k, tkc_result *out) {
       }
     }
     if (cnt == 0) break;
-    LB_TRY(cudaMemsetAsync(hist, 0, (size_t)B * cap * sizeof(u32), st));
+    LB_TRY(cudaMemsetAsync(hist, 0, (size_t)TB * cap * sizeof(u32), st));
+    LB_TRY(cudaMemsetAsync(srcs, 0xff, (size_t)TB * sizeof(u32), st));
     RunSetup rs;
     memset(&rs, 0, sizeof(rs));
     rs.g = g;
@@ -1155,9 +1170,11 @@ static int topk_bound(tkc_graph *g, uint32_t k, tkc_result *out) {
     rs.ng = 1;
     rs.lvl = lvl;
     rs.hist = hist;
+    rs.lvl_src = srcs;
     rs.hist_cap = cap;
+    rs.lvl_stride = TB;
     rs.keep_lists = nround > 0;
-    rs.force_teams = 1;
+    rs.force_teams = T;
     Ctl hc;
     LB_RC(run_search(ctx, rs, &hc));
     float ms = 0;
@@ -1170,7 +1187,7 @@ static int topk_bound(tkc_graph *g, uint32_t k, tkc_result *out) {
     total.bfs_finished += hc.bfs_finished;
     total.levels += hc.levels;
     total.alg_bytes += hc.alg_bytes;
-    LB_RC(lb_update(g, B, cnt, cand, lvl, hist, cap, depth, Ltab, w.res_r, bS, bR, key, done));
+    LB_RC(lb_update(g, TB, TB, srcs, lvl, hist, cap, depth, Ltab, w.res_r, bS, bR, key, done));
     ++nround;
   }
   RunSetup rs;

@@ -330,7 +330,7 @@ __device__ __forceinline__ void clear_frontier(u64 *F, uint32_t *FB, const uint3
 // this depth.
 template <int W>
 __device__ __forceinline__ void record_levels(const RunParams &p, uint32_t v, const u64 (&nw)[W], uint32_t depth) {
-  uint16_t *row = p.lvl + (size_t)v * p.B;
+  uint16_t *row = p.lvl + (size_t)v * p.lvl_stride + (size_t)p.team * p.B;
 #pragma unroll
   for (int q = 0; q < W; ++q) {
     u64 b = nw[q];
@@ -671,7 +671,7 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
       sl.d += 1;
       if (p.hist) {
         if (sl.d < p.hist_cap)
-          p.hist[(size_t)s * p.hist_cap + sl.d] = cn;
+          p.hist[((size_t)p.team * p.B + s) * p.hist_cap + sl.d] = cn;
         else
           atomicCAS(&c->err, 0, TKC_EOVERFLOW);
       }
@@ -815,7 +815,9 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
   }
   // take sources from the shared cursor, `room` positions at a time, so that
   // every position taken is either abandoned at level 0 or gets a slot
-  while (assigned < B) {
+  // (updateBoundsLB runs: one batch per team, its levels are read afterwards)
+  const bool lb_done = p.lvl && c->batches >= 1;
+  while (!lb_done && assigned < B) {
     const uint32_t room = B - assigned;
     if (threadIdx.x == 0) s_base = atomicAdd(&p.sh->cursor, room);
     __syncthreads();
@@ -879,6 +881,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       sl.nocut = idx < p.nocut_prefix;
       sl.pad = 0;
       sl.H = 0.0;
+      if (p.lvl_src) p.lvl_src[p.team * B + s] = v;
       p.slots[s] = sl;
       graph_count(p, gv, 1, 1);
       graph_count(p, gv, 0, od);

@@ -141,12 +141,16 @@ struct RunParams {
   // upper bound on h), stop when the bound is below the k-th h.
   const unsigned long long *lb_key;
   unsigned int *g_stop;  // several graphs: graph g's search has stopped (its later sources are skipped)
-  // updateBoundsLB (nullptr: off; one team, every search complete): the level
-  // at which each vertex is found by each slot, lvl[v * B + slot] (0xffff: not
-  // found), and each slot's level sizes hist[slot * hist_cap + level]
+  // updateBoundsLB (nullptr: off; every search complete, one batch per team):
+  // the level at which each vertex is found by each slot of each team,
+  // lvl[v * lvl_stride + team * B + slot] (0xffff: not found), each slot's
+  // level sizes hist[(team * B + slot) * hist_cap + level], and its source
+  // lvl_src[team * B + slot]
   uint16_t *lvl;
   uint32_t *hist;
+  uint32_t *lvl_src;
   uint32_t hist_cap;
+  uint32_t lvl_stride;
   uint32_t bu_num, bu_den;
   uint64_t timeout;
   // workspace

@@ -146,7 +146,7 @@ __global__ void k_lb_update(u32 n, u32 B, u32 nsrc, uint16_t *lvl, const u32 *sr
       if (l == 0xffffu) continue;
       row[s] = 0xffffu;
       const u32 src = srcs[s];
-      if (src == w || comp[src] != cw || od == 0) continue;
+      if (src == 0xffffffffu || src == w || comp[src] != cw || od == 0) continue;
       const u64 cS = Ltab[(size_t)s * cap + l] - od;
       const u64 cr = res_r[src];
       // keep the larger of cS/(cr-1)^2 and S/(r-1)^2 (r <= 1: no bound yet)
@@ -172,7 +172,7 @@ __global__ void k_lb_gather(u32 cnt, const u32 *cand, const u64 *key, u64 *out) 
 
 __global__ void k_lb_done(u32 nsrc, const u32 *srcs, uint8_t *done) {
   const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nsrc) done[srcs[i]] = 1;
+  if (i < nsrc && srcs[i] != 0xffffffffu) done[srcs[i]] = 1;
 }
 
 __global__ void k_lb_init(u32 n, const u64 *S0, const u32 *r0, const u64 *key0, u64 *bS, u32 *bR, u64 *key,
@@ -237,8 +237,9 @@ int lb_gather_keys(tkc_graph *g, u32 cnt, const u32 *cand, const u64 *key, u64 *
   return TKC_OK;
 }
 
-// After a round of complete searches from srcs[0..nsrc): level bounds per
-// source, then every vertex's bound.  lvl rows are reset to 0xffff.
+// After a round of complete searches from srcs[0..nsrc) (0xffffffff: slot
+// unused): level bounds per source, then every vertex's bound.  lvl rows (B =
+// row length) are reset to 0xffff.
 int lb_update(tkc_graph *g, u32 B, u32 nsrc, const u32 *srcs, uint16_t *lvl, u32 *hist, u32 cap, u32 *depth,
               u64 *Ltab, const u32 *res_r, u64 *bS, u32 *bR, u64 *key, uint8_t *done) {
   cudaStream_t st = g->ctx->stream;

@@ -119,14 +119,28 @@ __global__ void k_bfs_sweep(const u32 *off, const u32 *col, u32 n, const uint8_t
   }
 }
 
-// The listed heavy vertices of the level, each expanded by every thread.
+// The listed heavy vertices of the level: one block per vertex, and the whole
+// grid for the few above kBfsHuge out-arcs.
+constexpr u32 kBfsHuge = 1u << 16;
+
 __global__ void k_bfs_heavy(const u32 *off, const u32 *col, const uint8_t *active, u32 *dist, u32 level,
                             u32 *changed, const u32 *heavy, const u32 *nheavy) {
   const u32 nh = *nheavy;
   u32 ch = 0;
   for (u32 h = 0; h < nh; ++h) {
     const u32 x = heavy[h];
-    for (u32 i = off[x] + blockIdx.x * blockDim.x + threadIdx.x; i < off[x + 1]; i += gridDim.x * blockDim.x) {
+    const u32 b = off[x], e = off[x + 1];
+    u32 first, step;
+    if (e - b > kBfsHuge) {
+      first = b + blockIdx.x * blockDim.x + threadIdx.x;
+      step = gridDim.x * blockDim.x;
+    } else if (h % gridDim.x == blockIdx.x) {
+      first = b + threadIdx.x;
+      step = blockDim.x;
+    } else {
+      continue;
+    }
+    for (u32 i = first; i < e; i += step) {
       u32 w = col[i];
       if ((!active || active[w]) && dist[w] == INF) {
         dist[w] = level + 1;

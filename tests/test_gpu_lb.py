@@ -103,3 +103,21 @@ def test_bound_rejects_other_orders(gpu_lib, ctx):
     finally:
         tkc.tkc_free_graph(h)
         tkc.tkc_set_options(ctx, tkc.Options())
+
+
+def test_several_teams_per_round(gpu_lib, ctx):
+    """Rounds where several teams each run one batch: the same top-k."""
+    tkc = gpu_lib
+    for g in (gg.grid(30, 40, seed=5, drop=0.1), gg.grid(12, 12, directed=True, seed=6, drop=0.2),
+              gg.barabasi_albert(700, 3, 8), gg.random_tree(400, 9)):
+        ref = oracle.textbook_topk(g, 10)
+        for bits, teams, nb in ((64, 2, False), (64, 3, True), (128, 4, False), (256, 2, True)):
+            tkc.tkc_set_options(ctx, tkc.Options(batch_bits=bits, teams=teams,
+                                                 order=tkc.TKC_ORDER_NB if nb else tkc.TKC_ORDER_DEG))
+            h = tkc.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+            try:
+                got = tkc.tkc_topk_closeness_bound(h, 10)
+            finally:
+                tkc.tkc_free_graph(h)
+                tkc.tkc_set_options(ctx, tkc.Options())
+            _expect_equal(got, ref, g, 10)
