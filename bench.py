@@ -141,6 +141,20 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(ms_total, edges, dist, device):
+    """Whole-job figures of a replicated run: the slowest rank's time and the
+    arcs of all ranks (one rank, dist None: unchanged)."""
+    if not dist:
+        return float(ms_total), float(edges)
+    import torch
+
+    t = torch.tensor([float(ms_total)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(edges)], device=device, dtype=torch.float64)
+    dist.all_reduce(e)
+    return float(t.item()), float(e.item())
+
+
 def cpu_oracle_sample(g, k, sample_sources):
     """Sequential CPU BFSCut (the oracle as it stands) on a prefix of the
     degree order; returns (GTEPS, seconds, edges_visited)."""
@@ -301,16 +315,7 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = tkc.tkc_kernel_launches() - launches0
-    ms_total = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    edges = sum(r.edges_visited for r in results)
-    if dist:
-        t = torch.tensor([float(edges)], device=dev, dtype=torch.float64)
-        dist.all_reduce(t)
-        edges = float(t.item())
+    ms_total, edges = reduce_over_ranks(ev0.elapsed_time(ev1), sum(r.edges_visited for r in results), dist, dev)
     value = edges / (ms_total / 1e3) / 1e9
     ms_step = ms_total / args.steps
 
