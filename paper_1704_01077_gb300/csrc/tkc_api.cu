@@ -1265,7 +1265,6 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   std::vector<uint8_t> gdir(ng);
   for (u32 i = 0; i < ng; ++i) {
     TKC_RC(ensure_degree_order(gs[i]));
-    TKC_RC(ensure_reach_bounds(gs[i]));
     vbase[i + 1] = vbase[i] + gs[i]->n;
     abase[i + 1] = abase[i] + gs[i]->arcs;
     offptr[i] = (u64)gs[i]->off;
@@ -1283,7 +1282,8 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   int rc = TKC_OK;
   auto cleanup = [&]() {
     cudaStreamSynchronize(st);
-    void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.nb_S, U.nb_r, U.nb_key, U.nb_hkey,
+    void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.scc_size, U.comp, U.nb_S, U.nb_r,
+                    U.nb_key, U.nb_hkey,
                     U.nb_order, U.nb_horder, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir};
     for (void *q : ptrs)
       if (q) cudaFree(q);
@@ -1307,8 +1307,6 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   } while (0)
   MULTI_TRY(cudaMallocAsync(&U.off, ((size_t)nv + 1) * sizeof(u32), st));
   MULTI_TRY(cudaMallocAsync(&U.col, std::max<size_t>(na, 1) * sizeof(u32), st));
-  MULTI_TRY(cudaMallocAsync(&U.alpha, std::max<size_t>(nv, 1) * sizeof(u32), st));
-  MULTI_TRY(cudaMallocAsync(&U.omega, std::max<size_t>(nv, 1) * sizeof(u32), st));
   MULTI_TRY(cudaMallocAsync(&gid, std::max<size_t>(nv, 1) * sizeof(u32), st));
   MULTI_TRY(cudaMallocAsync(&d_vbase, (ng + 1) * sizeof(u32), st));
   MULTI_TRY(cudaMallocAsync(&d_abase, (ng + 1) * sizeof(u64), st));
@@ -1325,17 +1323,17 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   unsigned ga = (unsigned)std::max<u64>(1, std::min<u64>((na + 255) / 256, (u64)ctx->num_sms * 16));
   if (na) TKC_LAUNCH(k_union_cols<<<ga, 256, 0, st>>>(d_colptr, d_vbase, d_abase, ng, na, U.col));
   MULTI_TRY(cudaGetLastError());
-  for (u32 i = 0; i < ng; ++i)
-    if (gs[i]->n) {
-      MULTI_TRY(cudaMemcpyAsync(U.alpha + vbase[i], gs[i]->alpha, gs[i]->n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
-      MULTI_TRY(cudaMemcpyAsync(U.omega + vbase[i], gs[i]->omega, gs[i]->n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
-    }
   MULTI_RC(build_in_csr(&U));
+  // reach bounds once over the union, as a directed graph: the SCCs of the
+  // union are the graphs' SCCs (an undirected graph's are its components, each
+  // with alpha = omega = its size); only the biggest SCC of the union gets the
+  // exact reach by BFS, so the other graphs' omega may be looser than alone,
+  // which changes pruning, never results
+  MULTI_RC(ensure_reach_bounds(&U));
   if (nb) {
     // the sweeps run once over the union (each vertex's counts involve only its
     // own graph, so they equal the per-graph values); all sources of all graphs
     // are then ordered by (key, union id)
-    U.have_reach = true;
     MULTI_RC(ensure_nb_bounds(&U, nb_levels_of(o), gid, d_gdir));
   } else {
     MULTI_RC(ensure_degree_order(&U));
