@@ -137,8 +137,11 @@ void tkc_free_graph(tkc_graph *g);
 int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out);
 
 /* Exact top-k of each of ng graphs (all on ctx's device) in one persistent
- * launch, one k-list per graph; outs[i] receives graph i's result exactly as
- * tkc_topk_closeness would (counters per graph, ms_* shared).  Same errors. */
+ * launch, one k-list per graph; outs[i] receives graph i's top-k exactly as
+ * tkc_topk_closeness would give it.  Counters are per graph and may differ from
+ * a run of the graph alone (the reach bounds are computed once on the union,
+ * and the threshold evolves differently), ms_* are shared.  options.order:
+ * TKC_ORDER_DEG or TKC_ORDER_NB (each graph stops on its own).  Same errors. */
 int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
 
 /* Top-k harmonic centrality h(v) = sum over w != v of 1/d(v,w) (the paper's
