@@ -157,6 +157,14 @@ constexpr double kHMargin = 1.0 + 1.0 / 1048576.0;
 // bottom-up: in-degrees above this are walked by the whole warp
 constexpr uint32_t kHeavyIn = 24;
 
+// Threads per block of the search kernel (one block per SM).  The level loops
+// wait on dependent row gathers, so more resident warps hide more latency: the
+// 64-bit kernel runs 32 warps per SM and the 128-bit one 24, at the price of a
+// few spilled registers (measured on R-MAT 22, DegCut and NBCut: 1024 and 768
+// threads beat 512 by 30% and 14%).
+template <int W>
+constexpr int kThreads = W == 1 ? 1024 : W == 2 ? 768 : 512;
+
 __device__ __forceinline__ bool harmonic_below(double Hd, u64 d, u64 nd, u64 g, u64 omega, u64 xbits) {
   const u64 w = omega > nd ? omega - nd : 0;
   const u64 near_ = g < w ? g : w, far_ = w > g ? w - g : 0;
@@ -356,8 +364,8 @@ struct Smem {
   uint32_t cr[64 * W], cid[64 * W], cg[64 * W];
   unsigned ncand;
   unsigned nactive;
-  unsigned scan[kTPB / 32 + 1];
-  u64 scan64[kTPB / 32 + 1];
+  unsigned scan[kThreads<W> / 32 + 1];
+  u64 scan64[kThreads<W> / 32 + 1];
   u64 acc[4];
 };
 
@@ -377,16 +385,16 @@ __device__ uint32_t block_exscan(Smem<W> &sm, uint32_t x, uint32_t *total) {
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
-    for (int i = 0; i < kTPB / 32; ++i) {
+    for (int i = 0; i < kThreads<W> / 32; ++i) {
       uint32_t t = sm.scan[i];
       sm.scan[i] = run;
       run += t;
     }
-    sm.scan[kTPB / 32] = run;
+    sm.scan[kThreads<W> / 32] = run;
   }
   __syncthreads();
   uint32_t res = sm.scan[wid] + incl - x;
-  *total = sm.scan[kTPB / 32];
+  *total = sm.scan[kThreads<W> / 32];
   __syncthreads();
   return res;
 }
@@ -405,16 +413,16 @@ __device__ u64 block_exscan64(Smem<W> &sm, u64 x, u64 *total) {
   __syncthreads();
   if (threadIdx.x == 0) {
     u64 run = 0;
-    for (int i = 0; i < kTPB / 32; ++i) {
+    for (int i = 0; i < kThreads<W> / 32; ++i) {
       u64 t = sm.scan64[i];
       sm.scan64[i] = run;
       run += t;
     }
-    sm.scan64[kTPB / 32] = run;
+    sm.scan64[kThreads<W> / 32] = run;
   }
   __syncthreads();
   u64 res = sm.scan64[wid] + incl - x;
-  *total = sm.scan64[kTPB / 32];
+  *total = sm.scan64[kThreads<W> / 32];
   __syncthreads();
   return res;
 }
@@ -510,14 +518,14 @@ __device__ void merge_topk_one(const RunParams &p, Smem<W> &sm) {
   uint32_t ntop = p.g_ntop[0];
   uint32_t nc = sm.ncand;
   if (nc == 0) return;
-  for (uint32_t i = threadIdx.x; i < ntop; i += kTPB) {
+  for (uint32_t i = threadIdx.x; i < ntop; i += kThreads<W>) {
     sm.tS[i] = p.top_S[i];
     sm.tr[i] = p.top_r[i];
     sm.tid[i] = p.top_id[i];
   }
   __syncthreads();
   // rank of each candidate among existing entries and other candidates
-  for (uint32_t i = threadIdx.x; i < nc; i += kTPB) {
+  for (uint32_t i = threadIdx.x; i < nc; i += kThreads<W>) {
     u64 S = sm.cS[i];
     uint32_t r = sm.cr[i], id = sm.cid[i];
     uint32_t lo = 0, hi = ntop;  // first existing entry not less than the candidate
@@ -535,7 +543,7 @@ __device__ void merge_topk_one(const RunParams &p, Smem<W> &sm) {
       p.top_id[rank] = id;
     }
   }
-  for (uint32_t i = threadIdx.x; i < ntop; i += kTPB) {
+  for (uint32_t i = threadIdx.x; i < ntop; i += kThreads<W>) {
     uint32_t rank = i;
     for (uint32_t j = 0; j < nc; ++j)
       if (entry_less(p.harmonic, sm.cS[j], sm.cr[j], sm.cid[j], sm.tS[i], sm.tr[i], sm.tid[i])) ++rank;
@@ -557,7 +565,7 @@ template <int W>
 __device__ void merge_topk_many(const RunParams &p, Smem<W> &sm) {
   const uint32_t kk = p.kk;
   const uint32_t nc = sm.ncand;
-  for (uint32_t i = threadIdx.x; i < nc; i += kTPB) {
+  for (uint32_t i = threadIdx.x; i < nc; i += kThreads<W>) {
     const uint32_t g = sm.cg[i];
     bool first = true;
     for (uint32_t j = 0; j < i && first; ++j) first = sm.cg[j] != g;
@@ -641,14 +649,14 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
     sm.nactive = 0;
   }
   if (threadIdx.x < W) sm.active[threadIdx.x] = 0;
-  for (int i = threadIdx.x; i < 4; i += kTPB) sm.acc[i] = 0;
+  for (int i = threadIdx.x; i < 4; i += kThreads<W>) sm.acc[i] = 0;
   __syncthreads();
   // 1. per-slot level update
-  int cont[(64 * W + kTPB - 1) / kTPB];
+  int cont[(64 * W + kThreads<W> - 1) / kThreads<W>];
   uint32_t finished = 0;
 #pragma unroll
-  for (int t = 0; t < (64 * W + kTPB - 1) / kTPB; ++t) {
-    uint32_t s = threadIdx.x + t * kTPB;
+  for (int t = 0; t < (64 * W + kThreads<W> - 1) / kThreads<W>; ++t) {
+    uint32_t s = threadIdx.x + t * kThreads<W>;
     cont[t] = 0;
     if (s >= B) continue;
     Slot sl = p.slots[s];
@@ -692,8 +700,8 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
   uint32_t cuts = 0;
   u64 visited = 0;
 #pragma unroll
-  for (int t = 0; t < (64 * W + kTPB - 1) / kTPB; ++t) {
-    uint32_t s = threadIdx.x + t * kTPB;
+  for (int t = 0; t < (64 * W + kThreads<W> - 1) / kThreads<W>; ++t) {
+    uint32_t s = threadIdx.x + t * kThreads<W>;
     if (!cont[t]) continue;
     Slot sl = p.slots[s];
     Thresh x = thresh_of(p, sl.graph);
@@ -809,7 +817,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       for (int j = 0; j < W; ++j) c->active[j] = 0;
       c->step = 1;  // another empty clear step, then this check again
     }
-    for (uint32_t s = threadIdx.x; s < B; s += kTPB) p.slots[s].state = 0;
+    for (uint32_t s = threadIdx.x; s < B; s += kThreads<W>) p.slots[s].state = 0;
     __syncthreads();
     return;
   }
@@ -942,14 +950,14 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     }
   }
   // slots beyond `assigned` are free
-  for (uint32_t s = assigned + threadIdx.x; s < B; s += kTPB) p.slots[s].state = 0;
+  for (uint32_t s = assigned + threadIdx.x; s < B; s += kThreads<W>) p.slots[s].state = 0;
   __syncthreads();
 }
 
 // ------------------------------------------------------------------ the kernel
 
 template <int W>
-__global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
+__global__ void __launch_bounds__(kThreads<W>, 1) bfscut_kernel(RunParams p0) {
   __shared__ Smem<W> sm;
   // this block's team: its own control block, slots, rows, lists and stamps
   __shared__ RunParams p;
@@ -983,10 +991,10 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
   __syncthreads();
   Ctl *c = p.ctl;
   const int lane = threadIdx.x & 31;
-  const uint32_t gwarp = (tb * kTPB + threadIdx.x) >> 5;
-  const uint32_t nwarps = (bpt * kTPB) >> 5;
-  const uint32_t gthread = tb * kTPB + threadIdx.x;
-  const uint32_t nthreads = bpt * kTPB;
+  const uint32_t gwarp = (tb * kThreads<W> + threadIdx.x) >> 5;
+  const uint32_t nwarps = (bpt * kThreads<W>) >> 5;
+  const uint32_t gthread = tb * kThreads<W> + threadIdx.x;
+  const uint32_t nthreads = bpt * kThreads<W>;
 
   while (true) {
     const int step = ld_volatile_i32(&c->step);
@@ -1021,7 +1029,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
     const uint32_t depth = vc->bdepth + 1;  // depth of the level being discovered
     const u64 fl_arcs = vc->fl_arcs;
     if (threadIdx.x < W) sm.active[threadIdx.x] = vc->active[threadIdx.x];
-    for (int i = threadIdx.x; i < 64 * W; i += kTPB) {
+    for (int i = threadIdx.x; i < 64 * W; i += kThreads<W>) {
       sm.cnt[i] = 0;
       sm.wsum[i] = 0;
     }
@@ -1273,7 +1281,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
     if (lane == 0 && scanned) atomicAdd(&sm.acc[3], scanned);
     if (lane == 0 && scanned_v) atomicAdd(&sm.acc[2], scanned_v);
     __syncthreads();
-    for (int i = threadIdx.x; i < 64 * W; i += kTPB) {
+    for (int i = threadIdx.x; i < 64 * W; i += kThreads<W>) {
       if (sm.cnt[i]) {
         atomicAdd(&p.cnt[i], sm.cnt[i]);
         atomicAdd(&p.wsum[i], sm.wsum[i]);
@@ -1293,7 +1301,7 @@ __global__ void __launch_bounds__(kTPB, 1) bfscut_kernel(RunParams p0) {
 
 template <int W>
 static int occupancy_of(int *blocks_per_sm) {
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bfscut_kernel<W>, kTPB, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bfscut_kernel<W>, kThreads<W>, 0);
   return e == cudaSuccess ? TKC_OK : TKC_ECUDA;
 }
 
@@ -1315,7 +1323,7 @@ template <int W>
 static cudaError_t launch(const RunParams &p, int blocks, cudaStream_t st) {
   void *args[] = {(void *)&p};
   note_launches(1);
-  return cudaLaunchCooperativeKernel((const void *)bfscut_kernel<W>, dim3(blocks), dim3(kTPB), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void *)bfscut_kernel<W>, dim3(blocks), dim3(kThreads<W>), args, 0, st);
 }
 
 int run_bfscut(tkc_ctx *ctx, const RunParams &p, int words, int blocks) {

@@ -37,7 +37,6 @@ void note_launches(unsigned count);
     ::tkc::note_launches(1);       \
   } while (0)
 
-constexpr int kTPB = 512;            // threads per block of the persistent kernels
 constexpr uint32_t kMaxN = 1u << 26; // list counters pack the count in 26 bits
 constexpr int kMaxWords = 8;         // 512-bit source batches
 
