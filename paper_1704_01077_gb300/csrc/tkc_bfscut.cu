@@ -1166,7 +1166,7 @@ __global__ void __launch_bounds__(kThreads<W>, 1) bfscut_kernel(RunParams p0) {
             // U in-arcs per step: their columns and frontier bits are loaded
             // together, then the rows of those on a frontier; the early exit
             // is tested once per step (extra rows only repeat found bits)
-            constexpr int U = W >= 8 ? 2 : W >= 4 ? 4 : 8;
+            constexpr int U = W >= 8 ? 2 : 4;
             uint32_t e = e0;
             for (; e < ee; e += U) {
               uint32_t uu[U], fb[U];
