@@ -307,6 +307,8 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.col = g->col;
   p.ioff = g->ioff;
   p.icol = g->icol;
+  TKC_RC(ensure_bu_chunks(g));
+  p.bu_chunks = g->bu_chunks;
   p.alpha = g->alpha;
   p.omega = g->omega;
   p.order = rs.order;
@@ -685,7 +687,7 @@ void tkc_free_graph(tkc_graph *g) {
   if (g->icol && g->icol != g->col) cudaFree(g->icol);
   void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega, g->scc_size, g->features,
                   g->learned_order, g->seeded_order, g->nb_order, g->nb_S, g->nb_r, g->nb_key, g->nb_hkey,
-                  g->nb_horder, g->comp};
+                  g->nb_horder, g->comp, g->bu_chunks};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   g->ctx->graphs_alive--;
@@ -1284,7 +1286,7 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
     cudaStreamSynchronize(st);
     void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.scc_size, U.comp, U.nb_S, U.nb_r,
                     U.nb_key, U.nb_hkey,
-                    U.nb_order, U.nb_horder, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir};
+                    U.nb_order, U.nb_horder, U.bu_chunks, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir};
     for (void *q : ptrs)
       if (q) cudaFree(q);
   };

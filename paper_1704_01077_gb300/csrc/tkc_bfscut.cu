@@ -642,6 +642,7 @@ __device__ __forceinline__ void trace_stamp(const RunParams &p, int slot) {
 template <int W>
 __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
   Ctl *c = p.ctl;
+  if (threadIdx.x == 0) c->bu_next = 0;
   const uint32_t B = p.B;
   trace_stamp(p, 13);
   if (threadIdx.x == 0) {
@@ -785,6 +786,7 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
 template <int W>
 __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
   Ctl *c = p.ctl;
+  if (threadIdx.x == 0) c->bu_next = 0;
   trace_stamp(p, 13);
   const uint32_t B = p.B;
   u64 *Fcur = c->cur ? p.F1 : p.F0;
@@ -1140,130 +1142,142 @@ __global__ void __launch_bounds__(kThreads<W>, 1) bfscut_kernel(RunParams p0) {
       u64 act[W];
 #pragma unroll
       for (int q = 0; q < W; ++q) act[q] = sm.active[q];
-      for (uint32_t base = gwarp * 32; base < p.n; base += nwarps * 32) {
-        uint32_t w = base + lane;
-        bool valid = w < p.n;
-        u64 nw[W], sr[W], miss[W];
-        uint32_t od = 0, e0 = 0, ee = 0;
-        bool was_empty = false, any = false, heavy = false;
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-          nw[q] = 0;
-          miss[q] = 0;
-        }
-        if (valid) {
-          load_row<W>(p.seen, w, sr);
-          was_empty = !row_nonzero<W>(sr);
+      // warps take chunks of kBuChunkVerts vertices (whole bitmap words) from
+      // the team's counter as they finish, those with the most in-arcs first,
+      // so that a warp walking hubs does not hold the level up
+      const uint32_t nchunks = (p.n + kBuChunkVerts - 1) / kBuChunkVerts;
+      for (;;) {
+        uint32_t gi = 0;
+        if (lane == 0) gi = atomicAdd(&c->bu_next, 1u);
+        gi = __shfl_sync(FULL, gi, 0);
+        if (gi >= nchunks) break;
+        const uint32_t g0 = (p.bu_chunks ? p.bu_chunks[gi] : gi) * kBuChunkVerts;
+        const uint32_t g1 = g0 + kBuChunkVerts < p.n ? g0 + kBuChunkVerts : p.n;
+        for (uint32_t base = g0; base < g1; base += 32) {
+          uint32_t w = base + lane;
+          bool valid = w < p.n;
+          u64 nw[W], sr[W], miss[W];
+          uint32_t od = 0, e0 = 0, ee = 0;
+          bool was_empty = false, any = false, heavy = false;
 #pragma unroll
           for (int q = 0; q < W; ++q) {
-            miss[q] = act[q] & ~sr[q];
-            any |= miss[q] != 0;
+            nw[q] = 0;
+            miss[q] = 0;
           }
-          e0 = p.ioff[w];
-          ee = p.ioff[w + 1];
-          heavy = any && ee - e0 > kHeavyIn;
-          if (any && !heavy) {
-            // U in-arcs per step: their columns and frontier bits are loaded
-            // together, then the rows of those on a frontier; the early exit
-            // is tested once per step (extra rows only repeat found bits)
-            constexpr int U = W >= 8 ? 2 : 4;
-            uint32_t e = e0;
-            for (; e < ee; e += U) {
-              uint32_t uu[U], fb[U];
+          if (valid) {
+            load_row<W>(p.seen, w, sr);
+            was_empty = !row_nonzero<W>(sr);
 #pragma unroll
-              for (int j = 0; j < U; ++j) uu[j] = e + j < ee ? p.icol[e + j] : 0xffffffffu;
+            for (int q = 0; q < W; ++q) {
+              miss[q] = act[q] & ~sr[q];
+              any |= miss[q] != 0;
+            }
+            e0 = p.ioff[w];
+            ee = p.ioff[w + 1];
+            heavy = any && ee - e0 > kHeavyIn;
+            if (any && !heavy) {
+              // U in-arcs per step: their columns and frontier bits are loaded
+              // together, then the rows of those on a frontier; the early exit
+              // is tested once per step (extra rows only repeat found bits)
+              constexpr int U = W >= 8 ? 2 : 4;
+              uint32_t e = e0;
+              for (; e < ee; e += U) {
+                uint32_t uu[U], fb[U];
 #pragma unroll
-              for (int j = 0; j < U; ++j)
+                for (int j = 0; j < U; ++j) uu[j] = e + j < ee ? p.icol[e + j] : 0xffffffffu;
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                  fb[j] = uu[j] != 0xffffffffu ? (FBcur[uu[j] >> 5] >> (uu[j] & 31)) & 1u : 0u;
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                  if (fb[j]) {
+                    u64 fr[W];
+                    load_row<W>(Fcur, uu[j], fr);
+#pragma unroll
+                    for (int q = 0; q < W; ++q) nw[q] |= fr[q] & miss[q];
+                  }
+                }
+                bool full = true;
+#pragma unroll
+                for (int q = 0; q < W; ++q) full &= nw[q] == miss[q];
+                if (full) {
+                  e += U;
+                  break;
+                }
+              }
+              scanned += (e < ee ? e : ee) - e0;
+              scanned_v += 1;
+            }
+          }
+          // vertices of high in-degree: the whole warp walks their in-arcs
+          // (coalesced column reads, HU per lane per step) so that one lane does
+          // not hold the level up; same result as the lane loop (the OR of the
+          // frontier rows of in-neighbours, or every missing bit found)
+          for (unsigned hv = __ballot_sync(FULL, heavy); hv; hv &= hv - 1) {
+            const int src = __ffs(hv) - 1;
+            const uint32_t hb = __shfl_sync(FULL, e0, src), he = __shfl_sync(FULL, ee, src);
+            u64 hm[W], acc[W];
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+              hm[q] = __shfl_sync(FULL, miss[q], src);
+              acc[q] = 0;
+            }
+            constexpr int HU = W >= 8 ? 1 : W >= 4 ? 2 : 4;
+            uint32_t e = hb;
+            for (; e < he; e += 32 * HU) {
+              uint32_t uu[HU], fb[HU];
+#pragma unroll
+              for (int j = 0; j < HU; ++j) {
+                const uint32_t i = e + 32 * j + lane;
+                uu[j] = i < he ? p.icol[i] : 0xffffffffu;
+              }
+#pragma unroll
+              for (int j = 0; j < HU; ++j)
                 fb[j] = uu[j] != 0xffffffffu ? (FBcur[uu[j] >> 5] >> (uu[j] & 31)) & 1u : 0u;
 #pragma unroll
-              for (int j = 0; j < U; ++j) {
+              for (int j = 0; j < HU; ++j) {
                 if (fb[j]) {
                   u64 fr[W];
                   load_row<W>(Fcur, uu[j], fr);
 #pragma unroll
-                  for (int q = 0; q < W; ++q) nw[q] |= fr[q] & miss[q];
+                  for (int q = 0; q < W; ++q) acc[q] |= fr[q] & hm[q];
                 }
               }
               bool full = true;
 #pragma unroll
-              for (int q = 0; q < W; ++q) full &= nw[q] == miss[q];
+              for (int q = 0; q < W; ++q) full &= warp_or(acc[q]) == hm[q];
               if (full) {
-                e += U;
+                e += 32 * HU;
                 break;
               }
             }
-            scanned += (e < ee ? e : ee) - e0;
-            scanned_v += 1;
-          }
-        }
-        // vertices of high in-degree: the whole warp walks their in-arcs
-        // (coalesced column reads, HU per lane per step) so that one lane does
-        // not hold the level up; same result as the lane loop (the OR of the
-        // frontier rows of in-neighbours, or every missing bit found)
-        for (unsigned hv = __ballot_sync(FULL, heavy); hv; hv &= hv - 1) {
-          const int src = __ffs(hv) - 1;
-          const uint32_t hb = __shfl_sync(FULL, e0, src), he = __shfl_sync(FULL, ee, src);
-          u64 hm[W], acc[W];
 #pragma unroll
-          for (int q = 0; q < W; ++q) {
-            hm[q] = __shfl_sync(FULL, miss[q], src);
-            acc[q] = 0;
-          }
-          constexpr int HU = W >= 8 ? 1 : W >= 4 ? 2 : 4;
-          uint32_t e = hb;
-          for (; e < he; e += 32 * HU) {
-            uint32_t uu[HU], fb[HU];
+            for (int q = 0; q < W; ++q) acc[q] = warp_or(acc[q]);
+            if (lane == src) {
 #pragma unroll
-            for (int j = 0; j < HU; ++j) {
-              const uint32_t i = e + 32 * j + lane;
-              uu[j] = i < he ? p.icol[i] : 0xffffffffu;
-            }
-#pragma unroll
-            for (int j = 0; j < HU; ++j)
-              fb[j] = uu[j] != 0xffffffffu ? (FBcur[uu[j] >> 5] >> (uu[j] & 31)) & 1u : 0u;
-#pragma unroll
-            for (int j = 0; j < HU; ++j) {
-              if (fb[j]) {
-                u64 fr[W];
-                load_row<W>(Fcur, uu[j], fr);
-#pragma unroll
-                for (int q = 0; q < W; ++q) acc[q] |= fr[q] & hm[q];
-              }
-            }
-            bool full = true;
-#pragma unroll
-            for (int q = 0; q < W; ++q) full &= warp_or(acc[q]) == hm[q];
-            if (full) {
-              e += 32 * HU;
-              break;
+              for (int q = 0; q < W; ++q) nw[q] = acc[q];
+              scanned += (e < he ? e : he) - hb;
+              scanned_v += 1;
             }
           }
+          bool isnew = valid && row_nonzero<W>(nw);
+          if (isnew) {
+            od = p.off[w + 1] - p.off[w];
 #pragma unroll
-          for (int q = 0; q < W; ++q) acc[q] = warp_or(acc[q]);
-          if (lane == src) {
-#pragma unroll
-            for (int q = 0; q < W; ++q) nw[q] = acc[q];
-            scanned += (e < he ? e : he) - hb;
-            scanned_v += 1;
+            for (int q = 0; q < W; ++q) sr[q] |= nw[q];
+            store_row<W>(p.seen, w, sr);
+            store_row<W>(Fnext, w, nw);
+            if (p.lvl) record_levels<W>(p, w, nw, depth);
           }
+          {
+            // the warp owns the 32 consecutive vertices of one bitmap word
+            uint32_t word = __ballot_sync(FULL, isnew);
+            if (lane == 0) FBnext[base >> 5] = word;
+          }
+          warp_count_slots<W>(nw, od, sm.cnt, sm.wsum, lane);
+          warp_append(isnew, w, od, &c->nl_packed, NL, NLoff, lane);
+          warp_append_plain(isnew && was_empty, w, &c->vl_count, p.VL, lane);
         }
-        bool isnew = valid && row_nonzero<W>(nw);
-        if (isnew) {
-          od = p.off[w + 1] - p.off[w];
-#pragma unroll
-          for (int q = 0; q < W; ++q) sr[q] |= nw[q];
-          store_row<W>(p.seen, w, sr);
-          store_row<W>(Fnext, w, nw);
-          if (p.lvl) record_levels<W>(p, w, nw, depth);
-        }
-        {
-          // the warp owns the 32 consecutive vertices of one bitmap word
-          uint32_t word = __ballot_sync(FULL, isnew);
-          if (lane == 0) FBnext[base >> 5] = word;
-        }
-        warp_count_slots<W>(nw, od, sm.cnt, sm.wsum, lane);
-        warp_append(isnew, w, od, &c->nl_packed, NL, NLoff, lane);
-        warp_append_plain(isnew && was_empty, w, &c->vl_count, p.VL, lane);
       }
       if (tb == 0) trace_stamp(p, 9);
       if (!team_sync(c, p.sh, bpt, p.timeout, [] {})) break;

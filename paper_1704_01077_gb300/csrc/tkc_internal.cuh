@@ -39,6 +39,7 @@ void note_launches(unsigned count);
 
 constexpr uint32_t kMaxN = 1u << 26; // list counters pack the count in 26 bits
 constexpr int kMaxWords = 8;         // 512-bit source batches
+constexpr uint32_t kBuChunkVerts = 128;  // bottom-up levels: vertices per chunk a warp takes
 
 // Device-resident state of one persistent BFSCut run (one graph).
 struct Ctl {
@@ -75,7 +76,7 @@ struct Ctl {
   unsigned long long lvl_scan_a;
   unsigned long long trace_n;  // records written to the optional trace
   unsigned int bdepth;         // depth reached by the current batch (0 after seeding)
-  unsigned int pad1;
+  unsigned int bu_next;        // bottom-up level: next vertex chunk to hand out (zeroed by every epilogue)
 };
 
 // State shared by all teams of one run.
@@ -108,6 +109,9 @@ struct RunParams {
   uint64_t arcs;
   const uint32_t *off, *col, *ioff, *icol;
   const uint32_t *alpha, *omega;
+  // bottom-up levels: the graph's vertex chunks (kBuChunkVerts consecutive ids)
+  // by decreasing number of in-arcs; nullptr = chunks in id order
+  const uint32_t *bu_chunks;
   const uint32_t *order;
   uint32_t norder;  // sources in `order` to examine (all have out-degree >= 1)
   // search configuration
@@ -267,6 +271,7 @@ struct tkc_graph {
   unsigned long long *nb_key = nullptr;       //   floor(S~ * 2^46 / (r-1)^2)
   unsigned long long *nb_hkey = nullptr;      // harmonic: ~(FP64 bits of the upper bound on h)
   uint32_t *nb_horder = nullptr;              // harmonic NBCut order: by (nb_hkey, id)
+  mutable uint32_t *bu_chunks = nullptr;      // bottom-up work order: chunk ids by decreasing in-arcs
 };
 
 namespace tkc {
@@ -275,6 +280,7 @@ int validate_and_transpose(tkc_graph *g);
 int build_in_csr(tkc_graph *g);
 int ensure_degree_order(tkc_graph *g);
 int ensure_reach_bounds(tkc_graph *g);
+int ensure_bu_chunks(const tkc_graph *g);
 int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
 // tkc_nb.cu
 // gid/g_directed (several graphs as one union): per-vertex directedness
