@@ -164,6 +164,10 @@ constexpr uint32_t kHeavyIn = 24;
 // threads beat 512 by 30% and 14%).
 template <int W>
 constexpr int kThreads = W == 1 ? 1024 : W == 2 ? 768 : 512;
+// Small graphs and one-source searches: short levels, where the block-wide
+// barriers and scans of the larger blocks cost more than they hide.
+constexpr int kMinThreads = 512;
+constexpr int kMaxThreads = 1024;
 
 __device__ __forceinline__ bool harmonic_below(double Hd, u64 d, u64 nd, u64 g, u64 omega, u64 xbits) {
   const u64 w = omega > nd ? omega - nd : 0;
@@ -364,8 +368,8 @@ struct Smem {
   uint32_t cr[64 * W], cid[64 * W], cg[64 * W];
   unsigned ncand;
   unsigned nactive;
-  unsigned scan[kThreads<W> / 32 + 1];
-  u64 scan64[kThreads<W> / 32 + 1];
+  unsigned scan[kMaxThreads / 32 + 1];
+  u64 scan64[kMaxThreads / 32 + 1];
   u64 acc[4];
 };
 
@@ -385,16 +389,16 @@ __device__ uint32_t block_exscan(Smem<W> &sm, uint32_t x, uint32_t *total) {
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
-    for (int i = 0; i < kThreads<W> / 32; ++i) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
       uint32_t t = sm.scan[i];
       sm.scan[i] = run;
       run += t;
     }
-    sm.scan[kThreads<W> / 32] = run;
+    sm.scan[blockDim.x >> 5] = run;
   }
   __syncthreads();
   uint32_t res = sm.scan[wid] + incl - x;
-  *total = sm.scan[kThreads<W> / 32];
+  *total = sm.scan[blockDim.x >> 5];
   __syncthreads();
   return res;
 }
@@ -413,16 +417,16 @@ __device__ u64 block_exscan64(Smem<W> &sm, u64 x, u64 *total) {
   __syncthreads();
   if (threadIdx.x == 0) {
     u64 run = 0;
-    for (int i = 0; i < kThreads<W> / 32; ++i) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
       u64 t = sm.scan64[i];
       sm.scan64[i] = run;
       run += t;
     }
-    sm.scan64[kThreads<W> / 32] = run;
+    sm.scan64[blockDim.x >> 5] = run;
   }
   __syncthreads();
   u64 res = sm.scan64[wid] + incl - x;
-  *total = sm.scan64[kThreads<W> / 32];
+  *total = sm.scan64[blockDim.x >> 5];
   __syncthreads();
   return res;
 }
@@ -518,14 +522,14 @@ __device__ void merge_topk_one(const RunParams &p, Smem<W> &sm) {
   uint32_t ntop = p.g_ntop[0];
   uint32_t nc = sm.ncand;
   if (nc == 0) return;
-  for (uint32_t i = threadIdx.x; i < ntop; i += kThreads<W>) {
+  for (uint32_t i = threadIdx.x; i < ntop; i += blockDim.x) {
     sm.tS[i] = p.top_S[i];
     sm.tr[i] = p.top_r[i];
     sm.tid[i] = p.top_id[i];
   }
   __syncthreads();
   // rank of each candidate among existing entries and other candidates
-  for (uint32_t i = threadIdx.x; i < nc; i += kThreads<W>) {
+  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
     u64 S = sm.cS[i];
     uint32_t r = sm.cr[i], id = sm.cid[i];
     uint32_t lo = 0, hi = ntop;  // first existing entry not less than the candidate
@@ -543,7 +547,7 @@ __device__ void merge_topk_one(const RunParams &p, Smem<W> &sm) {
       p.top_id[rank] = id;
     }
   }
-  for (uint32_t i = threadIdx.x; i < ntop; i += kThreads<W>) {
+  for (uint32_t i = threadIdx.x; i < ntop; i += blockDim.x) {
     uint32_t rank = i;
     for (uint32_t j = 0; j < nc; ++j)
       if (entry_less(p.harmonic, sm.cS[j], sm.cr[j], sm.cid[j], sm.tS[i], sm.tr[i], sm.tid[i])) ++rank;
@@ -565,7 +569,7 @@ template <int W>
 __device__ void merge_topk_many(const RunParams &p, Smem<W> &sm) {
   const uint32_t kk = p.kk;
   const uint32_t nc = sm.ncand;
-  for (uint32_t i = threadIdx.x; i < nc; i += kThreads<W>) {
+  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
     const uint32_t g = sm.cg[i];
     bool first = true;
     for (uint32_t j = 0; j < i && first; ++j) first = sm.cg[j] != g;
@@ -650,14 +654,14 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
     sm.nactive = 0;
   }
   if (threadIdx.x < W) sm.active[threadIdx.x] = 0;
-  for (int i = threadIdx.x; i < 4; i += kThreads<W>) sm.acc[i] = 0;
+  for (int i = threadIdx.x; i < 4; i += blockDim.x) sm.acc[i] = 0;
   __syncthreads();
   // 1. per-slot level update
-  int cont[(64 * W + kThreads<W> - 1) / kThreads<W>];
+  int cont[(64 * W + kMinThreads - 1) / kMinThreads];
   uint32_t finished = 0;
 #pragma unroll
-  for (int t = 0; t < (64 * W + kThreads<W> - 1) / kThreads<W>; ++t) {
-    uint32_t s = threadIdx.x + t * kThreads<W>;
+  for (int t = 0; t < (64 * W + kMinThreads - 1) / kMinThreads; ++t) {
+    uint32_t s = threadIdx.x + t * blockDim.x;
     cont[t] = 0;
     if (s >= B) continue;
     Slot sl = p.slots[s];
@@ -701,8 +705,8 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
   uint32_t cuts = 0;
   u64 visited = 0;
 #pragma unroll
-  for (int t = 0; t < (64 * W + kThreads<W> - 1) / kThreads<W>; ++t) {
-    uint32_t s = threadIdx.x + t * kThreads<W>;
+  for (int t = 0; t < (64 * W + kMinThreads - 1) / kMinThreads; ++t) {
+    uint32_t s = threadIdx.x + t * blockDim.x;
     if (!cont[t]) continue;
     Slot sl = p.slots[s];
     Thresh x = thresh_of(p, sl.graph);
@@ -819,7 +823,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       for (int j = 0; j < W; ++j) c->active[j] = 0;
       c->step = 1;  // another empty clear step, then this check again
     }
-    for (uint32_t s = threadIdx.x; s < B; s += kThreads<W>) p.slots[s].state = 0;
+    for (uint32_t s = threadIdx.x; s < B; s += blockDim.x) p.slots[s].state = 0;
     __syncthreads();
     return;
   }
@@ -952,14 +956,14 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     }
   }
   // slots beyond `assigned` are free
-  for (uint32_t s = assigned + threadIdx.x; s < B; s += kThreads<W>) p.slots[s].state = 0;
+  for (uint32_t s = assigned + threadIdx.x; s < B; s += blockDim.x) p.slots[s].state = 0;
   __syncthreads();
 }
 
 // ------------------------------------------------------------------ the kernel
 
-template <int W>
-__global__ void __launch_bounds__(kThreads<W>, 1) bfscut_kernel(RunParams p0) {
+template <int W, int TPB>
+__global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
   __shared__ Smem<W> sm;
   // this block's team: its own control block, slots, rows, lists and stamps
   __shared__ RunParams p;
@@ -993,10 +997,10 @@ __global__ void __launch_bounds__(kThreads<W>, 1) bfscut_kernel(RunParams p0) {
   __syncthreads();
   Ctl *c = p.ctl;
   const int lane = threadIdx.x & 31;
-  const uint32_t gwarp = (tb * kThreads<W> + threadIdx.x) >> 5;
-  const uint32_t nwarps = (bpt * kThreads<W>) >> 5;
-  const uint32_t gthread = tb * kThreads<W> + threadIdx.x;
-  const uint32_t nthreads = bpt * kThreads<W>;
+  const uint32_t gwarp = (tb * TPB + threadIdx.x) >> 5;
+  const uint32_t nwarps = (bpt * TPB) >> 5;
+  const uint32_t gthread = tb * TPB + threadIdx.x;
+  const uint32_t nthreads = bpt * TPB;
 
   while (true) {
     const int step = ld_volatile_i32(&c->step);
@@ -1031,7 +1035,7 @@ __global__ void __launch_bounds__(kThreads<W>, 1) bfscut_kernel(RunParams p0) {
     const uint32_t depth = vc->bdepth + 1;  // depth of the level being discovered
     const u64 fl_arcs = vc->fl_arcs;
     if (threadIdx.x < W) sm.active[threadIdx.x] = vc->active[threadIdx.x];
-    for (int i = threadIdx.x; i < 64 * W; i += kThreads<W>) {
+    for (int i = threadIdx.x; i < 64 * W; i += TPB) {
       sm.cnt[i] = 0;
       sm.wsum[i] = 0;
     }
@@ -1295,7 +1299,7 @@ __global__ void __launch_bounds__(kThreads<W>, 1) bfscut_kernel(RunParams p0) {
     if (lane == 0 && scanned) atomicAdd(&sm.acc[3], scanned);
     if (lane == 0 && scanned_v) atomicAdd(&sm.acc[2], scanned_v);
     __syncthreads();
-    for (int i = threadIdx.x; i < 64 * W; i += kThreads<W>) {
+    for (int i = threadIdx.x; i < 64 * W; i += TPB) {
       if (sm.cnt[i]) {
         atomicAdd(&p.cnt[i], sm.cnt[i]);
         atomicAdd(&p.wsum[i], sm.wsum[i]);
@@ -1313,31 +1317,53 @@ __global__ void __launch_bounds__(kThreads<W>, 1) bfscut_kernel(RunParams p0) {
 
 // ------------------------------------------------------------------ host side
 
-template <int W>
+// The larger blocks pay off on batched searches of large graphs; one-source
+// searches and small graphs run 512 threads per block.
+static bool wide_blocks(const RunParams &p) { return p.B > 1 && p.n >= (1u << 16); }
+
+template <int W, int TPB>
 static int occupancy_of(int *blocks_per_sm) {
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bfscut_kernel<W>, kThreads<W>, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bfscut_kernel<W, TPB>, TPB, 0);
   return e == cudaSuccess ? TKC_OK : TKC_ECUDA;
+}
+
+// Co-resident blocks of the W-word kernel, the smaller of its two block sizes'
+// (either may be launched with this count).
+template <int W>
+static int occupancy_both(int *blocks_per_sm) {
+  int a = 0, b = 0;
+  int rc = occupancy_of<W, kThreads<W>>(&a);
+  if (rc == TKC_OK) rc = occupancy_of<W, kMinThreads>(&b);
+  if (rc != TKC_OK) return rc;
+  *blocks_per_sm = a < b ? a : b;
+  return TKC_OK;
 }
 
 int max_coresident_blocks(tkc_ctx *ctx, int words) {
   int per_sm = 0;
   int rc = TKC_OK;
   switch (words) {
-    case 1: rc = occupancy_of<1>(&per_sm); break;
-    case 2: rc = occupancy_of<2>(&per_sm); break;
-    case 4: rc = occupancy_of<4>(&per_sm); break;
-    case 8: rc = occupancy_of<8>(&per_sm); break;
+    case 1: rc = occupancy_both<1>(&per_sm); break;
+    case 2: rc = occupancy_both<2>(&per_sm); break;
+    case 4: rc = occupancy_both<4>(&per_sm); break;
+    case 8: rc = occupancy_both<8>(&per_sm); break;
     default: return 0;
   }
   if (rc != TKC_OK) return 0;
   return per_sm * ctx->num_sms;
 }
 
-template <int W>
-static cudaError_t launch(const RunParams &p, int blocks, cudaStream_t st) {
+template <int W, int TPB>
+static cudaError_t launch_tpb(const RunParams &p, int blocks, cudaStream_t st) {
   void *args[] = {(void *)&p};
   note_launches(1);
-  return cudaLaunchCooperativeKernel((const void *)bfscut_kernel<W>, dim3(blocks), dim3(kThreads<W>), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void *)bfscut_kernel<W, TPB>, dim3(blocks), dim3(TPB), args, 0, st);
+}
+
+template <int W>
+static cudaError_t launch(const RunParams &p, int blocks, cudaStream_t st) {
+  if (kThreads<W> != kMinThreads && wide_blocks(p)) return launch_tpb<W, kThreads<W>>(p, blocks, st);
+  return launch_tpb<W, kMinThreads>(p, blocks, st);
 }
 
 int run_bfscut(tkc_ctx *ctx, const RunParams &p, int words, int blocks) {

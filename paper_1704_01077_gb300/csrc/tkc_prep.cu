@@ -383,14 +383,16 @@ int ensure_degree_order(tkc_graph *g) {
 __global__ void k_bu_chunk_keys(const u32 *ioff, u32 n, u32 nch, u32 *key, u32 *val) {
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < nch; i += gridDim.x * blockDim.x) {
     const u32 a = i * kBuChunkVerts, b = a + kBuChunkVerts < n ? a + kBuChunkVerts : n;
-    key[i] = 0xffffffffu - (ioff[b] - ioff[a]);  // more in-arcs -> smaller key
-    val[i] = i;                                  // ids ascending: the sort is stable
+    const u32 arcs = ioff[b] - ioff[a];
+    key[i] = (u32)__clz(arcs);  // leading zeros: a longer bit length of the in-arc count sorts first
+    val[i] = i;                          // ids ascending: the sort is stable
   }
 }
 
-// Chunks of kBuChunkVerts vertices by decreasing in-arcs: bottom-up levels
-// hand them out in this order (longest first), so that the chunks holding
-// hubs start early.  Only the order of work depends on it, not any result.
+// Chunks of kBuChunkVerts vertices by decreasing in-arcs (to a power of two):
+// bottom-up levels hand them out in this order (longest first), so that the
+// chunks holding hubs start early.  Only the order of work depends on it, not
+// any result.
 int ensure_bu_chunks(const tkc_graph *g) {
   if (g->bu_chunks || g->n == 0) return TKC_OK;
   cudaStream_t st = g->ctx->stream;
@@ -400,7 +402,7 @@ int ensure_bu_chunks(const tkc_graph *g) {
   TKC_TRY(cudaMallocAsync(&keys, (size_t)nch * sizeof(u32), st));
   TKC_LAUNCH(k_bu_chunk_keys<<<grid_for(nch, 256), 256, 0, st>>>(g->ioff, g->n, nch, keys, ids));
   TKC_TRY(cudaGetLastError());
-  TKC_RC(radix_sort_pairs(keys, ids, nch, 32, st));
+  TKC_RC(radix_sort_pairs(keys, ids, nch, 6, st));
   TKC_TRY(cudaFreeAsync(keys, st));
   g->bu_chunks = ids;
   return TKC_OK;
