@@ -371,6 +371,7 @@ struct Smem {
   unsigned scan[kMaxThreads / 32 + 1];
   u64 scan64[kMaxThreads / 32 + 1];
   u64 acc[4];
+  unsigned bu_next;  // bottom-up level: next of this block's vertex chunks
 };
 
 // Block-wide exclusive scan of one uint32 per thread; returns the prefix and
@@ -646,7 +647,6 @@ __device__ __forceinline__ void trace_stamp(const RunParams &p, int slot) {
 template <int W>
 __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
   Ctl *c = p.ctl;
-  if (threadIdx.x == 0) c->bu_next = 0;
   const uint32_t B = p.B;
   trace_stamp(p, 13);
   if (threadIdx.x == 0) {
@@ -790,7 +790,6 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
 template <int W>
 __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
   Ctl *c = p.ctl;
-  if (threadIdx.x == 0) c->bu_next = 0;
   trace_stamp(p, 13);
   const uint32_t B = p.B;
   u64 *Fcur = c->cur ? p.F1 : p.F0;
@@ -1042,6 +1041,7 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
     if (threadIdx.x == 0) {
       sm.acc[2] = 0;
       sm.acc[3] = 0;
+      sm.bu_next = 0;
     }
     __syncthreads();
     u64 scanned = 0, scanned_v = 0;
@@ -1146,15 +1146,18 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
       u64 act[W];
 #pragma unroll
       for (int q = 0; q < W; ++q) act[q] = sm.active[q];
-      // warps take chunks of kBuChunkVerts vertices (whole bitmap words) from
-      // the team's counter as they finish, those with the most in-arcs first,
+      // chunks of kBuChunkVerts vertices (whole bitmap words), those with the
+      // most in-arcs first, are dealt round-robin to the team's blocks; a
+      // block's warps take its chunks from a shared counter as they finish,
       // so that a warp walking hubs does not hold the level up
       const uint32_t nchunks = (p.n + kBuChunkVerts - 1) / kBuChunkVerts;
       for (;;) {
-        uint32_t gi = 0;
-        if (lane == 0) gi = atomicAdd(&c->bu_next, 1u);
-        gi = __shfl_sync(FULL, gi, 0);
-        if (gi >= nchunks) break;
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(&sm.bu_next, 1u);
+        j = __shfl_sync(FULL, j, 0);
+        const u64 gi64 = (u64)tb + (u64)bpt * j;
+        if (gi64 >= nchunks) break;
+        const uint32_t gi = (uint32_t)gi64;
         const uint32_t g0 = (p.bu_chunks ? p.bu_chunks[gi] : gi) * kBuChunkVerts;
         const uint32_t g1 = g0 + kBuChunkVerts < p.n ? g0 + kBuChunkVerts : p.n;
         for (uint32_t base = g0; base < g1; base += 32) {

@@ -76,7 +76,7 @@ struct Ctl {
   unsigned long long lvl_scan_a;
   unsigned long long trace_n;  // records written to the optional trace
   unsigned int bdepth;         // depth reached by the current batch (0 after seeding)
-  unsigned int bu_next;        // bottom-up level: next vertex chunk to hand out (zeroed by every epilogue)
+  unsigned int pad1;
 };
 
 // State shared by all teams of one run.
