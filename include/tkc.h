@@ -78,6 +78,11 @@ typedef struct {
                               the threshold and the k-lists (0 = library default: one team of 8 SMs per
                               8 SMs for n >= 2^16; plain mode uses 1) */
   uint32_t nb_levels;      /* TKC_ORDER_NB: most level sweeps of computeBoundsNB, 1..65535 (0 = 256) */
+  uint32_t large_blocks;   /* threads per block of the search kernel: 0 = library choice (the larger blocks -- 1024
+                              threads for 64-bit batches, 768 for 128-bit -- for batched searches on graphs of
+                              2^20 vertices or more, else 512), 1 = always the larger blocks, 2 = always 512;
+                              wider batches always use 512.  Results never depend on it. */
+  uint32_t pad;
 } tkc_options;
 
 typedef struct {

@@ -309,6 +309,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.icol = g->icol;
   TKC_RC(ensure_bu_chunks(g));
   p.bu_chunks = g->bu_chunks;
+  p.large_blocks = o.large_blocks;
   p.alpha = g->alpha;
   p.omega = g->omega;
   p.order = rs.order;
@@ -567,7 +568,7 @@ static void tune_cache_load(tkc_ctx *ctx);
 static bool options_valid(const tkc_options *opt) {
   const u32 b = opt->batch_bits;
   if (!(b == 0 || b == 1 || b == 64 || b == 128 || b == 256 || b == 512)) return false;
-  return opt->order <= TKC_ORDER_NB && opt->nb_levels <= 65535;
+  return opt->order <= TKC_ORDER_NB && opt->nb_levels <= 65535 && opt->large_blocks <= 2;
 }
 
 int tkc_create(tkc_ctx **out, const tkc_options *opt) {

@@ -1323,7 +1323,10 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
 // The larger blocks pay off on batched searches of large graphs (R-MAT 20 and
 // 22); one-source searches and graphs below 2^20 vertices (BA 10^6: 1.75 ms of
 // kernel time at 512 threads, 1.98 ms at 768) run 512 threads per block.
-static bool wide_blocks(const RunParams &p) { return p.B > 1 && p.n >= (1u << 20); }
+static bool wide_blocks(const RunParams &p) {
+  if (p.large_blocks) return p.large_blocks == 1;
+  return p.B > 1 && p.n >= (1u << 20);
+}
 
 template <int W, int TPB>
 static int occupancy_of(int *blocks_per_sm) {

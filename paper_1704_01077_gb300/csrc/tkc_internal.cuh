@@ -112,6 +112,7 @@ struct RunParams {
   // bottom-up levels: the graph's vertex chunks (kBuChunkVerts consecutive ids)
   // by decreasing number of in-arcs; nullptr = chunks in id order
   const uint32_t *bu_chunks;
+  uint32_t large_blocks;  // tkc_options.large_blocks: 0 = by size, 1 = larger blocks, 2 = 512 threads
   const uint32_t *order;
   uint32_t norder;  // sources in `order` to examine (all have out-degree >= 1)
   // search configuration

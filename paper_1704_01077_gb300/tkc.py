@@ -49,7 +49,8 @@ class tkc_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("order", ctypes.c_uint32),
                 ("batch_bits", ctypes.c_uint32), ("bu_num", ctypes.c_uint32), ("bu_den", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("seed_factor", ctypes.c_uint32),
-                ("timeout_cycles", ctypes.c_uint64), ("teams", ctypes.c_uint32), ("nb_levels", ctypes.c_uint32)]
+                ("timeout_cycles", ctypes.c_uint64), ("teams", ctypes.c_uint32), ("nb_levels", ctypes.c_uint32),
+                ("large_blocks", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class tkc_result(ctypes.Structure):
@@ -170,10 +171,12 @@ class Options:
     timeout_cycles: int = 0
     teams: int = 0
     nb_levels: int = 0
+    large_blocks: int = 0
 
     def to_c(self) -> tkc_options:
         return tkc_options(self.device, self.stream, self.order, self.batch_bits, self.bu_num, self.bu_den,
-                           self.blocks, self.seed_factor, self.timeout_cycles, self.teams, self.nb_levels)
+                           self.blocks, self.seed_factor, self.timeout_cycles, self.teams, self.nb_levels,
+                           self.large_blocks, 0)
 
 
 @dataclass
@@ -395,7 +398,7 @@ def tkc_autotune(g, k: int) -> Options:
     _check(_lib.tkc_autotune(g, k, ctypes.byref(o)), "tkc_autotune")
     return Options(device=o.device, stream=o.stream, order=o.order, batch_bits=o.batch_bits, bu_num=o.bu_num,
                    bu_den=o.bu_den, blocks=o.blocks, seed_factor=o.seed_factor, timeout_cycles=o.timeout_cycles,
-                   teams=o.teams)
+                   teams=o.teams, nb_levels=o.nb_levels, large_blocks=o.large_blocks)
 
 
 def _dev(t):

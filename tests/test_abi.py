@@ -41,9 +41,10 @@ def test_binding_covers_every_declared_symbol():
 def test_struct_layouts_match_header():
     from paper_1704_01077_gb300 import tkc
 
-    # int + pad + pointer + 6 x uint32 + uint64 + 2 x uint32
-    assert ctypes.sizeof(tkc.tkc_options) == 56
+    # int + pad + pointer + 6 x uint32 + uint64 + 4 x uint32
+    assert ctypes.sizeof(tkc.tkc_options) == 64
     assert tkc.tkc_options.timeout_cycles.offset == 40
+    assert tkc.tkc_options.large_blocks.offset == 56
     # 5 pointers, 3 x uint32 (+pad), 6 x uint64, 2 x uint32, 2 x double
     assert ctypes.sizeof(tkc.tkc_result) == 144
     assert tkc.tkc_result.edges_visited.offset == 56
