@@ -490,6 +490,7 @@ int reach_directed_gpu(tkc_graph *g) {
   TKC_TRY(b.get(&active, n));
   TKC_TRY(b.get(&best, 1));
   int rc = TKC_OK;
+  u32 pivot0 = INF;  // the first pivot, whose full forward and backward reach fw/bw keep
   TKC_LAUNCH(k_trim_init<<<grid_of(n), 256, 0, st>>>(g->off, g->ioff, n, outd, ind, active));
   for (int round = 0;; ++round) {
     // trim until stable
@@ -510,10 +511,14 @@ int reach_directed_gpu(tkc_graph *g) {
     TKC_TRY(cudaStreamSynchronize(st));
     if (hb == 0) break;  // nothing left
     if (round == 0) {
+      // The BFS run over the whole graph, not only the untrimmed vertices: a
+      // trimmed vertex is its own SCC, so the intersection is the same, and
+      // the full reach sets serve again below when this SCC is the biggest.
       u32 pivot = 0xffffffffu - (u32)(hb & 0xffffffffu);
-      TKC_RC(bfs_levels(g->off, g->col, n, g->arcs, active, fw, pivot, flag, st));
-      TKC_RC(bfs_levels(g->ioff, g->icol, n, g->arcs, active, bw, pivot, flag, st));
+      TKC_RC(bfs_levels(g->off, g->col, n, g->arcs, nullptr, fw, pivot, flag, st));
+      TKC_RC(bfs_levels(g->ioff, g->icol, n, g->arcs, nullptr, bw, pivot, flag, st));
       TKC_LAUNCH(k_fwbw_mark<<<grid_of(n), 256, 0, st>>>(fw, bw, n, active, comp, pivot));
+      pivot0 = pivot;
       continue;  // trim again, then colour
     }
     // colouring round over the remaining vertices
@@ -554,9 +559,13 @@ int reach_directed_gpu(tkc_graph *g) {
   u32 big = 0;
   TKC_TRY(cudaMemcpyAsync(&big, comp + big_min, sizeof(u32), cudaMemcpyDeviceToHost, st));
   TKC_TRY(cudaStreamSynchronize(st));
-  // exact reach of the biggest SCC (forward), and the SCCs that reach it (backward)
-  TKC_RC(bfs_levels(g->off, g->col, n, g->arcs, nullptr, fw, big, flag, st));
-  TKC_RC(bfs_levels(g->ioff, g->icol, n, g->arcs, nullptr, bw, big, flag, st));
+  // exact reach of the biggest SCC (forward), and the SCCs that reach it
+  // (backward); only reachability is used, the same from every vertex of the
+  // SCC, so the first pivot's sweeps serve when it lies in the biggest SCC
+  if (big != pivot0) {
+    TKC_RC(bfs_levels(g->off, g->col, n, g->arcs, nullptr, fw, big, flag, st));
+    TKC_RC(bfs_levels(g->ioff, g->icol, n, g->arcs, nullptr, bw, big, flag, st));
+  }
   TKC_TRY(cudaMemsetAsync(flag, 0, sizeof(u32), st));
   TKC_LAUNCH(k_count_reached<<<grid_of(n), 256, 0, st>>>(fw, n, flag));
   const u64 reach_big = read_u32(flag, st, &rc);
