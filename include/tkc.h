@@ -187,15 +187,20 @@ int tkc_topk_closeness_bound(tkc_graph *g, uint32_t k, tkc_result *out);
 
 /* Autotuner (no paper counterpart: it only picks launch parameters).
  * Times candidate batch widths (64..512), team counts (1, 4, and SMs/16,
- * SMs/8, SMs/4, i.e. 16, 8 and 4 blocks per team) and bottom-up
- * thresholds on a sample of g's degree order (its first 1 024 sources, then
- * every s-th source, about a tenth of all), keeps the fastest in the
- * context's cache under g's class (directed, log2 n, log2 of the mean degree)
- * and writes it to *best (other fields copied from the context's options).
- * Later calls with options.batch_bits = 0 on a graph of the same class use
- * the cached choice.  With the environment variable TKC_TUNE_CACHE naming a
- * file, the cache is loaded at tkc_create and saved after each tuning.
- * Results never depend on these parameters. */
+ * SMs/8, SMs/4, i.e. 16, 8 and 4 blocks per team), then bottom-up
+ * thresholds, then (64- and 128-bit batches) the search kernel's block size
+ * (options.large_blocks 1 and 2 against the library's choice), on a sample of
+ * g's degree order (its first 1 024 sources, then every s-th source, about a
+ * tenth of all); keeps the fastest in the context's cache under g's class
+ * (directed, log2 n, log2 of the mean degree) and writes it to *best (other
+ * fields copied from the context's options).  Later calls with
+ * options.batch_bits = 0 on a graph of the same class use the cached choice
+ * (teams, thresholds and block size only where the options leave them at 0).
+ * With the environment variable TKC_TUNE_CACHE naming a file, the cache is
+ * loaded at tkc_create and saved after each tuning (one line per class:
+ * class=bits,teams,bu_num,bu_den,ms,large_blocks; lines without the last
+ * field mean the library's block size).  Results never depend on these
+ * parameters. */
 int tkc_autotune(tkc_graph *g, uint32_t k, tkc_options *best);
 
 /* computeBoundsDeg (Section 4): writes the degree order (out-degree

@@ -796,10 +796,17 @@ static void tune_cache_load(tkc_ctx *ctx) {
   if (!path) return;
   FILE *f = fopen(path, "r");
   if (!f) return;
-  char key[128];
-  TuneEntry e;
-  while (fscanf(f, " %127[^=]=%u,%u,%u,%u,%lf", key, &e.batch_bits, &e.teams, &e.bu_num, &e.bu_den, &e.ms) == 6)
+  char line[256], key[128];
+  // key=bits,teams,bu_num,bu_den,ms[,large_blocks] (files written before the
+  // block size was tuned lack the last field: library choice)
+  while (fgets(line, sizeof(line), f)) {
+    TuneEntry e{};
+    const int got = sscanf(line, " %127[^=]=%u,%u,%u,%u,%lf,%u", key, &e.batch_bits, &e.teams, &e.bu_num, &e.bu_den,
+                           &e.ms, &e.large_blocks);
+    if (got < 6) continue;
+    if (got == 6 || e.large_blocks > 2) e.large_blocks = 0;
     ctx->tune[key] = e;
+  }
   fclose(f);
 }
 
@@ -809,8 +816,8 @@ static void tune_cache_save(tkc_ctx *ctx) {
   FILE *f = fopen(path, "w");
   if (!f) return;
   for (auto &kv : ctx->tune)
-    fprintf(f, "%s=%u,%u,%u,%u,%.3f\n", kv.first.c_str(), kv.second.batch_bits, kv.second.teams, kv.second.bu_num,
-            kv.second.bu_den, kv.second.ms);
+    fprintf(f, "%s=%u,%u,%u,%u,%.3f,%u\n", kv.first.c_str(), kv.second.batch_bits, kv.second.teams,
+            kv.second.bu_num, kv.second.bu_den, kv.second.ms, kv.second.large_blocks);
   fclose(f);
 }
 
@@ -821,12 +828,14 @@ __global__ void k_sample_order(const u32 *order, u32 norder, u32 head, u32 strid
     out[i] = i < head ? order[i] : order[head + (u64)(i - head) * stride];
 }
 
-static int time_config(tkc_graph *g, const u32 *order, u32 norder, u32 kk, u32 bits, u32 teams, u32 bu, double *ms) {
+static int time_config(tkc_graph *g, const u32 *order, u32 norder, u32 kk, u32 bits, u32 teams, u32 bu, u32 large,
+                       double *ms) {
   tkc_ctx *ctx = g->ctx;
   tkc_options saved = ctx->opt;
   ctx->opt.teams = teams;
   ctx->opt.bu_num = bu;
   ctx->opt.bu_den = 1;
+  ctx->opt.large_blocks = large;
   RunSetup rs;
   memset(&rs, 0, sizeof(rs));
   rs.g = g;
@@ -879,6 +888,7 @@ static int topk_one(tkc_graph *g, uint32_t k, tkc_result *out, int harmonic) {
         ctx->opt.bu_num = it->second.bu_num;
         ctx->opt.bu_den = it->second.bu_den;
       }
+      if (!ctx->opt.large_blocks) ctx->opt.large_blocks = it->second.large_blocks;
     }
   }
   rs.g = g;
@@ -950,12 +960,12 @@ int tkc_autotune(tkc_graph *g, uint32_t k, tkc_options *best) {
   const u32 teams_c[] = {1, 4, (u32)std::max(1, maxb_t / 16), (u32)std::max(1, maxb_t / 8),
                          (u32)std::max(1, maxb_t / 4)};
   double best_ms = 1e300;
-  u32 bb = default_batch_bits(g->n), bt = 1, bu = 8;
+  u32 bb = default_batch_bits(g->n), bt = 1, bu = 8, bl = 0;
   int rc = TKC_OK;
   for (u32 b : bits_c)
     for (u32 t : teams_c) {
       double ms = 0;
-      rc = time_config(g, order, count, kk, b, t, 8, &ms);
+      rc = time_config(g, order, count, kk, b, t, 8, 0, &ms);
       if (rc != TKC_OK) break;
       if (ms < best_ms) {
         best_ms = ms;
@@ -966,22 +976,34 @@ int tkc_autotune(tkc_graph *g, uint32_t k, tkc_options *best) {
   for (u32 u : {4u, 16u, 32u}) {
     if (rc != TKC_OK) break;
     double ms = 0;
-    rc = time_config(g, order, count, kk, bb, bt, u, &ms);
+    rc = time_config(g, order, count, kk, bb, bt, u, 0, &ms);
     if (rc == TKC_OK && ms < best_ms) {
       best_ms = ms;
       bu = u;
     }
   }
+  // block shape: the larger blocks of 64- and 128-bit batches and 512 threads,
+  // each against the library's choice by graph size timed above
+  for (u32 l : {1u, 2u}) {
+    if (rc != TKC_OK || words_for(bb) > 2) break;
+    double ms = 0;
+    rc = time_config(g, order, count, kk, bb, bt, bu, l, &ms);
+    if (rc == TKC_OK && ms < best_ms) {
+      best_ms = ms;
+      bl = l;
+    }
+  }
   cudaFreeAsync(order, st);
   cudaStreamSynchronize(st);
   if (rc != TKC_OK) return rc;
-  TuneEntry e{bb, bt, bu, 1, best_ms};
+  TuneEntry e{bb, bt, bu, 1, best_ms, bl};
   ctx->tune[graph_class(g)] = e;
   tune_cache_save(ctx);
   best->batch_bits = bb;
   best->teams = bt;
   best->bu_num = bu;
   best->bu_den = 1;
+  best->large_blocks = bl;
   return TKC_OK;
 }
 

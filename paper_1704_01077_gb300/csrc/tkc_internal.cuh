@@ -227,6 +227,7 @@ struct MlpState {
 struct TuneEntry {
   uint32_t batch_bits, teams, bu_num, bu_den;
   double ms;
+  uint32_t large_blocks;  // tkc_options.large_blocks of the fastest run (1 or 2)
 };
 
 struct tkc_ctx {

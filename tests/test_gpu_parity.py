@@ -313,8 +313,48 @@ def test_autotune_picks_valid_parameters_and_keeps_results(gpu_lib, ctx):
         best = t.tkc_autotune(h, 10)
         assert best.batch_bits in (64, 128, 256, 512) and 1 <= best.teams <= 64
         assert best.bu_num in (4, 8, 16, 32) and best.bu_den == 1
+        assert best.large_blocks in (0, 1, 2) and (best.large_blocks == 0 or best.batch_bits <= 128)
         res = t.tkc_topk_closeness(h, 10)  # batch_bits = 0: the cached choice applies
         assert res.batch_bits == best.batch_bits
         _expect_equal(res, ref, g, 10)
     finally:
         t.tkc_free_graph(h)
+
+
+def test_tune_cache_file_round_trip(gpu_lib, tmp_path, monkeypatch):
+    """TKC_TUNE_CACHE: tuning writes one line per graph class with the block
+    size last; a new context loads it and applies it; a line without the block
+    size (the earlier format) still loads."""
+    import re
+
+    t = gpu_lib
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("TKC_TUNE_CACHE", str(path))
+    g = gg.rmat(13, 16, seed=gg.workload_seed(1) + 9)
+    ref = oracle.bfscut(g, 10)
+    c1 = t.tkc_create(t.Options())
+    try:
+        h = t.tkc_load_csr(c1, g.n, g.offsets, g.cols, g.directed)
+        try:
+            best = t.tkc_autotune(h, 10)
+        finally:
+            t.tkc_free_graph(h)
+    finally:
+        t.tkc_destroy(c1)
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1
+    m = re.fullmatch(r"(\w+)=(\d+),(\d+),(\d+),(\d+),([0-9.]+),(\d+)", lines[0])
+    assert m and int(m.group(2)) == best.batch_bits and int(m.group(7)) == best.large_blocks
+    for text, bits in ((lines[0], best.batch_bits), (f"{m.group(1)}=256,1,8,1,1.000", 256)):
+        path.write_text(text + "\n")
+        c2 = t.tkc_create(t.Options())
+        try:
+            h = t.tkc_load_csr(c2, g.n, g.offsets, g.cols, g.directed)
+            try:
+                res = t.tkc_topk_closeness(h, 10)
+            finally:
+                t.tkc_free_graph(h)
+        finally:
+            t.tkc_destroy(c2)
+        assert res.batch_bits == bits
+        _expect_equal(res, ref, g, 10)
