@@ -29,7 +29,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_rank_reduction_takes_slowest_time_and_all_arcs():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a threaded process
         out = m.dict()
         mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
