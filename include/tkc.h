@@ -75,8 +75,11 @@ typedef struct {
                               without cutting, so x starts from exact farness values (0 = none) */
   uint64_t timeout_cycles; /* budget of every device-side wait, in SM clock cycles (0 = default 2^34) */
   uint32_t teams;          /* independent groups of SMs, each running its own source batches and sharing
-                              the threshold and the k-lists (0 = library default: one team of 8 SMs per
-                              8 SMs for n >= 2^16; plain mode uses 1) */
+                              the threshold and the k-lists (0 = library default: 1 in plain mode and below
+                              2^14 vertices; NBCut on one graph one team per 32 SMs; otherwise one per 16 SMs
+                              below 2^16 vertices and one per 8 SMs from 2^16 up).  With several teams on one
+                              graph the first batch runs alone on the whole grid, so that a threshold exists
+                              before the teams start. */
   uint32_t nb_levels;      /* TKC_ORDER_NB: most level sweeps of computeBoundsNB, 1..65535 (0 = 256) */
   uint32_t large_blocks;   /* threads per block of the search kernel: 0 = library choice (the larger blocks -- 1024
                               threads for 64-bit batches, 768 for 128-bit -- for batched searches on graphs of
