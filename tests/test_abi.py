@@ -67,3 +67,50 @@ def test_constants_match_header():
                  "TKC_NOALLOC_MAX_N", "TKC_MLP_FEATURES", "TKC_MLP_HIDDEN", "TKC_MLP_PARAMS"):
         m = re.search(rf"#define {name} (-?\d+)", text)
         assert m and int(m.group(1)) == getattr(tkc, name), name
+
+
+def test_argument_errors_before_any_device_call(lib):
+    """Errors include/tkc.h documents for bad arguments, returned before the
+    library touches a device (so they hold on a machine without a GPU)."""
+    from paper_1704_01077_gb300 import tkc
+
+    EINVAL, EOVERFLOW = tkc.TKC_EINVAL, tkc.TKC_EOVERFLOW
+    vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    lib.tkc_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(tkc.tkc_options)]
+    good = tkc.Options().to_c()
+    assert lib.tkc_create(None, ctypes.byref(good)) == EINVAL
+    for bad in (dict(batch_bits=96), dict(batch_bits=1024), dict(order=9), dict(nb_levels=65536),
+                dict(large_blocks=3)):
+        out = vp(1234)
+        assert lib.tkc_create(ctypes.byref(out), ctypes.byref(tkc.Options(**bad).to_c())) == EINVAL, bad
+        assert out.value is None, bad
+    lib.tkc_set_options.argtypes = [vp, ctypes.POINTER(tkc.tkc_options)]
+    assert lib.tkc_set_options(None, ctypes.byref(good)) == EINVAL
+    lib.tkc_load_csr.argtypes = [vp, u32, u64, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+    g = vp(1234)
+    assert lib.tkc_load_csr(None, 4, 0, None, None, 1, 0, ctypes.byref(g)) == EINVAL
+    res = tkc.tkc_result()
+    for name in ("tkc_topk_closeness", "tkc_topk_harmonic", "tkc_topk_closeness_bound"):
+        fn = getattr(lib, name)
+        fn.argtypes = [vp, u32, ctypes.POINTER(tkc.tkc_result)]
+        assert fn(None, 10, ctypes.byref(res)) == EINVAL, name
+    for name in ("tkc_topk_closeness_multi", "tkc_topk_harmonic_multi"):
+        fn = getattr(lib, name)
+        fn.argtypes = [vp, vp, u32, u32, ctypes.POINTER(tkc.tkc_result)]
+        assert fn(None, None, 1, 10, ctypes.byref(res)) == EINVAL, name
+    lib.tkc_distance_sums.argtypes = [vp, u32, vp, vp, vp]
+    assert lib.tkc_distance_sums(None, 1, None, None, None) == EINVAL
+    lib.tkc_source_order.argtypes = [vp, vp]
+    assert lib.tkc_source_order(None, None) == EINVAL
+    lib.tkc_nb_bounds.argtypes = [vp, u32, vp, vp, vp, vp, vp, vp]
+    assert lib.tkc_nb_bounds(None, 0, None, None, None, None, None, None) == EINVAL
+    lib.tkc_distance_sums_noalloc.argtypes = [vp, vp, u32, u64, u32, vp, vp, vp, vp]
+    assert lib.tkc_distance_sums_noalloc(None, None, tkc.TKC_NOALLOC_MAX_N + 1, 0, 1, None, None, None,
+                                         None) == EINVAL
+    assert lib.tkc_distance_sums_noalloc(None, None, 10, 1 << 32, 1, None, None, None, None) == EOVERFLOW
+    assert lib.tkc_distance_sums_noalloc(None, None, 10, 0, 0, None, None, None, None) == tkc.TKC_OK
+    assert lib.tkc_distance_sums_noalloc(None, None, 10, 0, 1, None, None, None, None) == EINVAL
+    lib.tkc_destroy.argtypes = [vp]
+    lib.tkc_free_graph.argtypes = [vp]
+    lib.tkc_destroy(None)
+    lib.tkc_free_graph(None)
