@@ -89,6 +89,15 @@ MUTANTS = {
                            "if (lhs >= ((u128)Sx << ORC_NB_FRAC)) break; /* Algorithm 1: the head of Q exceeds x */",
                            [lambda: lbpins.test_bfsbound_equals_textbook_random(False),
                             lambda: lbpins.test_bfsbound_equals_textbook_families(0, False)]),
+    "ties_count_skips_kth": ("if (cmp_farness(S[v], r[v], e[kk - 1].S, e[kk - 1].r) == 0) ++t;",
+                             "if (cmp_farness(S[v], r[v], e[kk - 1].S, e[kk - 1].r) == 0 && v != e[kk - 1].id) ++t;",
+                             [pins.test_topk_against_fraction_brute_force]),
+    "farness_rounded_twice": ("*farness = num / den;", "*farness = (double)(n - 1) * ((double)S / den);",
+                              [pins.test_farness_doubles_are_single_rounded]),
+    "scc_cross_arc_as_back_arc": ("} else if (onstack[w] && index[w] < low[v]) {", "} else if (index[w] < low[v]) {",
+                                  [pins.test_scc_by_mutual_reachability]),
+    "scc_lowlink_not_propagated": ("if (low[v] < low[u]) low[u] = low[v];", "(void)u;",
+                                   [pins.test_scc_by_mutual_reachability]),
     "degree_order_unstable": ("for (uint32_t v = 0; v < n; ++v) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               "for (uint32_t v = n; v-- > 0;) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               [pins.test_degree_order_matches_lexsort]),
