@@ -98,6 +98,11 @@ MUTANTS = {
                                   [pins.test_scc_by_mutual_reachability]),
     "scc_lowlink_not_propagated": ("if (low[v] < low[u]) low[u] = low[v];", "(void)u;",
                                    [pins.test_scc_by_mutual_reachability]),
+    "cut_alpha_not_raised_to_nd": ("  if (lo < nd) lo = nd;\n  if (hi < lo) hi = lo;", "  if (hi < lo) hi = lo;",
+                                   [pins.test_cut_min_is_minimum_over_whole_interval,
+                                    pins.test_bfscut_equals_textbook_small_random]),
+    "cut_min_takes_largest": ("    if (lhs < rhs) { bl = L; br = r; }", "    if (lhs > rhs) { bl = L; br = r; }",
+                              [pins.test_cut_min_is_minimum_over_whole_interval]),
     "degree_order_unstable": ("for (uint32_t v = 0; v < n; ++v) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               "for (uint32_t v = n; v-- > 0;) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               [pins.test_degree_order_matches_lexsort]),
