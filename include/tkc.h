@@ -115,13 +115,19 @@ typedef struct {
 } tkc_result;
 
 /* Creates a context on opt->device (NULL opt = defaults).  No paper
- * counterpart: owns the stream, options and device workspace. */
+ * counterpart: owns the stream, options and device workspace; the caller owns
+ * *out until tkc_destroy.  Errors: TKC_EINVAL (null out, an option out of
+ * range: batch_bits, order, nb_levels, large_blocks), TKC_ENOMEM, TKC_ECUDA
+ * (no such device, no cooperative launch); *out is NULL on error. */
 int tkc_create(tkc_ctx **out, const tkc_options *opt);
 
-/* Replaces the context's options (same meaning as in tkc_create). */
+/* Replaces the context's options (same meaning as in tkc_create; no paper
+ * counterpart).  Errors: TKC_EINVAL (null argument, opt->device differs from
+ * the context's, an option out of range); the old options stay on error. */
 int tkc_set_options(tkc_ctx *ctx, const tkc_options *opt);
 
-/* Releases the context and its workspace.  Graphs must be freed first. */
+/* Releases the context and its workspace (no paper counterpart).  Graphs
+ * loaded on it must be freed first.  NULL is a no-op. */
 void tkc_destroy(tkc_ctx *ctx);
 
 /* Copies a CSR graph to the device, validates it, and builds its in-arc CSR
@@ -133,7 +139,8 @@ void tkc_destroy(tkc_ctx *ctx);
 int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offsets, const uint32_t *cols,
                  int directed, int ptr_on_device, tkc_graph **out);
 
-/* Frees a graph and everything derived from it. */
+/* Frees a graph and everything derived from it (orders, reach and NB bounds,
+ * features).  NULL is a no-op. */
 void tkc_free_graph(tkc_graph *g);
 
 /* Exact top-k closeness (Algorithm 1, DegCut or NBCut by options.order;
@@ -145,11 +152,16 @@ void tkc_free_graph(tkc_graph *g);
 int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out);
 
 /* Exact top-k of each of ng graphs (all on ctx's device) in one persistent
- * launch, one k-list per graph; outs[i] receives graph i's top-k exactly as
- * tkc_topk_closeness would give it.  Counters are per graph and may differ from
- * a run of the graph alone (the reach bounds are computed once on the union,
- * and the threshold evolves differently), ms_* are shared.  options.order:
- * TKC_ORDER_DEG or TKC_ORDER_NB (each graph stops on its own).  Same errors. */
+ * launch: Algorithm 1 on their disjoint union, one k-list per graph (no paper
+ * counterpart for the batching across graphs).  gs: ng handles loaded on ctx;
+ * outs: ng results, each with its own caller-allocated arrays; outs[i]
+ * receives graph i's top-k exactly as tkc_topk_closeness would give it.
+ * Counters are per graph and may differ from a run of the graph alone (the
+ * reach bounds are computed once on the union, and the threshold evolves
+ * differently); ms_* are shared.  options.order: TKC_ORDER_DEG or
+ * TKC_ORDER_NB (each graph stops on its own).  Errors: TKC_EINVAL (null ctx,
+ * null gs or outs with ng > 0, k > TKC_MAX_K, another order, a capacity too
+ * small), TKC_ENOMEM, TKC_ECUDA, TKC_ETIMEOUT. */
 int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
 
 /* Top-k harmonic centrality h(v) = sum over w != v of 1/d(v,w) (the paper's
@@ -166,8 +178,9 @@ int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, ui
  * tkc_topk_closeness.  Same errors. */
 int tkc_topk_harmonic(tkc_graph *g, uint32_t k, tkc_result *out);
 
-/* tkc_topk_harmonic for ng graphs in one persistent launch (as
- * tkc_topk_closeness_multi). */
+/* tkc_topk_harmonic for ng graphs in one persistent launch (Section 9 on the
+ * disjoint union, as tkc_topk_closeness_multi); same arguments and errors as
+ * tkc_topk_closeness_multi. */
 int tkc_topk_harmonic_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
 
 /* Exact top-k closeness by Algorithm 1 with updateBoundsLB (Section 7,
@@ -203,20 +216,27 @@ int tkc_topk_closeness_bound(tkc_graph *g, uint32_t k, tkc_result *out);
  * loaded at tkc_create and saved after each tuning (one line per class:
  * class=bits,teams,bu_num,bu_den,ms,large_blocks; lines without the last
  * field mean the library's block size).  Results never depend on these
- * parameters. */
+ * parameters.  Errors: TKC_EINVAL (null g or best, k > TKC_MAX_K),
+ * TKC_ENOMEM, TKC_ECUDA, TKC_ETIMEOUT. */
 int tkc_autotune(tkc_graph *g, uint32_t k, tkc_options *best);
 
 /* computeBoundsDeg (Section 4): writes the degree order (out-degree
- * descending, id ascending) to host array order[n]. */
+ * descending, id ascending) of all n vertices to host array order[n].
+ * Errors: TKC_EINVAL (null g, or null order with n > 0), TKC_ENOMEM,
+ * TKC_ECUDA. */
 int tkc_source_order(tkc_graph *g, uint32_t *order);
 
-/* Sets the source order used when options.order = TKC_ORDER_GIVEN: a
- * permutation of 0..n-1 in host memory (validated; TKC_EINVAL otherwise).
- * Any order gives the same top-k; only the work done changes. */
+/* Sets the order of Algorithm 1's queue Q (Section 4) used when
+ * options.order = TKC_ORDER_GIVEN: a permutation of 0..n-1 in host memory,
+ * copied.  Any order gives the same top-k; only the work done changes.
+ * Errors: TKC_EINVAL (null g, null order with n > 0, not a permutation),
+ * TKC_ENOMEM, TKC_ECUDA. */
 int tkc_set_source_order(tkc_graph *g, const uint32_t *order);
 
 /* Reach bounds alpha(v) <= r(v) <= omega(v) (Section 8.4, Algorithm 6; exact
- * component size for undirected graphs) into host arrays alpha[n], omega[n]. */
+ * component size for undirected graphs) into host arrays alpha[n], omega[n].
+ * Errors: TKC_EINVAL (null g, or a null array with n > 0), TKC_ENOMEM,
+ * TKC_ECUDA, TKC_ETIMEOUT (an SCC iteration exceeded n + 1 rounds). */
 int tkc_reach_bounds(tkc_graph *g, uint32_t *alpha, uint32_t *omega);
 
 /* computeBoundsNB (Section 5, Algorithm 3; Eq. 3 for directed graphs; Eq. 6
@@ -249,8 +269,11 @@ int tkc_nb_bounds(tkc_graph *g, uint32_t max_levels, uint64_t *S_lb, uint32_t *r
  * arrays, any may be NULL.  Errors as tkc_nb_bounds. */
 int tkc_nb_harmonic_bounds(tkc_graph *g, uint32_t max_levels, double *h_ub, uint32_t *order, uint32_t *n_order);
 
-/* Exact S(v) and r(v) of the listed sources by full BFS on the device, in
- * batches of 64 sources (no cutting).  srcs, S, r: host arrays of nsrc. */
+/* Exact S(v) and r(v) (Section 2 definitions) of the listed sources by full
+ * BFS on the device, in batches of 64 sources (no cutting).  srcs, S, r: host
+ * arrays of nsrc; a source may be listed more than once.  Errors: TKC_EINVAL
+ * (null g, a null array with nsrc > 0, a source >= n), TKC_ENOMEM, TKC_ECUDA,
+ * TKC_ETIMEOUT. */
 int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_t *S, uint32_t *r);
 
 /* Allocation-free variant of tkc_distance_sums, for callers that cannot
@@ -282,7 +305,8 @@ int tkc_distance_sums_noalloc(const uint32_t *offsets, const uint32_t *cols, uin
                               uint32_t nsrc, const uint32_t *srcs, uint64_t *S, uint32_t *r, void *stream);
 
 /* Number of CUDA kernels this library has launched in this process (all
- * contexts), for accounting of device work. */
+ * contexts), for accounting of device work (no paper counterpart; never
+ * fails). */
 uint64_t tkc_kernel_launches(void);
 
 /* ---- learned source order (beyond the paper) ------------------------------
@@ -302,31 +326,42 @@ uint64_t tkc_kernel_launches(void);
  * out-neighbours (the Section 6 lemma's gamma at d = 1, a bound on the 2-hop ball), an
  * h-index estimate of the core number (4 steps from the degree, out- and
  * in-neighbours), and the SCC size (component size if undirected); each
- * feature shifted and scaled to mean 0, variance 1 over the graph. */
+ * feature shifted and scaled to mean 0, variance 1 over the graph.  Errors:
+ * TKC_EINVAL (null g, or null x with n > 0), TKC_ENOMEM, TKC_ECUDA,
+ * TKC_ETIMEOUT. */
 int tkc_vertex_features(tkc_graph *g, float *x);
 
-/* Random He-uniform weights from `seed` (zero biases); resets Adam. */
+/* Random He-uniform weights from `seed` (zero biases); resets Adam.
+ * Errors: TKC_EINVAL (null ctx), TKC_ENOMEM, TKC_ECUDA. */
 int tkc_mlp_init(tkc_ctx *ctx, uint64_t seed);
 
 /* Sets / reads the fp32 master weights (host arrays of TKC_MLP_PARAMS);
- * setting enables TKC_ORDER_LEARNED and resets Adam. */
+ * setting enables TKC_ORDER_LEARNED and resets Adam.  Errors: TKC_EINVAL (null
+ * argument, nparams != TKC_MLP_PARAMS; reading before any model is set),
+ * TKC_ENOMEM, TKC_ECUDA. */
 int tkc_set_source_model(tkc_ctx *ctx, const float *params, uint32_t nparams);
 int tkc_get_source_model(tkc_ctx *ctx, float *params, uint32_t nparams);
 
-/* y[i] = model(x[i]) for m samples; x, y DEVICE arrays (m x 5, m). */
+/* y[i] = model(x[i]) for m samples; x, y DEVICE arrays (m x 5, m).
+ * Errors: TKC_EINVAL (null ctx, null x or y with m > 0, no model set),
+ * TKC_ECUDA. */
 int tkc_mlp_forward(tkc_ctx *ctx, const float *x, uint32_t m, float *y);
 
 /* Gradient of L = (1/m) sum_i (model(x_i) - t_i)^2 with respect to the
  * parameters (forward pass with the bf16 weights) into DEVICE grad[P]; the
- * loss into host *loss (may be NULL).  x, t: DEVICE arrays. */
+ * loss into host *loss (may be NULL).  x, t: DEVICE arrays.  Errors:
+ * TKC_EINVAL (null ctx, x, t or grad, m = 0, no model set), TKC_ENOMEM,
+ * TKC_ECUDA. */
 int tkc_mlp_gradient(tkc_ctx *ctx, const float *x, const float *t, uint32_t m, float *grad, float *loss);
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on that gradient with
  * learning rate lr; refreshes the bf16 weights; loss before the step into
- * host *loss (may be NULL). */
+ * host *loss (may be NULL).  Errors: TKC_EINVAL (null ctx, x or t, m = 0, no
+ * model set, lr not > 0), TKC_ENOMEM, TKC_ECUDA. */
 int tkc_mlp_train_step(tkc_ctx *ctx, const float *x, const float *t, uint32_t m, float lr, float *loss);
 
-/* Names a TKC_* return code. */
+/* Names a TKC_* return code ("unknown error" for any other value); the
+ * string is static. */
 const char *tkc_strerror(int code);
 
 #ifdef __cplusplus
