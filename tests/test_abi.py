@@ -114,3 +114,19 @@ def test_argument_errors_before_any_device_call(lib):
     lib.tkc_free_graph.argtypes = [vp]
     lib.tkc_destroy(None)
     lib.tkc_free_graph(None)
+
+
+def test_plain_c_client_compiles_and_links(lib, tmp_path):
+    """include/tkc.h is valid C99 (no C++ needed) and a C program links against
+    libtkc.so with every call it makes resolved (built, not run: no GPU here)."""
+    import subprocess
+
+    from paper_1704_01077_gb300 import build
+
+    src = os.path.join(ROOT, "tests", "c", "abi_client.c")
+    exe = tmp_path / "abi_client"
+    libdir = os.path.dirname(build.LIB)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           src, "-o", str(exe), "-L", libdir, "-l:" + os.path.basename(build.LIB),
+                           "-Wl,-rpath," + libdir, "-Wl,--no-undefined", "-Wl,--unresolved-symbols=ignore-in-shared-libs"])
+    assert exe.exists()
