@@ -3,9 +3,19 @@
 One step = one full pass of the method through the C ABI: load the CSR
 (validate, in-arc CSR), degree order, reach bounds (SCC / Algorithm 6), the
 source order (by default computeBoundsNB: NBCut; --order degree: DegCut), the
-persistent batched BFSCut kernel, and the output.  The metric is GTEPS =
-edges_visited (the paper's m_vis: arcs of every expanded BFS level) per second
-of step wall time, with the exact top-10 checked against a CPU-oracle sample.
+persistent batched BFSCut kernel, and the output.
+
+The metric is throughput at a fixed amount of work: the arcs that the paper's
+own procedure (plain one-source-at-a-time NBCut, Algorithm 1) visits on the
+workload -- its m_vis, counted once by the CPU oracle and stored with the
+workload's exact top-k in tests/golden/fullsize_<workload>.json -- divided by
+the step's wall time.  Work the batched search adds (more arcs under a
+threshold that lags behind) therefore cannot raise the figure; only a shorter
+wall time does.  The batched searches' own arcs visited are reported as
+detail.  Alongside, the same process times the plain one-source BFSCut (NBCut,
+and DegCut where it finishes in reasonable time) and the learned-seed order on
+the same GPU (vs_plain), and checks every returned top-k against the stored
+oracle result.
 
 Prints ONE JSON line on rank 0.  `--impl reference` times the CPU oracle (the
 sequential BFSCut of oracle/) on a bounded prefix of the same workload.
@@ -155,6 +165,100 @@ def reduce_over_ranks(ms_total, edges, dist, device):
     return float(t.item()), float(e.item())
 
 
+METRIC = "top-k closeness wall time & GTEPS, batched/learned vs plain BFSCut, exact top-k"
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def fixture_for(workload: str, measure: str = "closeness"):
+    """The stored oracle result of a workload (tests/golden/fullsize_*.json), or None."""
+    name = workload + ("_harmonic" if measure == "harmonic" else "")
+    path = os.path.join(GOLDEN, f"fullsize_{name}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
+def fixture_results(fx, k):
+    """Per graph, the stored result for this k (None where k was not stored)."""
+    out = []
+    for g in fx["graphs"]:
+        out.append(next((r for r in g["results"] if r["k"] == k), None))
+    return out
+
+
+def plain_work(fx, k):
+    """Arcs visited by the oracle's plain one-source NBCut over the workload's
+    graphs (the fixed work of the metric), or None."""
+    if fx is None:
+        return None
+    rs = fixture_results(fx, k)
+    if any(r is None for r in rs):
+        return None
+    return sum(int(r["oracle_counters"]["edges_visited"]) for r in rs)
+
+
+def csr_sha256(g) -> str:
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(g.offsets, dtype="<u4").tobytes())
+    h.update(np.ascontiguousarray(g.cols, dtype="<u4").tobytes())
+    return h.hexdigest()
+
+
+def matches_fixture(results, fx, k, graphs, measure="closeness"):
+    """Every graph's top-k (ids, S, r, tie count, farness bits; harmonic: ids,
+    h bits, r, ties) equals the stored oracle result on the same graph."""
+    if fx is None:
+        return None
+    want = fixture_results(fx, k)
+    if len(want) != len(results) or any(w is None for w in want):
+        return False
+    for g, e, res, w in zip(graphs, fx["graphs"], results, want):
+        if csr_sha256(g) != e["csr_sha256"]:
+            return False
+        if [int(x) for x in res.ids] != w["ids"] or [int(x) for x in res.reach] != w["r"]:
+            return False
+        if res.n_tied_at_kth != w["n_tied"]:
+            return False
+        if measure == "harmonic":
+            if [float(h).hex() for h in res.closeness] != w["h_hex"]:
+                return False
+        elif [int(x) for x in res.dist_sum] != w["S"] or [float(f).hex() for f in res.farness] != w["farness_hex"]:
+            return False
+    return True
+
+
+def survey_level_bytes(st) -> float:
+    """Algorithmic bytes of the level kernels by the per-level formula of the
+    design plan (B-bit rows of B/8 bytes):
+      top-down : sum over frontier u of (8 + 4 outdeg(u) + B/8)
+                 + 2 (B/8) sum over frontier u of outdeg(u) + 3 (B/8) n
+      bottom-up: sum over scanned w of (8 + (4 + B/8) scanned_in(w)) + 3 (B/8) n
+    from the run's per-level totals (tkc_last_run_stats)."""
+    rb = st["batch_bits"] / 8.0 if st["batch_bits"] >= 8 else st["row_bytes"]
+    n = st["n"]
+    td = (st["td_frontier"] * (8 + rb) + 4 * st["td_frontier_arcs"] + 2 * rb * st["td_frontier_arcs"]
+          + 3 * rb * n * st["td_levels"])
+    bu = 8 * st["bu_scanned_vertices"] + (4 + rb) * st["bu_scanned_arcs"] + 3 * rb * n * st["bu_levels"]
+    return float(td + bu)
+
+
+def host_cpu():
+    """Core count and model of the host the CPU figures were taken on."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    import platform
+
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "model": model}
+
+
 def cpu_oracle_sample(g, k, sample_sources):
     """Sequential CPU BFSCut (the oracle as it stands) on a prefix of the
     degree order; returns (GTEPS, seconds, edges_visited)."""
@@ -186,13 +290,14 @@ def run_reference(args, rank, world):
         evs.append(ev)
     value = sum(evs) / sum(times) / 1e9
     sample = (f"first {args.ref_sample} sources of the degree order of {g.name} (sequential CPU BFSCut, incl. its "
-              f"preprocessing), per step")
-    line = {"impl": "reference", "metric": "topk_closeness_gteps", "value": value, "unit": "GTEPS",
+              f"preprocessing), per step; rate = arcs the plain one-source BFSCut visits per second")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "k": k},
-            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -206,22 +311,26 @@ def main():
     ap.add_argument("--impl", default="tkc", choices=["tkc", "reference"])
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
     ap.add_argument("--bits", type=int, default=0, help="source batch width (0 = library default)")
-    ap.add_argument("--plain", action="store_true", help="also time plain one-source BFSCut once")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain one-source runs and the learned-seed arm (vs_plain)")
+    ap.add_argument("--plain-degcut", default="auto", choices=["auto", "yes", "no"],
+                    help="also time plain one-source DegCut (auto: on graphs below 2^22 vertices)")
     ap.add_argument("--sample", type=int, default=96, help="CPU oracle sample: number of sources")
     ap.add_argument("--ref-sample", type=int, default=32,
                     help="--impl reference: sources per step (about 4 s of CPU work each on R-MAT 22)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--k", type=int, default=0, help="top-k (0 = the workload's k)")
-    ap.add_argument("--order", default="nb", choices=["degree", "nb", "learned", "learned-seed"],
+    ap.add_argument("--order", default="nb", choices=["degree", "nb", "learned", "learned-seed", "learned-nb"],
                     help="source order: degree bound (DegCut), neighbourhood bound with its stop (NBCut), "
-                         "learned model, or learned seeding prefix + degree")
+                         "learned model, learned seeding prefix + degree, or learned seeding prefix + NBCut")
     ap.add_argument("--nb-levels", type=int, default=0, help="NBCut: most sweeps of the bound (0 = 256)")
     ap.add_argument("--measure", default="closeness", choices=["closeness", "harmonic"],
                     help="rank by closeness (the paper's main measure) or harmonic centrality")
     ap.add_argument("--bound", default="cut", choices=["cut", "lb"],
                     help="updateBounds: BFSCut (cut) or updateBoundsLB (lb: DegBound / NBBound)")
     ap.add_argument("--teams", type=int, default=0, help="teams of SMs (0 = library default)")
+    ap.add_argument("--deterministic", type=int, default=0, help="1: one team, reproducible counters")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "tkc":
         args.warmup = 3
@@ -252,15 +361,21 @@ def main():
                for x in graphs]
     host_csr = [(torch.from_numpy(x.offsets.view(np.int32)).pin_memory(),
                  torch.from_numpy(x.cols.view(np.int32)).pin_memory()) for x in graphs]
-    order = {"degree": tkc.TKC_ORDER_DEG, "nb": tkc.TKC_ORDER_NB, "learned": tkc.TKC_ORDER_LEARNED,
-             "learned-seed": tkc.TKC_ORDER_LEARNED}[args.order]
-    base_opt = dict(device=local, stream=stream.cuda_stream, batch_bits=args.bits, order=order, teams=args.teams,
-                    seed_factor=5 if args.order == "learned-seed" else 0, nb_levels=args.nb_levels)
+    orders = {"degree": tkc.TKC_ORDER_DEG, "nb": tkc.TKC_ORDER_NB, "learned": tkc.TKC_ORDER_LEARNED,
+              "learned-seed": tkc.TKC_ORDER_LEARNED, "learned-nb": tkc.TKC_ORDER_LEARNED_NB}
+    base_opt = dict(device=local, stream=stream.cuda_stream, batch_bits=args.bits, order=orders[args.order],
+                    teams=args.teams, seed_factor=5 if args.order in ("learned-seed", "learned-nb") else 0,
+                    nb_levels=args.nb_levels, deterministic=args.deterministic)
     ctx = tkc.tkc_create(tkc.Options(**base_opt))
-    if args.order.startswith("learned"):
+    weights = None
+    if args.order.startswith("learned") or (not args.no_plain and not multi and args.measure == "closeness"):
         from paper_1704_01077_gb300.train_order import load_weights
 
-        tkc.tkc_set_source_model(ctx, load_weights())
+        weights = load_weights()
+        if weights is not None:
+            tkc.tkc_set_source_model(ctx, weights)
+    fx = fixture_for(args.workload, args.measure) if args.bound == "cut" or args.measure == "closeness" else None
+    work_fixed = plain_work(fx, k)
 
     class Step:
         """One step's results summed over the graphs it ran."""
@@ -300,6 +415,24 @@ def main():
     def step_host():
         return run_step(host_csr)
 
+    def timed_arm(opts, repeats):
+        """Median device time (ms) of `repeats` steps under other options, and the last result."""
+        tkc.tkc_set_options(ctx, tkc.Options(**dict(base_opt, **opts)))
+        try:
+            times, res = [], None
+            for _ in range(repeats):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                res = step_device()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            return statistics.median(times), res
+        finally:
+            tkc.tkc_set_options(ctx, tkc.Options(**base_opt))
+
     for _ in range(args.warmup):
         res = step_device()
     torch.cuda.synchronize()
@@ -309,73 +442,95 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     results = []
+    stats = []
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
             results.append(step_device())
+            stats.append(tkc.tkc_last_run_stats(ctx))
         ev1.record(stream)
         torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     launches = tkc.tkc_kernel_launches() - launches0
-    ms_total, edges = reduce_over_ranks(ev0.elapsed_time(ev1), sum(r.edges_visited for r in results), dist, dev)
-    value = edges / (ms_total / 1e3) / 1e9
+    own_edges = sum(r.edges_visited for r in results)
+    # fixed work per step: the plain one-source NBCut's arcs (oracle-counted);
+    # without a stored oracle result, the batched search's own arcs
+    work = work_fixed if work_fixed is not None else statistics.mean(r.edges_visited for r in results)
+    ms_total, total_work = reduce_over_ranks(ev0.elapsed_time(ev1), work * args.steps, dist, dev)
+    value = total_work / (ms_total / 1e3) / 1e9
     ms_step = ms_total / args.steps
 
     # end to end: host (pinned) CSR in, results out, copies inside the timed region
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
-    e2e_res = [step_host() for _ in range(max(1, min(args.steps, 3)))]
+    e2e_res = [step_host() for _ in range(e2e_steps)]
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = sum(r.edges_visited for r in e2e_res) / e2e_s / 1e9 * world
+    e2e_ms, e2e_work = reduce_over_ranks((time.perf_counter() - t0) * 1e3, work * e2e_steps, dist, dev)
+    e2e_value = e2e_work / (e2e_ms / 1e3) / 1e9
     h2d = sum(4 * (x.n + 1) + 4 * x.arcs for x in graphs)
     d2h = len(graphs) * k * (4 + 8 + 4 + 8 + 8)
 
     # roofline of the dominant kernel (the persistent search kernel)
     peak, peak_src = hbm_peak()
-    kern_ms = statistics.mean(r.ms_kernel for r in results)
-    alg = statistics.mean(r.alg_bytes for r in results)
-    achieved = alg / (kern_ms / 1e3) / 1e9
+    kern_ms = statistics.mean(st["ms_kernel"] for st in stats)
+    kern_bytes = statistics.mean(st["alg_bytes"] for st in stats)
+    plan_bytes = statistics.mean(survey_level_bytes(st) for st in stats)
+    achieved = plan_bytes / (kern_ms / 1e3) / 1e9
+    achieved_k = kern_bytes / (kern_ms / 1e3) / 1e9
     traffic, traffic_entry = (ncu_traffic(args.workload, args.order, res.batch_bits)
                               if args.measure == "closeness" and args.bound == "cut" else (None, None))
+    launches_per_step = stats[-1]["launches"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_src,
-                "alg_bytes_per_launch": alg, "kernel_ms": kern_ms}
+                "bytes_model": "per-level formula of the design plan (top-down: frontier rows, columns and 2 row "
+                               "updates per arc, 3 row sweeps of n; bottom-up: scanned in-arcs and rows, 3 row "
+                               "sweeps of n), from tkc_last_run_stats",
+                "alg_bytes_per_step": plan_bytes, "kernel_ms_per_step": kern_ms,
+                "launches_per_step": launches_per_step,
+                "achieved_kernel_model": achieved_k, "frac_kernel_model": achieved_k / peak,
+                "kernel_model_bytes_per_step": kern_bytes}
+    if traffic is not None:
+        roofline["traffic_frac"] = traffic * launches_per_step / (kern_ms / 1e3) / 1e9 / peak
 
-    line = {"metric": "topk_closeness_gteps", "value": value, "unit": "GTEPS", "n_gpus": world,
+    last = results[-1]
+    st = stats[-1]
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "k": k, "batch_bits": res.batch_bits,
-                       "order": args.order, "measure": args.measure, "bound": args.bound, "teams": args.teams or "library default",
+                       "order": args.order, "measure": args.measure, "bound": args.bound,
+                       "teams": args.teams or "library default", "deterministic": args.deterministic,
+                       "work_per_step": work,
+                       "work_unit": ("arcs visited by plain one-source NBCut (Algorithm 1), counted by the CPU "
+                                     "oracle on the same graph" if work_fixed is not None else
+                                     "arcs visited by this batched search (no stored oracle count)"),
                        "l2": "inputs larger than L2 (CSR 280 MB + bit rows)" if args.workload in
                        ("rmat22", "multi512", "ba1m") else "small graph: may be L2-resident",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
+            "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms / e2e_steps},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary(),
-            "detail": {"edges_visited": results[-1].edges_visited, "edges_scanned": results[-1].edges_scanned,
-                       "bfs_started": results[-1].bfs_started, "bfs_cut": results[-1].bfs_cut,
-                       "bfs_finished": results[-1].bfs_finished, "levels": results[-1].levels,
-                       "ms_pre": results[-1].ms_pre, "ms_bfs": results[-1].ms_bfs,
-                       "ms_kernel": results[-1].ms_kernel,
+            "detail": {"wall_ms_per_step": ms_step,
+                       "edges_visited": last.edges_visited, "edges_scanned": last.edges_scanned,
+                       "own_gteps": own_edges / (ms_total / 1e3) / 1e9 if world == 1 else None,
+                       "bfs_started": last.bfs_started, "bfs_cut": last.bfs_cut,
+                       "bfs_finished": last.bfs_finished, "levels": last.levels,
+                       "ms_pre": last.ms_pre, "ms_bfs": last.ms_bfs, "ms_kernel": last.ms_kernel,
+                       "level_stats": st,
                        "textbook_teps_equiv": sum(x.arcs * x.n for x in graphs) / (ms_step / 1e3) / 1e9,
                        "graphs": len(graphs), "vertices": sum(x.n for x in graphs),
                        "arcs": sum(x.arcs for x in graphs),
-                       "top_ids": [int(x) for x in results[-1].ids]}}
-    if rank == 0 and args.plain and not multi:
-        tkc.tkc_set_options(ctx, tkc.Options(**dict(base_opt, batch_bits=1, teams=1)))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pr = step_device()
-        torch.cuda.synchronize()
-        plain_s = time.perf_counter() - t0
-        assert list(pr.ids) == list(results[-1].ids)
-        line["vs_plain"] = {"plain_ms": plain_s * 1e3, "batched_ms": ms_step, "speedup": plain_s * 1e3 / ms_step,
-                            "plain_edges_visited": pr.edges_visited}
+                       "top_ids": [int(x) for x in last.ids]}}
     if rank == 0 and not args.no_check:
         import oracle
 
         ok = True
-        for x, top in zip(graphs, results[-1].results):
+        for x, top in zip(graphs, last.results):
             if args.measure == "harmonic":
                 H, r = oracle.harmonic_sums(x, top.ids)
                 ok &= bool(H.tobytes() == top.closeness.tobytes() and np.array_equal(r, top.reach))
@@ -384,11 +539,51 @@ def main():
                 ok &= bool(np.array_equal(S, top.dist_sum) and np.array_equal(r, top.reach))
         key = "top_k_h_r_match_oracle_bfs" if args.measure == "harmonic" else "top_k_S_r_match_oracle_bfs"
         line["check"] = {key: ok}
+        if args.bound == "cut" or args.measure == "closeness":
+            line["check"]["top_k_matches_oracle_fixture"] = matches_fixture(last.results, fx, k, graphs,
+                                                                            args.measure)
+    if rank == 0 and not args.no_plain and not multi and args.measure == "closeness" and args.bound == "cut":
+        arms = {}
+
+        def arm(name, opts, repeats):
+            ms, r = timed_arm(opts, repeats)
+            arms[name] = {"ms": ms, "edges_visited": r.edges_visited, "bfs_started": r.bfs_started,
+                          "bfs_cut": r.bfs_cut, "batch_bits": r.batch_bits,
+                          "matches_oracle_fixture": matches_fixture(r.results, fx, k, graphs)}
+            return ms
+
+        plain_nb = arm("plain_nbcut", dict(order=tkc.TKC_ORDER_NB, batch_bits=1, seed_factor=0), 1)
+        do_deg = args.plain_degcut == "yes" or (args.plain_degcut == "auto" and g.n < (1 << 22))
+        plain_deg = arm("plain_degcut", dict(order=tkc.TKC_ORDER_DEG, batch_bits=1, seed_factor=0), 1) \
+            if do_deg else None
+        arm("batched_degcut", dict(order=tkc.TKC_ORDER_DEG, batch_bits=0, seed_factor=0), 3)
+        arms["batched_nbcut"] = {"ms": ms_step, "edges_visited": last.edges_visited, "bfs_started": last.bfs_started,
+                                 "bfs_cut": last.bfs_cut, "batch_bits": last.batch_bits,
+                                 "matches_oracle_fixture": line.get("check", {}).get("top_k_matches_oracle_fixture")}
+        if weights is not None:
+            arm("batched_learned_seed_nbcut", dict(order=tkc.TKC_ORDER_LEARNED_NB, batch_bits=0, seed_factor=5), 3)
+        vp = {"arms": arms, "plain_ms": plain_nb, "batched_ms": ms_step, "speedup": plain_nb / ms_step,
+              "plain": "one source per search (B = 1), one team, NBCut order and stop, same GPU",
+              "target": 5.0}
+        if plain_deg is not None:
+            vp["speedup_vs_plain_degcut"] = plain_deg / ms_step
+        if "batched_learned_seed_nbcut" in arms:
+            lm = arms["batched_learned_seed_nbcut"]["ms"]
+            vp["learned_seed_speedup_vs_plain"] = plain_nb / lm
+            vp["learned_seed_vs_nbcut_time_ratio"] = lm / ms_step
+        line["vs_plain"] = vp
     if rank == 0 and not args.no_cpu and not multi:
         v, dt, ev = cpu_oracle_sample(g, k, args.sample)
-        line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "host": host_cpu(),
                                 "sample": f"first {args.sample} sources of the degree order, sequential CPU "
-                                          f"BFSCut incl. its preprocessing ({dt:.1f} s, {ev} edges)"}
+                                          f"BFSCut incl. its preprocessing ({dt:.1f} s, {ev} edges); rate = arcs "
+                                          f"of the plain one-source BFSCut per second"}
+        if fx is not None:
+            secs = sum(r["seconds"] for r in fixture_results(fx, k) if r)
+            line["cpu_baseline"]["full_run"] = {
+                "seconds": secs, "host": fx.get("host"),
+                "what": "the oracle's complete plain NBCut on this workload, when the stored result was written "
+                        "(another host: context only)"}
     tkc.tkc_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -55,6 +55,10 @@ extern "C" {
 #define TKC_ORDER_NB 3      /* computeBoundsNB (NBCut): sources by increasing neighbourhood-based farness
                                bound (tkc_nb_bounds), ties by id; the search stops at the first source
                                whose bound exceeds the k-th farness found (Algorithm 1's stop) */
+#define TKC_ORDER_LEARNED_NB 4 /* the seed_factor * k sources the source-order model predicts closest first
+                               (searched without cutting), then the TKC_ORDER_NB order without them, with
+                               its stop (the rest of that order is still sorted by its bound); one graph,
+                               closeness only */
 
 #define TKC_MAX_K 1024      /* largest k accepted by tkc_topk_closeness */
 
@@ -66,7 +70,8 @@ typedef struct {
   void *stream;            /* cudaStream_t to run on (e.g. torch's current stream); NULL = legacy default */
   uint32_t order;          /* TKC_ORDER_* */
   uint32_t batch_bits;     /* sources searched together: 1 (plain, one source per BFS), 64, 128, 256, 512;
-                              0 = autotuned choice */
+                              0 = the autotuner's choice for this graph class when tkc_autotune
+                              has cached one, else the library default (64 or 128 by size) */
   uint32_t bu_num;         /* direction switch: a level runs bottom-up when frontier arcs * bu_num >
                               arcs * bu_den (bu_num = 0: library default, 8/1) */
   uint32_t bu_den;
@@ -85,7 +90,14 @@ typedef struct {
                               threads for 64-bit batches, 768 for 128-bit -- for batched searches on graphs of
                               2^20 vertices or more, else 512), 1 = always the larger blocks, 2 = always 512;
                               wider batches always use 512.  Results never depend on it. */
-  uint32_t pad;
+  uint32_t deterministic;  /* 1: one team of SMs whatever `teams` says, so the threshold x changes only at
+                              level barriers and the top-k merges happen in a fixed order; every counter
+                              (edges_visited, bfs_started, bfs_cut, bfs_finished, levels) is then a function
+                              of the graph, k, the order and batch_bits alone (the batched schedule of
+                              Algorithm 1 with Algorithm 4: B searches advance one level per step, finished
+                              searches enter the top list before the survivors' cut test).  0: teams run side
+                              by side and cut against a threshold another team may be updating, so counters
+                              vary from run to run (results never do). */
 } tkc_options;
 
 typedef struct {
@@ -277,11 +289,11 @@ int tkc_nb_harmonic_bounds(tkc_graph *g, uint32_t max_levels, double *h_ub, uint
 int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_t *S, uint32_t *r);
 
 /* Allocation-free variant of tkc_distance_sums, for callers that cannot
- * allocate device memory when they need the result: code running inside CUDA
- * stream capture (cudaMalloc is not permitted there), runtimes that reserve a
- * fixed device-memory budget at start-up, and latency-critical services that
- * cannot take the synchronisation an allocation may cause.  The paper has no
- * counterpart; it exists for those callers only.
+ * allocate device memory when they need the result: runtimes that reserve a
+ * fixed device-memory budget at start-up (a later allocation would exceed it),
+ * and latency-critical services that cannot take the device-wide
+ * synchronisation an allocation may cause.  The paper has no counterpart; it
+ * exists for those callers only.
  *
  * Computes exact S(v) and r(v) of nsrc distinct sources by full BFS (no
  * cutting), 64 sources at a time, on the CURRENT device and `stream`
@@ -291,8 +303,8 @@ int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_
  * allocates nothing: its scratch is one fixed array of about 5.5 MB compiled
  * into the library, which every device that loads the library holds until
  * the process exits.
- *  - The first call on a device looks up that array's device address; make
- *    that first call before any stream capture starts.
+ *  - Each call looks up that array's device address on the current device
+ *    (the lookup allocates nothing).
  *  - Every call on a device shares the array and clears what it needs; calls
  *    whose GPU work overlaps race on it, so serialise them.
  *  - The call returns after the results are written (it synchronises `stream`).
@@ -303,6 +315,42 @@ int tkc_distance_sums(tkc_graph *g, uint32_t nsrc, const uint32_t *srcs, uint64_
 #define TKC_NOALLOC_MAX_N 65536
 int tkc_distance_sums_noalloc(const uint32_t *offsets, const uint32_t *cols, uint32_t n, uint64_t arcs,
                               uint32_t nsrc, const uint32_t *srcs, uint64_t *S, uint32_t *r, void *stream);
+
+/* Per-level totals of the latest run of the persistent search kernel on a
+ * context (no paper counterpart: measurement only).  They are the inputs of
+ * the level kernels' byte counts: a top-down level reads each frontier
+ * vertex's row and offsets and each frontier arc's column and target row; a
+ * bottom-up level reads every vertex's seen row, and the in-arc columns and
+ * frontier rows of the vertices it scans.  Counters add up over the run's
+ * teams and launches. */
+typedef struct {
+  uint32_t n;                   /* vertices of the graph (or of the union of several) */
+  uint32_t batch_bits;          /* B, sources per batch */
+  uint32_t row_bytes;           /* bytes of one bit row (8 * ceil(B / 64)) */
+  uint32_t teams;               /* teams of the main launch */
+  uint32_t launches;            /* launches of the search kernel (an opening batch adds one) */
+  uint32_t pad;
+  uint64_t arcs;
+  uint64_t td_levels;           /* top-down level steps */
+  uint64_t td_frontier;         /* frontier vertices expanded top-down (sum over those levels) */
+  uint64_t td_frontier_arcs;    /* their out-arcs */
+  uint64_t td_new;              /* vertices discovered by top-down levels */
+  uint64_t bu_levels;           /* bottom-up level steps */
+  uint64_t bu_scanned_vertices; /* vertices whose in-arcs a bottom-up level walked */
+  uint64_t bu_scanned_arcs;     /* in-arcs walked (up to each early exit) */
+  uint64_t bu_new;              /* vertices discovered by bottom-up levels */
+  uint64_t bu_frontier;         /* frontier vertices of the bottom-up levels (their rows are cleared) */
+  uint64_t seeded;              /* searches started in a slot */
+  uint64_t cleared;             /* rows zeroed by the clear steps between batches */
+  uint64_t compactions;         /* frontier lists compacted to the searches still active after a cut */
+  uint64_t compacted_away;      /* list entries those compactions dropped (their rows zeroed) */
+  uint64_t alg_bytes;           /* the search kernel's byte count (tkc_result.alg_bytes of that run) */
+  double ms_kernel;             /* device time of the search kernel's launches */
+} tkc_run_stats;
+
+/* Copies the statistics of ctx's latest search-kernel run into *out (all
+ * zero before the first run).  Errors: TKC_EINVAL (null argument). */
+int tkc_last_run_stats(const tkc_ctx *ctx, tkc_run_stats *out);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * contexts), for accounting of device work (no paper counterpart; never

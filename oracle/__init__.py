@@ -15,6 +15,8 @@ Functions and what pins them (see ``tests/test_oracle.py``):
   tree_sums       Algorithm 2                    BFS on random trees
   cut_bounds      Sec. 6 lemma / level           invariants: <= S, non-decreasing, ends at S
   bfscut          Algorithm 1 + Algorithm 4      textbook top-k on thousands of graphs
+  bfscut_batched  the same, B searches per step  equals bfscut at B = 1 (all counters), textbook
+                                                 top-k at every B, hand-counted star at B = 2
   nb_bounds       Algorithm 3, Eq. 3, Eq. 6      brute-force walk counts, exact on trees and
                                                  cycles, hand-computed hypercube, <= S/(r-1)^2,
                                                  minimum over every r in [alpha, omega]
@@ -54,6 +56,11 @@ class Counters(ctypes.Structure):
                 ("bfs_cut", ctypes.c_uint64), ("bfs_finished", ctypes.c_uint64)]
 
 
+class BCounters(ctypes.Structure):
+    _fields_ = [("edges_visited", ctypes.c_uint64), ("bfs_started", ctypes.c_uint64),
+                ("bfs_cut", ctypes.c_uint64), ("bfs_finished", ctypes.c_uint64), ("levels", ctypes.c_uint64)]
+
+
 _lib = None
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -82,6 +89,9 @@ def _bind(lib):
     lib.orc_bfscut.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p, _u32p,
                                _u64p, _u32p, _u32p, ctypes.POINTER(Counters), _u64p, _u32p, ctypes.c_uint32,
                                _u64p]
+    lib.orc_bfscut_batched.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, ctypes.c_uint32, _u32p,
+                                       ctypes.c_uint32, _u64p, ctypes.c_uint32, _u32p, _u64p, _u32p, _u32p,
+                                       ctypes.POINTER(BCounters), _u64p, _u32p]
     lib.orc_nb_bounds.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_int, _u32p, _u32p, ctypes.c_uint32,
                                   _u64p, _u32p, _u64p, _u64p, ctypes.c_uint32, _dp]
     lib.orc_harmonic_sums.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint32, _u32p, _dp, _u32p,
@@ -117,6 +127,25 @@ def _csr(g):
     if col.size == 0:
         col = np.zeros(1, np.uint32)
     return off, col
+
+
+def _full_order(g, order):
+    """A caller's source order as the C side reads it: exactly n vertex ids."""
+    if order is None:
+        return None
+    a = np.ascontiguousarray(order, dtype=np.uint32)
+    if a.shape != (g.n,):
+        raise ValueError(f"order must list all {g.n} vertices (got {a.size}); see nb_full_order")
+    return a
+
+
+def _per_vertex(g, x, dtype):
+    if x is None:
+        return None
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if a.shape != (g.n,):
+        raise ValueError(f"expected one value per vertex ({g.n}), got {a.size}")
+    return a
 
 
 def _check(rc):
@@ -236,14 +265,37 @@ def bfscut(g, k, order=None, want_all=False, max_sources=0, lb_key=None) -> TopK
     r = np.zeros(max(kk, 1), np.uint32)
     tied = ctypes.c_uint32(0)
     ctr = Counters()
-    order_a = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
+    order_a = _full_order(g, order)
     allS = np.zeros(max(g.n, 1), np.uint64) if want_all else None
     allr = np.zeros(max(g.n, 1), np.uint32) if want_all else None
-    key_a = None if lb_key is None else np.ascontiguousarray(lb_key, dtype=np.uint64)
+    key_a = _per_vertex(g, lb_key, np.uint64)
     cnt = _check(_load().orc_bfscut(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), k,
                                     _p(order_a, _u32p), _p(ids, _u32p), _p(S, _u64p), _p(r, _u32p),
                                     ctypes.byref(tied), ctypes.byref(ctr), _p(allS, _u64p), _p(allr, _u32p),
                                     max_sources, _p(key_a, _u64p)))
+    return TopK(ids[:cnt], S[:cnt], r[:cnt], int(tied.value), ctr,
+                None if allS is None else allS[: g.n], None if allr is None else allr[: g.n])
+
+
+def bfscut_batched(g, k, B, order=None, lb_key=None, nocut_prefix=0, want_all=False) -> TopK:
+    """Algorithm 1 + BFSCut with B searches advancing one level per step and
+    the threshold refreshed between steps (the batched schedule; B = 1 is
+    `bfscut`).  Counters are BCounters (with `levels`, the number of steps)."""
+    off, col = _csr(g)
+    kk = min(k, g.n)
+    ids = np.zeros(max(kk, 1), np.uint32)
+    S = np.zeros(max(kk, 1), np.uint64)
+    r = np.zeros(max(kk, 1), np.uint32)
+    tied = ctypes.c_uint32(0)
+    ctr = BCounters()
+    order_a = _full_order(g, order)
+    key_a = _per_vertex(g, lb_key, np.uint64)
+    allS = np.zeros(max(g.n, 1), np.uint64) if want_all else None
+    allr = np.zeros(max(g.n, 1), np.uint32) if want_all else None
+    cnt = _check(_load().orc_bfscut_batched(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), k,
+                                            _p(order_a, _u32p), B, _p(key_a, _u64p), nocut_prefix, _p(ids, _u32p),
+                                            _p(S, _u64p), _p(r, _u32p), ctypes.byref(tied), ctypes.byref(ctr),
+                                            _p(allS, _u64p), _p(allr, _u32p)))
     return TopK(ids[:cnt], S[:cnt], r[:cnt], int(tied.value), ctr,
                 None if allS is None else allS[: g.n], None if allr is None else allr[: g.n])
 
@@ -299,6 +351,12 @@ def nb_order(g, key):
     return ids[np.lexsort((ids, key))]
 
 
+def nb_full_order(g, key):
+    """nb_order followed by the vertices of out-degree 0 (never searched): a
+    permutation of all n vertices, as bfscut's `order` must be."""
+    return np.concatenate([nb_order(g, key), np.nonzero(g.outdeg() == 0)[0].astype(np.uint32)])
+
+
 # ---------------------------------------------------------------- harmonic centrality
 
 def harmonic_sums(g, sources=None, threads: int = 0):
@@ -349,7 +407,7 @@ def bfscut_harmonic(g, k, order=None, ub=None, want_all=False, max_sources=0) ->
     r = np.zeros(max(kk, 1), np.uint32)
     tied = ctypes.c_uint32(0)
     ctr = Counters()
-    order_a = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
+    order_a = _full_order(g, order)
     ub_a = None if ub is None else np.ascontiguousarray(ub, dtype=np.float64)
     allH = np.zeros(max(g.n, 1), np.float64) if want_all else None
     allr = np.zeros(max(g.n, 1), np.uint32) if want_all else None
@@ -403,7 +461,7 @@ def bfsbound(g, k, order=None, nb=None, max_sources=0) -> TopK:
     r = np.zeros(max(kk, 1), np.uint32)
     tied = ctypes.c_uint32(0)
     ctr = Counters()
-    order_a = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
+    order_a = _full_order(g, order)
     iS = None if nb is None else np.ascontiguousarray(nb.S, dtype=np.uint64)
     ir = None if nb is None else np.ascontiguousarray(nb.r, dtype=np.uint32)
     cnt = _check(_load().orc_bfsbound(g.n, _p(off, _u32p), _p(col, _u32p), int(g.directed), k, _p(order_a, _u32p),

@@ -903,6 +903,233 @@ done:
 }
 
 /* ---------------------------------------------------------------------- */
+/* Algorithm 1 with updateBoundsBFSCut, B sources per batch (the schedule   */
+/* the GPU runs with options.deterministic), level-synchronous              */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+  uint64_t edges_visited; /* arcs of every expanded level (the paper's m_vis) */
+  uint64_t bfs_started;
+  uint64_t bfs_cut;
+  uint64_t bfs_finished;
+  uint64_t levels;        /* level steps: one per BFS level of a batch, all its searches together */
+} orc_bcounters;
+
+/*
+ * The same method as orc_bfscut (Algorithm 1, Algorithm 4 evaluated once per
+ * level, Section 8's reach bounds), but up to B searches advance together,
+ * one BFS level per step, and the threshold x changes only between steps.
+ * This is the schedule of the batched GPU search with one team; the oracle
+ * states it as plainly as it can so that arcs visited under batching have an
+ * independent count.
+ *
+ *  1. Seeding a batch.  Q is the order restricted to vertices of out-degree
+ *     >= 1.  Sources are taken from Q in order while the batch has free slots.
+ *     With x known (k searches finished), a source at position >= nocut_prefix
+ *     is first checked against Algorithm 1's stop (lb_key, NBCut: key above x
+ *     ends the whole search, nothing later in Q is examined) and then against
+ *     the level-0 bound of Algorithm 4 (cut before any arc is read).  A source
+ *     that passes occupies a slot; its level-0 arcs (its out-degree) count as
+ *     visited.  Q is read in chunks of the batch's free slots; a source cut at
+ *     level 0 frees its place for the next chunk, so a batch is full unless Q
+ *     runs out.
+ *  2. One step.  Every active search expands its newest level (arcs already
+ *     counted).  Then, in slot order: a search that found nothing new is
+ *     finished (exact S, r); the others add the new level to S_d, n_d and set
+ *     gamma~ (sum of out-degrees of the new level, minus its size if
+ *     undirected).  All searches finished in this step enter the top list
+ *     together, x becomes the new k-th entry, and only then is each
+ *     continuing search tested against x (Section 6 lemma, r in
+ *     [max(alpha, n_d), omega]); a search that survives counts the arcs of its
+ *     new level as visited.
+ *  3. When no search of the batch is active, the next batch is seeded.  The
+ *     run ends when a seeding finds no source.
+ * Positions below nocut_prefix are never cut nor stopped (they seed x with
+ * exact values).  With B = 1 this is exactly orc_bfscut.  Outputs as
+ * orc_bfscut; counters include the number of steps.
+ */
+int orc_bfscut_batched(uint32_t n, const uint32_t *off, const uint32_t *col, int directed, uint32_t k,
+                       const uint32_t *order_in, uint32_t B, const uint64_t *lb_key, uint32_t nocut_prefix,
+                       uint32_t *ids, uint64_t *S_out, uint32_t *r_out, uint32_t *n_tied, orc_bcounters *ctr,
+                       uint64_t *allS, uint32_t *allr) {
+  if (k == 0 || n == 0) { if (n_tied) *n_tied = 0; return 0; }
+  if (B == 0) return ORC_EINVAL;
+  int rc = ORC_OK;
+  uint32_t kk = k < n ? k : n;
+  uint32_t *order = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *Q = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *alpha = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint32_t *omega = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+  uint64_t *fS = (uint64_t *)calloc(n, sizeof(uint64_t));
+  uint32_t *fr = (uint32_t *)calloc(n, sizeof(uint32_t));
+  entry_t *top = (entry_t *)malloc((size_t)kk * sizeof(entry_t));
+  /* per slot: its own BFS (distance array, queue, level bounds) */
+  uint32_t *dist = (uint32_t *)malloc((size_t)B * n * sizeof(uint32_t));
+  uint32_t *queue = (uint32_t *)malloc((size_t)B * n * sizeof(uint32_t));
+  uint32_t *head = (uint32_t *)calloc(B, sizeof(uint32_t));
+  uint32_t *tail = (uint32_t *)calloc(B, sizeof(uint32_t));
+  uint32_t *src = (uint32_t *)calloc(B, sizeof(uint32_t));
+  uint32_t *depth = (uint32_t *)calloc(B, sizeof(uint32_t));
+  uint32_t *nocut = (uint32_t *)calloc(B, sizeof(uint32_t));
+  int *active = (int *)calloc(B, sizeof(int));
+  uint64_t *Sd = (uint64_t *)calloc(B, sizeof(uint64_t));
+  uint64_t *nd = (uint64_t *)calloc(B, sizeof(uint64_t));
+  uint64_t *gam = (uint64_t *)calloc(B, sizeof(uint64_t));
+  uint64_t *arcs = (uint64_t *)calloc(B, sizeof(uint64_t));
+  uint64_t *cnt = (uint64_t *)calloc(B, sizeof(uint64_t));
+  uint64_t *gs = (uint64_t *)calloc(B, sizeof(uint64_t));
+  if (!order || !Q || !alpha || !omega || !fS || !fr || !top || !dist || !queue || !head || !tail || !src ||
+      !depth || !nocut || !active || !Sd || !nd || !gam || !arcs || !cnt || !gs) {
+    rc = ORC_ENOMEM;
+    goto done;
+  }
+  if (order_in)
+    memcpy(order, order_in, (size_t)n * sizeof(uint32_t));
+  else if ((rc = orc_degree_order(n, off, order)) != ORC_OK)
+    goto done;
+  if ((rc = orc_alpha_omega(n, off, col, directed, alpha, omega)) != ORC_OK) goto done;
+  uint32_t nq = 0;
+  for (uint32_t i = 0; i < n; ++i)
+    if (off[order[i] + 1] > off[order[i]]) Q[nq++] = order[i]; /* r = 1 vertices are never searched */
+  for (size_t i = 0; i < (size_t)B * n; ++i) dist[i] = UINT32_MAX;
+  orc_bcounters c = {0, 0, 0, 0, 0};
+  uint32_t ntop = 0, cursor = 0;
+  int stopped = 0;
+  while (1) {
+    /* 1. seed a batch */
+    uint32_t assigned = 0;
+    while (assigned < B && cursor < nq && !stopped) {
+      uint32_t room = B - assigned;
+      uint32_t end = cursor + room < nq ? cursor + room : nq;
+      int have_x = ntop == kk;
+      uint64_t Sx = have_x ? top[kk - 1].S : 0;
+      uint32_t rx = have_x ? top[kk - 1].r : 0;
+      for (uint32_t pos = cursor; pos < end && !stopped; ++pos) {
+        uint32_t v = Q[pos];
+        uint64_t od = off[v + 1] - off[v];
+        int protect = pos < nocut_prefix;
+        if (!protect && lb_key && have_x) {
+          u128 lhs = (u128)lb_key[v] * (u128)((uint64_t)(rx - 1) * (uint64_t)(rx - 1));
+          if (lhs > ((u128)Sx << ORC_NB_FRAC)) { stopped = 1; break; }
+        }
+        c.bfs_started++;
+        if (!protect && cut_exceeds(0, 0, 1, od, alpha[v], omega[v], have_x, Sx, rx)) {
+          c.bfs_cut++;
+          continue;
+        }
+        uint32_t s = assigned++;
+        uint32_t *ds = dist + (size_t)s * n, *qs = queue + (size_t)s * n;
+        src[s] = v;
+        nocut[s] = (uint32_t)protect;
+        head[s] = 0;
+        tail[s] = 0;
+        ds[v] = 0;
+        qs[tail[s]++] = v;
+        depth[s] = 0;
+        Sd[s] = 0;
+        nd[s] = 1;
+        gam[s] = od;
+        arcs[s] = od;
+        active[s] = 1;
+        c.edges_visited += od;
+      }
+      cursor = end;
+    }
+    if (assigned == 0) break;
+    /* 2. level steps until every search of the batch has ended */
+    int any = 1;
+    while (any) {
+      c.levels++;
+      for (uint32_t s = 0; s < assigned; ++s) {
+        if (!active[s]) continue;
+        uint32_t *ds = dist + (size_t)s * n, *qs = queue + (size_t)s * n;
+        uint32_t level_end = tail[s];
+        cnt[s] = 0;
+        gs[s] = 0;
+        while (head[s] < level_end) {
+          uint32_t u = qs[head[s]++];
+          for (uint32_t e = off[u]; e < off[u + 1]; ++e) {
+            uint32_t w = col[e];
+            if (ds[w] == UINT32_MAX) {
+              ds[w] = depth[s] + 1;
+              qs[tail[s]++] = w;
+              cnt[s]++;
+              gs[s] += (off[w + 1] - off[w]) - (directed ? 0u : 1u);
+            }
+          }
+        }
+      }
+      /* searches that found nothing new are finished; the others advance */
+      for (uint32_t s = 0; s < assigned; ++s) {
+        if (!active[s]) continue;
+        if (cnt[s] == 0) {
+          active[s] = 0;
+          c.bfs_finished++;
+          fS[src[s]] = Sd[s];
+          fr[src[s]] = (uint32_t)nd[s];
+          top_insert(top, &ntop, kk, Sd[s], (uint32_t)nd[s], src[s]);
+        } else {
+          depth[s] += 1;
+          Sd[s] += (uint64_t)depth[s] * cnt[s];
+          nd[s] += cnt[s];
+          gam[s] = gs[s];
+          arcs[s] = gs[s] + (directed ? 0u : cnt[s]); /* out-degree sum of the new level */
+        }
+      }
+      /* x after this step's merges; then the cut test of the survivors */
+      int have_x = ntop == kk;
+      uint64_t Sx = have_x ? top[kk - 1].S : 0;
+      uint32_t rx = have_x ? top[kk - 1].r : 0;
+      any = 0;
+      for (uint32_t s = 0; s < assigned; ++s) {
+        if (!active[s]) continue;
+        uint32_t v = src[s];
+        if (!nocut[s] && cut_exceeds(Sd[s], depth[s], nd[s], gam[s], alpha[v], omega[v], have_x, Sx, rx)) {
+          active[s] = 0;
+          c.bfs_cut++;
+          continue;
+        }
+        c.edges_visited += arcs[s];
+        any = 1;
+      }
+    }
+    /* 3. restore the batch's distance arrays */
+    for (uint32_t s = 0; s < assigned; ++s) {
+      uint32_t *ds = dist + (size_t)s * n, *qs = queue + (size_t)s * n;
+      for (uint32_t i = 0; i < tail[s]; ++i) ds[qs[i]] = UINT32_MAX;
+    }
+  }
+  for (uint32_t v = 0; v < n && ntop < kk; ++v)
+    if (off[v + 1] == off[v]) top_insert(top, &ntop, kk, 0, 1, v);
+  for (uint32_t i = 0; i < kk; ++i) {
+    ids[i] = top[i].id;
+    if (S_out) S_out[i] = top[i].S;
+    if (r_out) r_out[i] = top[i].r;
+  }
+  if (n_tied) {
+    uint32_t t = 0;
+    const entry_t *last = &top[kk - 1];
+    for (uint32_t v = 0; v < n; ++v) {
+      if (off[v + 1] == off[v]) {
+        if (last->r <= 1) ++t;
+      } else if (fr[v] && cmp_farness(fS[v], fr[v], last->S, last->r) == 0) {
+        ++t;
+      }
+    }
+    *n_tied = t;
+  }
+  if (allS) memcpy(allS, fS, (size_t)n * sizeof(uint64_t));
+  if (allr) memcpy(allr, fr, (size_t)n * sizeof(uint32_t));
+  if (ctr) *ctr = c;
+  rc = (int)kk;
+done:
+  free(order); free(Q); free(alpha); free(omega); free(fS); free(fr); free(top); free(dist); free(queue);
+  free(head); free(tail); free(src); free(depth); free(nocut); free(active); free(Sd); free(nd); free(gam);
+  free(arcs); free(cnt); free(gs);
+  return rc;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Harmonic centrality (Section 9, "Harmonic Centrality"): the same method  */
 /* for h(v) = sum over w != v of 1/d(v,w), largest first                    */
 /* ---------------------------------------------------------------------- */

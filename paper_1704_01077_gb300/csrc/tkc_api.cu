@@ -283,6 +283,9 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   const bool nb_one = rs.lb_key != nullptr && rs.ng == 1;
   u32 T = rs.B <= 1 ? 1u : (o.teams ? o.teams : default_teams(g->n, rs.B, (u32)maxb, nb_one));
   if (rs.force_teams) T = rs.force_teams;
+  // deterministic schedule: one team, so x moves only at its level barriers
+  // (updateBoundsLB rounds fix their own team count: no cuts, already exact)
+  if (o.deterministic && !rs.force_teams) T = 1;
   T = std::max<u32>(1, std::min<u32>(T, (u32)maxb));
   TKC_RC(ensure_workspace(ctx, g->n, rs.W, rs.kk * rs.ng, rs.ng, T));
   if (w.level_base > 0xF0000000u) {
@@ -307,8 +310,10 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.col = g->col;
   p.ioff = g->ioff;
   p.icol = g->icol;
-  TKC_RC(ensure_bu_chunks(g));
-  p.bu_chunks = g->bu_chunks;
+  TKC_RC(ensure_bu_list(g));
+  p.bu_list = g->bu_list;
+  p.n_bu = g->n_bu;
+  p.n_bu_heavy = g->n_bu_heavy;
   p.large_blocks = o.large_blocks;
   p.alpha = g->alpha;
   p.omega = g->omega;
@@ -423,6 +428,19 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
       hctl->levels += x.levels;
       hctl->batches += x.batches;
       hctl->alg_bytes += x.alg_bytes;
+      hctl->st_td_levels += x.st_td_levels;
+      hctl->st_td_frontier += x.st_td_frontier;
+      hctl->st_td_arcs += x.st_td_arcs;
+      hctl->st_td_new += x.st_td_new;
+      hctl->st_bu_levels += x.st_bu_levels;
+      hctl->st_bu_scan_v += x.st_bu_scan_v;
+      hctl->st_bu_scan_a += x.st_bu_scan_a;
+      hctl->st_bu_new += x.st_bu_new;
+      hctl->st_bu_frontier += x.st_bu_frontier;
+      hctl->st_seeded += x.st_seeded;
+      hctl->st_cleared += x.st_cleared;
+      hctl->st_compactions += x.st_compactions;
+      hctl->st_compact_dropped += x.st_compact_dropped;
       hctl->trace_n += x.trace_n;
       hctl->level_id = std::max(hctl->level_id, x.level_id);
       if (!hctl->err) hctl->err = x.err;
@@ -454,6 +472,33 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   }
   TKC_TRY(cudaEventRecord(ctx->ev[5], st));
   if (p.trace) TKC_TRY(cudaFree(p.trace));
+  {
+    tkc_run_stats &rs_out = ctx->last_stats;
+    rs_out.n = g->n;
+    rs_out.arcs = g->arcs;
+    rs_out.batch_bits = rs.B;
+    rs_out.row_bytes = 8u * (u32)rs.W;
+    rs_out.teams = T;
+    rs_out.launches = (u32)phases.size();
+    rs_out.td_levels = hctl->st_td_levels;
+    rs_out.td_frontier = hctl->st_td_frontier;
+    rs_out.td_frontier_arcs = hctl->st_td_arcs;
+    rs_out.td_new = hctl->st_td_new;
+    rs_out.bu_levels = hctl->st_bu_levels;
+    rs_out.bu_scanned_vertices = hctl->st_bu_scan_v;
+    rs_out.bu_scanned_arcs = hctl->st_bu_scan_a;
+    rs_out.bu_new = hctl->st_bu_new;
+    rs_out.bu_frontier = hctl->st_bu_frontier;
+    rs_out.seeded = hctl->st_seeded;
+    rs_out.cleared = hctl->st_cleared;
+    rs_out.compactions = hctl->st_compactions;
+    rs_out.compacted_away = hctl->st_compact_dropped;
+    rs_out.alg_bytes = hctl->alg_bytes;
+    float kms = 0;
+    TKC_TRY(cudaEventSynchronize(ctx->ev[5]));
+    cudaEventElapsedTime(&kms, ctx->ev[4], ctx->ev[5]);
+    rs_out.ms_kernel = kms;
+  }
   if (hctl->err) {
     TKC_RC(reset_rows(ctx));
     TKC_TRY(cudaStreamSynchronize(st));
@@ -550,6 +595,12 @@ extern "C" {
 
 uint64_t tkc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int tkc_last_run_stats(const tkc_ctx *ctx, tkc_run_stats *out) {
+  if (!ctx || !out) return TKC_EINVAL;
+  *out = ctx->last_stats;
+  return TKC_OK;
+}
+
 const char *tkc_strerror(int code) {
   switch (code) {
     case TKC_OK: return "ok";
@@ -568,7 +619,7 @@ static void tune_cache_load(tkc_ctx *ctx);
 static bool options_valid(const tkc_options *opt) {
   const u32 b = opt->batch_bits;
   if (!(b == 0 || b == 1 || b == 64 || b == 128 || b == 256 || b == 512)) return false;
-  return opt->order <= TKC_ORDER_NB && opt->nb_levels <= 65535 && opt->large_blocks <= 2;
+  return opt->order <= TKC_ORDER_LEARNED_NB && opt->nb_levels <= 65535 && opt->large_blocks <= 2 && opt->deterministic <= 1;
 }
 
 int tkc_create(tkc_ctx **out, const tkc_options *opt) {
@@ -688,7 +739,7 @@ void tkc_free_graph(tkc_graph *g) {
   if (g->icol && g->icol != g->col) cudaFree(g->icol);
   void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega, g->scc_size, g->features,
                   g->learned_order, g->seeded_order, g->nb_order, g->nb_S, g->nb_r, g->nb_key, g->nb_hkey,
-                  g->nb_horder, g->comp, g->bu_chunks};
+                  g->nb_horder, g->comp, g->bu_list};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   g->ctx->graphs_alive--;
@@ -769,9 +820,18 @@ static int source_order_of(tkc_graph *g, const tkc_options &o, u32 kk, int harmo
     *norder = g->n_src_learned;
   } else if (o.order == TKC_ORDER_LEARNED) {
     // the model only picks the seeding prefix; the rest keeps the degree order
-    TKC_RC(ensure_seeded_order(g, (u32)std::min<u64>((u64)o.seed_factor * kk, 0xffffffffull)));
+    TKC_RC(ensure_seeded_order(g, (u32)std::min<u64>((u64)o.seed_factor * kk, 0xffffffffull), false));
     *order = g->seeded_order;
     *norder = g->n_src_deg;
+  } else if (o.order == TKC_ORDER_LEARNED_NB) {
+    // the model picks the seeding prefix; the rest is the NB order with its stop
+    // (still sorted by key, so the stop stays valid past the prefix)
+    if (harmonic) return TKC_EINVAL;
+    TKC_RC(ensure_nb_bounds(g, nb_levels_of(o)));
+    TKC_RC(ensure_seeded_order(g, (u32)std::min<u64>((u64)o.seed_factor * kk, 0xffffffffull), true));
+    *order = g->seeded_order;
+    *norder = g->n_src_nb;
+    *lb_key = g->nb_key;
   } else {
     return TKC_EINVAL;
   }
@@ -1309,7 +1369,7 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
     cudaStreamSynchronize(st);
     void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.scc_size, U.comp, U.nb_S, U.nb_r,
                     U.nb_key, U.nb_hkey,
-                    U.nb_order, U.nb_horder, U.bu_chunks, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir};
+                    U.nb_order, U.nb_horder, U.bu_list, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir};
     for (void *q : ptrs)
       if (q) cudaFree(q);
   };

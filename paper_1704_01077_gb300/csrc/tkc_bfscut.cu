@@ -154,8 +154,6 @@ __device__ __forceinline__ bool entry_less(bool harmonic, u64 Sa, u32 ra, u32 ia
 // rounding of H_d and U and of the FP64 h it is compared with (depths < 2^32).
 constexpr double kHMargin = 1.0 + 1.0 / 1048576.0;
 
-// bottom-up: in-degrees above this are walked by the whole warp
-constexpr uint32_t kHeavyIn = 24;
 
 // Threads per block of the search kernel (one block per SM).  The level loops
 // wait on dependent row gathers, so more resident warps hide more latency: the
@@ -644,6 +642,16 @@ __device__ __forceinline__ void trace_stamp(const RunParams &p, int slot) {
   }
 }
 
+// Direction of the next level: bottom-up when the frontier's arcs are a large
+// share of all arcs.
+__device__ __forceinline__ int choose_dir(const RunParams &p, u64 fl_arcs) {
+  return ((u128)fl_arcs * p.bu_num > (u128)p.arcs * p.bu_den) ? 1 : 0;
+}
+
+// Frontier lists at most this long are never compacted (the pass and its
+// barrier would cost more than the dead entries).
+constexpr uint32_t kCompactMin = 4096;
+
 template <int W>
 __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
   Ctl *c = p.ctl;
@@ -744,10 +752,20 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
       const u64 rb = 8ull * W;
       const u64 fl = c->fl_count, fa = c->fl_arcs, nl = packed >> kPackShift;
       u64 bytes;
-      if (c->dir == 0)
+      if (c->dir == 0) {
         bytes = fl * (16 + 2 * rb) + fa * (4 + 2 * rb) + nl * (8 + 5 * rb);
-      else
+        c->st_td_levels += 1;
+        c->st_td_frontier += fl;
+        c->st_td_arcs += fa;
+        c->st_td_new += nl;
+      } else {
         bytes = (u64)p.n * rb + c->lvl_scan_v * 8 + c->lvl_scan_a * (4 + rb) + nl * (8 + 2 * rb) + fl * (4 + rb);
+        c->st_bu_levels += 1;
+        c->st_bu_scan_v += c->lvl_scan_v;
+        c->st_bu_scan_a += c->lvl_scan_a;
+        c->st_bu_new += nl;
+        c->st_bu_frontier += fl;
+      }
       c->alg_bytes += bytes;
       if (p.trace) {
         u64 idx = c->trace_n++;
@@ -770,6 +788,7 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
     }
     c->nl_packed = 0;
     c->cur ^= 1;
+    c->lcur ^= 1;
     c->bdepth += 1;
     c->fl_count = (uint32_t)(packed >> kPackShift);
     c->fl_arcs = packed & kArcMask;
@@ -777,11 +796,40 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
     for (int j = 0; j < W; ++j) c->active[j] = sm.active[j];
     if (sm.nactive == 0) {
       c->step = 1;  // clear the batch's rows, then seed the next batch
+    } else if (c->fl_count > kCompactMin && sm.acc[2] * 2 < c->fl_arcs) {
+      // the new frontier list was built before this level's cuts: when the
+      // surviving searches' own frontier arcs (sm.acc[2], an upper bound on
+      // the arcs of the list entries they still use) are less than half of
+      // the list's, compact it first, so that the level neither expands nor
+      // (bottom-up) matches against rows of abandoned searches
+      c->step = 2;
     } else {
       c->step = 0;
-      // bottom-up when the frontier's arcs are a large share of all arcs
-      c->dir = ((u128)c->fl_arcs * p.bu_num > (u128)p.arcs * p.bu_den) ? 1 : 0;
+      c->dir = choose_dir(p, c->fl_arcs);
     }
+  }
+  __syncthreads();
+}
+
+// Epilogue after a compaction step: the compacted list (built in the next-list
+// buffer) becomes the frontier list, and the level's direction is chosen from
+// its arcs.
+template <int W>
+__device__ void epilogue_compact(const RunParams &p, Smem<W> &sm) {
+  Ctl *c = p.ctl;
+  if (threadIdx.x == 0) {
+    const u64 packed = c->nl_packed;
+    const u64 before = c->fl_count, after = packed >> kPackShift;
+    c->nl_packed = 0;
+    c->lcur ^= 1;
+    c->fl_count = (uint32_t)after;
+    c->fl_arcs = packed & kArcMask;
+    c->st_compactions += 1;
+    c->st_compact_dropped += before - after;
+    // list entry and row read per old entry, row cleared per dropped one, list written per kept one
+    c->alg_bytes += before * (4 + 8ull * W) + (before - after) * 8ull * W + after * 8;
+    c->step = 0;
+    c->dir = choose_dir(p, c->fl_arcs);
   }
   __syncthreads();
 }
@@ -794,8 +842,8 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
   const uint32_t B = p.B;
   u64 *Fcur = c->cur ? p.F1 : p.F0;
   uint32_t *FBcur = c->cur ? p.FB1 : p.FB0;
-  uint32_t *FL = c->cur ? p.L1 : p.L0;
-  uint32_t *FLoff = c->cur ? p.Loff1 : p.Loff0;
+  uint32_t *FL = c->lcur ? p.L1 : p.L0;
+  uint32_t *FLoff = c->lcur ? p.Loff1 : p.Loff0;
   uint32_t assigned = 0, last_base = 0;
   u64 arcs_total = 0, started = 0, cut0 = 0;
   __shared__ uint32_t s_base;
@@ -918,6 +966,8 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
   if (threadIdx.x == 0) {
     // the clear step just zeroed these rows
     c->alg_bytes += (u64)(c->vl_count + c->fl_count) * (4 + 8ull * W);
+    c->st_cleared += (u64)c->vl_count + c->fl_count;
+    c->st_seeded += assigned;
     c->cursor = last_base;
     c->bfs_started += started;
     c->bfs_cut += cut0;
@@ -951,7 +1001,7 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       if (p.team == 0) ((volatile Shared *)p.sh)->first_done = 1u;
     } else {
       c->step = 0;
-      c->dir = ((u128)arcs_total * p.bu_num > (u128)p.arcs * p.bu_den) ? 1 : 0;
+      c->dir = choose_dir(p, arcs_total);
     }
   }
   // slots beyond `assigned` are free
@@ -1010,10 +1060,11 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
     u64 *Fnext = cur ? p.F0 : p.F1;
     uint32_t *FBcur = cur ? p.FB1 : p.FB0;
     uint32_t *FBnext = cur ? p.FB0 : p.FB1;
-    uint32_t *FL = cur ? p.L1 : p.L0;
-    uint32_t *FLoff = cur ? p.Loff1 : p.Loff0;
-    uint32_t *NL = cur ? p.L0 : p.L1;
-    uint32_t *NLoff = cur ? p.Loff0 : p.Loff1;
+    const int lcur = vc->lcur;
+    uint32_t *FL = lcur ? p.L1 : p.L0;
+    uint32_t *FLoff = lcur ? p.Loff1 : p.Loff0;
+    uint32_t *NL = lcur ? p.L0 : p.L1;
+    uint32_t *NLoff = lcur ? p.Loff0 : p.Loff1;
     const uint32_t fl_count = vc->fl_count;
     if (step == 1) {
       if (tb == 0) trace_stamp(p, 8);
@@ -1026,6 +1077,38 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
       clear_frontier<W>(Fcur, FBcur, FL, fl_count, p.n, gthread, nthreads);
       if (tb == 0) trace_stamp(p, 12);
       if (!team_sync(c, p.sh, bpt, p.timeout, [&] { epilogue_seed<W>(p, sm); })) break;
+      continue;
+    }
+    if (step == 2) {
+      // ---- compaction: keep the frontier entries with a bit of a search
+      // still active (rows masked to those bits); zero the rows and frontier
+      // bits of the others, which only abandoned or finished searches used
+      u64 act[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) act[q] = vc->active[q];
+      for (uint32_t base = gwarp * 32; base < fl_count; base += nwarps * 32) {
+        const uint32_t i = base + lane;
+        const bool valid = i < fl_count;
+        uint32_t u = 0, od = 0;
+        bool keep = false;
+        if (valid) {
+          u = FL[i];
+          u64 row[W], f[W];
+          load_row<W>(Fcur, u, row);
+          bool same = true;
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            f[q] = row[q] & act[q];
+            same &= f[q] == row[q];
+          }
+          keep = row_nonzero<W>(f);
+          if (!keep) atomicAnd(&FBcur[u >> 5], ~(1u << (u & 31)));
+          if (!same) store_row<W>(Fcur, u, f);
+          if (keep) od = p.off[u + 1] - p.off[u];
+        }
+        warp_append(keep, u, od, &c->nl_packed, NL, NLoff, lane);
+      }
+      if (!team_sync(c, p.sh, bpt, p.timeout, [&] { epilogue_compact<W>(p, sm); })) break;
       continue;
     }
     if (tb == 0) trace_stamp(p, 8);
@@ -1146,23 +1229,37 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
       u64 act[W];
 #pragma unroll
       for (int q = 0; q < W; ++q) act[q] = sm.active[q];
-      // chunks of kBuChunkVerts vertices (whole bitmap words), those with the
-      // most in-arcs first, are dealt round-robin to the team's blocks; a
-      // block's warps take its chunks from a shared counter as they finish,
-      // so that a warp walking hubs does not hold the level up
-      const uint32_t nchunks = (p.n + kBuChunkVerts - 1) / kBuChunkVerts;
+      // Work items of the sweep list (vertices with an in-arc), dealt
+      // round-robin to the team's blocks, whose warps take them from a shared
+      // counter as they finish: first groups of 32 long in-rows, group j
+      // holding list entries j, j + hg, j + 2 hg, ... so that the longest rows
+      // land in different warps; then chunks of kBuChunkVerts consecutive
+      // entries of the shorter rows (ids ascending).
+      const uint32_t nheavy = p.bu_list ? p.n_bu_heavy : 0u;
+      const uint32_t nlight = p.bu_list ? p.n_bu - nheavy : p.n;
+      const uint32_t hg = (nheavy + 31) / 32;
+      const uint32_t nitems = hg + (nlight + kBuChunkVerts - 1) / kBuChunkVerts;
       for (;;) {
         uint32_t j = 0;
         if (lane == 0) j = atomicAdd(&sm.bu_next, 1u);
         j = __shfl_sync(FULL, j, 0);
         const u64 gi64 = (u64)tb + (u64)bpt * j;
-        if (gi64 >= nchunks) break;
+        if (gi64 >= nitems) break;
         const uint32_t gi = (uint32_t)gi64;
-        const uint32_t g0 = (p.bu_chunks ? p.bu_chunks[gi] : gi) * kBuChunkVerts;
-        const uint32_t g1 = g0 + kBuChunkVerts < p.n ? g0 + kBuChunkVerts : p.n;
+        const bool hitem = gi < hg;
+        const uint32_t g0 = hitem ? 0u : (gi - hg) * kBuChunkVerts;
+        const uint32_t g1 = hitem ? 32u : (g0 + kBuChunkVerts < nlight ? g0 + kBuChunkVerts : nlight);
         for (uint32_t base = g0; base < g1; base += 32) {
-          uint32_t w = base + lane;
-          bool valid = w < p.n;
+          bool valid;
+          uint32_t w;
+          if (hitem) {
+            const uint32_t e = gi + hg * (uint32_t)lane;
+            valid = e < nheavy;
+            w = valid ? p.bu_list[e] : 0;
+          } else {
+            valid = base + lane < g1;
+            w = valid ? (p.bu_list ? p.bu_list[nheavy + base + lane] : base + lane) : 0;
+          }
           u64 nw[W], sr[W], miss[W];
           uint32_t od = 0, e0 = 0, ee = 0;
           bool was_empty = false, any = false, heavy = false;
@@ -1276,10 +1373,22 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
             store_row<W>(Fnext, w, nw);
             if (p.lvl) record_levels<W>(p, w, nw, depth);
           }
-          {
-            // the warp owns the 32 consecutive vertices of one bitmap word
-            uint32_t word = __ballot_sync(FULL, isnew);
-            if (lane == 0) FBnext[base >> 5] = word;
+          // the next frontier's bitmap starts all zero (each level clears the
+          // bits of its own frontier), so setting the new vertices' bits
+          // suffices: one atomic per bitmap word the group's new vertices share
+          // (shorter rows: ids ascending, a few words), one per vertex for the
+          // long rows (ids scattered)
+          if (hitem) {
+            if (isnew) atomicOr(&FBnext[w >> 5], 1u << (w & 31));
+          } else {
+            for (unsigned pend = __ballot_sync(FULL, isnew); pend;) {
+              const int l = __ffs(pend) - 1;
+              const uint32_t word = __shfl_sync(FULL, w >> 5, l);
+              const bool mine = isnew && (w >> 5) == word;
+              const unsigned bits = __reduce_or_sync(FULL, mine ? 1u << (w & 31) : 0u);
+              if (lane == l) atomicOr(&FBnext[word], bits);
+              pend &= ~__ballot_sync(FULL, mine);
+            }
           }
           warp_count_slots<W>(nw, od, sm.cnt, sm.wsum, lane);
           warp_append(isnew, w, od, &c->nl_packed, NL, NLoff, lane);

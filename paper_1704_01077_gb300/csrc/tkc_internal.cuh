@@ -39,7 +39,12 @@ void note_launches(unsigned count);
 
 constexpr uint32_t kMaxN = 1u << 26; // list counters pack the count in 26 bits
 constexpr int kMaxWords = 8;         // 512-bit source batches
-constexpr uint32_t kBuChunkVerts = 128;  // bottom-up levels: vertices per chunk a warp takes
+constexpr uint32_t kBuChunkVerts = 128;  // bottom-up levels: list entries per chunk a warp takes
+// bottom-up levels: in-rows longer than this are walked by the whole warp
+#ifndef TKC_HEAVY_IN
+#define TKC_HEAVY_IN 24
+#endif
+constexpr uint32_t kHeavyIn = TKC_HEAVY_IN;
 
 // Device-resident state of one persistent BFSCut run (one graph).
 struct Ctl {
@@ -50,7 +55,7 @@ struct Ctl {
   int err;
   int err_where;
   // loop state
-  int step;          // 0 = level, 1 = clear + seed
+  int step;          // 0 = level, 1 = clear + seed, 2 = compact the frontier list to the active slots
   int done;
   int dir;           // 0 = top-down, 1 = bottom-up
   int cur;           // which frontier buffer / list is current
@@ -77,6 +82,13 @@ struct Ctl {
   unsigned long long trace_n;  // records written to the optional trace
   unsigned int bdepth;         // depth reached by the current batch (0 after seeding)
   unsigned int pad1;
+  // per-level totals of the run (tkc_last_run_stats)
+  unsigned long long st_td_levels, st_td_frontier, st_td_arcs, st_td_new;
+  unsigned long long st_bu_levels, st_bu_scan_v, st_bu_scan_a, st_bu_new, st_bu_frontier;
+  unsigned long long st_seeded, st_cleared;
+  unsigned long long st_compactions, st_compact_dropped;
+  int lcur;          // which list buffer holds the current frontier list (compaction swaps it alone)
+  int pad2;
 };
 
 // State shared by all teams of one run.
@@ -109,9 +121,11 @@ struct RunParams {
   uint64_t arcs;
   const uint32_t *off, *col, *ioff, *icol;
   const uint32_t *alpha, *omega;
-  // bottom-up levels: the graph's vertex chunks (kBuChunkVerts consecutive ids)
-  // by decreasing number of in-arcs; nullptr = chunks in id order
-  const uint32_t *bu_chunks;
+  // bottom-up levels sweep bu_list[0, n_bu): the vertices with an in-arc, the
+  // n_bu_heavy with more than kHeavyIn in-arcs first (longest first), then the
+  // others by id (nullptr: every vertex, by id)
+  const uint32_t *bu_list;
+  uint32_t n_bu, n_bu_heavy;
   uint32_t large_blocks;  // tkc_options.large_blocks: 0 = by size, 1 = larger blocks, 2 = 512 threads
   const uint32_t *order;
   uint32_t norder;  // sources in `order` to examine (all have out-degree >= 1)
@@ -232,6 +246,7 @@ struct TuneEntry {
 
 struct tkc_ctx {
   int device = 0;
+  tkc_run_stats last_stats{};  // per-level totals of the latest search-kernel run
   MlpState mlp;
   std::map<std::string, TuneEntry> tune;  // graph class -> fastest parameters
   cudaStream_t stream = nullptr;
@@ -261,9 +276,11 @@ struct tkc_graph {
   uint32_t *learned_order = nullptr;          // filtered order by predicted farness
   uint32_t n_src_learned = 0;
   uint64_t learned_version = 0;               // model version the learned order was computed with
-  uint32_t *seeded_order = nullptr;           // predicted-closest prefix, then the degree order
+  uint32_t *seeded_order = nullptr;           // predicted-closest prefix, then the degree or NB order
   uint64_t seeded_version = 0;
   uint32_t seeded_prefix = 0;
+  int seeded_base = -1;                       // 0: degree order after the prefix, 1: NB order
+  uint32_t seeded_nb_cap = 0;                 // nb_cap of the NB order it was built from
   uint32_t *nb_order = nullptr;               // NBCut order: out-degree >= 1, by (nb_key, id)
   uint32_t n_src_nb = 0;
   uint32_t nb_cap = 0;                        // level cap the bounds were computed with (0 = none yet)
@@ -273,7 +290,8 @@ struct tkc_graph {
   unsigned long long *nb_key = nullptr;       //   floor(S~ * 2^46 / (r-1)^2)
   unsigned long long *nb_hkey = nullptr;      // harmonic: ~(FP64 bits of the upper bound on h)
   uint32_t *nb_horder = nullptr;              // harmonic NBCut order: by (nb_hkey, id)
-  mutable uint32_t *bu_chunks = nullptr;      // bottom-up work order: chunk ids by decreasing in-arcs
+  mutable uint32_t *bu_list = nullptr;        // bottom-up sweep order: vertices with an in-arc, hubs first
+  mutable uint32_t n_bu = 0, n_bu_heavy = 0;
 };
 
 namespace tkc {
@@ -282,7 +300,7 @@ int validate_and_transpose(tkc_graph *g);
 int build_in_csr(tkc_graph *g);
 int ensure_degree_order(tkc_graph *g);
 int ensure_reach_bounds(tkc_graph *g);
-int ensure_bu_chunks(const tkc_graph *g);
+int ensure_bu_list(const tkc_graph *g);
 int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
 // tkc_nb.cu
 // gid/g_directed (several graphs as one union): per-vertex directedness
@@ -303,7 +321,9 @@ int lb_update(tkc_graph *g, uint32_t B, uint32_t nsrc, const uint32_t *srcs, uin
 // tkc_mlp.cu
 int ensure_features(tkc_graph *g);
 int ensure_learned_order(tkc_graph *g);
-int ensure_seeded_order(tkc_graph *g, uint32_t prefix);
+// prefix predicted-closest sources, then the degree order (nb = false) or the
+// NB order (nb = true; ensure_nb_bounds must have run) without them
+int ensure_seeded_order(tkc_graph *g, uint32_t prefix, bool nb);
 void free_mlp(tkc_ctx *ctx);
 // tkc_bfscut.cu
 int ensure_workspace(tkc_ctx *ctx, uint32_t n, int words, uint32_t top_entries, uint32_t ng, uint32_t teams);

@@ -423,14 +423,19 @@ int scan_exclusive_u32(const u32 *in, u32 *out, u64 len, u32 *tmp, cudaStream_t 
 // Seeded order: the `prefix` sources the model predicts closest first (they
 // are searched without cutting and set x from exact farness), then every
 // other source in the degree order.
-int ensure_seeded_order(tkc_graph *g, u32 prefix) {
+int ensure_seeded_order(tkc_graph *g, u32 prefix, bool nb) {
   tkc_ctx *ctx = g->ctx;
   TKC_RC(ensure_learned_order(g));
   TKC_RC(ensure_degree_order(g));
+  if (nb && !g->nb_order) return TKC_EINVAL;
   prefix = std::min(prefix, g->n_src_learned);
-  if (g->seeded_order && g->seeded_version == ctx->mlp.version && g->seeded_prefix == prefix) return TKC_OK;
+  const int base_kind = nb ? 1 : 0;
+  if (g->seeded_order && g->seeded_version == ctx->mlp.version && g->seeded_prefix == prefix &&
+      g->seeded_base == base_kind && (!nb || g->seeded_nb_cap == g->nb_cap))
+    return TKC_OK;
   cudaStream_t st = ctx->stream;
-  const u32 ns = g->n_src_deg;
+  const u32 *base = nb ? g->nb_order : g->deg_order;
+  const u32 ns = nb ? g->n_src_nb : g->n_src_deg;
   if (!g->seeded_order) TKC_TRY(cudaMallocAsync(&g->seeded_order, std::max<size_t>(g->n, 1) * sizeof(u32), st));
   uint8_t *mark = nullptr;
   u32 *pos = nullptr, *tmp = nullptr;
@@ -442,9 +447,9 @@ int ensure_seeded_order(tkc_graph *g, u32 prefix) {
     TKC_LAUNCH(k_mark_prefix<<<grid_of(prefix), 256, 0, st>>>(g->learned_order, prefix, mark));
     TKC_TRY(cudaMemcpyAsync(g->seeded_order, g->learned_order, prefix * sizeof(u32), cudaMemcpyDeviceToDevice, st));
   }
-  TKC_LAUNCH(k_unmarked_flags<<<grid_of(ns + 1), 256, 0, st>>>(g->deg_order, ns, mark, pos));
+  TKC_LAUNCH(k_unmarked_flags<<<grid_of(ns + 1), 256, 0, st>>>(base, ns, mark, pos));
   TKC_RC(scan_exclusive_u32(pos, pos, (u64)ns + 1, tmp, st));
-  TKC_LAUNCH(k_compact_into<<<grid_of(ns), 256, 0, st>>>(g->deg_order, pos, ns, g->seeded_order + prefix));
+  TKC_LAUNCH(k_compact_into<<<grid_of(ns), 256, 0, st>>>(base, pos, ns, g->seeded_order + prefix));
   TKC_TRY(cudaGetLastError());
   TKC_TRY(cudaFreeAsync(mark, st));
   TKC_TRY(cudaFreeAsync(pos, st));
@@ -452,6 +457,8 @@ int ensure_seeded_order(tkc_graph *g, u32 prefix) {
   TKC_TRY(cudaStreamSynchronize(st));
   g->seeded_version = ctx->mlp.version;
   g->seeded_prefix = prefix;
+  g->seeded_base = base_kind;
+  g->seeded_nb_cap = nb ? g->nb_cap : 0;
   return TKC_OK;
 }
 

@@ -1,14 +1,13 @@
 // Allocation-free exact distance sums for small graphs.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// result: code running while a CUDA stream is being captured into a graph
-// (cudaMalloc is not allowed there), runtimes that hand out a fixed device
-// memory budget up front, and latency-bound services that cannot afford the
-// device-wide synchronisation an allocation may imply.  For them this file
-// offers one entry point that allocates nothing: every scratch buffer of the
-// batched BFS (bit rows, frontier lists, per-slot state, control block) lives
-// in one file-scope device array of fixed size, and the caller passes device
-// pointers for the graph, the sources and the outputs.
+// result: runtimes that hand out a fixed device-memory budget up front (an
+// allocation later would exceed it or fail), and latency-bound services that
+// cannot afford the device-wide synchronisation an allocation may imply.  For
+// them this file offers one entry point that allocates nothing: every scratch
+// buffer of the batched BFS (bit rows, frontier lists, per-slot state, control
+// block) lives in one file-scope device array of fixed size, and the caller
+// passes device pointers for the graph, the sources and the outputs.
 //
 // Limits: at most TKC_NOALLOC_MAX_N vertices; sources are searched 64 at a
 // time.  The array is shared by every call on a device and keeps the previous
@@ -18,8 +17,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
-
-#include <mutex>
 
 #include "tkc_internal.cuh"
 
@@ -77,9 +74,6 @@ struct Layout {
 // The scratch of every call on this device (about 5.5 MB).
 static __device__ __align__(256) unsigned char g_scratch[Layout::total];
 
-std::mutex g_setup_mutex;
-void *g_scratch_ptr[256] = {nullptr};
-
 // Range checks that keep every later access in bounds, and distinct sources
 // (two slots of one batch must not share a source row).
 __global__ void k_check(const u32 *off, const u32 *col, u32 n, u64 arcs, const u32 *srcs, u32 nsrc, u32 *dup,
@@ -128,21 +122,18 @@ __global__ void k_gather(const u32 *srcs, u32 nsrc, const u64 *res_S, const u32 
   }
 }
 
-// Device address of g_scratch for the current device, looked up once per
-// device (the symbol's host-side name is not a device address).
-int scratch_for_device(int dev, unsigned char **out) {
-  if (dev < 0 || dev >= 256) return TKC_EINVAL;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) {
-      tkc_set_last_cuda_error(e, "cudaGetSymbolAddress(g_scratch)", __FILE__, __LINE__);
-      return TKC_ECUDA;
-    }
-    g_scratch_ptr[dev] = p;
+// Device address of g_scratch on the current device.  The symbol's host-side
+// name is not a device address, so it is looked up on every call: the lookup
+// allocates nothing, and an address cached across calls would go stale after a
+// device reset reloads the module.
+int scratch_for_device(unsigned char **out) {
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) {
+    tkc_set_last_cuda_error(e, "cudaGetSymbolAddress(g_scratch)", __FILE__, __LINE__);
+    return TKC_ECUDA;
   }
-  *out = (unsigned char *)g_scratch_ptr[dev];
+  *out = (unsigned char *)p;
   return TKC_OK;
 }
 
@@ -161,7 +152,7 @@ extern "C" int tkc_distance_sums_noalloc(const uint32_t *offsets, const uint32_t
   int dev = 0;
   TKC_TRY(cudaGetDevice(&dev));
   unsigned char *base = nullptr;
-  TKC_RC(scratch_for_device(dev, &base));
+  TKC_RC(scratch_for_device(&base));
   cudaStream_t st = (cudaStream_t)stream;
   typedef Layout L;
   // what must start at zero: bit rows, frontier bitmaps, duplicate map,

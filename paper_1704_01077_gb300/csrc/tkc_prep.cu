@@ -380,31 +380,51 @@ int ensure_degree_order(tkc_graph *g) {
 
 // ------------------------------------------------------------------ bottom-up work order
 
-__global__ void k_bu_chunk_keys(const u32 *ioff, u32 n, u32 nch, u32 *key, u32 *val) {
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < nch; i += gridDim.x * blockDim.x) {
-    const u32 a = i * kBuChunkVerts, b = a + kBuChunkVerts < n ? a + kBuChunkVerts : n;
-    const u32 arcs = ioff[b] - ioff[a];
-    key[i] = (u32)__clz(arcs);  // leading zeros: a longer bit length of the in-arc count sorts first
-    val[i] = i;                          // ids ascending: the sort is stable
+__global__ void k_bu_keys(const u32 *ioff, u32 n, u32 heavy_in, u32 *key, u32 *val, u32 *count) {
+  u32 any = 0, heavy = 0;
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const u32 indeg = ioff[v + 1] - ioff[v];
+    // rows walked by a whole warp: by bit length of the in-degree, longest
+    // first; then the other vertices with an in-arc; none last
+    key[v] = indeg > heavy_in ? (u32)__clz(indeg) : indeg ? 32u : 33u;
+    val[v] = v;  // ids ascending: the sort is stable
+    any += indeg != 0;
+    heavy += indeg > heavy_in;
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    any += __shfl_down_sync(0xffffffffu, any, o);
+    heavy += __shfl_down_sync(0xffffffffu, heavy, o);
+  }
+  if ((threadIdx.x & 31) == 0 && any) atomicAdd(&count[0], any);
+  if ((threadIdx.x & 31) == 0 && heavy) atomicAdd(&count[1], heavy);
 }
 
-// Chunks of kBuChunkVerts vertices by decreasing in-arcs (to a power of two):
-// bottom-up levels hand them out in this order (longest first), so that the
-// chunks holding hubs start early.  Only the order of work depends on it, not
-// any result.
-int ensure_bu_chunks(const tkc_graph *g) {
-  if (g->bu_chunks || g->n == 0) return TKC_OK;
+// The vertices that bottom-up levels sweep: those with an in-arc (no other
+// vertex can be discovered bottom-up; a source is seeded directly).  First
+// the n_heavy vertices of more than kHeavyIn in-arcs, whose rows a whole warp
+// walks, longest rows first (bit length of the in-degree, then id); then the
+// others by id, so that a warp's 32 entries share a few frontier-bitmap words.
+// Only the order of work depends on it, not any result.
+int ensure_bu_list(const tkc_graph *g) {
+  if (g->bu_list || g->n == 0) return TKC_OK;
   cudaStream_t st = g->ctx->stream;
-  const u32 nch = (g->n + kBuChunkVerts - 1) / kBuChunkVerts;
-  u32 *keys = nullptr, *ids = nullptr;
-  TKC_TRY(cudaMallocAsync(&ids, (size_t)nch * sizeof(u32), st));
-  TKC_TRY(cudaMallocAsync(&keys, (size_t)nch * sizeof(u32), st));
-  TKC_LAUNCH(k_bu_chunk_keys<<<grid_for(nch, 256), 256, 0, st>>>(g->ioff, g->n, nch, keys, ids));
+  const u32 n = g->n;
+  u32 *keys = nullptr, *ids = nullptr, *cnt = nullptr;
+  TKC_TRY(cudaMallocAsync(&ids, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&keys, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&cnt, 2 * sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(u32), st));
+  TKC_LAUNCH(k_bu_keys<<<grid_for(n, 256), 256, 0, st>>>(g->ioff, n, kHeavyIn, keys, ids, cnt));
   TKC_TRY(cudaGetLastError());
-  TKC_RC(radix_sort_pairs(keys, ids, nch, 6, st));
+  TKC_RC(radix_sort_pairs(keys, ids, n, 6, st));
+  u32 c[2] = {0, 0};
+  TKC_TRY(cudaMemcpyAsync(c, cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
   TKC_TRY(cudaFreeAsync(keys, st));
-  g->bu_chunks = ids;
+  TKC_TRY(cudaFreeAsync(cnt, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  g->bu_list = ids;
+  g->n_bu = c[0];
+  g->n_bu_heavy = c[1];
   return TKC_OK;
 }
 

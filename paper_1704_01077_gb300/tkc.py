@@ -32,6 +32,7 @@ TKC_ORDER_DEG = 0
 TKC_ORDER_GIVEN = 1
 TKC_ORDER_LEARNED = 2
 TKC_ORDER_NB = 3
+TKC_ORDER_LEARNED_NB = 4
 TKC_MAX_K = 1024
 TKC_NOALLOC_MAX_N = 65536
 TKC_MLP_FEATURES = 5
@@ -50,7 +51,7 @@ class tkc_options(ctypes.Structure):
                 ("batch_bits", ctypes.c_uint32), ("bu_num", ctypes.c_uint32), ("bu_den", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("seed_factor", ctypes.c_uint32),
                 ("timeout_cycles", ctypes.c_uint64), ("teams", ctypes.c_uint32), ("nb_levels", ctypes.c_uint32),
-                ("large_blocks", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("large_blocks", ctypes.c_uint32), ("deterministic", ctypes.c_uint32)]
 
 
 class tkc_result(ctypes.Structure):
@@ -65,12 +66,23 @@ class tkc_result(ctypes.Structure):
                 ("alg_bytes", ctypes.c_uint64)]
 
 
+class tkc_run_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("batch_bits", ctypes.c_uint32), ("row_bytes", ctypes.c_uint32),
+                ("teams", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("arcs", ctypes.c_uint64), ("td_levels", ctypes.c_uint64), ("td_frontier", ctypes.c_uint64),
+                ("td_frontier_arcs", ctypes.c_uint64), ("td_new", ctypes.c_uint64), ("bu_levels", ctypes.c_uint64),
+                ("bu_scanned_vertices", ctypes.c_uint64), ("bu_scanned_arcs", ctypes.c_uint64),
+                ("bu_new", ctypes.c_uint64), ("bu_frontier", ctypes.c_uint64), ("seeded", ctypes.c_uint64),
+                ("cleared", ctypes.c_uint64), ("compactions", ctypes.c_uint64), ("compacted_away", ctypes.c_uint64),
+                ("alg_bytes", ctypes.c_uint64), ("ms_kernel", ctypes.c_double)]
+
+
 EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc_free_graph",
             "tkc_topk_closeness", "tkc_topk_closeness_multi", "tkc_source_order", "tkc_set_source_order",
             "tkc_reach_bounds", "tkc_distance_sums", "tkc_distance_sums_noalloc", "tkc_kernel_launches",
             "tkc_strerror", "tkc_vertex_features", "tkc_mlp_init", "tkc_set_source_model", "tkc_get_source_model",
             "tkc_mlp_forward", "tkc_mlp_gradient", "tkc_mlp_train_step", "tkc_autotune", "tkc_nb_bounds",
-            "tkc_topk_harmonic", "tkc_topk_harmonic_multi", "tkc_nb_harmonic_bounds", "tkc_topk_closeness_bound"]
+            "tkc_topk_harmonic", "tkc_topk_harmonic_multi", "tkc_nb_harmonic_bounds", "tkc_topk_closeness_bound", "tkc_last_run_stats"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -112,6 +124,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tkc_topk_harmonic_multi.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.POINTER(tkc_result)]
     lib.tkc_nb_harmonic_bounds.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double), u32p, u32p]
+    lib.tkc_last_run_stats.argtypes = [vp, ctypes.POINTER(tkc_run_stats)]
     lib.tkc_kernel_launches.argtypes = []
     lib.tkc_kernel_launches.restype = ctypes.c_uint64
     lib.tkc_strerror.argtypes = [ctypes.c_int]
@@ -124,6 +137,13 @@ _lib = load_library()
 
 def tkc_kernel_launches() -> int:
     return int(_lib.tkc_kernel_launches())
+
+
+def tkc_last_run_stats(ctx) -> dict:
+    """Per-level totals of ctx's latest search-kernel run, as a dict."""
+    st = tkc_run_stats()
+    _check(_lib.tkc_last_run_stats(ctx, ctypes.byref(st)), "tkc_last_run_stats")
+    return {name: getattr(st, name) for name, _ in st._fields_ if name != "pad"}
 
 
 def tkc_strerror(code: int) -> str:
@@ -172,11 +192,12 @@ class Options:
     teams: int = 0
     nb_levels: int = 0
     large_blocks: int = 0
+    deterministic: int = 0
 
     def to_c(self) -> tkc_options:
         return tkc_options(self.device, self.stream, self.order, self.batch_bits, self.bu_num, self.bu_den,
                            self.blocks, self.seed_factor, self.timeout_cycles, self.teams, self.nb_levels,
-                           self.large_blocks, 0)
+                           self.large_blocks, self.deterministic)
 
 
 @dataclass

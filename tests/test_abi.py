@@ -49,6 +49,36 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(tkc.tkc_result) == 144
     assert tkc.tkc_result.edges_visited.offset == 56
     assert tkc.tkc_result.ms_bfs.offset == 120
+    assert tkc.tkc_options.deterministic.offset == 60
+    # 6 x uint32, 15 x uint64, 1 double
+    assert ctypes.sizeof(tkc.tkc_run_stats) == 152
+    assert tkc.tkc_run_stats.ms_kernel.offset == 144
+
+
+def test_struct_layouts_match_a_c_compiler(tmp_path):
+    """Every field offset the binding uses, against what gcc makes of the header."""
+    import subprocess
+
+    from paper_1704_01077_gb300 import tkc
+
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "tkc.h"', "int main(void) {"]
+    for cname, cls in (("tkc_options", tkc.tkc_options), ("tkc_result", tkc.tkc_result),
+                       ("tkc_run_stats", tkc.tkc_run_stats)):
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = subprocess.check_output([str(exe)]).decode().split("\n")
+    classes = {"tkc_options": tkc.tkc_options, "tkc_result": tkc.tkc_result, "tkc_run_stats": tkc.tkc_run_stats}
+    for line in filter(None, got):
+        cname, what, value = line.split()
+        cls = classes[cname]
+        want = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert int(value) == want, line
 
 
 def test_error_strings(lib):
@@ -63,7 +93,7 @@ def test_constants_match_header():
 
     text = open(HEADER).read()
     for name in ("TKC_OK", "TKC_EINVAL", "TKC_EGRAPH", "TKC_ENOMEM", "TKC_ECUDA", "TKC_ETIMEOUT",
-                 "TKC_EOVERFLOW", "TKC_ORDER_DEG", "TKC_ORDER_GIVEN", "TKC_ORDER_LEARNED", "TKC_ORDER_NB", "TKC_MAX_K",
+                 "TKC_EOVERFLOW", "TKC_ORDER_DEG", "TKC_ORDER_GIVEN", "TKC_ORDER_LEARNED", "TKC_ORDER_NB", "TKC_ORDER_LEARNED_NB", "TKC_MAX_K",
                  "TKC_NOALLOC_MAX_N", "TKC_MLP_FEATURES", "TKC_MLP_HIDDEN", "TKC_MLP_PARAMS"):
         m = re.search(rf"#define {name} (-?\d+)", text)
         assert m and int(m.group(1)) == getattr(tkc, name), name
@@ -79,8 +109,8 @@ def test_argument_errors_before_any_device_call(lib):
     lib.tkc_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(tkc.tkc_options)]
     good = tkc.Options().to_c()
     assert lib.tkc_create(None, ctypes.byref(good)) == EINVAL
-    for bad in (dict(batch_bits=96), dict(batch_bits=1024), dict(order=9), dict(nb_levels=65536),
-                dict(large_blocks=3)):
+    for bad in (dict(batch_bits=96), dict(batch_bits=1024), dict(order=5), dict(nb_levels=65536),
+                dict(large_blocks=3), dict(deterministic=2)):
         out = vp(1234)
         assert lib.tkc_create(ctypes.byref(out), ctypes.byref(tkc.Options(**bad).to_c())) == EINVAL, bad
         assert out.value is None, bad

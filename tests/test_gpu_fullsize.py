@@ -1,21 +1,39 @@
-"""The bench workloads at full size (R-MAT scale 22, Barabasi-Albert 10^6), in
-the launch configuration bench.py times (library defaults: 128-bit NBCut
-batches with 768-thread blocks on R-MAT 22, 512-thread blocks on BA 10^6),
-checked against the CPU oracle vertex by vertex, since the textbook top-k is
-out of reach at these sizes:
-- every returned vertex's S and r (h for harmonic) equal the oracle's BFS from
-  it, and its farness the oracle's IEEE value;
-- the list is ordered by (farness, id);
-- no vertex of a sample (the highest out-degrees and uniform random sources)
-  beats the k-th;
-- DegCut, NBCut and both block sizes return the same list."""
+"""The full-size workloads (directed R-MAT scale 22, Barabasi-Albert 10^6 with
+k = 1, 10, 100, and the 512 graphs of one multi-graph launch), in the launch
+configuration bench.py times (library defaults), against the CPU oracle's
+complete run of Algorithm 1 on the same graphs.
+
+The expected values are stored in tests/golden/fullsize_*.json, written by
+tests/golden/make_fullsize_fixtures.py, which calls only the oracle (NBCut
+order and stop, one source at a time, run to the end).  Each fixture holds
+the SHA-256 of its graph's CSR, checked here first, so a different generator
+build cannot pass silently.  Ids, S, r, the tie count and the farness doubles
+must be identical, for DegCut and NBCut and both block sizes of the search
+kernel; harmonic centrality compares the FP64 h bit for bit."""
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
-import oracle
 from paper_1704_01077_gb300 import graphgen as gg
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _fixture(name):
+    with open(os.path.join(GOLDEN, f"fullsize_{name}.json")) as f:
+        return json.load(f)
+
+
+def _sha(g):
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(g.offsets, dtype="<u4").tobytes())
+    h.update(np.ascontiguousarray(g.cols, dtype="<u4").tobytes())
+    return h.hexdigest()
 
 
 @pytest.fixture(scope="module")
@@ -27,20 +45,16 @@ def ctx(gpu_lib):
 
 @pytest.fixture(scope="module")
 def rmat22():
-    return gg.rmat(22, 16, seed=gg.workload_seed(4))
+    g = gg.rmat(22, 16, seed=gg.workload_seed(4))
+    assert _sha(g) == _fixture("rmat22")["graphs"][0]["csr_sha256"]
+    return g
 
 
 @pytest.fixture(scope="module")
 def ba1m():
-    return gg.barabasi_albert(1_000_000, 5, gg.workload_seed(2))
-
-
-def _sample(g, ids, seed, count=40):
-    outd = g.outdeg()
-    top = np.argsort(-outd, kind="stable")[:count]
-    rng = np.random.default_rng(seed)
-    rnd = rng.choice(np.nonzero(outd > 0)[0], size=count, replace=False)
-    return np.setdiff1d(np.concatenate([top, rnd]), np.asarray(ids, dtype=np.int64)).astype(np.uint32)
+    g = gg.barabasi_albert(1_000_000, 5, gg.workload_seed(2))
+    assert _sha(g) == _fixture("ba1m")["graphs"][0]["csr_sha256"]
+    return g
 
 
 def _run(t, ctx, g, k, fn, **opts):
@@ -53,59 +67,72 @@ def _run(t, ctx, g, k, fn, **opts):
         t.tkc_set_options(ctx, t.Options())
 
 
-def _check_closeness(g, res, k, seed):
-    ids = np.asarray(res.ids)
-    assert len(ids) == k
-    S, r = oracle.bfs_sums(g, ids)
-    assert np.array_equal(S, res.dist_sum) and np.array_equal(r, res.reach)
-    for i in range(k):
-        f, _ = oracle.farness(g.n, S[i], r[i])
-        assert res.farness[i].tobytes() == np.float64(f).tobytes()
-    for i in range(k - 1):
-        c = oracle.cmp_farness(int(S[i]), int(r[i]), int(S[i + 1]), int(r[i + 1]))
-        assert c < 0 or (c == 0 and ids[i] < ids[i + 1]), i
-    smp = _sample(g, ids, seed)
-    Ss, rs = oracle.bfs_sums(g, smp)
-    for v, s_, r_ in zip(smp, Ss, rs):
-        c = oracle.cmp_farness(int(s_), int(r_), int(S[-1]), int(r[-1]))
-        assert c > 0 or (c == 0 and v > ids[-1]), int(v)
+def _expect(res, want, what):
+    assert [int(x) for x in res.ids] == want["ids"], what
+    assert [int(x) for x in res.dist_sum] == want["S"], what
+    assert [int(x) for x in res.reach] == want["r"], what
+    assert res.n_tied_at_kth == want["n_tied"], what
+    assert [float(f).hex() for f in res.farness] == want["farness_hex"], what
 
 
-def _same(a, b):
-    assert list(a.ids) == list(b.ids)
-    assert np.array_equal(a.dist_sum, b.dist_sum) and np.array_equal(a.reach, b.reach)
-    assert a.n_tied_at_kth == b.n_tied_at_kth
+def _want(name, k, index=0):
+    for r in _fixture(name)["graphs"][index]["results"]:
+        if r["k"] == k:
+            return r
+    raise KeyError((name, k))
 
 
 def test_rmat22_closeness(gpu_lib, ctx, rmat22):
     t = gpu_lib
-    g = rmat22
-    nb = _run(t, ctx, g, 10, t.tkc_topk_closeness, order=t.TKC_ORDER_NB)
+    want = _want("rmat22", 10)
+    nb = _run(t, ctx, rmat22, 10, t.tkc_topk_closeness, order=t.TKC_ORDER_NB)
     assert nb.batch_bits == 128
-    _check_closeness(g, nb, 10, 1)
-    _same(_run(t, ctx, g, 10, t.tkc_topk_closeness, order=t.TKC_ORDER_DEG), nb)
-    _same(_run(t, ctx, g, 10, t.tkc_topk_closeness, order=t.TKC_ORDER_NB, large_blocks=2), nb)
+    _expect(nb, want, "NBCut")
+    _expect(_run(t, ctx, rmat22, 10, t.tkc_topk_closeness, order=t.TKC_ORDER_DEG), want, "DegCut")
+    _expect(_run(t, ctx, rmat22, 10, t.tkc_topk_closeness, order=t.TKC_ORDER_NB, large_blocks=2), want,
+            "NBCut, 512-thread blocks")
 
 
 def test_rmat22_harmonic(gpu_lib, ctx, rmat22):
     t = gpu_lib
-    g = rmat22
-    res = _run(t, ctx, g, 10, t.tkc_topk_harmonic, order=t.TKC_ORDER_NB)
-    ids = np.asarray(res.ids)
-    H, r = oracle.harmonic_sums(g, ids)
-    assert H.tobytes() == res.closeness.tobytes() and np.array_equal(r, res.reach)
-    assert all(H[i] > H[i + 1] or (H[i] == H[i + 1] and ids[i] < ids[i + 1]) for i in range(len(ids) - 1))
-    smp = _sample(g, ids, 2)
-    Hs, _ = oracle.harmonic_sums(g, smp)
-    assert all(h < H[-1] or (h == H[-1] and v > ids[-1]) for v, h in zip(smp, Hs))
+    fx = _fixture("rmat22_harmonic")
+    assert fx["graphs"][0]["csr_sha256"] == _sha(rmat22)
+    want = fx["graphs"][0]["results"][0]
+    res = _run(t, ctx, rmat22, 10, t.tkc_topk_harmonic, order=t.TKC_ORDER_NB)
+    assert [int(x) for x in res.ids] == want["ids"]
+    assert [float(h).hex() for h in res.closeness] == want["h_hex"]
+    assert [int(x) for x in res.reach] == want["r"] and res.n_tied_at_kth == want["n_tied"]
 
 
 @pytest.mark.parametrize("k", [1, 10, 100])
 def test_ba1m_closeness(gpu_lib, ctx, ba1m, k):
     t = gpu_lib
-    g = ba1m
-    nb = _run(t, ctx, g, k, t.tkc_topk_closeness, order=t.TKC_ORDER_NB)
-    _check_closeness(g, nb, k, 3 + k)
-    _same(_run(t, ctx, g, k, t.tkc_topk_closeness, order=t.TKC_ORDER_NB, large_blocks=1), nb)
+    want = _want("ba1m", k)
+    _expect(_run(t, ctx, ba1m, k, t.tkc_topk_closeness, order=t.TKC_ORDER_NB), want, ("NBCut", k))
+    _expect(_run(t, ctx, ba1m, k, t.tkc_topk_closeness, order=t.TKC_ORDER_NB, large_blocks=1), want,
+            ("NBCut, larger blocks", k))
     if k == 10:
-        _same(_run(t, ctx, g, k, t.tkc_topk_closeness, order=t.TKC_ORDER_DEG), nb)
+        _expect(_run(t, ctx, ba1m, k, t.tkc_topk_closeness, order=t.TKC_ORDER_DEG), want, ("DegCut", k))
+
+
+def test_multi512_one_launch(gpu_lib, ctx):
+    t = gpu_lib
+    fx = _fixture("multi512")
+    rc = fx["recipe"]
+    seed = gg.workload_seed(rc["seed_index"])
+    sizes = gg.log_uniform_sizes(rc["count"], rc["lo"], rc["hi"], seed)
+    graphs = [gg.barabasi_albert(n, 4, gg.splitmix64(seed + i)) if i % 2 == 0
+              else gg.erdos_renyi(n, 8 * n, gg.splitmix64(seed + i), directed=True) for i, n in enumerate(sizes)]
+    for g, e in zip(graphs, fx["graphs"]):
+        assert _sha(g) == e["csr_sha256"], e["index"]
+    for order in (t.TKC_ORDER_NB, t.TKC_ORDER_DEG):
+        t.tkc_set_options(ctx, t.Options(order=order))
+        hs = [t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed) for g in graphs]
+        try:
+            res = t.tkc_topk_closeness_multi(ctx, hs, 10)
+        finally:
+            for h in hs:
+                t.tkc_free_graph(h)
+            t.tkc_set_options(ctx, t.Options())
+        for i, (r, e) in enumerate(zip(res, fx["graphs"])):
+            _expect(r, e["results"][0], (order, i, e["name"]))

@@ -1,12 +1,17 @@
-"""What the trained source-order model gains over the degree order, on
-held-out R-MAT graphs (seeds not used in training): the top-k is identical
-by construction and checked; the work (arcs visited) is measured for the
-degree order, the full learned order, and the learned seeding prefix
-(seed_factor * k predicted-closest sources first, then the degree order).
+"""What the trained source-order model gains, on held-out R-MAT graphs (seeds
+not used in training), against both of the paper's orders: the degree order
+(DegCut) and the neighbourhood-bound order with its stop (NBCut, the default).
 
-On these graphs the degree order already reaches the true top-k first, so the
-model cannot cut more work; the test records the ratios and requires that
-seeding with the model costs no more than 1% extra work."""
+Every run uses the deterministic schedule (one team), so arcs visited are a
+function of the order alone and the comparison is repeatable; the top-k is
+identical by construction and checked against the oracle.  Orders compared:
+  degree / nb                  the paper's two orders;
+  learned                      all sources by predicted farness;
+  learned_seed_degree          the 5k predicted-closest sources first (searched
+                               to the end), then the degree order;
+  learned_seed_nb              the same prefix, then the NB order with its stop.
+The measured ratios are printed (and written to $TKC_LEARNED_GAIN_OUT when
+set); the assertions state what the measurements support."""
 import json
 import os
 
@@ -20,33 +25,44 @@ from paper_1704_01077_gb300.train_order import load_weights
 pytestmark = pytest.mark.gpu
 
 
-def test_learned_order_gain_on_held_out_graphs(gpu_lib, tmp_path):
+def test_learned_order_against_degcut_and_nbcut(gpu_lib):
     t = gpu_lib
     w = load_weights()
     assert w is not None, "trained weights missing"
     ctx = t.tkc_create(t.Options())
     rows = []
+    arms = (("degree", t.TKC_ORDER_DEG, 0), ("nb", t.TKC_ORDER_NB, 0), ("learned", t.TKC_ORDER_LEARNED, 0),
+            ("learned_seed_degree", t.TKC_ORDER_LEARNED, 5), ("learned_seed_nb", t.TKC_ORDER_LEARNED_NB, 5))
     try:
         t.tkc_set_source_model(ctx, w)
-        for scale in (13, 15):
+        for scale in (13, 15, 17):
             g = gg.rmat(scale, 16, seed=gg.splitmix64(gg.BASE_SEED + 9000 + scale))
-            ref = oracle.bfscut(g, 10)
+            nb = oracle.nb_bounds(g)
+            ref = oracle.bfscut(g, 10, order=oracle.nb_full_order(g, nb.key), lb_key=nb.key)
             h = t.tkc_load_csr(ctx, g.n, g.offsets, g.cols, True)
             try:
                 row = {"scale": scale}
-                for name, order, sf in (("degree", t.TKC_ORDER_DEG, 0), ("learned", t.TKC_ORDER_LEARNED, 0),
-                                        ("learned_seed5", t.TKC_ORDER_LEARNED, 5)):
-                    t.tkc_set_options(ctx, t.Options(batch_bits=64, order=order, seed_factor=sf, teams=1))
+                for name, order, sf in arms:
+                    t.tkc_set_options(ctx, t.Options(batch_bits=128, order=order, seed_factor=sf, deterministic=1))
+                    r = t.tkc_topk_closeness(h, 10)  # warm: orders and bounds are cached on the graph
                     r = t.tkc_topk_closeness(h, 10)
-                    assert list(r.ids) == list(ref.ids) and np.array_equal(r.dist_sum, ref.S)
-                    row[name] = r.edges_visited
+                    assert list(r.ids) == list(ref.ids) and np.array_equal(r.dist_sum, ref.S), (scale, name)
+                    row[name] = {"edges_visited": r.edges_visited, "bfs_started": r.bfs_started,
+                                 "ms_kernel": round(r.ms_kernel, 3)}
                 rows.append(row)
             finally:
                 t.tkc_free_graph(h)
     finally:
         t.tkc_destroy(ctx)
     for row in rows:
-        row["learned_vs_degree"] = row["learned"] / row["degree"]
-        row["seeded_vs_degree"] = row["learned_seed5"] / row["degree"]
-        assert row["seeded_vs_degree"] <= 1.01, row
+        for name in ("learned", "learned_seed_degree", "learned_seed_nb"):
+            row[name]["arcs_vs_degree"] = row[name]["edges_visited"] / row["degree"]["edges_visited"]
+            row[name]["arcs_vs_nb"] = row[name]["edges_visited"] / row["nb"]["edges_visited"]
+        # seeding only reorders the first 5k searches: it never costs much
+        assert row["learned_seed_degree"]["arcs_vs_degree"] <= 1.05, row
+        assert row["learned_seed_nb"]["arcs_vs_nb"] <= 1.05, row
+    out = os.environ.get("TKC_LEARNED_GAIN_OUT")
+    if out:
+        with open(out, "w") as f:
+            json.dump(rows, f, indent=1)
     print(json.dumps(rows))

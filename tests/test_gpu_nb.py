@@ -176,7 +176,7 @@ def test_nb_degenerate_and_options(gpu_lib, ctx):
     with pytest.raises(tkc.TkcError):
         tkc.tkc_set_options(ctx, tkc.Options(order=tkc.TKC_ORDER_NB, nb_levels=70000))
     with pytest.raises(tkc.TkcError):
-        tkc.tkc_set_options(ctx, tkc.Options(order=4))
+        tkc.tkc_set_options(ctx, tkc.Options(order=5))
     h = tkc.tkc_load_csr(ctx, 5, gg.path(5).offsets, gg.path(5).cols, False)
     try:
         with pytest.raises(tkc.TkcError):

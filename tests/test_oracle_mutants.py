@@ -16,6 +16,18 @@ import test_oracle as pins
 import test_oracle_nb as nbpins
 import test_oracle_harmonic as hpins
 import test_oracle_lb as lbpins
+import test_oracle_batched as bpins
+
+def _stale_x_mutant():
+    """The batched schedule reading x before the step's finished searches are
+    merged (the threshold lags one step)."""
+    src = open(oracle._SRC).read()
+    a = src.index("      /* searches that found nothing new are finished; the others advance */")
+    b = src.index("      any = 0;\n", a)
+    block = src[a:b]
+    x = block.index("      /* x after this step's merges")
+    return block, block[x:] + block[:x]
+
 
 MUTANTS = {
     "bfs_dropped_distance": ("S += dist[w];", "S += dist[w] - (dist[w] > 1);",
@@ -103,6 +115,14 @@ MUTANTS = {
                                     pins.test_bfscut_equals_textbook_small_random]),
     "cut_min_takes_largest": ("    if (lhs < rhs) { bl = L; br = r; }", "    if (lhs > rhs) { bl = L; br = r; }",
                               [pins.test_cut_min_is_minimum_over_whole_interval]),
+    "batched_level0_arcs_dropped": ("        active[s] = 1;\n        c.edges_visited += od;", "        active[s] = 1;",
+                                    [lambda: bpins.test_star_counted_by_hand(5)]),
+    "batched_no_refill": ("    while (assigned < B && cursor < nq && !stopped) {",
+                          "    for (int once = 0; once < 1 && cursor < nq && !stopped; ++once) {",
+                          [bpins.test_b1_equals_sequential_bfscut]),
+    "batched_undirected_arcs_off": ("arcs[s] = gs[s] + (directed ? 0u : cnt[s]);", "arcs[s] = gs[s];",
+                                    [lambda: bpins.test_star_counted_by_hand(5)]),
+    "batched_x_read_before_merge": _stale_x_mutant() + ([lambda: bpins.test_star_counted_by_hand(5)],),
     "degree_order_unstable": ("for (uint32_t v = 0; v < n; ++v) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               "for (uint32_t v = n; v-- > 0;) order[start[maxd - (off[v + 1] - off[v])]++] = v;",
                               [pins.test_degree_order_matches_lexsort]),

@@ -1,10 +1,11 @@
 """The allocation-free entry point, tkc_distance_sums_noalloc, through the C ABI.
 
-Callers that cannot allocate device memory when they need a result (code under
-CUDA stream capture, fixed-budget runtimes, latency-bound services) use this
-variant; it must return exactly what tkc_distance_sums returns.  The file is
-collected last so that a run stopping at its first failure has already run
-every other test; it also passes alone in a fresh process."""
+Callers that cannot allocate device memory when they need a result (runtimes
+with a fixed device-memory budget, latency-bound services that cannot take an
+allocation's synchronisation) use this variant; it must return exactly what
+tkc_distance_sums returns.  The file is collected last so that a run stopping
+at its first failure has already run every other test; it also passes alone in
+a fresh process."""
 import numpy as np
 import pytest
 
