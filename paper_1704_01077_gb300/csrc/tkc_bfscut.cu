@@ -1328,12 +1328,21 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
             }
             constexpr int HU = W >= 8 ? 1 : W >= 4 ? 2 : 4;
             uint32_t e = hb;
+            // the next step's columns are loaded before this step's frontier
+            // bits and rows are waited on, so their latency overlaps
+            uint32_t nx[HU];
+#pragma unroll
+            for (int j = 0; j < HU; ++j) {
+              const uint32_t i = hb + 32 * j + lane;
+              nx[j] = i < he ? p.icol[i] : 0xffffffffu;
+            }
             for (; e < he; e += 32 * HU) {
               uint32_t uu[HU], fb[HU];
 #pragma unroll
               for (int j = 0; j < HU; ++j) {
-                const uint32_t i = e + 32 * j + lane;
-                uu[j] = i < he ? p.icol[i] : 0xffffffffu;
+                uu[j] = nx[j];
+                const uint32_t i = e + 32 * HU + 32 * j + lane;
+                nx[j] = i < he ? p.icol[i] : 0xffffffffu;
               }
 #pragma unroll
               for (int j = 0; j < HU; ++j)

@@ -110,22 +110,41 @@ enum : u32 { kBadOffsets = 1, kBadRange = 2, kSelfLoop = 4, kUnsorted = 8, kAsym
 
 // One warp per vertex: offsets monotone and within arcs, ids in range, no
 // self-loop, each row strictly increasing (sorted, no duplicates).
+// A lane checks the row of its own vertex when it has at most 16 arcs, the
+// warp longer rows; a row is read only after its offsets are known to lie
+// within [0, arcs].
 __global__ void k_validate(const u32 *off, const u32 *col, u32 n, u64 arcs, u32 *flags) {
   int lane = threadIdx.x & 31;
-  u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  u32 nw = (gridDim.x * blockDim.x) >> 5;
   u32 f = 0;
-  for (u32 v = warp; v < n; v += nw) {
-    u32 b = off[v], e = off[v + 1];
-    if (e < b || e > arcs) {
-      f |= kBadOffsets;
-      continue;
+  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
+    const u32 v = base + lane;
+    u32 b = 0, e = 0;
+    if (v < n) {
+      b = off[v];
+      e = off[v + 1];
+      if (e < b || e > arcs) {
+        f |= kBadOffsets;
+        b = e = 0;
+      }
     }
-    for (u32 i = b + lane; i < e; i += 32) {
-      u32 c = col[i];
-      if (c >= n) f |= kBadRange;
-      if (c == v) f |= kSelfLoop;
-      if (i > b && col[i - 1] >= c) f |= kUnsorted;
+    const bool light = e - b <= 16;
+    if (light)
+      for (u32 i = b; i < e; ++i) {
+        const u32 c = col[i];
+        if (c >= n) f |= kBadRange;
+        if (c == v) f |= kSelfLoop;
+        if (i > b && col[i - 1] >= c) f |= kUnsorted;
+      }
+    for (unsigned hv = __ballot_sync(FULL, !light); hv; hv &= hv - 1) {
+      const int src = __ffs(hv) - 1;
+      const u32 hb = __shfl_sync(FULL, b, src), he = __shfl_sync(FULL, e, src);
+      const u32 x = base + src;
+      for (u32 i = hb + lane; i < he; i += 32) {
+        const u32 c = col[i];
+        if (c >= n) f |= kBadRange;
+        if (c == x) f |= kSelfLoop;
+        if (i > hb && col[i - 1] >= c) f |= kUnsorted;
+      }
     }
   }
   f = __reduce_or_sync(FULL, f);
@@ -154,24 +173,40 @@ __global__ void k_symmetric(const u32 *off, const u32 *col, u32 n, u32 *flags) {
   if (lane == 0 && f) atomicOr(flags, f);
 }
 
-__global__ void k_indeg(const u32 *off, const u32 *col, u32 n, u32 *indeg) {
-  int lane = threadIdx.x & 31;
-  u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  u32 nw = (gridDim.x * blockDim.x) >> 5;
-  for (u32 u = warp; u < n; u += nw)
-    for (u32 i = off[u] + lane; i < off[u + 1]; i += 32) atomicAdd(&indeg[col[i]], 1u);
-}
+// In-degrees (scatter = false: cnt[v] += 1 per arc u -> v) or the in-arc
+// columns (scatter = true: u appended to v's in-row at ioff[v] + cnt[v]++).
+// A lane walks the out-row of its own vertex when it has at most kLaneRow
+// arcs, the warp longer rows.
+constexpr u32 kLaneRow = 16;
 
-__global__ void k_transpose_scatter(const u32 *off, const u32 *col, u32 n, const u32 *ioff, u32 *cursor,
-                                    u32 *icol) {
-  int lane = threadIdx.x & 31;
-  u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  u32 nw = (gridDim.x * blockDim.x) >> 5;
-  for (u32 u = warp; u < n; u += nw)
-    for (u32 i = off[u] + lane; i < off[u + 1]; i += 32) {
-      u32 v = col[i];
-      icol[ioff[v] + atomicAdd(&cursor[v], 1u)] = u;
+template <bool scatter>
+__global__ void k_in_arcs(const u32 *off, const u32 *col, u32 n, const u32 *ioff, u32 *cnt, u32 *icol) {
+  const int lane = threadIdx.x & 31;
+  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
+    const u32 u = base + lane;
+    u32 b = 0, e = 0;
+    if (u < n) {
+      b = off[u];
+      e = off[u + 1];
     }
+    const bool light = e - b <= kLaneRow;
+    if (light)
+      for (u32 i = b; i < e; ++i) {
+        const u32 v = col[i];
+        if (scatter) icol[ioff[v] + atomicAdd(&cnt[v], 1u)] = u;
+        else atomicAdd(&cnt[v], 1u);
+      }
+    for (unsigned hv = __ballot_sync(0xffffffffu, !light); hv; hv &= hv - 1) {
+      const int src = __ffs(hv) - 1;
+      const u32 hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
+      const u32 x = base + src;
+      for (u32 i = hb + lane; i < he; i += 32) {
+        const u32 v = col[i];
+        if (scatter) icol[ioff[v] + atomicAdd(&cnt[v], 1u)] = x;
+        else atomicAdd(&cnt[v], 1u);
+      }
+    }
+  }
 }
 
 static unsigned grid_for(u64 work, unsigned tpb, unsigned cap = 152 * 16) {
@@ -188,7 +223,7 @@ int validate_and_transpose(tkc_graph *g) {
   u32 *flags = nullptr;
   TKC_TRY(cudaMallocAsync(&flags, sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(flags, 0, sizeof(u32), st));
-  TKC_LAUNCH(k_validate<<<grid_for((u64)n * 32, 256), 256, 0, st>>>(g->off, g->col, n, g->arcs, flags));
+  TKC_LAUNCH(k_validate<<<grid_for(n, 256), 256, 0, st>>>(g->off, g->col, n, g->arcs, flags));
   TKC_TRY(cudaGetLastError());
   u32 hf = 0;
   TKC_TRY(cudaMemcpyAsync(&hf, flags, sizeof(u32), cudaMemcpyDeviceToHost, st));
@@ -221,10 +256,10 @@ int build_in_csr(tkc_graph *g) {
   TKC_TRY(cudaMallocAsync(&tmp, (((size_t)n + 1) / kScanTile + 2) * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(g->ioff, 0, ((size_t)n + 1) * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(u32), st));
-  TKC_LAUNCH(k_indeg<<<grid_for((u64)n * 32, 256), 256, 0, st>>>(g->off, g->col, n, g->ioff));
+  TKC_LAUNCH(k_in_arcs<false><<<grid_for(n, 256), 256, 0, st>>>(g->off, g->col, n, nullptr, g->ioff, nullptr));
   TKC_TRY(cudaGetLastError());
   TKC_RC(scan_exclusive(g->ioff, g->ioff, (u64)n + 1, tmp, st));
-  TKC_LAUNCH(k_transpose_scatter<<<grid_for((u64)n * 32, 256), 256, 0, st>>>(g->off, g->col, n, g->ioff, cursor, g->icol));
+  TKC_LAUNCH(k_in_arcs<true><<<grid_for(n, 256), 256, 0, st>>>(g->off, g->col, n, g->ioff, cursor, g->icol));
   TKC_TRY(cudaGetLastError());
   TKC_TRY(cudaFreeAsync(cursor, st));
   TKC_TRY(cudaFreeAsync(tmp, st));

@@ -80,97 +80,228 @@ __global__ void k_trim_round(const u32 *off, const u32 *col, const u32 *ioff, co
   }
 }
 
-// ---------------------------------------------------------------- level BFS by sweeps
+// ---------------------------------------------------------------- reach BFS, one cooperative launch
 
-// One level of a BFS restricted to `active` (nullable): vertices at `level`
-// label their unlabelled neighbours with level + 1.  Warps collect the
-// frontier vertices of 32 consecutive ids and expand each with all lanes.
-// Frontier vertices of out-degree above this are expanded by the whole grid.
-constexpr u32 kBfsHeavy = 2048;
+// Control block of the reach BFS: grid barrier alone in its cache line, then
+// the frontier queues' packed counters (count << 38 | out-arcs).
+struct BfsCtl {
+  unsigned bar_count, bar_gen, bar_pad[30];
+  int err;
+  unsigned level;
+  unsigned long long q[2];
+};
 
-// One BFS level: the vertices at `level` relax their arcs (a warp per vertex);
-// those of degree above kBfsHeavy are listed for k_bfs_heavy instead, so that
-// a hub does not keep one warp busy while the rest of the grid waits.
-__global__ void k_bfs_sweep(const u32 *off, const u32 *col, u32 n, const uint8_t *active, u32 *dist, u32 level,
-                            u32 *changed, u32 *heavy, u32 *nheavy) {
-  const int lane = threadIdx.x & 31;
-  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
-    u32 v = base + lane;
-    u32 mask = __ballot_sync(FULL, v < n && dist[v] == level);
-    u32 ch = 0;
-    while (mask) {
-      int src = __ffs(mask) - 1;
-      mask &= mask - 1;
-      u32 x = base + src;
-      const u32 b = off[x], e = off[x + 1];
-      if (e - b > kBfsHeavy) {
-        if (lane == 0) heavy[atomicAdd(nheavy, 1u)] = x;
-        continue;
+constexpr int kBfsThreads = 512;
+constexpr int kQShift = 38;
+constexpr u64 kQArcs = (1ull << kQShift) - 1;
+
+__device__ __forceinline__ unsigned ld_acq(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier of the cooperative launch; the last block to arrive runs
+// `epi` (thread 0) first.  Every wait is bounded: on expiry the kernel
+// records TKC_ETIMEOUT and returns false, as do all blocks once it is set.
+template <typename Epi>
+__device__ bool bfs_sync(BfsCtl *c, u64 timeout, Epi epi) {
+  __shared__ int s_last;
+  __shared__ unsigned s_gen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_gen = ld_acq(&c->bar_gen);
+    __threadfence();
+    s_last = atomicAdd(&c->bar_count, 1u) + 1u == gridDim.x;
+  }
+  __syncthreads();
+  if (s_last) {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      epi();
+      c->bar_count = 0;
+      __threadfence();
+      st_rel(&c->bar_gen, s_gen + 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    while (ld_acq(&c->bar_gen) == s_gen) {
+      if (*(volatile int *)&c->err) break;
+      if ((u64)(clock64() - t0) > timeout) {
+        atomicCAS(&c->err, 0, TKC_ETIMEOUT);
+        break;
       }
-      for (u32 i = b + lane; i < e; i += 32) {
-        u32 w = col[i];
-        if ((!active || active[w]) && dist[w] == INF) {
-          dist[w] = level + 1;
-          ch = 1;
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int *)&c->err == 0;
+}
+
+// Appends the lanes with `pred` to a queue whose counter packs count << 38 |
+// out-arcs (one atomic per warp); qo[pos] = the arcs of the entries before.
+__device__ __forceinline__ void q_append(bool pred, u32 v, u32 od, unsigned long long *packed, u32 *q, u64 *qo,
+                                         int lane) {
+  const unsigned m = __ballot_sync(FULL, pred);
+  if (!m) return;
+  u32 a = pred ? od : 0u;
+  u32 incl = a;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const u32 tot = __shfl_sync(FULL, incl, 31);
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(packed, ((unsigned long long)__popc(m) << kQShift) | tot);
+  base = __shfl_sync(FULL, base, leader);
+  if (pred) {
+    const u32 pos = (u32)(base >> kQShift) + __popc(m & ((1u << lane) - 1u));
+    q[pos] = v;
+    qo[pos] = (base & kQArcs) + (incl - a);
+  }
+}
+
+// Reachability from src along the arcs (off, col); (roff, rcol) are the same
+// arcs reversed.  mark[v] = the step at which v was reached, INF if never
+// (src: 0).  A step expands the frontier queue top-down (its arcs split evenly
+// over the warps, so a hub's row is shared by many; a vertex is claimed by
+// compare-and-swap) or, when the frontier's arcs exceed 1/8 of all arcs,
+// bottom-up: every unreached vertex looks for any reached in-neighbour and
+// stops at the first (only reachability is asked for).
+__global__ void __launch_bounds__(kBfsThreads) k_bfs_reach(const u32 *off, const u32 *col, const u32 *roff,
+                                                          const u32 *rcol, u32 n, u64 arcs, u32 *mark, u32 *q0,
+                                                          u32 *q1, u64 *qo0, u64 *qo1, BfsCtl *c, u64 timeout) {
+  const int lane = threadIdx.x & 31;
+  const u32 gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int cur = 0;; cur ^= 1) {
+    const unsigned long long qp = ((volatile BfsCtl *)c)->q[cur];
+    const u32 qn = (u32)(qp >> kQShift);
+    const u64 qa = qp & kQArcs;
+    if (qn == 0) break;
+    const u32 step = ((volatile BfsCtl *)c)->level + 1;
+    const u32 *Q = cur ? q1 : q0;
+    const u64 *QO = cur ? qo1 : qo0;
+    u32 *NQ = cur ? q0 : q1;
+    u64 *NQO = cur ? qo0 : qo1;
+    unsigned long long *npk = &c->q[cur ^ 1];
+    if (qa * 8 <= arcs) {
+      // about two arc ranges per warp, whole warp steps of 32 arcs
+      u64 ch = (qa + 2ull * nwarps - 1) / (2ull * nwarps);
+      ch = (ch + 31) / 32 * 32;
+      for (u64 a0 = (u64)gwarp * ch; a0 < qa; a0 += (u64)nwarps * ch) {
+        const u64 a1 = a0 + ch < qa ? a0 + ch : qa;
+        u32 lo = 0, hi = qn;  // last entry with QO <= a0
+        while (hi - lo > 1) {
+          const u32 mid = (lo + hi) >> 1;
+          if (QO[mid] <= a0) lo = mid;
+          else hi = mid;
+        }
+        u32 ent = lo;
+        for (u64 s0 = a0; s0 < a1; s0 += 32) {
+          const u64 a = s0 + lane;
+          u32 w = 0;
+          bool got = false;
+          u32 e = ent;
+          if (a < a1) {
+            while (e + 1 < qn && QO[e + 1] <= a) ++e;
+            w = col[off[Q[e]] + (u32)(a - QO[e])];
+            got = mark[w] == INF && atomicCAS(&mark[w], INF, step) == INF;
+          }
+          q_append(got, w, got ? off[w + 1] - off[w] : 0u, npk, NQ, NQO, lane);
+          ent = __reduce_max_sync(FULL, e);
         }
       }
-    }
-    if (__any_sync(FULL, ch) && lane == 0) *changed = 1;
-  }
-}
-
-// The listed heavy vertices of the level: one block per vertex, and the whole
-// grid for the few above kBfsHuge out-arcs.
-constexpr u32 kBfsHuge = 1u << 16;
-
-__global__ void k_bfs_heavy(const u32 *off, const u32 *col, const uint8_t *active, u32 *dist, u32 level,
-                            u32 *changed, const u32 *heavy, const u32 *nheavy) {
-  const u32 nh = *nheavy;
-  u32 ch = 0;
-  for (u32 h = 0; h < nh; ++h) {
-    const u32 x = heavy[h];
-    const u32 b = off[x], e = off[x + 1];
-    u32 first, step;
-    if (e - b > kBfsHuge) {
-      first = b + blockIdx.x * blockDim.x + threadIdx.x;
-      step = gridDim.x * blockDim.x;
-    } else if (h % gridDim.x == blockIdx.x) {
-      first = b + threadIdx.x;
-      step = blockDim.x;
     } else {
-      continue;
-    }
-    for (u32 i = first; i < e; i += step) {
-      u32 w = col[i];
-      if ((!active || active[w]) && dist[w] == INF) {
-        dist[w] = level + 1;
-        ch = 1;
+      for (u32 base = gwarp * 32; base < n; base += nwarps * 32) {
+        const u32 v = base + lane;
+        bool got = false;
+        u32 b = 0, e = 0;
+        if (v < n && mark[v] == INF) {
+          b = roff[v];
+          e = roff[v + 1];
+        }
+        const bool light = e - b <= 32;
+        // short in-rows: the lane alone, four in-neighbours per step
+        if (light)
+          for (u32 k = b; k < e && !got; k += 4) {
+            u32 mu[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mu[j] = k + j < e ? mark[rcol[k + j]] : INF;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) got |= mu[j] < step;
+          }
+        // long in-rows: the whole warp, 32 in-neighbours per step, until one is reached
+        for (unsigned hv = __ballot_sync(FULL, !light); hv; hv &= hv - 1) {
+          const int src = __ffs(hv) - 1;
+          const u32 hb = __shfl_sync(FULL, b, src), he = __shfl_sync(FULL, e, src);
+          bool hit = false;
+          for (u32 k0 = hb; k0 < he && !hit; k0 += 32) {
+            const u32 k = k0 + lane;
+            hit = __any_sync(FULL, k < he && mark[rcol[k]] < step);
+          }
+          if (lane == src) got = hit;
+        }
+        if (got) mark[v] = step;
+        q_append(got, v, got ? off[v + 1] - off[v] : 0u, npk, NQ, NQO, lane);
       }
     }
+    const bool ok = bfs_sync(c, timeout, [&] {
+      c->q[cur] = 0;
+      c->level = step;
+    });
+    if (!ok) return;
   }
-  if (__any_sync(FULL, ch) && (threadIdx.x & 31) == 0) *changed = 1;
 }
 
-// BFS levels from src over the arcs (off, col), restricted to active vertices
-// (nullptr: all); flag must hold 2 words.
-int bfs_levels(const u32 *off, const u32 *col, u32 n, u64 arcs, const uint8_t *active, u32 *dist, u32 src,
-               u32 *flag, cudaStream_t st) {
-  u32 *heavy = nullptr;
-  TKC_TRY(cudaMallocAsync(&heavy, (size_t)(arcs / kBfsHeavy + 1) * sizeof(u32), st));
-  TKC_TRY(cudaMemsetAsync(dist, 0xff, (size_t)n * sizeof(u32), st));
-  TKC_TRY(cudaMemsetAsync(dist + src, 0, sizeof(u32), st));
-  for (u32 level = 0;; ++level) {
-    if (level > n) return TKC_ETIMEOUT;
-    TKC_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(u32), st));
-    TKC_LAUNCH(k_bfs_sweep<<<grid_of(n), 256, 0, st>>>(off, col, n, active, dist, level, flag, heavy, flag + 1));
-    TKC_LAUNCH(k_bfs_heavy<<<grid_of(arcs / 8 + 1), 256, 0, st>>>(off, col, active, dist, level, flag, heavy, flag + 1));
-    u32 h = 0;
-    TKC_TRY(cudaMemcpyAsync(&h, flag, sizeof(u32), cudaMemcpyDeviceToHost, st));
-    TKC_TRY(cudaStreamSynchronize(st));
-    if (!h) break;
+__global__ void k_bfs_start(const u32 *off, u32 *mark, u32 *q0, u64 *qo0, BfsCtl *c, u32 src) {
+  mark[src] = 0;
+  q0[0] = src;
+  qo0[0] = 0;
+  c->q[0] = (1ull << kQShift) | (unsigned long long)(off[src + 1] - off[src]);
+}
+
+// Reachability from src along (off, col) into mark (see k_bfs_reach); one
+// cooperative launch.
+int bfs_reach(tkc_ctx *ctx, const u32 *off, const u32 *col, const u32 *roff, const u32 *rcol, u32 n, u64 arcs,
+              u32 *mark, u32 src, cudaStream_t st) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    TKC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_reach, kBfsThreads, 0));
+    if (per_sm <= 0) return TKC_ECUDA;
   }
-  TKC_TRY(cudaFreeAsync(heavy, st));
-  return TKC_OK;
+  u32 *q = nullptr;
+  u64 *qo = nullptr;
+  BfsCtl *c = nullptr;
+  TKC_TRY(cudaMallocAsync(&q, (size_t)2 * n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&qo, (size_t)2 * n * sizeof(u64), st));
+  TKC_TRY(cudaMallocAsync(&c, sizeof(BfsCtl), st));
+  TKC_TRY(cudaMemsetAsync(c, 0, sizeof(BfsCtl), st));
+  TKC_TRY(cudaMemsetAsync(mark, 0xff, (size_t)n * sizeof(u32), st));
+  u32 *q0 = q, *q1 = q + n;
+  u64 *qo0 = qo, *qo1 = qo + n;
+  TKC_LAUNCH(k_bfs_start<<<1, 1, 0, st>>>(off, mark, q0, qo0, c, src));
+  u64 timeout = ctx->opt.timeout_cycles ? ctx->opt.timeout_cycles : (1ull << 34);
+  void *args[] = {(void *)&off,  (void *)&col, (void *)&roff, (void *)&rcol, (void *)&n,
+                  (void *)&arcs, (void *)&mark, (void *)&q0,  (void *)&q1,   (void *)&qo0,
+                  (void *)&qo1,  (void *)&c,    (void *)&timeout};
+  const int blocks = std::max(1, std::min(per_sm * ctx->num_sms, (int)((n + kBfsThreads - 1) / kBfsThreads)));
+  note_launches(1);
+  TKC_TRY(cudaLaunchCooperativeKernel((const void *)k_bfs_reach, dim3(blocks), dim3(kBfsThreads), args, 0, st));
+  int err = 0;
+  TKC_TRY(cudaMemcpyAsync(&err, &c->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  TKC_TRY(cudaFreeAsync(q, st));
+  TKC_TRY(cudaFreeAsync(qo, st));
+  TKC_TRY(cudaFreeAsync(c, st));
+  return err ? err : TKC_OK;
 }
 
 // ---------------------------------------------------------------- pivot and FW-BW
@@ -277,10 +408,20 @@ __global__ void k_color_assign(u32 n, uint8_t *active, const u32 *color, const u
 
 // ---------------------------------------------------------------- component statistics
 
+// Size and smallest vertex of every SCC.  Lanes holding the same SCC add up
+// in the warp first: one big SCC would otherwise take one atomic per vertex on
+// a single address.
 __global__ void k_comp_stats(const u32 *comp, u32 n, u32 *wgt, u32 *minid) {
-  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    atomicAdd(&wgt[comp[v]], 1u);
-    atomicMin(&minid[comp[v]], v);
+  const int lane = threadIdx.x & 31;
+  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
+    const u32 v = base + lane;
+    const bool valid = v < n;
+    const u32 c = valid ? comp[v] : INF;
+    const unsigned grp = __match_any_sync(FULL, c);
+    if (valid && lane == __ffs(grp) - 1) {
+      atomicAdd(&wgt[c], (u32)__popc(grp));
+      atomicMin(&minid[c], v);  // the group's first lane holds its smallest id
+    }
   }
 }
 
@@ -307,34 +448,47 @@ __global__ void k_count_reached(const u32 *dist, u32 n, u32 *cnt) {
 
 // ---------------------------------------------------------------- condensation
 
-__global__ void k_cross_count(const u32 *off, const u32 *col, const u32 *comp, u32 n, u32 *cnt) {
+// Arcs between different SCCs, a warp per vertex (grid-stride).  The count
+// pass writes each block's count; after an exclusive scan of those, the emit
+// pass (same grid, so the same vertices per block) writes each block's arcs
+// from its offset on, placed by a shared-memory cursor: no global atomics.
+template <bool emit>
+__global__ void k_cross(const u32 *off, const u32 *col, const u32 *comp, u32 n, u32 *blk, u32 *cu, u32 *cv) {
+  __shared__ u32 s_cnt;
   const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  const u32 base = emit ? blk[blockIdx.x] : 0u;
   u32 c = 0;
-  for (u32 v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5)
-    for (u32 i = off[v] + lane; i < off[v + 1]; i += 32) c += comp[col[i]] != comp[v];
-  c = __reduce_add_sync(FULL, c);
-  if (lane == 0 && c) atomicAdd(cnt, c);
-}
-
-__global__ void k_cross_emit(const u32 *off, const u32 *col, const u32 *comp, u32 n, u32 *cursor, u32 *cu,
-                             u32 *cv) {
-  const int lane = threadIdx.x & 31;
   for (u32 v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
-    u32 a = comp[v];
-    for (u32 i0 = off[v]; i0 < off[v + 1]; i0 += 32) {
-      u32 i = i0 + lane;
-      u32 b = i < off[v + 1] ? comp[col[i]] : a;
-      bool cross = b != a;
-      u32 m = __ballot_sync(FULL, cross);
+    const u32 b = off[v], e = off[v + 1];
+    if (b == e) continue;
+    const u32 a = comp[v];
+    for (u32 i0 = b; i0 < e; i0 += 32) {
+      const u32 i = i0 + lane;
+      const u32 t = i < e ? comp[col[i]] : a;
+      const bool cross = t != a;
+      if (!emit) {
+        c += cross;
+        continue;
+      }
+      const unsigned m = __ballot_sync(FULL, cross);
+      if (!m) continue;
       u32 pos = 0;
-      if (lane == 0 && m) pos = atomicAdd(cursor, (u32)__popc(m));
+      if (lane == 0) pos = atomicAdd(&s_cnt, (u32)__popc(m));
       pos = __shfl_sync(FULL, pos, 0);
       if (cross) {
-        u32 k = pos + __popc(m & ((1u << lane) - 1u));
+        const u32 k = base + pos + __popc(m & ((1u << lane) - 1u));
         cu[k] = a;
-        cv[k] = b;
+        cv[k] = t;
       }
     }
+  }
+  if (!emit) {
+    c = __reduce_add_sync(FULL, c);
+    if (lane == 0 && c) atomicAdd(&s_cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) blk[blockIdx.x] = s_cnt;
   }
 }
 
@@ -345,21 +499,39 @@ __global__ void k_unique_flags(const u32 *cu, const u32 *cv, u32 m, u32 *flag) {
   if (blockIdx.x == 0 && threadIdx.x == 0) flag[m] = 0;
 }
 
+// Keeps the first of each run of equal pairs and counts successors and
+// predecessors per SCC; lanes holding the same SCC add up in the warp first
+// (one SCC may be the target of a large share of all pairs).
 __global__ void k_unique_compact(const u32 *cu, const u32 *cv, const u32 *pos, u32 m, u32 *ou, u32 *ov,
                                  u32 *succ_cnt, u32 *pred_cnt) {
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    if (pos[i + 1] != pos[i]) {
-      ou[pos[i]] = cu[i];
-      ov[pos[i]] = cv[i];
-      atomicAdd(&succ_cnt[cu[i]], 1u);
-      atomicAdd(&pred_cnt[cv[i]], 1u);
+  const int lane = threadIdx.x & 31;
+  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < m; base += gridDim.x * blockDim.x) {
+    const u32 i = base + lane;
+    const bool keep = i < m && pos[i + 1] != pos[i];
+    const u32 a = keep ? cu[i] : INF, t = keep ? cv[i] : INF;
+    if (keep) {
+      ou[pos[i]] = a;
+      ov[pos[i]] = t;
     }
+    const unsigned ga = __match_any_sync(FULL, a), gt = __match_any_sync(FULL, t);
+    if (keep && lane == __ffs(ga) - 1) atomicAdd(&succ_cnt[a], (u32)__popc(ga));
+    if (keep && lane == __ffs(gt) - 1) atomicAdd(&pred_cnt[t], (u32)__popc(gt));
+  }
 }
 
+// Predecessor lists: each pair's source into its target's list (positions
+// claimed once per warp and target SCC).
 __global__ void k_pred_scatter(const u32 *ou, const u32 *ov, u32 m, const u32 *poff, u32 *pcur, u32 *pred) {
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    u32 c = ov[i];
-    pred[poff[c] + atomicAdd(&pcur[c], 1u)] = ou[i];
+  const int lane = threadIdx.x & 31;
+  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < m; base += gridDim.x * blockDim.x) {
+    const u32 i = base + lane;
+    const u32 c = i < m ? ov[i] : INF;
+    const unsigned grp = __match_any_sync(FULL, c);
+    const int leader = __ffs(grp) - 1;
+    u32 at = 0;
+    if (c != INF && lane == leader) at = atomicAdd(&pcur[c], (u32)__popc(grp));
+    at = __shfl_sync(FULL, at, leader);
+    if (c != INF) pred[poff[c] + at + __popc(grp & ((1u << lane) - 1u))] = ou[i];
   }
 }
 
@@ -374,63 +546,146 @@ __global__ void k_sinks(const u32 *wgt, const u32 *soff, u32 n, u32 *rem, u32 *l
   }
 }
 
-// Evaluates alpha/omega of the ready SCCs (all successors done), one warp
-// per SCC reducing over its successors.
+// Evaluates alpha/omega of the ready SCCs (all successors done).  A lane
+// reduces over the successors of its own SCC when there are at most 32; the
+// whole warp over longer successor lists.
 __global__ void k_dp_eval(const u32 *list, u32 cnt, const u32 *soff, const u32 *succ, const u32 *wgt,
                           const u32 *dist_from_big, const u32 *dist_to_big, u32 big, u64 reach_big, u32 n, u64 *A,
-                          u64 *O, u32 *npred, const u32 *poff) {
+                          u64 *O) {
   const int lane = threadIdx.x & 31;
-  for (u32 i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < cnt; i += (gridDim.x * blockDim.x) >> 5) {
-    u32 c = list[i];
+  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < cnt; base += gridDim.x * blockDim.x) {
+    const u32 i = base + lane;
+    const u32 c = i < cnt ? list[i] : INF;
+    u32 b = 0, e = 0;
+    if (c != INF && c != big) {
+      b = soff[c];
+      e = soff[c + 1];
+    }
+    const bool light = e - b <= 32;
     u64 amax = 0, osum = 0, onot = 0;
-    if (c != big) {
-      for (u32 e = soff[c] + lane; e < soff[c + 1]; e += 32) {
-        u32 y = succ[e];
+    if (light)
+      for (u32 k = b; k < e; ++k) {
+        const u32 y = succ[k];
         amax = A[y] > amax ? A[y] : amax;
         osum += O[y];
         if (dist_from_big[y] == INF) onot += O[y];
       }
+    for (unsigned hv = __ballot_sync(FULL, !light); hv; hv &= hv - 1) {
+      const int src = __ffs(hv) - 1;
+      const u32 hb = __shfl_sync(FULL, b, src), he = __shfl_sync(FULL, e, src);
+      u64 wa = 0, wo = 0, wn = 0;
+      for (u32 k = hb + lane; k < he; k += 32) {
+        const u32 y = succ[k];
+        wa = A[y] > wa ? A[y] : wa;
+        wo += O[y];
+        if (dist_from_big[y] == INF) wn += O[y];
+      }
       for (int o = 16; o; o >>= 1) {
-        u64 t = __shfl_down_sync(FULL, amax, o);
-        amax = t > amax ? t : amax;
-        osum += __shfl_down_sync(FULL, osum, o);
-        onot += __shfl_down_sync(FULL, onot, o);
+        const u64 t = __shfl_xor_sync(FULL, wa, o);
+        wa = t > wa ? t : wa;
+        wo += __shfl_xor_sync(FULL, wo, o);
+        wn += __shfl_xor_sync(FULL, wn, o);
+      }
+      if (lane == src) {
+        amax = wa;
+        osum = wo;
+        onot = wn;
       }
     }
-    if (lane == 0) {
-      u64 a, o;
-      if (c == big) {
-        a = o = reach_big;
-      } else {
-        if (dist_to_big[c] != INF) osum = onot + O[big];
-        a = amax + wgt[c];
-        o = osum + wgt[c];
-        if (o > n) o = n;
-      }
-      A[c] = a;
-      O[c] = o;
-      npred[i] = poff[c + 1] - poff[c];
+    if (c == INF) continue;
+    u64 a, o;
+    if (c == big) {
+      a = o = reach_big;
+    } else {
+      if (dist_to_big[c] != INF) osum = onot + O[big];
+      a = amax + wgt[c];
+      o = osum + wgt[c];
+      if (o > n) o = n;
     }
+    A[c] = a;
+    O[c] = o;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) npred[cnt] = 0;
 }
 
-// Releases the predecessors of the SCCs just evaluated, one thread per
-// predecessor arc (pos: exclusive prefix of the predecessor counts); an SCC
-// whose last successor this was joins the next ready list.
-__global__ void k_dp_release(const u32 *list, u32 cnt, const u32 *pos, const u32 *poff, const u32 *pred, u32 *rem,
-                             u32 *next, u32 *next_cnt) {
-  const u32 total = pos[cnt];
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    u32 lo = 0, hi = cnt;  // last j with pos[j] <= i
-    while (hi - lo > 1) {
-      u32 mid = (lo + hi) >> 1;
-      if (pos[mid] <= i) lo = mid;
-      else hi = mid;
+// Predecessor lists longer than this are released by the whole grid.
+constexpr u32 kDpHuge = 4096;
+
+// Appends the lanes with `rel` to the ready list (one atomic per warp).
+__device__ __forceinline__ void ready_append(bool rel, u32 p, u32 *next, u32 *next_cnt, int lane) {
+  const unsigned m = __ballot_sync(FULL, rel);
+  if (!m) return;
+  u32 pos = 0;
+  if (lane == 0) pos = atomicAdd(next_cnt, (u32)__popc(m));
+  pos = __shfl_sync(FULL, pos, 0);
+  if (rel) next[pos + __popc(m & ((1u << lane) - 1u))] = p;
+}
+
+// Releases the predecessors of the SCCs just evaluated: an SCC whose last
+// unevaluated successor this was joins the next ready list.  A lane walks
+// lists of at most 32, the warp longer ones; lists above kDpHuge are left to
+// k_dp_release_huge (listed in huge[]).
+__global__ void k_dp_release(const u32 *list, u32 cnt, const u32 *poff, const u32 *pred, u32 *rem, u32 *next,
+                             u32 *next_cnt, u32 *huge, u32 *nhuge) {
+  const int lane = threadIdx.x & 31;
+  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < cnt; base += gridDim.x * blockDim.x) {
+    const u32 i = base + lane;
+    u32 b = 0, e = 0;
+    if (i < cnt) {
+      const u32 c = list[i];
+      b = poff[c];
+      e = poff[c + 1];
+      if (e - b > kDpHuge) {
+        huge[atomicAdd(nhuge, 1u)] = c;
+        e = b;
+      }
     }
-    u32 c = list[lo];
-    u32 p = pred[poff[c] + (i - pos[lo])];
-    if (atomicSub(&rem[p], 1u) == 1u) next[atomicAdd(next_cnt, 1u)] = p;
+    const bool light = e - b <= 32;
+    const u32 np = light ? e - b : 0;
+    const u32 maxn = __reduce_max_sync(FULL, np);
+    for (u32 j = 0; j < maxn; ++j) {
+      u32 p = 0;
+      bool rel = false;
+      if (j < np) {
+        p = pred[b + j];
+        rel = atomicSub(&rem[p], 1u) == 1u;
+      }
+      ready_append(rel, p, next, next_cnt, lane);
+    }
+    for (unsigned hv = __ballot_sync(FULL, !light); hv; hv &= hv - 1) {
+      const int src = __ffs(hv) - 1;
+      const u32 hb = __shfl_sync(FULL, b, src), he = __shfl_sync(FULL, e, src);
+      for (u32 k0 = hb; k0 < he; k0 += 32) {
+        const u32 k = k0 + lane;
+        u32 p = 0;
+        bool rel = false;
+        if (k < he) {
+          p = pred[k];
+          rel = atomicSub(&rem[p], 1u) == 1u;
+        }
+        ready_append(rel, p, next, next_cnt, lane);
+      }
+    }
+  }
+}
+
+// The listed SCCs with more than kDpHuge predecessors, each by the whole grid.
+__global__ void k_dp_release_huge(const u32 *huge, const u32 *nhuge, const u32 *poff, const u32 *pred, u32 *rem,
+                                  u32 *next, u32 *next_cnt) {
+  const int lane = threadIdx.x & 31;
+  const u32 nh = *nhuge;
+  for (u32 h = 0; h < nh; ++h) {
+    const u32 c = huge[h];
+    const u32 b = poff[c], e = poff[c + 1];
+    for (u32 k0 = b + ((blockIdx.x * blockDim.x + threadIdx.x) & ~31u); k0 < e; k0 += gridDim.x * blockDim.x) {
+      const u32 k = k0 + lane;
+      u32 p = 0;
+      bool rel = false;
+      if (k < e) {
+        p = pred[k];
+        rel = atomicSub(&rem[p], 1u) == 1u;
+      }
+      ready_append(rel, p, next, next_cnt, lane);
+    }
   }
 }
 
@@ -515,8 +770,8 @@ int reach_directed_gpu(tkc_graph *g) {
       // trimmed vertex is its own SCC, so the intersection is the same, and
       // the full reach sets serve again below when this SCC is the biggest.
       u32 pivot = 0xffffffffu - (u32)(hb & 0xffffffffu);
-      TKC_RC(bfs_levels(g->off, g->col, n, g->arcs, nullptr, fw, pivot, flag, st));
-      TKC_RC(bfs_levels(g->ioff, g->icol, n, g->arcs, nullptr, bw, pivot, flag, st));
+      TKC_RC(bfs_reach(g->ctx, g->off, g->col, g->ioff, g->icol, n, g->arcs, fw, pivot, st));
+      TKC_RC(bfs_reach(g->ctx, g->ioff, g->icol, g->off, g->col, n, g->arcs, bw, pivot, st));
       TKC_LAUNCH(k_fwbw_mark<<<grid_of(n), 256, 0, st>>>(fw, bw, n, active, comp, pivot));
       pivot0 = pivot;
       continue;  // trim again, then colour
@@ -563,17 +818,22 @@ int reach_directed_gpu(tkc_graph *g) {
   // (backward); only reachability is used, the same from every vertex of the
   // SCC, so the first pivot's sweeps serve when it lies in the biggest SCC
   if (big != pivot0) {
-    TKC_RC(bfs_levels(g->off, g->col, n, g->arcs, nullptr, fw, big, flag, st));
-    TKC_RC(bfs_levels(g->ioff, g->icol, n, g->arcs, nullptr, bw, big, flag, st));
+    TKC_RC(bfs_reach(g->ctx, g->off, g->col, g->ioff, g->icol, n, g->arcs, fw, big, st));
+    TKC_RC(bfs_reach(g->ctx, g->ioff, g->icol, g->off, g->col, n, g->arcs, bw, big, st));
   }
   TKC_TRY(cudaMemsetAsync(flag, 0, sizeof(u32), st));
   TKC_LAUNCH(k_count_reached<<<grid_of(n), 256, 0, st>>>(fw, n, flag));
   const u64 reach_big = read_u32(flag, st, &rc);
   TKC_RC(rc);
   // condensation arcs, sorted by (cu, cv) and deduplicated
-  TKC_TRY(cudaMemsetAsync(flag, 0, sizeof(u32), st));
-  TKC_LAUNCH(k_cross_count<<<grid_of((u64)n * 32), 256, 0, st>>>(g->off, g->col, comp, n, flag));
-  const u32 m = read_u32(flag, st, &rc);
+  const unsigned cross_grid = grid_of((u64)n * 32);
+  u32 *blk = nullptr, *blk_tmp = nullptr;
+  TKC_TRY(b.get(&blk, (size_t)cross_grid + 1));
+  TKC_TRY(b.get(&blk_tmp, ((size_t)cross_grid + 1) / 4096 + 2));
+  TKC_TRY(cudaMemsetAsync(blk + cross_grid, 0, sizeof(u32), st));
+  TKC_LAUNCH(k_cross<false><<<cross_grid, 256, 0, st>>>(g->off, g->col, comp, n, blk, nullptr, nullptr));
+  TKC_RC(scan_exclusive_u32(blk, blk, (u64)cross_grid + 1, blk_tmp, st));
+  const u32 m = read_u32(blk + cross_grid, st, &rc);
   TKC_RC(rc);
   u32 *cu, *cv, *pos, *tmp, *su, *sv, *soff, *poff, *pcur, *pred, *rem, *listA, *listB;
   u64 *A, *O;
@@ -586,8 +846,7 @@ int reach_directed_gpu(tkc_graph *g) {
   TKC_TRY(b.get(&poff, (size_t)n + 1));
   TKC_TRY(b.get(&pcur, n));
   TKC_TRY(b.get(&tmp, (std::max<size_t>(m, n) + 1) / 4096 + 2));
-  TKC_TRY(cudaMemsetAsync(flag, 0, sizeof(u32), st));
-  TKC_LAUNCH(k_cross_emit<<<grid_of((u64)n * 32), 256, 0, st>>>(g->off, g->col, comp, n, flag, cu, cv));
+  TKC_LAUNCH(k_cross<true><<<cross_grid, 256, 0, st>>>(g->off, g->col, comp, n, blk, cu, cv));
   int bits = 0;
   while (bits < 32 && ((n - 1) >> bits) != 0) ++bits;
   TKC_RC(radix_sort_u32_pairs(cv, cu, m, bits, st));  // by target
@@ -615,17 +874,17 @@ int reach_directed_gpu(tkc_graph *g) {
   TKC_LAUNCH(k_sinks<<<grid_of(n), 256, 0, st>>>(wgt, soff, n, rem, listA, flag));
   u32 cnt = read_u32(flag, st, &rc);
   TKC_RC(rc);
-  u32 *cur_list = listA, *nxt_list = listB, *ppos = nullptr, *ptmp = nullptr;
-  TKC_TRY(b.get(&ppos, (size_t)n + 1));
-  TKC_TRY(b.get(&ptmp, ((size_t)n + 1) / 4096 + 2));
+  u32 *cur_list = listA, *nxt_list = listB, *huge = nullptr;
+  TKC_TRY(b.get(&huge, (size_t)mu / kDpHuge + 1));
   for (u32 round = 0; cnt > 0; ++round) {
     if (round > n) return TKC_ETIMEOUT;
-    TKC_TRY(cudaMemsetAsync(flag + 1, 0, sizeof(u32), st));
-    TKC_LAUNCH(k_dp_eval<<<grid_of((u64)cnt * 32), 256, 0, st>>>(cur_list, cnt, soff, sv, wgt, fw, bw, big,
-                                                                    reach_big, n, A, O, ppos, poff));
-    TKC_RC(scan_exclusive_u32(ppos, ppos, (u64)cnt + 1, ptmp, st));
-    TKC_LAUNCH(k_dp_release<<<grid_of((u64)cnt * 8), 256, 0, st>>>(cur_list, cnt, ppos, poff, pred, rem, nxt_list,
-                                                                     flag + 1));
+    TKC_TRY(cudaMemsetAsync(flag + 1, 0, 2 * sizeof(u32), st));
+    TKC_LAUNCH(k_dp_eval<<<grid_of(cnt), 256, 0, st>>>(cur_list, cnt, soff, sv, wgt, fw, bw, big, reach_big, n, A,
+                                                         O));
+    TKC_LAUNCH(k_dp_release<<<grid_of(cnt), 256, 0, st>>>(cur_list, cnt, poff, pred, rem, nxt_list, flag + 1, huge,
+                                                            flag + 2));
+    TKC_LAUNCH(k_dp_release_huge<<<grid_of((u64)mu / 4 + 1), 256, 0, st>>>(huge, flag + 2, poff, pred, rem,
+                                                                             nxt_list, flag + 1));
     TKC_TRY(cudaGetLastError());
     cnt = read_u32(flag + 1, st, &rc);
     TKC_RC(rc);
