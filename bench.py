@@ -80,14 +80,14 @@ def hbm_peak():
 
 
 def ncu_traffic(workload: str, order: str, bits: int):
-    """Per-launch DRAM bytes of the search kernel from a committed ncu summary,
-    only if it was taken on the current kernel source."""
+    """DRAM bytes per step (all launches) of the search kernel from a committed
+    ncu summary, only if it was taken on the current kernel source."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
         e = d.get(f"{workload}_{order}_b{bits}")
         if e and e.get("kernel_sha") == kernel_hash():
-            return e["dram_bytes_per_launch"], e
+            return e["dram_bytes_per_step"], e
     except Exception:
         pass
     return None, None
@@ -229,8 +229,11 @@ def matches_fixture(results, fx, k, graphs, measure="closeness"):
 
 
 def survey_level_bytes(st) -> float:
-    """Algorithmic bytes of the level kernels by the per-level formula of the
-    design plan (B-bit rows of B/8 bytes):
+    """Bytes of the level kernels by the per-level formula of the design plan
+    (B-bit rows of B/8 bytes), reported beside the kernel's own count: it
+    charges three row sweeps of all n vertices at every level, which this
+    kernel does not perform (it touches only listed vertices), so on runs of
+    many short levels it exceeds what any memory could move in the time:
       top-down : sum over frontier u of (8 + 4 outdeg(u) + B/8)
                  + 2 (B/8) sum over frontier u of outdeg(u) + 3 (B/8) n
       bottom-up: sum over scanned w of (8 + (4 + B/8) scanned_in(w)) + 3 (B/8) n
@@ -480,22 +483,25 @@ def main():
     kern_ms = statistics.mean(st["ms_kernel"] for st in stats)
     kern_bytes = statistics.mean(st["alg_bytes"] for st in stats)
     plan_bytes = statistics.mean(survey_level_bytes(st) for st in stats)
-    achieved = plan_bytes / (kern_ms / 1e3) / 1e9
-    achieved_k = kern_bytes / (kern_ms / 1e3) / 1e9
+    achieved = kern_bytes / (kern_ms / 1e3) / 1e9
+    achieved_plan = plan_bytes / (kern_ms / 1e3) / 1e9
     traffic, traffic_entry = (ncu_traffic(args.workload, args.order, res.batch_bits)
                               if args.measure == "closeness" and args.bound == "cut" else (None, None))
     launches_per_step = stats[-1]["launches"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_src,
-                "bytes_model": "per-level formula of the design plan (top-down: frontier rows, columns and 2 row "
-                               "updates per arc, 3 row sweeps of n; bottom-up: scanned in-arcs and rows, 3 row "
-                               "sweeps of n), from tkc_last_run_stats",
-                "alg_bytes_per_step": plan_bytes, "kernel_ms_per_step": kern_ms,
-                "launches_per_step": launches_per_step,
-                "achieved_kernel_model": achieved_k, "frac_kernel_model": achieved_k / peak,
-                "kernel_model_bytes_per_step": kern_bytes}
+                "bytes_model": "the level kernels' own accesses at their load sizes (top-down: per frontier vertex "
+                               "its list entry, offsets, row read and clear; per frontier arc its column, the "
+                               "target's seen row and next-row update; per new vertex list, seen and row writes. "
+                               "Bottom-up: per swept vertex its list entry and seen row; per scanned vertex its "
+                               "in-offsets; per scanned in-arc its column and frontier-bitmap word; per frontier "
+                               "in-neighbour found its row; per new vertex list, seen and row writes) -- "
+                               "tkc_result.alg_bytes, summed on the device",
+                "alg_bytes_per_step": kern_bytes, "kernel_ms_per_step": kern_ms,
+                "launches_per_step": launches_per_step, "per": "step (all launches of the search kernel)",
+                "plan_formula_bytes_per_step": plan_bytes, "achieved_plan_formula": achieved_plan}
     if traffic is not None:
-        roofline["traffic_frac"] = traffic * launches_per_step / (kern_ms / 1e3) / 1e9 / peak
+        roofline["traffic_frac"] = traffic / (kern_ms / 1e3) / 1e9 / peak
 
     last = results[-1]
     st = stats[-1]

@@ -340,6 +340,8 @@ typedef struct {
   uint64_t bu_scanned_arcs;     /* in-arcs walked (up to each early exit) */
   uint64_t bu_new;              /* vertices discovered by bottom-up levels */
   uint64_t bu_frontier;         /* frontier vertices of the bottom-up levels (their rows are cleared) */
+  uint64_t bu_rows_read;        /* frontier rows the bottom-up walks loaded (in-neighbours on the frontier) */
+  uint64_t bu_swept;            /* vertices the bottom-up levels swept (those with an in-arc, per level) */
   uint64_t seeded;              /* searches started in a slot */
   uint64_t cleared;             /* rows zeroed by the clear steps between batches */
   uint64_t compactions;         /* frontier lists compacted to the searches still active after a cut */

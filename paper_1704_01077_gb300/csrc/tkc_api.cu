@@ -437,6 +437,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
       hctl->st_bu_scan_a += x.st_bu_scan_a;
       hctl->st_bu_new += x.st_bu_new;
       hctl->st_bu_frontier += x.st_bu_frontier;
+      hctl->st_bu_rows += x.st_bu_rows;
       hctl->st_seeded += x.st_seeded;
       hctl->st_cleared += x.st_cleared;
       hctl->st_compactions += x.st_compactions;
@@ -489,6 +490,8 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
     rs_out.bu_scanned_arcs = hctl->st_bu_scan_a;
     rs_out.bu_new = hctl->st_bu_new;
     rs_out.bu_frontier = hctl->st_bu_frontier;
+    rs_out.bu_rows_read = hctl->st_bu_rows;
+    rs_out.bu_swept = (uint64_t)(g->bu_list ? g->n_bu : g->n) * hctl->st_bu_levels;
     rs_out.seeded = hctl->st_seeded;
     rs_out.cleared = hctl->st_cleared;
     rs_out.compactions = hctl->st_compactions;

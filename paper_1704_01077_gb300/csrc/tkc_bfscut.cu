@@ -746,9 +746,12 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
       //  top-down : per frontier vertex list+offsets (16) + F row read and clear;
       //             per frontier arc column (4) + seen row read + N row update;
       //             per new vertex list (8) + N read/clear, seen read/write, F write
-      //  bottom-up: every seen row; per scanned vertex in-offsets (8); per scanned
-      //             in-arc column (4) + F row; per new vertex seen/F writes + list (8);
-      //             per old frontier vertex list (4) + F row clear
+      //  bottom-up: per swept list entry (vertices with an in-arc) the entry (4)
+      //             and its seen row; per scanned vertex in-offsets (8); per
+      //             scanned in-arc its column (4) and frontier-bitmap word (4);
+      //             per frontier in-neighbour found its F row; per new vertex
+      //             seen/F writes + list (8); per old frontier vertex list (4) +
+      //             F row clear
       const u64 rb = 8ull * W;
       const u64 fl = c->fl_count, fa = c->fl_arcs, nl = packed >> kPackShift;
       u64 bytes;
@@ -759,8 +762,11 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
         c->st_td_arcs += fa;
         c->st_td_new += nl;
       } else {
-        bytes = (u64)p.n * rb + c->lvl_scan_v * 8 + c->lvl_scan_a * (4 + rb) + nl * (8 + 2 * rb) + fl * (4 + rb);
+        const u64 swept = p.bu_list ? p.n_bu : p.n;
+        bytes = swept * (4 + rb) + c->lvl_scan_v * 8 + c->lvl_scan_a * 8 + c->lvl_scan_r * rb + nl * (8 + 2 * rb) +
+                fl * (4 + rb);
         c->st_bu_levels += 1;
+        c->st_bu_rows += c->lvl_scan_r;
         c->st_bu_scan_v += c->lvl_scan_v;
         c->st_bu_scan_a += c->lvl_scan_a;
         c->st_bu_new += nl;
@@ -785,6 +791,7 @@ __device__ void epilogue_level(const RunParams &p, Smem<W> &sm) {
       }
       c->lvl_scan_v = 0;
       c->lvl_scan_a = 0;
+      c->lvl_scan_r = 0;
     }
     c->nl_packed = 0;
     c->cur ^= 1;
@@ -1128,6 +1135,7 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
     }
     __syncthreads();
     u64 scanned = 0, scanned_v = 0;
+    uint32_t rows_read = 0;
     if (dir == 0) {
       // ---- phase A, top-down: OR each frontier row into its out-neighbours' N rows
       constexpr uint32_t APS = 32 / W;  // arcs per warp step
@@ -1297,6 +1305,7 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
                   if (fb[j]) {
                     u64 fr[W];
                     load_row<W>(Fcur, uu[j], fr);
+                    ++rows_read;
 #pragma unroll
                     for (int q = 0; q < W; ++q) nw[q] |= fr[q] & miss[q];
                   }
@@ -1352,6 +1361,7 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
                 if (fb[j]) {
                   u64 fr[W];
                   load_row<W>(Fcur, uu[j], fr);
+                  ++rows_read;
 #pragma unroll
                   for (int q = 0; q < W; ++q) acc[q] |= fr[q] & hm[q];
                 }
@@ -1412,13 +1422,16 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
     }
     if (tb == 0) trace_stamp(p, 11);
     // flush the block's per-slot counters
+    u64 rows64 = rows_read;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       scanned += __shfl_down_sync(FULL, scanned, o);
       scanned_v += __shfl_down_sync(FULL, scanned_v, o);
+      rows64 += __shfl_down_sync(FULL, rows64, o);
     }
     if (lane == 0 && scanned) atomicAdd(&sm.acc[3], scanned);
     if (lane == 0 && scanned_v) atomicAdd(&sm.acc[2], scanned_v);
+    if (lane == 0 && rows64) atomicAdd(&c->lvl_scan_r, rows64);
     __syncthreads();
     for (int i = threadIdx.x; i < 64 * W; i += TPB) {
       if (sm.cnt[i]) {

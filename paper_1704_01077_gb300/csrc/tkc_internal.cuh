@@ -79,12 +79,13 @@ struct Ctl {
   unsigned long long alg_bytes;
   unsigned long long lvl_scan_v;
   unsigned long long lvl_scan_a;
+  unsigned long long lvl_scan_r;  // this level's frontier rows loaded by the bottom-up walks
   unsigned long long trace_n;  // records written to the optional trace
   unsigned int bdepth;         // depth reached by the current batch (0 after seeding)
   unsigned int pad1;
   // per-level totals of the run (tkc_last_run_stats)
   unsigned long long st_td_levels, st_td_frontier, st_td_arcs, st_td_new;
-  unsigned long long st_bu_levels, st_bu_scan_v, st_bu_scan_a, st_bu_new, st_bu_frontier;
+  unsigned long long st_bu_levels, st_bu_scan_v, st_bu_scan_a, st_bu_new, st_bu_frontier, st_bu_rows;
   unsigned long long st_seeded, st_cleared;
   unsigned long long st_compactions, st_compact_dropped;
   int lcur;          // which list buffer holds the current frontier list (compaction swaps it alone)

@@ -72,7 +72,8 @@ class tkc_run_stats(ctypes.Structure):
                 ("arcs", ctypes.c_uint64), ("td_levels", ctypes.c_uint64), ("td_frontier", ctypes.c_uint64),
                 ("td_frontier_arcs", ctypes.c_uint64), ("td_new", ctypes.c_uint64), ("bu_levels", ctypes.c_uint64),
                 ("bu_scanned_vertices", ctypes.c_uint64), ("bu_scanned_arcs", ctypes.c_uint64),
-                ("bu_new", ctypes.c_uint64), ("bu_frontier", ctypes.c_uint64), ("seeded", ctypes.c_uint64),
+                ("bu_new", ctypes.c_uint64), ("bu_frontier", ctypes.c_uint64), ("bu_rows_read", ctypes.c_uint64),
+                ("bu_swept", ctypes.c_uint64), ("seeded", ctypes.c_uint64),
                 ("cleared", ctypes.c_uint64), ("compactions", ctypes.c_uint64), ("compacted_away", ctypes.c_uint64),
                 ("alg_bytes", ctypes.c_uint64), ("ms_kernel", ctypes.c_double)]
 

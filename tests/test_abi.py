@@ -50,9 +50,9 @@ def test_struct_layouts_match_header():
     assert tkc.tkc_result.edges_visited.offset == 56
     assert tkc.tkc_result.ms_bfs.offset == 120
     assert tkc.tkc_options.deterministic.offset == 60
-    # 6 x uint32, 15 x uint64, 1 double
-    assert ctypes.sizeof(tkc.tkc_run_stats) == 152
-    assert tkc.tkc_run_stats.ms_kernel.offset == 144
+    # 6 x uint32, 17 x uint64, 1 double
+    assert ctypes.sizeof(tkc.tkc_run_stats) == 168
+    assert tkc.tkc_run_stats.ms_kernel.offset == 160
 
 
 def test_struct_layouts_match_a_c_compiler(tmp_path):

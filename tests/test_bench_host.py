@@ -10,7 +10,7 @@ import bench
 
 def test_traffic_only_for_the_current_kernel(tmp_path, monkeypatch):
     entry = {"kernel_sha": bench.kernel_hash(), "dram_bytes_read": 70, "dram_bytes_write": 30,
-             "dram_bytes_per_launch": 100}
+             "dram_bytes_per_step": 100}
     cur = tmp_path / "traffic.json"
     cur.write_text(json.dumps({"rmat22_nb_b128": entry}))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(cur))
@@ -29,7 +29,7 @@ def test_committed_traffic_entries_are_consistent():
     if not os.path.exists(bench.TRAFFIC_FILE):
         return
     for v in json.load(open(bench.TRAFFIC_FILE)).values():
-        assert v["dram_bytes_read"] + v["dram_bytes_write"] == v["dram_bytes_per_launch"]
+        assert v["dram_bytes_read"] + v["dram_bytes_write"] == v["dram_bytes_per_step"]
 
 
 def test_fixed_work_and_fixture_check():
