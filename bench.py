@@ -151,15 +151,19 @@ def dist_env():
     return rank, world, local
 
 
-def reduce_over_ranks(ms_total, edges, dist, device):
-    """Whole-job figures of a replicated run: the slowest rank's time and the
-    arcs of all ranks (one rank, dist None: unchanged)."""
+def reduce_over_ranks(ms_total, edges, dist, device, shared=False):
+    """Whole-job figures over the ranks: the slowest rank's time, and the work
+    of all ranks -- summed when each rank ran its own replica, taken once when
+    the ranks shared one query (shared=True: sources sharded over the ranks).
+    One rank (dist None): unchanged."""
     if not dist:
         return float(ms_total), float(edges)
     import torch
 
     t = torch.tensor([float(ms_total)], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    if shared:
+        return float(t.item()), float(edges)
     e = torch.tensor([float(edges)], device=device, dtype=torch.float64)
     dist.all_reduce(e)
     return float(t.item()), float(e.item())
@@ -394,9 +398,40 @@ def main():
                          "ids", "dist_sum", "reach", "closeness"):
                 setattr(self, name, getattr(r0, name))
 
+    # several GPUs on one graph: the sources are sharded over the ranks (the
+    # k best entries exchanged after an opening batch and at the end)
+    sharded = world > 1 and not multi and args.measure == "closeness" and args.bound == "cut" and \
+        args.order in ("nb", "degree")
+    if sharded:
+        from types import SimpleNamespace
+
+        from paper_1704_01077_gb300 import shard
+
+        allgather, allreduce = shard.torch_exchange(dist)
+        opening = args.bits or (128 if args.order == "nb" and g.n >= (1 << 16) else 64)
+
+    def run_sharded(h):
+        ls = shard.LibraryShard(tkc, h, k, rank, world)
+        kk = min(k, g.n)
+        res = shard.topk_sharded(ls, kk, opening, allgather, allreduce)
+        mine = ls.last
+        S = np.array([e[0] for e in res.entries], np.uint64)
+        r = np.array([e[1] for e in res.entries], np.uint32)
+        far = np.array([float(g.n - 1) * float(a) / float((int(b) - 1) ** 2) if b > 1 else float("inf")
+                        for a, b in zip(S, r)])
+        view = SimpleNamespace(ids=np.array([e[2] for e in res.entries], np.uint32), dist_sum=S, reach=r,
+                               farness=far, closeness=np.where(far > 0, 1.0 / far, 0.0),
+                               n_tied_at_kth=res.n_tied_at_kth)
+        for name in ("edges_visited", "bfs_started", "bfs_cut", "bfs_finished", "edges_scanned", "levels", "ms_pre",
+                     "ms_bfs", "ms_kernel", "alg_bytes", "batch_bits"):
+            setattr(view, name, getattr(mine, name))
+        return Step([view])
+
     def run_step(csr):
         hs = [tkc.tkc_load_csr(ctx, x.n, o, c, x.directed) for x, (o, c) in zip(graphs, csr)]
         try:
+            if sharded:
+                return run_sharded(hs[0])
             if args.bound == "lb":
                 if multi or args.measure != "closeness":
                     raise SystemExit("--bound lb runs closeness on one graph")
@@ -461,7 +496,7 @@ def main():
     # fixed work per step: the plain one-source NBCut's arcs (oracle-counted);
     # without a stored oracle result, the batched search's own arcs
     work = work_fixed if work_fixed is not None else statistics.mean(r.edges_visited for r in results)
-    ms_total, total_work = reduce_over_ranks(ev0.elapsed_time(ev1), work * args.steps, dist, dev)
+    ms_total, total_work = reduce_over_ranks(ev0.elapsed_time(ev1), work * args.steps, dist, dev, shared=sharded)
     value = total_work / (ms_total / 1e3) / 1e9
     ms_step = ms_total / args.steps
 
@@ -473,7 +508,8 @@ def main():
     t0 = time.perf_counter()
     e2e_res = [step_host() for _ in range(e2e_steps)]
     torch.cuda.synchronize()
-    e2e_ms, e2e_work = reduce_over_ranks((time.perf_counter() - t0) * 1e3, work * e2e_steps, dist, dev)
+    e2e_ms, e2e_work = reduce_over_ranks((time.perf_counter() - t0) * 1e3, work * e2e_steps, dist, dev,
+                                         shared=sharded)
     e2e_value = e2e_work / (e2e_ms / 1e3) / 1e9
     h2d = sum(4 * (x.n + 1) + 4 * x.arcs for x in graphs)
     d2h = len(graphs) * k * (4 + 8 + 4 + 8 + 8)
@@ -507,7 +543,7 @@ def main():
     st = stats[-1]
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "k": k, "batch_bits": res.batch_bits,
                        "order": args.order, "measure": args.measure, "bound": args.bound,
                        "teams": args.teams or "library default", "deterministic": args.deterministic,
@@ -517,7 +553,8 @@ def main():
                                      "arcs visited by this batched search (no stored oracle count)"),
                        "l2": "inputs larger than L2 (CSR 280 MB + bit rows)" if args.workload in
                        ("rmat22", "multi512", "ba1m") else "small graph: may be L2-resident",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
+                       "parallelism": (f"sources sharded over {world} GPUs, k best entries exchanged over NCCL"
+                                       if sharded else f"replicas x{world}" if world > 1 else "single")},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms / e2e_steps},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk.summary(),
@@ -548,7 +585,8 @@ def main():
         if args.bound == "cut" or args.measure == "closeness":
             line["check"]["top_k_matches_oracle_fixture"] = matches_fixture(last.results, fx, k, graphs,
                                                                             args.measure)
-    if rank == 0 and not args.no_plain and not multi and args.measure == "closeness" and args.bound == "cut":
+    if rank == 0 and world == 1 and not args.no_plain and not multi and args.measure == "closeness" and \
+            args.bound == "cut":
         arms = {}
 
         def arm(name, opts, repeats):
@@ -578,7 +616,7 @@ def main():
             vp["learned_seed_speedup_vs_plain"] = plain_nb / lm
             vp["learned_seed_vs_nbcut_time_ratio"] = lm / ms_step
         line["vs_plain"] = vp
-    if rank == 0 and not args.no_cpu and not multi:
+    if rank == 0 and world == 1 and not args.no_cpu and not multi:
         v, dt, ev = cpu_oracle_sample(g, k, args.sample)
         line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "host": host_cpu(),
                                 "sample": f"first {args.sample} sources of the degree order, sequential CPU "

@@ -259,6 +259,11 @@ struct RunSetup {
   u32 lvl_stride;
   int keep_lists;
   u32 force_teams;
+  // a starting k-list (one graph; host arrays, best first): exact entries of
+  // vertices searched elsewhere, so that x is tight from the start
+  const u64 *seed_S;
+  const u32 *seed_r, *seed_id;
+  u32 nseed;
 };
 
 // Teams used when the options leave it to the library: one team for small
@@ -292,6 +297,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
     TKC_TRY(cudaMemsetAsync(w.stamp, 0xff, (size_t)w.teams_cap * w.n_cap * sizeof(u32), st));
     w.level_base = 0;
   }
+  ctx->last_shard = nullptr;  // this run replaces the finished searches' (S, r)
   if (!rs.keep_lists) {
     TKC_TRY(cudaMemsetAsync(w.res_r, 0, (size_t)g->n * sizeof(u32), st));
     TKC_TRY(cudaMemsetAsync(w.res_S, 0, (size_t)g->n * sizeof(u64), st));
@@ -300,6 +306,19 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
     TKC_TRY(cudaMemsetAsync(w.g_ctr, 0, (size_t)rs.ng * 4 * sizeof(u64), st));
     TKC_TRY(cudaMemsetAsync(w.x_seq, 0, (size_t)rs.ng * sizeof(unsigned), st));
     TKC_TRY(cudaMemsetAsync(w.x_r, 0, (size_t)rs.ng * sizeof(u32), st));
+  }
+  if (rs.nseed) {
+    const unsigned ns = rs.nseed;
+    TKC_TRY(cudaMemcpyAsync(w.g_ntop, &ns, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    TKC_TRY(cudaMemcpyAsync(w.top_S, rs.seed_S, ns * sizeof(u64), cudaMemcpyHostToDevice, st));
+    TKC_TRY(cudaMemcpyAsync(w.top_r, rs.seed_r, ns * sizeof(u32), cudaMemcpyHostToDevice, st));
+    TKC_TRY(cudaMemcpyAsync(w.top_id, rs.seed_id, ns * sizeof(u32), cudaMemcpyHostToDevice, st));
+    if (ns == rs.kk) {  // a full list: its k-th entry is the published threshold
+      TKC_TRY(cudaMemcpyAsync(w.x_S, rs.seed_S + ns - 1, sizeof(u64), cudaMemcpyHostToDevice, st));
+      TKC_TRY(cudaMemcpyAsync(w.x_r, rs.seed_r + ns - 1, sizeof(u32), cudaMemcpyHostToDevice, st));
+      TKC_TRY(cudaMemcpyAsync(w.x_id, rs.seed_id + ns - 1, sizeof(u32), cudaMemcpyHostToDevice, st));
+    }
+    TKC_TRY(cudaStreamSynchronize(st));  // the seed arrays are the caller's pageable memory
   }
   RunParams p;
   memset(&p, 0, sizeof(p));
@@ -736,6 +755,7 @@ int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offset
 
 void tkc_free_graph(tkc_graph *g) {
   if (!g) return;
+  if (g->ctx->last_shard == g) g->ctx->last_shard = nullptr;
   cudaSetDevice(g->ctx->device);
   cudaStreamSynchronize(g->ctx->stream);
   if (g->ioff && g->ioff != g->off) cudaFree(g->ioff);
@@ -993,6 +1013,123 @@ static int topk_one(tkc_graph *g, uint32_t k, tkc_result *out, int harmonic) {
   r.ms_pre = ms0;
   r.ms_bfs = ms1;
   r.ms_kernel = ms2;
+  *out = r;
+  return TKC_OK;
+}
+
+// The positions shard, shard + nshards, ... of a source order (at most
+// `limit` of them, 0 = all).
+__global__ void k_shard_order(const u32 *order, u32 norder, u32 shard, u32 nshards, u32 count, u32 *out) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    out[i] = order[shard + (u64)i * nshards];
+}
+
+// Finished searches of the latest run whose farness equals S/(r-1)^2 exactly.
+__global__ void k_count_key(const u64 *res_S, const u32 *res_r, u32 n, u64 S, u32 r, unsigned *cnt) {
+  unsigned c = 0;
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const u32 rv = res_r[v];
+    if (rv < 2) continue;
+    const unsigned __int128 a = (unsigned __int128)res_S[v] * (unsigned __int128)((u64)(r - 1) * (u64)(r - 1));
+    const unsigned __int128 b = (unsigned __int128)S * (unsigned __int128)((u64)(rv - 1) * (u64)(rv - 1));
+    c += a == b;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+static bool entry_before(u64 Sa, u32 ra, u32 ia, u64 Sb, u32 rb, u32 ib) {
+  const unsigned __int128 l = (unsigned __int128)Sa * (unsigned __int128)((u64)(rb - 1) * (u64)(rb - 1));
+  const unsigned __int128 h = (unsigned __int128)Sb * (unsigned __int128)((u64)(ra - 1) * (u64)(ra - 1));
+  return l != h ? l < h : ia < ib;
+}
+
+// Algorithm 1 over one shard of the source order (see tkc_topk_closeness_shard).
+static int topk_shard(tkc_graph *g, uint32_t k, uint32_t shard, uint32_t nshards, uint32_t limit, const uint64_t *seed_S,
+                      const uint32_t *seed_r, const uint32_t *seed_id, uint32_t nseed, tkc_result *out) {
+  if (!g || !out || nshards == 0 || shard >= nshards || k > TKC_MAX_K) return TKC_EINVAL;
+  if (nseed && (!seed_S || !seed_r || !seed_id)) return TKC_EINVAL;
+  tkc_ctx *ctx = g->ctx;
+  const tkc_options &o = ctx->opt;
+  if (o.order != TKC_ORDER_DEG && o.order != TKC_ORDER_NB) return TKC_EINVAL;
+  const u32 kk = std::min<u32>(k, g->n);
+  if (kk > 0 && out->capacity < kk) return TKC_EINVAL;
+  if (nseed > kk) return TKC_EINVAL;
+  for (u32 i = 0; i < nseed; ++i) {
+    if (seed_id[i] >= g->n || seed_r[i] < 2 || seed_r[i] > g->n) return TKC_EINVAL;
+    if (i && !entry_before(seed_S[i - 1], seed_r[i - 1], seed_id[i - 1], seed_S[i], seed_r[i], seed_id[i]))
+      return TKC_EINVAL;  // best first, no repeats
+  }
+  TKC_TRY(cudaSetDevice(ctx->device));
+  tkc_result r = *out;
+  reset_result(&r, kk);
+  if (kk == 0) {
+    *out = r;
+    return TKC_OK;
+  }
+  cudaStream_t st = ctx->stream;
+  TKC_TRY(cudaEventRecord(ctx->ev[0], st));
+  TKC_RC(ensure_degree_order(g));
+  TKC_RC(ensure_reach_bounds(g));
+  RunSetup rs;
+  memset(&rs, 0, sizeof(rs));
+  const u32 *full = nullptr;
+  u32 nfull = 0;
+  TKC_RC(source_order_of(g, o, kk, 0, &full, &nfull, &rs.lb_key));
+  u32 count = nfull > shard ? (nfull - shard + nshards - 1) / nshards : 0;
+  if (limit && count > limit) count = limit;
+  u32 *sorder = nullptr;
+  TKC_TRY(cudaMallocAsync(&sorder, std::max<size_t>(count, 1) * sizeof(u32), st));
+  if (count)
+    TKC_LAUNCH(k_shard_order<<<(count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096, 256, 0, st>>>(
+        full, nfull, shard, nshards, count, sorder));
+  TKC_TRY(cudaEventRecord(ctx->ev[1], st));
+  const u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g->n, rs.lb_key != nullptr);
+  rs.g = g;
+  rs.order = sorder;
+  rs.norder = count;
+  rs.B = bits;
+  rs.W = words_for(bits);
+  rs.kk = kk;
+  rs.ng = 1;
+  rs.seed_S = reinterpret_cast<const u64 *>(seed_S);
+  rs.seed_r = seed_r;
+  rs.seed_id = seed_id;
+  rs.nseed = nseed;
+  r.batch_bits = bits;
+  Ctl hc;
+  memset(&hc, 0, sizeof(hc));
+  const int rc_run = run_search(ctx, rs, &hc);  // also with no source: the list is the seed
+  TKC_TRY(cudaFreeAsync(sorder, st));
+  TKC_RC(rc_run);
+  std::vector<GraphOut> go(1);
+  go[0].n = g->n;
+  go[0].base = 0;
+  go[0].kk = kk;
+  go[0].nzero = g->n - g->n_src_deg;
+  go[0].zero_ids = g->deg_order + g->n_src_deg;
+  std::vector<unsigned> ntop, tied;
+  std::vector<u64> gctr;
+  TKC_RC(finish_run(ctx, rs, go, &r, ntop, tied, gctr));
+  TKC_TRY(cudaEventRecord(ctx->ev[2], st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  r.n_tied_at_kth = tied[0];
+  r.edges_visited = hc.edges_visited;
+  r.edges_scanned = hc.edges_scanned;
+  r.bfs_started = hc.bfs_started;
+  r.bfs_cut = hc.bfs_cut;
+  r.bfs_finished = hc.bfs_finished;
+  r.levels = hc.levels;
+  r.alg_bytes = hc.alg_bytes;
+  float ms0 = 0, ms1 = 0;
+  cudaEventElapsedTime(&ms0, ctx->ev[0], ctx->ev[1]);
+  cudaEventElapsedTime(&ms1, ctx->ev[1], ctx->ev[2]);
+  r.ms_pre = ms0;
+  r.ms_bfs = ms1;
+  float ms2 = 0;
+  cudaEventElapsedTime(&ms2, ctx->ev[4], ctx->ev[5]);
+  r.ms_kernel = ms2;
+  ctx->last_shard = g;
   *out = r;
   return TKC_OK;
 }
@@ -1483,6 +1620,33 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
 }
 
 int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) { return topk_one(g, k, out, 0); }
+
+int tkc_topk_closeness_shard(tkc_graph *g, uint32_t k, uint32_t shard, uint32_t nshards, uint32_t max_sources,
+                             const uint64_t *seed_S, const uint32_t *seed_r, const uint32_t *seed_id, uint32_t nseed,
+                             tkc_result *out) {
+  return topk_shard(g, k, shard, nshards, max_sources, seed_S, seed_r, seed_id, nseed, out);
+}
+
+int tkc_count_tied(tkc_graph *g, uint64_t S, uint32_t r, uint32_t *count) {
+  if (!g || !count || r < 2) return TKC_EINVAL;
+  if (g->ctx->last_shard != g) return TKC_EINVAL;
+  tkc_ctx *ctx = g->ctx;
+  TKC_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  unsigned *d = nullptr;
+  TKC_TRY(cudaMallocAsync(&d, sizeof(unsigned), st));
+  TKC_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned), st));
+  const u32 n = g->n;
+  const unsigned blocks = (unsigned)std::max<u64>(1, std::min<u64>(((u64)n + 255) / 256, (u64)ctx->num_sms * 8));
+  if (n) TKC_LAUNCH(k_count_key<<<blocks, 256, 0, st>>>(ctx->ws.res_S, ctx->ws.res_r, n, S, r, d));
+  TKC_TRY(cudaGetLastError());
+  unsigned h = 0;
+  TKC_TRY(cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaFreeAsync(d, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  *count = h;
+  return TKC_OK;
+}
 
 int tkc_topk_harmonic(tkc_graph *g, uint32_t k, tkc_result *out) { return topk_one(g, k, out, 1); }
 

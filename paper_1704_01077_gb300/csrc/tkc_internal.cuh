@@ -248,6 +248,7 @@ struct TuneEntry {
 struct tkc_ctx {
   int device = 0;
   tkc_run_stats last_stats{};  // per-level totals of the latest search-kernel run
+  const tkc_graph *last_shard = nullptr;  // graph of the latest run, when it was a shard run
   MlpState mlp;
   std::map<std::string, TuneEntry> tune;  // graph class -> fastest parameters
   cudaStream_t stream = nullptr;

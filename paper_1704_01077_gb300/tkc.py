@@ -83,7 +83,8 @@ EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc
             "tkc_reach_bounds", "tkc_distance_sums", "tkc_distance_sums_noalloc", "tkc_kernel_launches",
             "tkc_strerror", "tkc_vertex_features", "tkc_mlp_init", "tkc_set_source_model", "tkc_get_source_model",
             "tkc_mlp_forward", "tkc_mlp_gradient", "tkc_mlp_train_step", "tkc_autotune", "tkc_nb_bounds",
-            "tkc_topk_harmonic", "tkc_topk_harmonic_multi", "tkc_nb_harmonic_bounds", "tkc_topk_closeness_bound", "tkc_last_run_stats"]
+            "tkc_topk_harmonic", "tkc_topk_harmonic_multi", "tkc_nb_harmonic_bounds", "tkc_topk_closeness_bound", "tkc_last_run_stats", "tkc_topk_closeness_shard",
+            "tkc_count_tied"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -126,6 +127,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                             ctypes.POINTER(tkc_result)]
     lib.tkc_nb_harmonic_bounds.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double), u32p, u32p]
     lib.tkc_last_run_stats.argtypes = [vp, ctypes.POINTER(tkc_run_stats)]
+    lib.tkc_topk_closeness_shard.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                             u64p, u32p, u32p, ctypes.c_uint32, ctypes.POINTER(tkc_result)]
+    lib.tkc_count_tied.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32, u32p]
     lib.tkc_kernel_launches.argtypes = []
     lib.tkc_kernel_launches.restype = ctypes.c_uint64
     lib.tkc_strerror.argtypes = [ctypes.c_int]
@@ -296,6 +300,32 @@ def tkc_topk_closeness(g, k: int, capacity: int | None = None) -> Result:
     res, arrays = _new_result(cap)
     _check(_lib.tkc_topk_closeness(g, k, ctypes.byref(res)), "tkc_topk_closeness")
     return _to_result(res, arrays)
+
+
+def tkc_topk_closeness_shard(g, k: int, shard: int, nshards: int, max_sources: int = 0, seed=None,
+                             capacity: int | None = None) -> Result:
+    """One shard of the source order (see include/tkc.h); seed = (S, r, ids)
+    host arrays, best first, or None."""
+    cap = k if capacity is None else capacity
+    res, arrays = _new_result(cap)
+    if seed is None or len(seed[2]) == 0:
+        sS = sr = si = None
+        ns = 0
+    else:
+        sS = np.ascontiguousarray(seed[0], dtype=np.uint64)
+        sr = np.ascontiguousarray(seed[1], dtype=np.uint32)
+        si = np.ascontiguousarray(seed[2], dtype=np.uint32)
+        ns = len(si)
+    _check(_lib.tkc_topk_closeness_shard(g, k, shard, nshards, max_sources, None if sS is None else _u64p(sS),
+                                         None if sr is None else _u32p(sr), None if si is None else _u32p(si), ns,
+                                         ctypes.byref(res)), "tkc_topk_closeness_shard")
+    return _to_result(res, arrays)
+
+
+def tkc_count_tied(g, S: int, r: int) -> int:
+    cnt = ctypes.c_uint32(0)
+    _check(_lib.tkc_count_tied(g, int(S), int(r), ctypes.byref(cnt)), "tkc_count_tied")
+    return int(cnt.value)
 
 
 def tkc_topk_closeness_multi(ctx, graphs, k: int) -> list[Result]:

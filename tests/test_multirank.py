@@ -1,6 +1,7 @@
-"""The multi-GPU path runs independent replicas (one per rank, no data-path
-collective); the only cross-rank step is the bench's reduction of the timed
-figures.  Checked here on CPU with two gloo ranks."""
+"""The bench's reduction of the timed figures over ranks, on CPU with two gloo
+ranks: the slowest rank's time, with the work summed over replicas (each rank
+its own query) or taken once when the ranks shared one query (sources
+sharded; the exchange itself is tested in test_shard.py)."""
 import os
 import socket
 
@@ -22,7 +23,8 @@ def _rank_main(rank, world, port, out):
     import bench
 
     ms, edges = bench.reduce_over_ranks(100.0 + 50.0 * rank, 1_000_000 * (rank + 1), dist, "cpu")
-    out[rank] = (ms, edges)
+    ms2, work = bench.reduce_over_ranks(100.0 + 50.0 * rank, 5_000_000, dist, "cpu", shared=True)
+    out[rank] = (ms, edges, ms2, work)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -34,7 +36,7 @@ def test_two_rank_reduction_takes_slowest_time_and_all_arcs():
         mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
     for rank in range(world):
-        assert res[rank] == (150.0, 3_000_000.0)
+        assert res[rank] == (150.0, 3_000_000.0, 150.0, 5_000_000.0)
 
 
 def test_one_rank_is_unchanged():
