@@ -176,29 +176,32 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out);
  * small), TKC_ENOMEM, TKC_ECUDA, TKC_ETIMEOUT. */
 int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
 
-/* One shard of Algorithm 1 (Section 4) for sharding the sources of one graph
- * over several GPUs, each holding a copy of the graph.  Algorithm 1 is exact
- * for any threshold x that is the k-th best of exactly known farness values,
- * so shard s of nshards searches the sources at positions s, s + nshards,
- * s + 2 nshards, ... of the order options.order gives (TKC_ORDER_DEG or
- * TKC_ORDER_NB; with NB the stop applies to the shard's own positions, still
- * sorted by key), at most max_sources of them (0 = all), starting from a
- * k-list seeded with nseed <= min(k, n) exact entries found by other shards
- * (host arrays seed_S/seed_r/seed_id, best first by farness then id, r >= 2,
- * distinct ids none of which lies in this shard).  The result is the best
- * min(k, n) of the seed and this shard's finished searches (padded with
- * closeness-0 vertices as tkc_topk_closeness does); n_tied_at_kth counts
- * only this shard's finished searches tied with the returned k-th (the seed's
- * vertices were finished elsewhere).  The merged result of all shards, given
- * the best k of their results as each other's seed, is the exact top-k; the
- * exact tie count is the sum over shards of tkc_count_tied with the merged
- * k-th.  No paper counterpart for the sharding itself.  Errors: TKC_EINVAL
+/* Algorithm 1 (Section 4) over part of the source order, for sharding the
+ * sources of one graph over several GPUs (each holding a copy of the graph)
+ * and for resuming a run from a checkpoint.  Algorithm 1 is exact for any
+ * threshold x that is the k-th best of exactly known farness values, so the
+ * call searches the sources at positions first + shard, first + shard +
+ * nshards, first + shard + 2 nshards, ... of the order options.order gives
+ * (TKC_ORDER_DEG or TKC_ORDER_NB; with NB the stop applies to these
+ * positions, still sorted by key), at most max_sources of them (0 = all), from
+ * a k-list seeded with nseed <= min(k, n) exact entries of vertices searched
+ * elsewhere (host arrays seed_S/seed_r/seed_id, best first by farness then
+ * id, r >= 2, distinct; none of them may be among the positions this call
+ * searches: a k-list holds each vertex once).  The result is the best min(k,
+ * n) of the seed and the searches finished here (padded with closeness-0
+ * vertices as tkc_topk_closeness does); n_tied_at_kth counts only the
+ * searches finished here that tie with the returned k-th.  Sharding: with
+ * first = 0, shard s of N, and each shard seeded with the best k of the
+ * others' results, the merged results are the exact top-k and the exact tie
+ * count is the sum over shards of tkc_count_tied with the merged k-th.
+ * Resuming: shard 0 of 1 from position `first` with the k-list reached
+ * before it.  No paper counterpart for the split itself.  Errors: TKC_EINVAL
  * (null g or out, nshards = 0, shard >= nshards, k > TKC_MAX_K, an order
  * other than DEG or NB, capacity too small, a seed not sorted, repeated, with
  * r < 2 or an id >= n, nseed > min(k, n)), TKC_ENOMEM, TKC_ECUDA, TKC_ETIMEOUT. */
-int tkc_topk_closeness_shard(tkc_graph *g, uint32_t k, uint32_t shard, uint32_t nshards, uint32_t max_sources,
-                             const uint64_t *seed_S, const uint32_t *seed_r, const uint32_t *seed_id, uint32_t nseed,
-                             tkc_result *out);
+int tkc_topk_closeness_shard(tkc_graph *g, uint32_t k, uint32_t first, uint32_t shard, uint32_t nshards,
+                             uint32_t max_sources, const uint64_t *seed_S, const uint32_t *seed_r,
+                             const uint32_t *seed_id, uint32_t nseed, tkc_result *out);
 
 /* Number of searches finished by the latest tkc_topk_closeness_shard run on g
  * (the latest run on g's context) whose farness equals S/(r-1)^2 exactly

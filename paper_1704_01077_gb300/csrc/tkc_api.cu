@@ -1017,11 +1017,10 @@ static int topk_one(tkc_graph *g, uint32_t k, tkc_result *out, int harmonic) {
   return TKC_OK;
 }
 
-// The positions shard, shard + nshards, ... of a source order (at most
-// `limit` of them, 0 = all).
-__global__ void k_shard_order(const u32 *order, u32 norder, u32 shard, u32 nshards, u32 count, u32 *out) {
+// The positions first, first + nshards, ... of a source order (count of them).
+__global__ void k_shard_order(const u32 *order, u32 first, u32 nshards, u32 count, u32 *out) {
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
-    out[i] = order[shard + (u64)i * nshards];
+    out[i] = order[first + (u64)i * nshards];
 }
 
 // Finished searches of the latest run whose farness equals S/(r-1)^2 exactly.
@@ -1045,8 +1044,9 @@ static bool entry_before(u64 Sa, u32 ra, u32 ia, u64 Sb, u32 rb, u32 ib) {
 }
 
 // Algorithm 1 over one shard of the source order (see tkc_topk_closeness_shard).
-static int topk_shard(tkc_graph *g, uint32_t k, uint32_t shard, uint32_t nshards, uint32_t limit, const uint64_t *seed_S,
-                      const uint32_t *seed_r, const uint32_t *seed_id, uint32_t nseed, tkc_result *out) {
+static int topk_shard(tkc_graph *g, uint32_t k, uint32_t first, uint32_t shard, uint32_t nshards, uint32_t limit,
+                      const uint64_t *seed_S, const uint32_t *seed_r, const uint32_t *seed_id, uint32_t nseed,
+                      tkc_result *out) {
   if (!g || !out || nshards == 0 || shard >= nshards || k > TKC_MAX_K) return TKC_EINVAL;
   if (nseed && (!seed_S || !seed_r || !seed_id)) return TKC_EINVAL;
   tkc_ctx *ctx = g->ctx;
@@ -1076,13 +1076,14 @@ static int topk_shard(tkc_graph *g, uint32_t k, uint32_t shard, uint32_t nshards
   const u32 *full = nullptr;
   u32 nfull = 0;
   TKC_RC(source_order_of(g, o, kk, 0, &full, &nfull, &rs.lb_key));
-  u32 count = nfull > shard ? (nfull - shard + nshards - 1) / nshards : 0;
+  const u64 start = (u64)first + shard;
+  u32 count = nfull > start ? (u32)((nfull - start + nshards - 1) / nshards) : 0;
   if (limit && count > limit) count = limit;
   u32 *sorder = nullptr;
   TKC_TRY(cudaMallocAsync(&sorder, std::max<size_t>(count, 1) * sizeof(u32), st));
   if (count)
     TKC_LAUNCH(k_shard_order<<<(count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096, 256, 0, st>>>(
-        full, nfull, shard, nshards, count, sorder));
+        full, (u32)start, nshards, count, sorder));
   TKC_TRY(cudaEventRecord(ctx->ev[1], st));
   const u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g->n, rs.lb_key != nullptr);
   rs.g = g;
@@ -1621,10 +1622,10 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
 
 int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out) { return topk_one(g, k, out, 0); }
 
-int tkc_topk_closeness_shard(tkc_graph *g, uint32_t k, uint32_t shard, uint32_t nshards, uint32_t max_sources,
-                             const uint64_t *seed_S, const uint32_t *seed_r, const uint32_t *seed_id, uint32_t nseed,
-                             tkc_result *out) {
-  return topk_shard(g, k, shard, nshards, max_sources, seed_S, seed_r, seed_id, nseed, out);
+int tkc_topk_closeness_shard(tkc_graph *g, uint32_t k, uint32_t first, uint32_t shard, uint32_t nshards,
+                             uint32_t max_sources, const uint64_t *seed_S, const uint32_t *seed_r,
+                             const uint32_t *seed_id, uint32_t nseed, tkc_result *out) {
+  return topk_shard(g, k, first, shard, nshards, max_sources, seed_S, seed_r, seed_id, nseed, out);
 }
 
 int tkc_count_tied(tkc_graph *g, uint64_t S, uint32_t r, uint32_t *count) {

@@ -119,7 +119,7 @@ class LibraryShard:
         if seed:
             sd = (np.array([e[0] for e in seed], np.uint64), np.array([e[1] for e in seed], np.uint32),
                   np.array([e[2] for e in seed], np.uint32))
-        self.last = self.tkc.tkc_topk_closeness_shard(self.g, self.k, self.rank, self.world, max_sources, sd)
+        self.last = self.tkc.tkc_topk_closeness_shard(self.g, self.k, self.rank, self.world, max_sources, sd, first=0)
         return [(int(S), int(r), int(i)) for S, r, i in zip(self.last.dist_sum, self.last.reach, self.last.ids)]
 
     def count_tied(self, entry: Entry) -> int:

@@ -128,7 +128,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tkc_nb_harmonic_bounds.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double), u32p, u32p]
     lib.tkc_last_run_stats.argtypes = [vp, ctypes.POINTER(tkc_run_stats)]
     lib.tkc_topk_closeness_shard.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
-                                             u64p, u32p, u32p, ctypes.c_uint32, ctypes.POINTER(tkc_result)]
+                                             ctypes.c_uint32, u64p, u32p, u32p, ctypes.c_uint32,
+                                             ctypes.POINTER(tkc_result)]
     lib.tkc_count_tied.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32, u32p]
     lib.tkc_kernel_launches.argtypes = []
     lib.tkc_kernel_launches.restype = ctypes.c_uint64
@@ -303,9 +304,10 @@ def tkc_topk_closeness(g, k: int, capacity: int | None = None) -> Result:
 
 
 def tkc_topk_closeness_shard(g, k: int, shard: int, nshards: int, max_sources: int = 0, seed=None,
-                             capacity: int | None = None) -> Result:
-    """One shard of the source order (see include/tkc.h); seed = (S, r, ids)
-    host arrays, best first, or None."""
+                             capacity: int | None = None, first: int = 0) -> Result:
+    """Part of the source order (see include/tkc.h): positions first + shard,
+    first + shard + nshards, ...; seed = (S, r, ids) host arrays, best first,
+    or None."""
     cap = k if capacity is None else capacity
     res, arrays = _new_result(cap)
     if seed is None or len(seed[2]) == 0:
@@ -316,7 +318,7 @@ def tkc_topk_closeness_shard(g, k: int, shard: int, nshards: int, max_sources: i
         sr = np.ascontiguousarray(seed[1], dtype=np.uint32)
         si = np.ascontiguousarray(seed[2], dtype=np.uint32)
         ns = len(si)
-    _check(_lib.tkc_topk_closeness_shard(g, k, shard, nshards, max_sources, None if sS is None else _u64p(sS),
+    _check(_lib.tkc_topk_closeness_shard(g, k, first, shard, nshards, max_sources, None if sS is None else _u64p(sS),
                                          None if sr is None else _u32p(sr), None if si is None else _u32p(si), ns,
                                          ctypes.byref(res)), "tkc_topk_closeness_shard")
     return _to_result(res, arrays)
