@@ -407,9 +407,11 @@ uint64_t tkc_kernel_launches(void);
 
 /* Standardized features of every vertex into DEVICE array x[n][5]:
  * log1p of out-degree, in-degree, the 2-walk count sum of out-degrees of
- * out-neighbours (the Section 6 lemma's gamma at d = 1, a bound on the 2-hop ball), an
- * h-index estimate of the core number (4 steps from the degree, out- and
- * in-neighbours), and the SCC size (component size if undirected); each
+ * out-neighbours (the Section 6 lemma's gamma at d = 1, a bound on the 2-hop ball), the
+ * core number of the graph with arc directions dropped (degree = out-degree +
+ * in-degree when directed; h-index iteration from the degree run until no
+ * value changes, Lu et al. 2016), and the SCC size (component size if
+ * undirected); each
  * feature shifted and scaled to mean 0, variance 1 over the graph.  Errors:
  * TKC_EINVAL (null g, or null x with n > 0), TKC_ENOMEM, TKC_ECUDA,
  * TKC_ETIMEOUT. */

@@ -65,24 +65,51 @@ __global__ void k_core_init(const u32 *off, const u32 *ioff, u32 n, int directed
 
 // One h-index step of the core-number iteration (Lu, Zhou, Zhang, Stanley,
 // Nat. Commun. 2016): c'(v) = the largest h such that at least h neighbours
-// have c >= h, neighbours taken over out-arcs (and in-arcs when directed).
-// Started from the degree it decreases towards the k-core number.
+// have c >= h, neighbours taken over out-arcs (and in-arcs when directed,
+// so a vertex linked both ways counts twice: the graph with arc directions
+// dropped).  Started from the degree it never rises, and once no value
+// changes it is the core number.  Only vertices with a neighbour whose value
+// changed in the previous step (dirty_in) are recomputed; a vertex whose value
+// changes marks its neighbours in dirty_out and sets *changed.
 __global__ void k_core_step(const u32 *off, const u32 *col, const u32 *ioff, const u32 *icol, u32 n, int directed,
-                            const u32 *c, u32 *c2) {
+                            const u32 *c, u32 *c2, const uint8_t *dirty_in, uint8_t *dirty_out, u32 *changed) {
   const int lane = threadIdx.x & 31;
-  for (u32 v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
-    u32 lo = 0, hi = c[v];  // answer in [lo, hi]
-    while (lo < hi) {
-      u32 mid = (lo + hi + 1) >> 1;
-      u32 cnt = 0;
-      for (u32 i = off[v] + lane; i < off[v + 1]; i += 32) cnt += c[col[i]] >= mid;
-      if (directed)
-        for (u32 i = ioff[v] + lane; i < ioff[v + 1]; i += 32) cnt += c[icol[i]] >= mid;
-      cnt = __reduce_add_sync(FULL, cnt);
-      if (cnt >= mid) lo = mid;
-      else hi = mid - 1;
+  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
+    // lane per vertex: copy the clean ones; the warp then takes the dirty ones
+    const u32 mine = base + lane;
+    bool dirty = false;
+    if (mine < n) {
+      dirty = dirty_in[mine] != 0;
+      if (!dirty) c2[mine] = c[mine];
     }
-    if (lane == 0) c2[v] = lo;
+    for (unsigned dm = __ballot_sync(FULL, dirty); dm; dm &= dm - 1) {
+      const u32 v = base + (__ffs(dm) - 1);
+      const u32 cv = c[v];
+      // the value never rises: one pass checks whether it stays (the common
+      // case once most values have settled), else a binary search lowers it
+      auto count_at_least = [&](u32 h) {
+        u32 cnt = 0;
+        for (u32 i = off[v] + lane; i < off[v + 1]; i += 32) cnt += c[col[i]] >= h;
+        if (directed)
+          for (u32 i = ioff[v] + lane; i < ioff[v + 1]; i += 32) cnt += c[icol[i]] >= h;
+        return __reduce_add_sync(FULL, cnt);
+      };
+      u32 lo = 0, hi = cv;  // answer in [lo, hi]
+      if (count_at_least(cv) >= cv) lo = cv;
+      else hi = cv - 1;
+      while (lo < hi) {
+        const u32 mid = (lo + hi + 1) >> 1;
+        if (count_at_least(mid) >= mid) lo = mid;
+        else hi = mid - 1;
+      }
+      if (lane == 0) c2[v] = lo;
+      if (lo != cv) {
+        if (lane == 0) *changed = 1;
+        for (u32 i = off[v] + lane; i < off[v + 1]; i += 32) dirty_out[col[i]] = 1;
+        if (directed)
+          for (u32 i = ioff[v] + lane; i < ioff[v + 1]; i += 32) dirty_out[icol[i]] = 1;
+      }
+    }
   }
 }
 
@@ -350,11 +377,30 @@ int ensure_features(tkc_graph *g) {
   TKC_TRY(cudaMallocAsync(&sums, 2 * F * sizeof(double), st));
   TKC_LAUNCH(k_two_walks<<<grid_of((u64)n * 32), 256, 0, st>>>(g->off, g->col, n, w2));
   TKC_LAUNCH(k_core_init<<<grid_of(n), 256, 0, st>>>(g->off, g->ioff, n, g->directed, c0));
-  for (int it = 0; it < 4; ++it) {
-    TKC_LAUNCH(k_core_step<<<grid_of((u64)n * 32), 256, 0, st>>>(g->off, g->col, g->ioff, g->icol, n, g->directed,
-                                                                 c0, c1));
+  u32 *flag = nullptr;
+  uint8_t *d0 = nullptr, *d1 = nullptr;
+  TKC_TRY(cudaMallocAsync(&flag, sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&d0, n, st));
+  TKC_TRY(cudaMallocAsync(&d1, n, st));
+  TKC_TRY(cudaMemsetAsync(d0, 1, n, st));  // every vertex is computed in the first step
+  for (u64 it = 0;; ++it) {
+    // a step that changes something lowers at least one value, and the values
+    // start at the degrees: 2 arcs + 1 steps suffice
+    if (it > 2 * g->arcs + 1) return TKC_ETIMEOUT;
+    TKC_TRY(cudaMemsetAsync(flag, 0, sizeof(u32), st));
+    TKC_TRY(cudaMemsetAsync(d1, 0, n, st));
+    TKC_LAUNCH(k_core_step<<<grid_of(n), 256, 0, st>>>(g->off, g->col, g->ioff, g->icol, n, g->directed, c0, c1, d0,
+                                                       d1, flag));
     std::swap(c0, c1);
+    std::swap(d0, d1);
+    u32 h = 0;
+    TKC_TRY(cudaMemcpyAsync(&h, flag, sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TKC_TRY(cudaStreamSynchronize(st));
+    if (!h) break;
   }
+  TKC_TRY(cudaFreeAsync(flag, st));
+  TKC_TRY(cudaFreeAsync(d0, st));
+  TKC_TRY(cudaFreeAsync(d1, st));
   TKC_TRY(cudaMemsetAsync(sums, 0, 2 * F * sizeof(double), st));
   TKC_LAUNCH(k_features_raw<<<grid_of(n), 256, 0, st>>>(g->off, g->ioff, w2, c0, g->scc_size, n, g->features, sums));
   TKC_LAUNCH(k_features_standardize<<<grid_of((u64)n * F), 256, 0, st>>>(g->features, n, sums));
