@@ -337,6 +337,8 @@ def main():
     ap.add_argument("--bound", default="cut", choices=["cut", "lb"],
                     help="updateBounds: BFSCut (cut) or updateBoundsLB (lb: DegBound / NBBound)")
     ap.add_argument("--teams", type=int, default=0, help="teams of SMs (0 = library default)")
+    ap.add_argument("--bu-num", type=int, default=0,
+                    help="a level runs bottom-up when its frontier arcs exceed arcs / BU_NUM (0 = library default)")
     ap.add_argument("--deterministic", type=int, default=0, help="1: one team, reproducible counters")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "tkc":
@@ -372,7 +374,7 @@ def main():
               "learned-seed": tkc.TKC_ORDER_LEARNED, "learned-nb": tkc.TKC_ORDER_LEARNED_NB}
     base_opt = dict(device=local, stream=stream.cuda_stream, batch_bits=args.bits, order=orders[args.order],
                     teams=args.teams, seed_factor=5 if args.order in ("learned-seed", "learned-nb") else 0,
-                    nb_levels=args.nb_levels, deterministic=args.deterministic)
+                    nb_levels=args.nb_levels, deterministic=args.deterministic, bu_num=args.bu_num, bu_den=1)
     ctx = tkc.tkc_create(tkc.Options(**base_opt))
     weights = None
     if args.order.startswith("learned") or (not args.no_plain and not multi and args.measure == "closeness"):
@@ -546,7 +548,7 @@ def main():
             "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "k": k, "batch_bits": res.batch_bits,
                        "order": args.order, "measure": args.measure, "bound": args.bound,
-                       "teams": args.teams or "library default", "deterministic": args.deterministic,
+                       "teams": args.teams or "library default", "bu_num": args.bu_num or "library default", "deterministic": args.deterministic,
                        "work_per_step": work,
                        "work_unit": ("arcs visited by plain one-source NBCut (Algorithm 1), counted by the CPU "
                                      "oracle on the same graph" if work_fixed is not None else

@@ -167,12 +167,15 @@ constexpr double kHMargin = 1.0 + 1.0 / 1048576.0;
 #endif
 
 // Threads per block of the search kernel (one block per SM).  The level loops
-// wait on dependent row gathers, so more resident warps hide more latency: the
-// 64-bit kernel runs 32 warps per SM and the 128-bit one 24, at the price of a
-// few spilled registers (measured on R-MAT 22, DegCut and NBCut: 1024 and 768
-// threads beat 512 by 30% and 14%).
+// wait on dependent row gathers, so more resident warps hide more latency:
+// the 64- and 128-bit kernels run 32 warps per SM, at the price of a few
+// spilled registers (measured on R-MAT 22, NBCut: 1024 threads beat 768 by 5%
+// for 128-bit batches; DegCut and NBCut, 64-bit: 1024 beat 512 by 30%).
+#ifndef TKC_THREADS_W2
+#define TKC_THREADS_W2 1024
+#endif
 template <int W>
-constexpr int kThreads = W == 1 ? 1024 : W == 2 ? 768 : 512;
+constexpr int kThreads = W == 1 ? 1024 : W == 2 ? TKC_THREADS_W2 : 512;
 // Small graphs and one-source searches: short levels, where the block-wide
 // barriers and scans of the larger blocks cost more than they hide.
 constexpr int kMinThreads = 512;
@@ -221,39 +224,49 @@ __device__ __forceinline__ void warp_count_slots(const u64 (&nw)[W], uint32_t od
   uint32_t odm = anyw ? od : 0u;
   uint32_t maxod = __reduce_max_sync(FULL, odm);
   int planes = 32 - __clz(maxod);
+  // all 2W halves transposed first, so that the out-degree bit planes (one
+  // ballot each) serve every half
+  uint32_t colv[2 * W], cv[2 * W];
+  uint32_t cmax = 0;
 #pragma unroll
-  for (int j = 0; j < W; ++j) {
+  for (int jh = 0; jh < 2 * W; ++jh) {
+    const uint32_t x = (uint32_t)(nw[jh >> 1] >> (32 * (jh & 1)));
+    colv[jh] = __ballot_sync(FULL, x != 0) ? warp_transpose32(x, lane) : 0u;
+    cv[jh] = __popc(colv[jh]);
+    cmax = cv[jh] > cmax ? cv[jh] : cmax;
+  }
+  const uint32_t maxc = __reduce_max_sync(FULL, cmax);
+  u64 ws[2 * W];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      uint32_t x = (uint32_t)(nw[j] >> (32 * h));
-      if (__ballot_sync(FULL, x != 0) == 0) continue;
-      uint32_t col = warp_transpose32(x, lane);
-      uint32_t c = __popc(col);
-      uint32_t maxc = __reduce_max_sync(FULL, c);
-      u64 ws = 0;
-      if ((int)maxc * 6 <= planes * 5) {
-        // walk the set bits: fetch each contributing lane's out-degree
-        uint32_t m = col;
-        for (uint32_t it = 0; it < maxc; ++it) {
-          int src = m ? (__ffs(m) - 1) : 0;
-          uint32_t v = __shfl_sync(FULL, odm, src);
-          if (m) {
-            ws += v;
-            m &= m - 1;
-          }
-        }
-      } else {
-        // bit planes of the out-degrees: sum = sum_p 2^p popc(col & plane_p)
-        for (int p = 0; p < planes; ++p) {
-          uint32_t plane = __ballot_sync(FULL, (odm >> p) & 1u);
-          ws += (u64)__popc(col & plane) << p;
+  for (int jh = 0; jh < 2 * W; ++jh) ws[jh] = 0;
+  // about 6 instructions per half for a walk step or a plane, 1 more per plane
+  if ((int)maxc * 12 * W <= planes * (1 + 12 * W)) {
+    // walk the set bits: fetch each contributing lane's out-degree
+    for (uint32_t it = 0; it < maxc; ++it) {
+#pragma unroll
+      for (int jh = 0; jh < 2 * W; ++jh) {
+        const int src = colv[jh] ? (__ffs(colv[jh]) - 1) : 0;
+        const uint32_t v = __shfl_sync(FULL, odm, src);
+        if (colv[jh]) {
+          ws[jh] += v;
+          colv[jh] &= colv[jh] - 1;
         }
       }
-      if (c) {
-        int slot = 64 * j + 32 * h + lane;
-        atomicAdd(&s_cnt[slot], c);
-        atomicAdd(&s_wsum[slot], ws);
-      }
+    }
+  } else {
+    // bit planes of the out-degrees: sum = sum_p 2^p popc(col & plane_p)
+    for (int p = 0; p < planes; ++p) {
+      const uint32_t plane = __ballot_sync(FULL, (odm >> p) & 1u);
+#pragma unroll
+      for (int jh = 0; jh < 2 * W; ++jh) ws[jh] += (u64)__popc(colv[jh] & plane) << p;
+    }
+  }
+#pragma unroll
+  for (int jh = 0; jh < 2 * W; ++jh) {
+    if (cv[jh]) {
+      const int slot = 32 * jh + lane;
+      atomicAdd(&s_cnt[slot], cv[jh]);
+      atomicAdd(&s_wsum[slot], ws[jh]);
     }
   }
 }
@@ -1300,23 +1313,35 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
             ee = p.ioff[w + 1];
             heavy = any && ee - e0 > kHeavyIn;
             if (any && !heavy) {
-              // U in-arcs per step: their columns and frontier bits are loaded
-              // together, then the rows of those on a frontier; the early exit
-              // is tested once per step (extra rows only repeat found bits)
+              // U in-arcs per step, software-pipelined: step i's rows (of the
+              // in-neighbours on a frontier) are loaded together with step
+              // i+1's frontier bits and step i+2's columns, so a step waits on
+              // one round trip instead of three (1.5% off the kernel on R-MAT
+              // 22); the early exit is tested once per step (extra rows only
+              // repeat found bits)
               constexpr int U = W >= 8 ? 2 : TKC_BU_U;
               uint32_t e = e0;
-              for (; e < ee; e += U) {
-                uint32_t uu[U], fb[U];
+              uint32_t c0[U], c1[U], f0[U];
 #pragma unroll
-                for (int j = 0; j < U; ++j) uu[j] = e + j < ee ? p.icol[e + j] : 0xffffffffu;
+              for (int j = 0; j < U; ++j) {
+                c0[j] = e + j < ee ? p.icol[e + j] : 0xffffffffu;
+                c1[j] = e + U + j < ee ? p.icol[e + U + j] : 0xffffffffu;
+              }
+#pragma unroll
+              for (int j = 0; j < U; ++j)
+                f0[j] = c0[j] != 0xffffffffu ? (FBcur[c0[j] >> 5] >> (c0[j] & 31)) & 1u : 0u;
+              for (; e < ee; e += U) {
+                uint32_t c2[U], f1[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j) c2[j] = e + 2 * U + j < ee ? p.icol[e + 2 * U + j] : 0xffffffffu;
 #pragma unroll
                 for (int j = 0; j < U; ++j)
-                  fb[j] = uu[j] != 0xffffffffu ? (FBcur[uu[j] >> 5] >> (uu[j] & 31)) & 1u : 0u;
+                  f1[j] = c1[j] != 0xffffffffu ? (FBcur[c1[j] >> 5] >> (c1[j] & 31)) & 1u : 0u;
 #pragma unroll
                 for (int j = 0; j < U; ++j) {
-                  if (fb[j]) {
+                  if (f0[j]) {
                     u64 fr[W];
-                    load_row<W>(Fcur, uu[j], fr);
+                    load_row<W>(Fcur, c0[j], fr);
                     ++rows_read;
 #pragma unroll
                     for (int q = 0; q < W; ++q) nw[q] |= fr[q] & miss[q];
@@ -1328,6 +1353,12 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
                 if (full) {
                   e += U;
                   break;
+                }
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                  c0[j] = c1[j];
+                  c1[j] = c2[j];
+                  f0[j] = f1[j];
                 }
               }
               scanned += (e < ee ? e : ee) - e0;

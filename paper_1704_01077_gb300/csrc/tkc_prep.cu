@@ -7,6 +7,7 @@
 
 #include <algorithm>
 
+#include "tkc_arcs.cuh"
 #include "tkc_internal.cuh"
 
 namespace tkc {
@@ -108,105 +109,86 @@ static int scan_exclusive(const u32 *in, u32 *out, u64 len, u32 *tmp, cudaStream
 
 enum : u32 { kBadOffsets = 1, kBadRange = 2, kSelfLoop = 4, kUnsorted = 8, kAsymmetric = 16 };
 
-// One warp per vertex: offsets monotone and within arcs, ids in range, no
-// self-loop, each row strictly increasing (sorted, no duplicates).
-// A lane checks the row of its own vertex when it has at most 16 arcs, the
-// warp longer rows; a row is read only after its offsets are known to lie
-// within [0, arcs].
+// Offsets monotone and within arcs (a thread per vertex); ids in range, no
+// self-loop, each row strictly increasing (sorted, no duplicates), checked
+// arc by arc.
 __global__ void k_validate(const u32 *off, const u32 *col, u32 n, u64 arcs, u32 *flags) {
-  int lane = threadIdx.x & 31;
-  u32 f = 0;
-  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
-    const u32 v = base + lane;
-    u32 b = 0, e = 0;
-    if (v < n) {
-      b = off[v];
-      e = off[v + 1];
-      if (e < b || e > arcs) {
-        f |= kBadOffsets;
-        b = e = 0;
-      }
-    }
-    const bool light = e - b <= 16;
-    if (light)
-      for (u32 i = b; i < e; ++i) {
-        const u32 c = col[i];
-        if (c >= n) f |= kBadRange;
-        if (c == v) f |= kSelfLoop;
-        if (i > b && col[i - 1] >= c) f |= kUnsorted;
-      }
-    for (unsigned hv = __ballot_sync(FULL, !light); hv; hv &= hv - 1) {
-      const int src = __ffs(hv) - 1;
-      const u32 hb = __shfl_sync(FULL, b, src), he = __shfl_sync(FULL, e, src);
-      const u32 x = base + src;
-      for (u32 i = hb + lane; i < he; i += 32) {
-        const u32 c = col[i];
-        if (c >= n) f |= kBadRange;
-        if (c == x) f |= kSelfLoop;
-        if (i > hb && col[i - 1] >= c) f |= kUnsorted;
-      }
-    }
-  }
-  f = __reduce_or_sync(FULL, f);
-  if (lane == 0 && f) atomicOr(flags, f);
-}
-
-// Undirected input: every arc u->v needs the arc v->u (binary search in v's row).
-__global__ void k_symmetric(const u32 *off, const u32 *col, u32 n, u32 *flags) {
-  int lane = threadIdx.x & 31;
-  u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  u32 nw = (gridDim.x * blockDim.x) >> 5;
-  u32 f = 0;
-  for (u32 u = warp; u < n; u += nw) {
-    for (u32 i = off[u] + lane; i < off[u + 1]; i += 32) {
-      u32 v = col[i];
-      u32 lo = off[v], hi = off[v + 1];
-      while (lo < hi) {
-        u32 mid = (lo + hi) >> 1;
-        if (col[mid] < u) lo = mid + 1;
-        else hi = mid;
-      }
-      if (lo >= off[v + 1] || col[lo] != u) f |= kAsymmetric;
-    }
-  }
-  f = __reduce_or_sync(FULL, f);
-  if (lane == 0 && f) atomicOr(flags, f);
-}
-
-// In-degrees (scatter = false: cnt[v] += 1 per arc u -> v) or the in-arc
-// columns (scatter = true: u appended to v's in-row at ioff[v] + cnt[v]++).
-// A lane walks the out-row of its own vertex when it has at most kLaneRow
-// arcs, the warp longer rows.
-constexpr u32 kLaneRow = 16;
-
-template <bool scatter>
-__global__ void k_in_arcs(const u32 *off, const u32 *col, u32 n, const u32 *ioff, u32 *cnt, u32 *icol) {
   const int lane = threadIdx.x & 31;
-  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
-    const u32 u = base + lane;
-    u32 b = 0, e = 0;
-    if (u < n) {
-      b = off[u];
-      e = off[u + 1];
-    }
-    const bool light = e - b <= kLaneRow;
-    if (light)
-      for (u32 i = b; i < e; ++i) {
-        const u32 v = col[i];
-        if (scatter) icol[ioff[v] + atomicAdd(&cnt[v], 1u)] = u;
-        else atomicAdd(&cnt[v], 1u);
-      }
-    for (unsigned hv = __ballot_sync(0xffffffffu, !light); hv; hv &= hv - 1) {
-      const int src = __ffs(hv) - 1;
-      const u32 hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
-      const u32 x = base + src;
-      for (u32 i = hb + lane; i < he; i += 32) {
-        const u32 v = col[i];
-        if (scatter) icol[ioff[v] + atomicAdd(&cnt[v], 1u)] = x;
-        else atomicAdd(&cnt[v], 1u);
-      }
-    }
+  u32 f = 0;
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (u64)gridDim.x * blockDim.x) {
+    const u32 b = off[v], e = off[v + 1];
+    if (e < b || e > arcs) f |= kBadOffsets;
   }
+  // the arcs in chunks with their sources (tkc_arcs.cuh: a hub's row is
+  // spread over many warps; reads stay in bounds even when the offsets are
+  // bad, which the loop above reports)
+  grid_walk_arcs<true>(off, n, arcs, [&](u32 u, u64 i, bool valid, u32 rs) {
+    if (!valid) return;
+    const u32 c = col[i];
+    if (c >= n) f |= kBadRange;
+    if (c == u) f |= kSelfLoop;
+    if (i > rs && col[i - 1] >= c) f |= kUnsorted;
+  });
+  f = __reduce_or_sync(FULL, f);
+  if (lane == 0 && f) atomicOr(flags, f);
+}
+
+// Undirected input: every arc u->v needs the arc v->u (binary search in v's
+// row; the graph already passed k_validate, so rows are sorted).  Arcs in
+// chunks with their sources (tkc_arcs.cuh), so a hub's row is spread over
+// many warps.
+__global__ void k_symmetric(const u32 *off, const u32 *col, u32 n, u64 arcs, u32 *flags) {
+  const int lane = threadIdx.x & 31;
+  u32 f = 0;
+  grid_walk_arcs(off, n, arcs, [&](u32 u, u64 i, bool valid, u32) {
+    if (!valid) return;
+    const u32 v = col[i];
+    u32 lo = off[v], hi = off[v + 1];
+    const u32 end = hi;
+    while (lo < hi) {
+      const u32 mid = (lo + hi) >> 1;
+      if (col[mid] < u) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo >= end || col[lo] != u) f |= kAsymmetric;
+  });
+  f = __reduce_or_sync(FULL, f);
+  if (lane == 0 && f) atomicOr(flags, f);
+}
+
+// In-degrees: cnt[v] += 1 per arc u -> v, 32 consecutive arcs per warp step
+// (coalesced column reads).  Lanes adding to the same vertex (the hubs of
+// skewed in-degree distributions) add their count in one atomic.
+__global__ void k_in_count(const u32 *__restrict__ col, u64 arcs, u32 *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  for (u64 base = ((u64)blockIdx.x * blockDim.x + threadIdx.x) & ~31ull; base < arcs;
+       base += (u64)gridDim.x * blockDim.x) {
+    const u64 i = base + lane;
+    const bool valid = i < arcs;
+    const u32 v = valid ? col[i] : 0xffffffffu;
+    const unsigned peers = __match_any_sync(FULL, v);
+    if (valid && __ffs(peers) - 1 == lane) atomicAdd(&cnt[v], (u32)__popc(peers));
+  }
+}
+
+// The in-arc columns: arc u -> v takes slot cursor[v]++ of v's in-row (cursor
+// starts at ioff).  Arcs are dealt to warps in fixed chunks with their
+// sources found by search (tkc_arcs.cuh), so a hub's out-row is spread over
+// many warps.  Lanes writing the same in-row take consecutive slots from one
+// atomic.  In-rows come out roughly in ascending source order (chunks are
+// taken in arc order).
+__global__ void k_in_fill(const u32 *__restrict__ off, const u32 *__restrict__ col, u32 n, u64 arcs,
+                          u32 *__restrict__ cursor, u32 *__restrict__ icol) {
+  const int lane = threadIdx.x & 31;
+  grid_walk_arcs(off, n, arcs, [&](u32 u, u64 i, bool valid, u32) {
+    const u32 v = valid ? col[i] : 0xffffffffu;
+    const unsigned peers = __match_any_sync(FULL, v);
+    const int leader = __ffs(peers) - 1;
+    u32 pos = 0;
+    if (valid && leader == lane) pos = atomicAdd(&cursor[v], (u32)__popc(peers));
+    pos = __shfl_sync(FULL, pos, leader) + (u32)__popc(peers & ((1u << lane) - 1u));
+    if (valid) icol[pos] = u;
+  });
 }
 
 static unsigned grid_for(u64 work, unsigned tpb, unsigned cap = 152 * 16) {
@@ -223,13 +205,15 @@ int validate_and_transpose(tkc_graph *g) {
   u32 *flags = nullptr;
   TKC_TRY(cudaMallocAsync(&flags, sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(flags, 0, sizeof(u32), st));
-  TKC_LAUNCH(k_validate<<<grid_for(n, 256), 256, 0, st>>>(g->off, g->col, n, g->arcs, flags));
+  TKC_LAUNCH(k_validate<<<grid_for(std::max<u64>(n, (g->arcs + kArcChunk - 1) / kArcChunk * 32), 256), 256, 0, st>>>(
+      g->off, g->col, n, g->arcs, flags));
   TKC_TRY(cudaGetLastError());
   u32 hf = 0;
   TKC_TRY(cudaMemcpyAsync(&hf, flags, sizeof(u32), cudaMemcpyDeviceToHost, st));
   TKC_TRY(cudaStreamSynchronize(st));
   if (hf == 0 && !g->directed) {
-    TKC_LAUNCH(k_symmetric<<<grid_for((u64)n * 32, 256), 256, 0, st>>>(g->off, g->col, n, flags));
+    TKC_LAUNCH(k_symmetric<<<grid_for((g->arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
+        g->off, g->col, n, g->arcs, flags));
     TKC_TRY(cudaGetLastError());
     TKC_TRY(cudaMemcpyAsync(&hf, flags, sizeof(u32), cudaMemcpyDeviceToHost, st));
     TKC_TRY(cudaStreamSynchronize(st));
@@ -244,7 +228,8 @@ int validate_and_transpose(tkc_graph *g) {
   return build_in_csr(g);
 }
 
-// In-arc CSR of g (rows unsorted: the in-arcs of a vertex in scatter order).
+// In-arc CSR of g (rows not sorted: an in-row holds its arcs in the order the
+// fill reached them, roughly ascending source id).
 int build_in_csr(tkc_graph *g) {
   cudaStream_t st = g->ctx->stream;
   const u32 n = g->n;
@@ -255,12 +240,17 @@ int build_in_csr(tkc_graph *g) {
   TKC_TRY(cudaMallocAsync(&cursor, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&tmp, (((size_t)n + 1) / kScanTile + 2) * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(g->ioff, 0, ((size_t)n + 1) * sizeof(u32), st));
-  TKC_TRY(cudaMemsetAsync(cursor, 0, (size_t)n * sizeof(u32), st));
-  TKC_LAUNCH(k_in_arcs<false><<<grid_for(n, 256), 256, 0, st>>>(g->off, g->col, n, nullptr, g->ioff, nullptr));
-  TKC_TRY(cudaGetLastError());
+  if (g->arcs) {
+    TKC_LAUNCH(k_in_count<<<grid_for(g->arcs, 256), 256, 0, st>>>(g->col, g->arcs, g->ioff));
+    TKC_TRY(cudaGetLastError());
+  }
   TKC_RC(scan_exclusive(g->ioff, g->ioff, (u64)n + 1, tmp, st));
-  TKC_LAUNCH(k_in_arcs<true><<<grid_for(n, 256), 256, 0, st>>>(g->off, g->col, n, g->ioff, cursor, g->icol));
-  TKC_TRY(cudaGetLastError());
+  TKC_TRY(cudaMemcpyAsync(cursor, g->ioff, (size_t)n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  if (g->arcs) {
+    TKC_LAUNCH(k_in_fill<<<grid_for((g->arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
+        g->off, g->col, n, g->arcs, cursor, g->icol));
+    TKC_TRY(cudaGetLastError());
+  }
   TKC_TRY(cudaFreeAsync(cursor, st));
   TKC_TRY(cudaFreeAsync(tmp, st));
   return TKC_OK;

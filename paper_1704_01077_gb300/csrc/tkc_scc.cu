@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "tkc_arcs.cuh"
 #include "tkc_internal.cuh"
 
 namespace tkc {
@@ -448,42 +449,41 @@ __global__ void k_count_reached(const u32 *dist, u32 n, u32 *cnt) {
 
 // ---------------------------------------------------------------- condensation
 
-// Arcs between different SCCs, a warp per vertex (grid-stride).  The count
-// pass writes each block's count; after an exclusive scan of those, the emit
-// pass (same grid, so the same vertices per block) writes each block's arcs
-// from its offset on, placed by a shared-memory cursor: no global atomics.
+// Arcs between different SCCs.  Arcs are dealt to warps in fixed chunks with
+// their sources found by search (tkc_arcs.cuh), so a hub's out-row is spread
+// over many warps.  The count pass writes each block's count; after an
+// exclusive scan of those, the emit pass (same grid, so the same arcs per
+// block) writes each block's arcs from its offset on, placed by a
+// shared-memory cursor: no global atomics.  (The pairs are sorted afterwards,
+// so their order within a block does not matter.)
 template <bool emit>
-__global__ void k_cross(const u32 *off, const u32 *col, const u32 *comp, u32 n, u32 *blk, u32 *cu, u32 *cv) {
+__global__ void k_cross(const u32 *off, const u32 *col, const u32 *comp, u32 n, u64 arcs, u32 *blk, u32 *cu,
+                        u32 *cv) {
   __shared__ u32 s_cnt;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   const u32 base = emit ? blk[blockIdx.x] : 0u;
   u32 c = 0;
-  for (u32 v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
-    const u32 b = off[v], e = off[v + 1];
-    if (b == e) continue;
-    const u32 a = comp[v];
-    for (u32 i0 = b; i0 < e; i0 += 32) {
-      const u32 i = i0 + lane;
-      const u32 t = i < e ? comp[col[i]] : a;
-      const bool cross = t != a;
-      if (!emit) {
-        c += cross;
-        continue;
-      }
-      const unsigned m = __ballot_sync(FULL, cross);
-      if (!m) continue;
-      u32 pos = 0;
-      if (lane == 0) pos = atomicAdd(&s_cnt, (u32)__popc(m));
-      pos = __shfl_sync(FULL, pos, 0);
-      if (cross) {
-        const u32 k = base + pos + __popc(m & ((1u << lane) - 1u));
-        cu[k] = a;
-        cv[k] = t;
-      }
+  grid_walk_arcs(off, n, arcs, [&](u32 u, u64 i, bool valid, u32) {
+    const u32 a = valid ? comp[u] : 0u;
+    const u32 t = valid ? comp[col[i]] : 0u;
+    const bool cross = valid && t != a;
+    if (!emit) {
+      c += cross;
+      return;
     }
-  }
+    const unsigned m = __ballot_sync(FULL, cross);
+    if (!m) return;
+    u32 pos = 0;
+    if (lane == 0) pos = atomicAdd(&s_cnt, (u32)__popc(m));
+    pos = __shfl_sync(FULL, pos, 0);
+    if (cross) {
+      const u32 k = base + pos + __popc(m & ((1u << lane) - 1u));
+      cu[k] = a;
+      cv[k] = t;
+    }
+  });
   if (!emit) {
     c = __reduce_add_sync(FULL, c);
     if (lane == 0 && c) atomicAdd(&s_cnt, c);
@@ -826,12 +826,12 @@ int reach_directed_gpu(tkc_graph *g) {
   const u64 reach_big = read_u32(flag, st, &rc);
   TKC_RC(rc);
   // condensation arcs, sorted by (cu, cv) and deduplicated
-  const unsigned cross_grid = grid_of((u64)n * 32);
+  const unsigned cross_grid = grid_of((g->arcs + kArcChunk - 1) / kArcChunk * 32);
   u32 *blk = nullptr, *blk_tmp = nullptr;
   TKC_TRY(b.get(&blk, (size_t)cross_grid + 1));
   TKC_TRY(b.get(&blk_tmp, ((size_t)cross_grid + 1) / 4096 + 2));
   TKC_TRY(cudaMemsetAsync(blk + cross_grid, 0, sizeof(u32), st));
-  TKC_LAUNCH(k_cross<false><<<cross_grid, 256, 0, st>>>(g->off, g->col, comp, n, blk, nullptr, nullptr));
+  TKC_LAUNCH(k_cross<false><<<cross_grid, 256, 0, st>>>(g->off, g->col, comp, n, g->arcs, blk, nullptr, nullptr));
   TKC_RC(scan_exclusive_u32(blk, blk, (u64)cross_grid + 1, blk_tmp, st));
   const u32 m = read_u32(blk + cross_grid, st, &rc);
   TKC_RC(rc);
@@ -846,7 +846,7 @@ int reach_directed_gpu(tkc_graph *g) {
   TKC_TRY(b.get(&poff, (size_t)n + 1));
   TKC_TRY(b.get(&pcur, n));
   TKC_TRY(b.get(&tmp, (std::max<size_t>(m, n) + 1) / 4096 + 2));
-  TKC_LAUNCH(k_cross<true><<<cross_grid, 256, 0, st>>>(g->off, g->col, comp, n, blk, cu, cv));
+  TKC_LAUNCH(k_cross<true><<<cross_grid, 256, 0, st>>>(g->off, g->col, comp, n, g->arcs, blk, cu, cv));
   int bits = 0;
   while (bits < 32 && ((n - 1) >> bits) != 0) ++bits;
   TKC_RC(radix_sort_u32_pairs(cv, cu, m, bits, st));  // by target
