@@ -98,6 +98,12 @@ typedef struct {
                               searches enter the top list before the survivors' cut test).  0: teams run side
                               by side and cut against a threshold another team may be updating, so counters
                               vary from run to run (results never do). */
+  uint32_t relabel;        /* vertex labels of the search's rows: 0 = library choice (batched searches on graphs
+                              of 2^20 vertices or more walk a copy of the graph whose vertices are numbered by
+                              in-degree, largest first, so that the rows levels touch most share L2; else the
+                              graph itself), 1 = always that copy, 2 = never.  Sources, ties and every id in
+                              the results are the graph's own ids whatever the choice; results never depend
+                              on it, edges_scanned does. */
 } tkc_options;
 
 typedef struct {
@@ -129,7 +135,7 @@ typedef struct {
 /* Creates a context on opt->device (NULL opt = defaults).  No paper
  * counterpart: owns the stream, options and device workspace; the caller owns
  * *out until tkc_destroy.  Errors: TKC_EINVAL (null out, an option out of
- * range: batch_bits, order, nb_levels, large_blocks), TKC_ENOMEM, TKC_ECUDA
+ * range: batch_bits, order, nb_levels, large_blocks, deterministic, relabel), TKC_ENOMEM, TKC_ECUDA
  * (no such device, no cooperative launch); *out is NULL on error. */
 int tkc_create(tkc_ctx **out, const tkc_options *opt);
 

@@ -325,11 +325,17 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.n = g->n;
   p.directed = g->directed;
   p.arcs = g->arcs;
-  p.off = g->off;
-  p.col = g->col;
-  p.ioff = g->ioff;
-  p.icol = g->icol;
-  TKC_RC(ensure_bu_list(g));
+  // batched searches of large graphs walk the in-degree labelling (its hot
+  // rows stay in L2); one-source searches and small graphs the graph itself
+  const bool relabel = o.relabel == 1 || (o.relabel == 0 && rs.B > 1 && g->n >= (1u << 20));
+  TKC_RC(ensure_search_csr(g, relabel));
+  const bool lab = g->s_mode == 1;
+  p.off = lab ? g->s_off : g->off;
+  p.col = lab ? g->s_col : g->col;
+  p.ioff = lab ? g->s_ioff : g->ioff;
+  p.icol = lab ? g->s_icol : g->icol;
+  p.lab = lab ? g->s_lab : nullptr;
+  p.unlab = lab ? g->s_unlab : nullptr;
   p.bu_list = g->bu_list;
   p.n_bu = g->n_bu;
   p.n_bu_heavy = g->n_bu_heavy;
@@ -641,7 +647,8 @@ static void tune_cache_load(tkc_ctx *ctx);
 static bool options_valid(const tkc_options *opt) {
   const u32 b = opt->batch_bits;
   if (!(b == 0 || b == 1 || b == 64 || b == 128 || b == 256 || b == 512)) return false;
-  return opt->order <= TKC_ORDER_LEARNED_NB && opt->nb_levels <= 65535 && opt->large_blocks <= 2 && opt->deterministic <= 1;
+  return opt->order <= TKC_ORDER_LEARNED_NB && opt->nb_levels <= 65535 && opt->large_blocks <= 2 && opt->deterministic <= 1 &&
+         opt->relabel <= 2;
 }
 
 int tkc_create(tkc_ctx **out, const tkc_options *opt) {
@@ -760,9 +767,10 @@ void tkc_free_graph(tkc_graph *g) {
   cudaStreamSynchronize(g->ctx->stream);
   if (g->ioff && g->ioff != g->off) cudaFree(g->ioff);
   if (g->icol && g->icol != g->col) cudaFree(g->icol);
+  free_search_csr(g);
   void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega, g->scc_size, g->features,
                   g->learned_order, g->seeded_order, g->nb_order, g->nb_S, g->nb_r, g->nb_key, g->nb_hkey,
-                  g->nb_horder, g->comp, g->bu_list};
+                  g->nb_horder, g->comp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   g->ctx->graphs_alive--;
@@ -1508,9 +1516,10 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   int rc = TKC_OK;
   auto cleanup = [&]() {
     cudaStreamSynchronize(st);
+    free_search_csr(&U);
     void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.scc_size, U.comp, U.nb_S, U.nb_r,
                     U.nb_key, U.nb_hkey,
-                    U.nb_order, U.nb_horder, U.bu_list, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir};
+                    U.nb_order, U.nb_horder, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir};
     for (void *q : ptrs)
       if (q) cudaFree(q);
   };

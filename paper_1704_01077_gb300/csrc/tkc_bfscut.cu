@@ -364,7 +364,8 @@ __device__ __forceinline__ void clear_frontier(u64 *F, uint32_t *FB, const uint3
 // updateBoundsLB: the slots whose bits are new in this vertex's row found it at
 // this depth.
 template <int W>
-__device__ __forceinline__ void record_levels(const RunParams &p, uint32_t v, const u64 (&nw)[W], uint32_t depth) {
+__device__ __forceinline__ void record_levels(const RunParams &p, uint32_t w, const u64 (&nw)[W], uint32_t depth) {
+  const uint32_t v = p.unlab ? p.unlab[w] : w;  // the vertex whose search label is w
   uint16_t *row = p.lvl + (size_t)v * p.lvl_stride + (size_t)p.team * p.B;
 #pragma unroll
   for (int q = 0; q < W; ++q) {
@@ -922,7 +923,8 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     const uint32_t idx = base + threadIdx.x;
     const bool valid = threadIdx.x < cnt;
     uint32_t v = valid ? p.order[idx] : 0;
-    uint32_t od = valid ? p.off[v + 1] - p.off[v] : 0;
+    const uint32_t sv = valid && p.lab ? p.lab[v] : v;  // its row's label
+    uint32_t od = valid ? p.off[sv + 1] - p.off[sv] : 0;
     uint32_t a = valid ? p.alpha[v] : 0, o = valid ? p.omega[v] : 0;
     uint32_t gv = (valid && p.gid) ? p.gid[v] : 0;
     // level 0: S_0 = 0, n_0 = 1, gamma_1 = out-degree
@@ -979,12 +981,12 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
       graph_count(p, gv, 1, 1);
       graph_count(p, gv, 0, od);
       u64 bit = 1ull << (s & 63);
-      p.seen[(size_t)v * W + (s >> 6)] = bit;
-      Fcur[(size_t)v * W + (s >> 6)] = bit;
-      atomicOr(&FBcur[v >> 5], 1u << (v & 31));
-      FL[s] = v;
+      p.seen[(size_t)sv * W + (s >> 6)] = bit;
+      Fcur[(size_t)sv * W + (s >> 6)] = bit;
+      atomicOr(&FBcur[sv >> 5], 1u << (sv & 31));
+      FL[s] = sv;
       FLoff[s] = (uint32_t)(arcs_total + arcs_pre);
-      p.VL[s] = v;
+      p.VL[s] = sv;
       atomicOr(&sm.active[s >> 6], bit);
     }
     uint32_t ncut;

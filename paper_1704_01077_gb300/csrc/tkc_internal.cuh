@@ -121,6 +121,12 @@ struct RunParams {
   int directed;
   uint64_t arcs;
   const uint32_t *off, *col, *ioff, *icol;
+  // labels of the search's rows (nullptr: a vertex's label is its id).
+  // off/col/ioff/icol, bu_list and every per-vertex row, bit and list of the
+  // search are indexed by label; the source order, alpha, omega, lb_key, gid,
+  // res_S/res_r, lvl and every id in a slot or list entry by id.
+  const uint32_t *lab;    // id -> label
+  const uint32_t *unlab;  // label -> id
   const uint32_t *alpha, *omega;
   // bottom-up levels sweep bu_list[0, n_bu): the vertices with an in-arc, the
   // n_bu_heavy with more than kHeavyIn in-arcs first (longest first), then the
@@ -292,7 +298,13 @@ struct tkc_graph {
   unsigned long long *nb_key = nullptr;       //   floor(S~ * 2^46 / (r-1)^2)
   unsigned long long *nb_hkey = nullptr;      // harmonic: ~(FP64 bits of the upper bound on h)
   uint32_t *nb_horder = nullptr;              // harmonic NBCut order: by (nb_hkey, id)
-  mutable uint32_t *bu_list = nullptr;        // bottom-up sweep order: vertices with an in-arc, hubs first
+  // the graph as the search kernel walks it (ensure_search_csr): s_mode 0 =
+  // the graph itself, 1 = a copy whose vertex i is vertex s_unlab[i] (s_lab is
+  // the inverse), vertices by in-degree, largest first; -1 = not built yet
+  mutable int s_mode = -1;
+  mutable uint32_t *s_off = nullptr, *s_col = nullptr, *s_ioff = nullptr, *s_icol = nullptr;
+  mutable uint32_t *s_lab = nullptr, *s_unlab = nullptr;
+  mutable uint32_t *bu_list = nullptr;        // bottom-up sweep order of that CSR: vertices with an in-arc, hubs first
   mutable uint32_t n_bu = 0, n_bu_heavy = 0;
 };
 
@@ -302,7 +314,9 @@ int validate_and_transpose(tkc_graph *g);
 int build_in_csr(tkc_graph *g);
 int ensure_degree_order(tkc_graph *g);
 int ensure_reach_bounds(tkc_graph *g);
-int ensure_bu_list(const tkc_graph *g);
+// the search kernel's CSR and bottom-up list (relabel: the in-degree labelling)
+int ensure_search_csr(const tkc_graph *g, bool relabel);
+void free_search_csr(const tkc_graph *g);
 int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
 // tkc_nb.cu
 // gid/g_directed (several graphs as one union): per-vertex directedness

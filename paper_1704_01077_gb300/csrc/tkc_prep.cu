@@ -228,32 +228,37 @@ int validate_and_transpose(tkc_graph *g) {
   return build_in_csr(g);
 }
 
-// In-arc CSR of g (rows not sorted: an in-row holds its arcs in the order the
-// fill reached them, roughly ascending source id).
-int build_in_csr(tkc_graph *g) {
-  cudaStream_t st = g->ctx->stream;
-  const u32 n = g->n;
-  if (n == 0) return TKC_OK;
+// Transpose of the CSR (off, col) with n vertices: the in-arc CSR (rows not
+// sorted: an in-row holds its arcs in the order the fill reached them, roughly
+// ascending source id).  *ioff and *icol are allocated here.
+static int transpose_csr(const u32 *off, const u32 *col, u32 n, u64 arcs, u32 **ioff, u32 **icol,
+                         cudaStream_t st) {
   u32 *tmp = nullptr, *cursor = nullptr;
-  TKC_TRY(cudaMallocAsync(&g->ioff, ((size_t)n + 1) * sizeof(u32), st));
-  TKC_TRY(cudaMallocAsync(&g->icol, std::max<size_t>(g->arcs, 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(ioff, ((size_t)n + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(icol, std::max<size_t>(arcs, 1) * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&cursor, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&tmp, (((size_t)n + 1) / kScanTile + 2) * sizeof(u32), st));
-  TKC_TRY(cudaMemsetAsync(g->ioff, 0, ((size_t)n + 1) * sizeof(u32), st));
-  if (g->arcs) {
-    TKC_LAUNCH(k_in_count<<<grid_for(g->arcs, 256), 256, 0, st>>>(g->col, g->arcs, g->ioff));
+  TKC_TRY(cudaMemsetAsync(*ioff, 0, ((size_t)n + 1) * sizeof(u32), st));
+  if (arcs) {
+    TKC_LAUNCH(k_in_count<<<grid_for(arcs, 256), 256, 0, st>>>(col, arcs, *ioff));
     TKC_TRY(cudaGetLastError());
   }
-  TKC_RC(scan_exclusive(g->ioff, g->ioff, (u64)n + 1, tmp, st));
-  TKC_TRY(cudaMemcpyAsync(cursor, g->ioff, (size_t)n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
-  if (g->arcs) {
-    TKC_LAUNCH(k_in_fill<<<grid_for((g->arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
-        g->off, g->col, n, g->arcs, cursor, g->icol));
+  TKC_RC(scan_exclusive(*ioff, *ioff, (u64)n + 1, tmp, st));
+  TKC_TRY(cudaMemcpyAsync(cursor, *ioff, (size_t)n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  if (arcs) {
+    TKC_LAUNCH(k_in_fill<<<grid_for((arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
+        off, col, n, arcs, cursor, *icol));
     TKC_TRY(cudaGetLastError());
   }
   TKC_TRY(cudaFreeAsync(cursor, st));
   TKC_TRY(cudaFreeAsync(tmp, st));
   return TKC_OK;
+}
+
+// In-arc CSR of g.
+int build_in_csr(tkc_graph *g) {
+  if (g->n == 0) return TKC_OK;
+  return transpose_csr(g->off, g->col, g->n, g->arcs, &g->ioff, &g->icol, g->ctx->stream);
 }
 
 // ------------------------------------------------------------------ stable LSD radix sort (4-bit digits)
@@ -424,22 +429,20 @@ __global__ void k_bu_keys(const u32 *ioff, u32 n, u32 heavy_in, u32 *key, u32 *v
   if ((threadIdx.x & 31) == 0 && heavy) atomicAdd(&count[1], heavy);
 }
 
-// The vertices that bottom-up levels sweep: those with an in-arc (no other
-// vertex can be discovered bottom-up; a source is seeded directly).  First
-// the n_heavy vertices of more than kHeavyIn in-arcs, whose rows a whole warp
-// walks, longest rows first (bit length of the in-degree, then id); then the
-// others by id, so that a warp's 32 entries share a few frontier-bitmap words.
-// Only the order of work depends on it, not any result.
-int ensure_bu_list(const tkc_graph *g) {
-  if (g->bu_list || g->n == 0) return TKC_OK;
-  cudaStream_t st = g->ctx->stream;
-  const u32 n = g->n;
+// The vertices that bottom-up levels sweep, for the in-arc CSR `ioff`: those
+// with an in-arc (no other vertex can be discovered bottom-up; a source is
+// seeded directly).  First the n_heavy vertices of more than kHeavyIn in-arcs,
+// whose rows a whole warp walks, longest rows first (bit length of the
+// in-degree, then id); then the others by id, so that a warp's 32 entries
+// share a few frontier-bitmap words.  Only the order of work depends on it,
+// not any result.  *list is allocated here.
+static int build_bu_list(const u32 *ioff, u32 n, cudaStream_t st, u32 **list, u32 *n_bu, u32 *n_heavy) {
   u32 *keys = nullptr, *ids = nullptr, *cnt = nullptr;
   TKC_TRY(cudaMallocAsync(&ids, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&keys, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&cnt, 2 * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(u32), st));
-  TKC_LAUNCH(k_bu_keys<<<grid_for(n, 256), 256, 0, st>>>(g->ioff, n, kHeavyIn, keys, ids, cnt));
+  TKC_LAUNCH(k_bu_keys<<<grid_for(n, 256), 256, 0, st>>>(ioff, n, kHeavyIn, keys, ids, cnt));
   TKC_TRY(cudaGetLastError());
   TKC_RC(radix_sort_pairs(keys, ids, n, 6, st));
   u32 c[2] = {0, 0};
@@ -447,9 +450,119 @@ int ensure_bu_list(const tkc_graph *g) {
   TKC_TRY(cudaFreeAsync(keys, st));
   TKC_TRY(cudaFreeAsync(cnt, st));
   TKC_TRY(cudaStreamSynchronize(st));
-  g->bu_list = ids;
-  g->n_bu = c[0];
-  g->n_bu_heavy = c[1];
+  *list = ids;
+  *n_bu = c[0];
+  *n_heavy = c[1];
+  return TKC_OK;
+}
+
+// ------------------------------------------------------------------ the search kernel's copy of the graph
+
+// Relabelling key: in-degree, larger first (the stable sort keeps ids
+// ascending among equal in-degrees).
+__global__ void k_relabel_keys(const u32 *ioff, u32 n, u32 maxd, u32 *key, u32 *val) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    key[v] = maxd - (ioff[v + 1] - ioff[v]);
+    val[v] = v;
+  }
+}
+
+// lab = the inverse of unlab; rowlen[i] = out-degree of vertex unlab[i].
+__global__ void k_relabel_rows(const u32 *unlab, const u32 *off, u32 n, u32 *lab, u32 *rowlen) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const u32 v = unlab[i];
+    lab[v] = i;
+    rowlen[i] = off[v + 1] - off[v];
+  }
+}
+
+// Row i of the relabelled out-CSR: the out-row of vertex unlab[i], each target
+// replaced by its label.  Arcs are dealt to warps in fixed ranges.
+__global__ void k_relabel_cols(const u32 *__restrict__ s_off, const u32 *__restrict__ unlab,
+                               const u32 *__restrict__ off, const u32 *__restrict__ col,
+                               const u32 *__restrict__ lab, u32 n, u64 arcs, u32 *__restrict__ s_col) {
+  grid_walk_arcs<true>(s_off, n, arcs, [&](u32 i, u64 a, bool valid, u32 rs) {
+    if (valid) s_col[a] = lab[col[off[unlab[i]] + (u32)(a - rs)]];
+  });
+}
+
+void free_search_csr(const tkc_graph *g) {
+  if (g->s_ioff && g->s_ioff != g->s_off) cudaFree(g->s_ioff);
+  if (g->s_icol && g->s_icol != g->s_col) cudaFree(g->s_icol);
+  void *ptrs[] = {g->s_off, g->s_col, g->s_lab, g->s_unlab, g->bu_list};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  g->s_off = g->s_col = g->s_ioff = g->s_icol = g->s_lab = g->s_unlab = nullptr;
+  g->bu_list = nullptr;
+  g->n_bu = g->n_bu_heavy = 0;
+  g->s_mode = -1;
+}
+
+// The graph as the search kernel walks it.  Plain: the graph itself.
+// Relabelled: vertex i of the copy is vertex unlab[i] of the graph, the
+// vertices taken by in-degree, largest first.  Bottom-up levels gather the
+// frontier rows of in-neighbours, and in-neighbours are mostly vertices of
+// large degree; with those first, the rows and frontier bits that levels
+// touch most sit together in a few megabytes that stay in L2 (R-MAT 22,
+// NBCut: search kernel 51 -> 35 ms).  The copy's in-rows come out in
+// ascending label order, largest in-degree first, so that a walk meets the
+// likely frontier vertices early.  An undirected graph's copy serves both
+// directions (its transpose is itself).  Every result is the same: sources,
+// slots, ties and outputs keep the graph's own ids; only the search's rows
+// are indexed by labels.
+int ensure_search_csr(const tkc_graph *g, bool relabel) {
+  const int want = relabel ? 1 : 0;
+  if (g->s_mode == want || g->n == 0) return TKC_OK;
+  free_search_csr(g);  // the other labelling's copy, or what a failed build left
+  cudaStream_t st = g->ctx->stream;
+  const u32 n = g->n;
+  if (!relabel) {
+    TKC_RC(build_bu_list(g->ioff, n, st, &g->bu_list, &g->n_bu, &g->n_bu_heavy));
+    g->s_mode = 0;
+    return TKC_OK;
+  }
+  u32 *keys = nullptr, *stats = nullptr, *gcol = nullptr, *tmp = nullptr;
+  TKC_TRY(cudaMallocAsync(&g->s_unlab, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&g->s_lab, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&g->s_off, ((size_t)n + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&gcol, std::max<size_t>(g->arcs, 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&keys, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&tmp, (((size_t)n + 1) / kScanTile + 2) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&stats, 2 * sizeof(u32), st));
+  TKC_TRY(cudaMemsetAsync(stats, 0, 2 * sizeof(u32), st));
+  TKC_LAUNCH(k_maxdeg<<<grid_for(n, 256), 256, 0, st>>>(g->ioff, n, stats, stats + 1));
+  TKC_TRY(cudaGetLastError());
+  u32 hs[2];
+  TKC_TRY(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  TKC_LAUNCH(k_relabel_keys<<<grid_for(n, 256), 256, 0, st>>>(g->ioff, n, hs[0], keys, g->s_unlab));
+  TKC_TRY(cudaGetLastError());
+  int bits = 0;
+  while (bits < 32 && (hs[0] >> bits) != 0) ++bits;
+  TKC_RC(radix_sort_pairs(keys, g->s_unlab, n, bits, st));
+  TKC_TRY(cudaMemsetAsync(g->s_off + n, 0, sizeof(u32), st));
+  TKC_LAUNCH(k_relabel_rows<<<grid_for(n, 256), 256, 0, st>>>(g->s_unlab, g->off, n, g->s_lab, g->s_off));
+  TKC_TRY(cudaGetLastError());
+  TKC_RC(scan_exclusive(g->s_off, g->s_off, (u64)n + 1, tmp, st));
+  if (g->arcs) {
+    TKC_LAUNCH(k_relabel_cols<<<grid_for((g->arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
+        g->s_off, g->s_unlab, g->off, g->col, g->s_lab, n, g->arcs, gcol));
+    TKC_TRY(cudaGetLastError());
+  }
+  TKC_RC(transpose_csr(g->s_off, gcol, n, g->arcs, &g->s_ioff, &g->s_icol, st));
+  if (g->directed) {
+    g->s_col = gcol;
+  } else {
+    TKC_TRY(cudaFreeAsync(g->s_off, st));
+    TKC_TRY(cudaFreeAsync(gcol, st));
+    g->s_off = g->s_ioff;
+    g->s_col = g->s_icol;
+  }
+  TKC_TRY(cudaFreeAsync(keys, st));
+  TKC_TRY(cudaFreeAsync(tmp, st));
+  TKC_TRY(cudaFreeAsync(stats, st));
+  TKC_RC(build_bu_list(g->s_ioff, n, st, &g->bu_list, &g->n_bu, &g->n_bu_heavy));
+  g->s_mode = 1;
   return TKC_OK;
 }
 

@@ -51,7 +51,7 @@ class tkc_options(ctypes.Structure):
                 ("batch_bits", ctypes.c_uint32), ("bu_num", ctypes.c_uint32), ("bu_den", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("seed_factor", ctypes.c_uint32),
                 ("timeout_cycles", ctypes.c_uint64), ("teams", ctypes.c_uint32), ("nb_levels", ctypes.c_uint32),
-                ("large_blocks", ctypes.c_uint32), ("deterministic", ctypes.c_uint32)]
+                ("large_blocks", ctypes.c_uint32), ("deterministic", ctypes.c_uint32), ("relabel", ctypes.c_uint32)]
 
 
 class tkc_result(ctypes.Structure):
@@ -199,11 +199,12 @@ class Options:
     nb_levels: int = 0
     large_blocks: int = 0
     deterministic: int = 0
+    relabel: int = 0
 
     def to_c(self) -> tkc_options:
         return tkc_options(self.device, self.stream, self.order, self.batch_bits, self.bu_num, self.bu_den,
                            self.blocks, self.seed_factor, self.timeout_cycles, self.teams, self.nb_levels,
-                           self.large_blocks, self.deterministic)
+                           self.large_blocks, self.deterministic, self.relabel)
 
 
 @dataclass

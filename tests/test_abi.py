@@ -41,8 +41,8 @@ def test_binding_covers_every_declared_symbol():
 def test_struct_layouts_match_header():
     from paper_1704_01077_gb300 import tkc
 
-    # int + pad + pointer + 6 x uint32 + uint64 + 4 x uint32
-    assert ctypes.sizeof(tkc.tkc_options) == 64
+    # int + pad + pointer + 6 x uint32 + uint64 + 5 x uint32 (+ pad)
+    assert ctypes.sizeof(tkc.tkc_options) == 72
     assert tkc.tkc_options.timeout_cycles.offset == 40
     assert tkc.tkc_options.large_blocks.offset == 56
     # 5 pointers, 3 x uint32 (+pad), 6 x uint64, 2 x uint32, 2 x double
@@ -50,6 +50,7 @@ def test_struct_layouts_match_header():
     assert tkc.tkc_result.edges_visited.offset == 56
     assert tkc.tkc_result.ms_bfs.offset == 120
     assert tkc.tkc_options.deterministic.offset == 60
+    assert tkc.tkc_options.relabel.offset == 64
     # 6 x uint32, 17 x uint64, 1 double
     assert ctypes.sizeof(tkc.tkc_run_stats) == 168
     assert tkc.tkc_run_stats.ms_kernel.offset == 160
