@@ -340,6 +340,8 @@ def main():
     ap.add_argument("--bu-num", type=int, default=0,
                     help="a level runs bottom-up when its frontier arcs exceed arcs / BU_NUM (0 = library default)")
     ap.add_argument("--deterministic", type=int, default=0, help="1: one team, reproducible counters")
+    ap.add_argument("--relabel", type=int, default=0, choices=[0, 1, 2],
+                    help="search on the in-degree labelling: 0 = library choice, 1 = always, 2 = never")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "tkc":
         args.warmup = 3
@@ -374,7 +376,8 @@ def main():
               "learned-seed": tkc.TKC_ORDER_LEARNED, "learned-nb": tkc.TKC_ORDER_LEARNED_NB}
     base_opt = dict(device=local, stream=stream.cuda_stream, batch_bits=args.bits, order=orders[args.order],
                     teams=args.teams, seed_factor=5 if args.order in ("learned-seed", "learned-nb") else 0,
-                    nb_levels=args.nb_levels, deterministic=args.deterministic, bu_num=args.bu_num, bu_den=1)
+                    nb_levels=args.nb_levels, deterministic=args.deterministic, bu_num=args.bu_num, bu_den=1,
+                    relabel=args.relabel)
     ctx = tkc.tkc_create(tkc.Options(**base_opt))
     weights = None
     if args.order.startswith("learned") or (not args.no_plain and not multi and args.measure == "closeness"):
@@ -549,6 +552,7 @@ def main():
             "config": {"workload": args.workload, "description": desc, "k": k, "batch_bits": res.batch_bits,
                        "order": args.order, "measure": args.measure, "bound": args.bound,
                        "teams": args.teams or "library default", "bu_num": args.bu_num or "library default", "deterministic": args.deterministic,
+                       "relabel": args.relabel or "library default",
                        "work_per_step": work,
                        "work_unit": ("arcs visited by plain one-source NBCut (Algorithm 1), counted by the CPU "
                                      "oracle on the same graph" if work_fixed is not None else

@@ -339,6 +339,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.bu_list = g->bu_list;
   p.n_bu = g->n_bu;
   p.n_bu_heavy = g->n_bu_heavy;
+  p.heavy_in = g->heavy_in ? g->heavy_in : kHeavyIn;
   p.large_blocks = o.large_blocks;
   p.alpha = g->alpha;
   p.omega = g->omega;

@@ -1269,7 +1269,7 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
       // counter as they finish: first groups of 32 long in-rows, group j
       // holding list entries j, j + hg, j + 2 hg, ... so that the longest rows
       // land in different warps; then chunks of kBuChunkVerts consecutive
-      // entries of the shorter rows (ids ascending).
+      // entries of the shorter rows (labels ascending).
       const uint32_t nheavy = p.bu_list ? p.n_bu_heavy : 0u;
       const uint32_t nlight = p.bu_list ? p.n_bu - nheavy : p.n;
       const uint32_t hg = (nheavy + 31) / 32;
@@ -1313,7 +1313,7 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
             }
             e0 = p.ioff[w];
             ee = p.ioff[w + 1];
-            heavy = any && ee - e0 > kHeavyIn;
+            heavy = any && ee - e0 > p.heavy_in;
             if (any && !heavy) {
               // U in-arcs per step, software-pipelined: step i's rows (of the
               // in-neighbours on a frontier) are loaded together with step
@@ -1441,8 +1441,8 @@ __global__ void __launch_bounds__(TPB, 1) bfscut_kernel(RunParams p0) {
           // the next frontier's bitmap starts all zero (each level clears the
           // bits of its own frontier), so setting the new vertices' bits
           // suffices: one atomic per bitmap word the group's new vertices share
-          // (shorter rows: ids ascending, a few words), one per vertex for the
-          // long rows (ids scattered)
+          // (shorter rows: labels ascending, a few words), one per vertex for the
+          // long rows (labels scattered)
           if (hitem) {
             if (isnew) atomicOr(&FBnext[w >> 5], 1u << (w & 31));
           } else {

@@ -40,11 +40,20 @@ void note_launches(unsigned count);
 constexpr uint32_t kMaxN = 1u << 26; // list counters pack the count in 26 bits
 constexpr int kMaxWords = 8;         // 512-bit source batches
 constexpr uint32_t kBuChunkVerts = 128;  // bottom-up levels: list entries per chunk a warp takes
-// bottom-up levels: in-rows longer than this are walked by the whole warp
+// bottom-up levels: in-rows longer than this are walked by the whole warp.
+// In id order a warp's 32 lanes hold rows of unrelated lengths, so rows
+// beyond a few steps of a lane go to the warp (kHeavyIn); in the in-degree
+// labelling neighbouring rows have similar lengths and a lane may keep longer
+// ones (kHeavyInLabelled; R-MAT 22, NBCut, search kernel: 24 -> 34.5 ms,
+// 48 -> 33.1, 96 -> 32.4, 192 to 384 -> 32.5).
 #ifndef TKC_HEAVY_IN
 #define TKC_HEAVY_IN 24
 #endif
+#ifndef TKC_HEAVY_IN_LABELLED
+#define TKC_HEAVY_IN_LABELLED 96
+#endif
 constexpr uint32_t kHeavyIn = TKC_HEAVY_IN;
+constexpr uint32_t kHeavyInLabelled = TKC_HEAVY_IN_LABELLED;
 
 // Device-resident state of one persistent BFSCut run (one graph).
 struct Ctl {
@@ -129,10 +138,11 @@ struct RunParams {
   const uint32_t *unlab;  // label -> id
   const uint32_t *alpha, *omega;
   // bottom-up levels sweep bu_list[0, n_bu): the vertices with an in-arc, the
-  // n_bu_heavy with more than kHeavyIn in-arcs first (longest first), then the
-  // others by id (nullptr: every vertex, by id)
+  // n_bu_heavy with more than heavy_in in-arcs first (longest first), then the
+  // others by label (nullptr: every vertex, by label)
   const uint32_t *bu_list;
   uint32_t n_bu, n_bu_heavy;
+  uint32_t heavy_in;  // in-rows longer than this are walked by the whole warp
   uint32_t large_blocks;  // tkc_options.large_blocks: 0 = by size, 1 = larger blocks, 2 = 512 threads
   const uint32_t *order;
   uint32_t norder;  // sources in `order` to examine (all have out-degree >= 1)
@@ -306,6 +316,7 @@ struct tkc_graph {
   mutable uint32_t *s_lab = nullptr, *s_unlab = nullptr;
   mutable uint32_t *bu_list = nullptr;        // bottom-up sweep order of that CSR: vertices with an in-arc, hubs first
   mutable uint32_t n_bu = 0, n_bu_heavy = 0;
+  mutable uint32_t heavy_in = 0;              // the list's long-row threshold (kHeavyIn or kHeavyInLabelled)
 };
 
 namespace tkc {

@@ -228,15 +228,29 @@ int validate_and_transpose(tkc_graph *g) {
   return build_in_csr(g);
 }
 
-// Transpose of the CSR (off, col) with n vertices: the in-arc CSR (rows not
-// sorted: an in-row holds its arcs in the order the fill reached them, roughly
-// ascending source id).  *ioff and *icol are allocated here.
+// Fills the in-arc columns of the CSR (off, col) with n vertices into icol,
+// given its in-row offsets ioff (rows not sorted: an in-row holds its arcs in
+// the order the fill reached them, roughly ascending source id).
+static int fill_in_arcs(const u32 *off, const u32 *col, u32 n, u64 arcs, const u32 *ioff, u32 *icol,
+                        cudaStream_t st) {
+  if (!arcs) return TKC_OK;
+  u32 *cursor = nullptr;
+  TKC_TRY(cudaMallocAsync(&cursor, (size_t)n * sizeof(u32), st));
+  TKC_TRY(cudaMemcpyAsync(cursor, ioff, (size_t)n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  TKC_LAUNCH(k_in_fill<<<grid_for((arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
+      off, col, n, arcs, cursor, icol));
+  TKC_TRY(cudaGetLastError());
+  TKC_TRY(cudaFreeAsync(cursor, st));
+  return TKC_OK;
+}
+
+// Transpose of the CSR (off, col) with n vertices: the in-arc CSR.  *ioff and
+// *icol are allocated here.
 static int transpose_csr(const u32 *off, const u32 *col, u32 n, u64 arcs, u32 **ioff, u32 **icol,
                          cudaStream_t st) {
-  u32 *tmp = nullptr, *cursor = nullptr;
+  u32 *tmp = nullptr;
   TKC_TRY(cudaMallocAsync(ioff, ((size_t)n + 1) * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(icol, std::max<size_t>(arcs, 1) * sizeof(u32), st));
-  TKC_TRY(cudaMallocAsync(&cursor, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&tmp, (((size_t)n + 1) / kScanTile + 2) * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(*ioff, 0, ((size_t)n + 1) * sizeof(u32), st));
   if (arcs) {
@@ -244,13 +258,7 @@ static int transpose_csr(const u32 *off, const u32 *col, u32 n, u64 arcs, u32 **
     TKC_TRY(cudaGetLastError());
   }
   TKC_RC(scan_exclusive(*ioff, *ioff, (u64)n + 1, tmp, st));
-  TKC_TRY(cudaMemcpyAsync(cursor, *ioff, (size_t)n * sizeof(u32), cudaMemcpyDeviceToDevice, st));
-  if (arcs) {
-    TKC_LAUNCH(k_in_fill<<<grid_for((arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
-        off, col, n, arcs, cursor, *icol));
-    TKC_TRY(cudaGetLastError());
-  }
-  TKC_TRY(cudaFreeAsync(cursor, st));
+  TKC_RC(fill_in_arcs(off, col, n, arcs, *ioff, *icol, st));
   TKC_TRY(cudaFreeAsync(tmp, st));
   return TKC_OK;
 }
@@ -431,18 +439,19 @@ __global__ void k_bu_keys(const u32 *ioff, u32 n, u32 heavy_in, u32 *key, u32 *v
 
 // The vertices that bottom-up levels sweep, for the in-arc CSR `ioff`: those
 // with an in-arc (no other vertex can be discovered bottom-up; a source is
-// seeded directly).  First the n_heavy vertices of more than kHeavyIn in-arcs,
+// seeded directly).  First the n_heavy vertices of more than heavy_in in-arcs,
 // whose rows a whole warp walks, longest rows first (bit length of the
 // in-degree, then id); then the others by id, so that a warp's 32 entries
 // share a few frontier-bitmap words.  Only the order of work depends on it,
 // not any result.  *list is allocated here.
-static int build_bu_list(const u32 *ioff, u32 n, cudaStream_t st, u32 **list, u32 *n_bu, u32 *n_heavy) {
+static int build_bu_list(const u32 *ioff, u32 n, u32 heavy_in, cudaStream_t st, u32 **list, u32 *n_bu,
+                         u32 *n_heavy) {
   u32 *keys = nullptr, *ids = nullptr, *cnt = nullptr;
   TKC_TRY(cudaMallocAsync(&ids, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&keys, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&cnt, 2 * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(u32), st));
-  TKC_LAUNCH(k_bu_keys<<<grid_for(n, 256), 256, 0, st>>>(ioff, n, kHeavyIn, keys, ids, cnt));
+  TKC_LAUNCH(k_bu_keys<<<grid_for(n, 256), 256, 0, st>>>(ioff, n, heavy_in, keys, ids, cnt));
   TKC_TRY(cudaGetLastError());
   TKC_RC(radix_sort_pairs(keys, ids, n, 6, st));
   u32 c[2] = {0, 0};
@@ -467,12 +476,15 @@ __global__ void k_relabel_keys(const u32 *ioff, u32 n, u32 maxd, u32 *key, u32 *
   }
 }
 
-// lab = the inverse of unlab; rowlen[i] = out-degree of vertex unlab[i].
-__global__ void k_relabel_rows(const u32 *unlab, const u32 *off, u32 n, u32 *lab, u32 *rowlen) {
+// lab = the inverse of unlab; out_len[i] and in_len[i] = out- and in-degree
+// of vertex unlab[i] (in_len may be null).
+__global__ void k_relabel_rows(const u32 *unlab, const u32 *off, const u32 *ioff, u32 n, u32 *lab, u32 *out_len,
+                               u32 *in_len) {
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const u32 v = unlab[i];
     lab[v] = i;
-    rowlen[i] = off[v + 1] - off[v];
+    out_len[i] = off[v + 1] - off[v];
+    if (in_len) in_len[i] = ioff[v + 1] - ioff[v];
   }
 }
 
@@ -517,7 +529,8 @@ int ensure_search_csr(const tkc_graph *g, bool relabel) {
   cudaStream_t st = g->ctx->stream;
   const u32 n = g->n;
   if (!relabel) {
-    TKC_RC(build_bu_list(g->ioff, n, st, &g->bu_list, &g->n_bu, &g->n_bu_heavy));
+    g->heavy_in = kHeavyIn;
+    TKC_RC(build_bu_list(g->ioff, n, g->heavy_in, st, &g->bu_list, &g->n_bu, &g->n_bu_heavy));
     g->s_mode = 0;
     return TKC_OK;
   }
@@ -540,16 +553,24 @@ int ensure_search_csr(const tkc_graph *g, bool relabel) {
   int bits = 0;
   while (bits < 32 && (hs[0] >> bits) != 0) ++bits;
   TKC_RC(radix_sort_pairs(keys, g->s_unlab, n, bits, st));
+  // the copy's row lengths are the graph's degrees in label order: its
+  // in-rows need no counting pass
+  TKC_TRY(cudaMallocAsync(&g->s_ioff, ((size_t)n + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&g->s_icol, std::max<size_t>(g->arcs, 1) * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(g->s_off + n, 0, sizeof(u32), st));
-  TKC_LAUNCH(k_relabel_rows<<<grid_for(n, 256), 256, 0, st>>>(g->s_unlab, g->off, n, g->s_lab, g->s_off));
+  TKC_TRY(cudaMemsetAsync(g->s_ioff + n, 0, sizeof(u32), st));
+  TKC_LAUNCH(k_relabel_rows<<<grid_for(n, 256), 256, 0, st>>>(g->s_unlab, g->off, g->ioff, n, g->s_lab, g->s_off,
+                                                              g->s_ioff));
   TKC_TRY(cudaGetLastError());
   TKC_RC(scan_exclusive(g->s_off, g->s_off, (u64)n + 1, tmp, st));
+  TKC_RC(scan_exclusive(g->s_ioff, g->s_ioff, (u64)n + 1, tmp, st));
   if (g->arcs) {
     TKC_LAUNCH(k_relabel_cols<<<grid_for((g->arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
         g->s_off, g->s_unlab, g->off, g->col, g->s_lab, n, g->arcs, gcol));
     TKC_TRY(cudaGetLastError());
   }
-  TKC_RC(transpose_csr(g->s_off, gcol, n, g->arcs, &g->s_ioff, &g->s_icol, st));
+  // in-rows by transposition, so that each runs in ascending label order
+  TKC_RC(fill_in_arcs(g->s_off, gcol, n, g->arcs, g->s_ioff, g->s_icol, st));
   if (g->directed) {
     g->s_col = gcol;
   } else {
@@ -561,7 +582,8 @@ int ensure_search_csr(const tkc_graph *g, bool relabel) {
   TKC_TRY(cudaFreeAsync(keys, st));
   TKC_TRY(cudaFreeAsync(tmp, st));
   TKC_TRY(cudaFreeAsync(stats, st));
-  TKC_RC(build_bu_list(g->s_ioff, n, st, &g->bu_list, &g->n_bu, &g->n_bu_heavy));
+  g->heavy_in = kHeavyInLabelled;
+  TKC_RC(build_bu_list(g->s_ioff, n, g->heavy_in, st, &g->bu_list, &g->n_bu, &g->n_bu_heavy));
   g->s_mode = 1;
   return TKC_OK;
 }
