@@ -99,7 +99,8 @@ typedef struct {
                               by side and cut against a threshold another team may be updating, so counters
                               vary from run to run (results never do). */
   uint32_t relabel;        /* vertex labels of the search's rows: 0 = library choice (batched searches on graphs
-                              of 2^20 vertices or more walk a copy of the graph whose vertices are numbered by
+                              of 2^20 vertices or more -- for several graphs in one launch, when the largest has
+                              -- walk a copy of the graph whose vertices are numbered by
                               in-degree, largest first, so that the rows levels touch most share L2; else the
                               graph itself), 1 = always that copy, 2 = never.  Sources, ties and every id in
                               the results are the graph's own ids whatever the choice; results never depend

@@ -264,6 +264,9 @@ struct RunSetup {
   const u64 *seed_S;
   const u32 *seed_r, *seed_id;
   u32 nseed;
+  // size that decides the library's labelling choice: the largest graph of a
+  // multi-graph union (0: g->n)
+  u32 size_n;
 };
 
 // Teams used when the options leave it to the library: one team for small
@@ -326,8 +329,10 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.directed = g->directed;
   p.arcs = g->arcs;
   // batched searches of large graphs walk the in-degree labelling (its hot
-  // rows stay in L2); one-source searches and small graphs the graph itself
-  const bool relabel = o.relabel == 1 || (o.relabel == 0 && rs.B > 1 && g->n >= (1u << 20));
+  // rows stay in L2); one-source searches and small graphs (of a union: when
+  // no graph is large, each one's rows fit L2 anyway) the graph itself
+  const u32 size_n = rs.size_n ? rs.size_n : g->n;
+  const bool relabel = o.relabel == 1 || (o.relabel == 0 && rs.B > 1 && size_n >= (1u << 20));
   TKC_RC(ensure_search_csr(g, relabel));
   const bool lab = g->s_mode == 1;
   p.off = lab ? g->s_off : g->off;
@@ -1590,6 +1595,7 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   rs.ng = ng;
   rs.gid = gid;
   rs.g_directed = d_gdir;
+  rs.size_n = maxn;
   Ctl hc;
   MULTI_RC(run_search(ctx, rs, &hc));
   std::vector<GraphOut> go(ng);
