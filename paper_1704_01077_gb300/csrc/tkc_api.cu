@@ -1570,7 +1570,7 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   // with alpha = omega = its size); only the biggest SCC of the union gets the
   // exact reach by BFS, so the other graphs' omega may be looser than alone,
   // which changes pruning, never results
-  MULTI_RC(ensure_reach_bounds(&U));
+  MULTI_RC(ensure_reach_bounds(&U, gid, ng));
   if (nb) {
     // the sweeps run once over the union (each vertex's counts involve only its
     // own graph, so they equal the per-graph values); all sources of all graphs

@@ -324,7 +324,9 @@ namespace tkc {
 int validate_and_transpose(tkc_graph *g);
 int build_in_csr(tkc_graph *g);
 int ensure_degree_order(tkc_graph *g);
-int ensure_reach_bounds(tkc_graph *g);
+// gid/ng (several graphs as one union, graphs in contiguous vertex ranges):
+// one pivot per graph in the first forward-backward round
+int ensure_reach_bounds(tkc_graph *g, const uint32_t *gid = nullptr, uint32_t ng = 0);
 // the search kernel's CSR and bottom-up list (relabel: the in-degree labelling)
 int ensure_search_csr(const tkc_graph *g, bool relabel);
 void free_search_csr(const tkc_graph *g);

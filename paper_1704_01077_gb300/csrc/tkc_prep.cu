@@ -709,9 +709,9 @@ static int reach_undirected(tkc_graph *g) {
 // ------------------------------------------------------------------ reach: directed
 
 // SCCs and Algorithm 6 run on the device (tkc_scc.cu).
-int reach_directed_gpu(tkc_graph *g);
+int reach_directed_gpu(tkc_graph *g, const u32 *gid, u32 ng);
 
-int ensure_reach_bounds(tkc_graph *g) {
+int ensure_reach_bounds(tkc_graph *g, const u32 *gid, u32 ng) {
   if (g->have_reach) return TKC_OK;
   cudaStream_t st = g->ctx->stream;
   if (g->n == 0) {
@@ -722,7 +722,7 @@ int ensure_reach_bounds(tkc_graph *g) {
   if (!g->omega) TKC_TRY(cudaMallocAsync(&g->omega, (size_t)g->n * sizeof(u32), st));
   if (!g->scc_size) TKC_TRY(cudaMallocAsync(&g->scc_size, (size_t)g->n * sizeof(u32), st));
   if (!g->comp) TKC_TRY(cudaMallocAsync(&g->comp, (size_t)g->n * sizeof(u32), st));
-  TKC_RC(g->directed ? reach_directed_gpu(g) : reach_undirected(g));
+  TKC_RC(g->directed ? reach_directed_gpu(g, gid, ng) : reach_undirected(g));
   g->have_reach = true;
   return TKC_OK;
 }

@@ -269,10 +269,25 @@ __global__ void k_bfs_start(const u32 *off, u32 *mark, u32 *q0, u64 *qo0, BfsCtl
   c->q[0] = (1ull << kQShift) | (unsigned long long)(off[src + 1] - off[src]);
 }
 
-// Reachability from src along (off, col) into mark (see k_bfs_reach); one
-// cooperative launch.
+// Several sources at once (nsrc distinct vertices, device array): all at step 0.
+__global__ void k_bfs_start_many(const u32 *off, const u32 *src, u32 nsrc, u32 *mark, u32 *q0, u64 *qo0,
+                                 BfsCtl *c) {
+  u64 arcs = 0;
+  for (u32 i = 0; i < nsrc; ++i) {
+    const u32 v = src[i];
+    mark[v] = 0;
+    q0[i] = v;
+    qo0[i] = arcs;
+    arcs += off[v + 1] - off[v];
+  }
+  c->q[0] = ((unsigned long long)nsrc << kQShift) | arcs;
+}
+
+// Reachability from src (or, with srcs, from the nsrc vertices of the device
+// array srcs) along (off, col) into mark (see k_bfs_reach); one cooperative
+// launch.
 int bfs_reach(tkc_ctx *ctx, const u32 *off, const u32 *col, const u32 *roff, const u32 *rcol, u32 n, u64 arcs,
-              u32 *mark, u32 src, cudaStream_t st) {
+              u32 *mark, u32 src, cudaStream_t st, const u32 *srcs = nullptr, u32 nsrc = 0) {
   static int per_sm = 0;
   if (!per_sm) {
     TKC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_reach, kBfsThreads, 0));
@@ -288,7 +303,11 @@ int bfs_reach(tkc_ctx *ctx, const u32 *off, const u32 *col, const u32 *roff, con
   TKC_TRY(cudaMemsetAsync(mark, 0xff, (size_t)n * sizeof(u32), st));
   u32 *q0 = q, *q1 = q + n;
   u64 *qo0 = qo, *qo1 = qo + n;
-  TKC_LAUNCH(k_bfs_start<<<1, 1, 0, st>>>(off, mark, q0, qo0, c, src));
+  if (srcs) {
+    TKC_LAUNCH(k_bfs_start_many<<<1, 1, 0, st>>>(off, srcs, nsrc, mark, q0, qo0, c));
+  } else {
+    TKC_LAUNCH(k_bfs_start<<<1, 1, 0, st>>>(off, mark, q0, qo0, c, src));
+  }
   u64 timeout = ctx->opt.timeout_cycles ? ctx->opt.timeout_cycles : (1ull << 34);
   void *args[] = {(void *)&off,  (void *)&col, (void *)&roff, (void *)&rcol, (void *)&n,
                   (void *)&arcs, (void *)&mark, (void *)&q0,  (void *)&q1,   (void *)&qo0,
@@ -327,6 +346,51 @@ __global__ void k_fwbw_mark(const u32 *fw, const u32 *bw, u32 n, uint8_t *active
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
     if (active[v] && fw[v] != INF && bw[v] != INF) {
       comp[v] = pivot;
+      active[v] = 0;
+    }
+}
+
+// Several graphs as one union (gid: graph of each vertex, graphs in
+// contiguous vertex ranges): the pivot of every graph, best[g] packed like
+// k_pivot's.  Lanes of one graph first take their warp's maximum, so each
+// graph sees about one atomic per warp.
+__global__ void k_pivot_many(const u32 *outd, const u32 *ind, const uint8_t *active, const u32 *gid, u32 n,
+                             u64 *best) {
+  for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
+    const u32 v = base + (threadIdx.x & 31);
+    u32 score = 0, g = 0xffffffffu;
+    if (v < n) {
+      g = gid[v];
+      if (active[v]) {
+        const u64 s = (u64)outd[v] * (u64)ind[v];
+        score = s > 0xffffffffull ? 0xffffffffu : (u32)s;
+      }
+    }
+    const unsigned peers = __match_any_sync(FULL, g);
+    const u32 hi = __reduce_max_sync(peers, score);
+    const u32 lo = __reduce_max_sync(peers, score == hi && v < n ? 0xffffffffu - v : 0u);
+    if (v < n && hi > 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+      atomicMax(&best[g], ((u64)hi << 32) | (u64)lo);
+  }
+}
+
+// The graphs' pivots as a list (graphs without one are skipped); count in *cnt.
+__global__ void k_pivot_list(const u64 *best, u32 ng, u32 *piv, u32 *list, u32 *cnt) {
+  for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    const u64 b = best[g];
+    piv[g] = b ? 0xffffffffu - (u32)(b & 0xffffffffu) : INF;
+    if (b) list[atomicAdd(cnt, 1u)] = piv[g];
+  }
+}
+
+// fw, bw: reach from / to all pivots at once.  The graphs are disjoint, so a
+// vertex reached either way is reached by its own graph's pivot only, and it
+// lies in that pivot's SCC when reached both ways.
+__global__ void k_fwbw_mark_many(const u32 *fw, const u32 *bw, const u32 *gid, const u32 *piv, u32 n,
+                                 uint8_t *active, u32 *comp) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (active[v] && fw[v] != INF && bw[v] != INF) {
+      comp[v] = piv[gid[v]];
       active[v] = 0;
     }
 }
@@ -726,7 +790,7 @@ u32 read_u32(const u32 *d, cudaStream_t st, int *rc) {
 
 }  // namespace
 
-int reach_directed_gpu(tkc_graph *g) {
+int reach_directed_gpu(tkc_graph *g, const u32 *gid, u32 ng) {
   cudaStream_t st = g->ctx->stream;
   const u32 n = g->n;
   DevBufs b;
@@ -765,6 +829,28 @@ int reach_directed_gpu(tkc_graph *g) {
     TKC_TRY(cudaMemcpyAsync(&hb, best, sizeof(u64), cudaMemcpyDeviceToHost, st));
     TKC_TRY(cudaStreamSynchronize(st));
     if (hb == 0) break;  // nothing left
+    if (round == 0 && gid && ng > 1) {
+      // Several graphs: one pivot per graph and one forward and one backward
+      // search from all of them, so that every graph's largest SCC is found in
+      // this round (with a single pivot, only one graph's would be, and the
+      // colouring rounds would take the rest).
+      u64 *gbest;
+      u32 *piv, *plist, *pcnt;
+      TKC_TRY(b.get(&gbest, ng));
+      TKC_TRY(b.get(&piv, ng));
+      TKC_TRY(b.get(&plist, ng));
+      TKC_TRY(b.get(&pcnt, 1));
+      TKC_TRY(cudaMemsetAsync(gbest, 0, (size_t)ng * sizeof(u64), st));
+      TKC_TRY(cudaMemsetAsync(pcnt, 0, sizeof(u32), st));
+      TKC_LAUNCH(k_pivot_many<<<grid_of(n), 256, 0, st>>>(outd, ind, active, gid, n, gbest));
+      TKC_LAUNCH(k_pivot_list<<<grid_of(ng), 256, 0, st>>>(gbest, ng, piv, plist, pcnt));
+      const u32 np = read_u32(pcnt, st, &rc);
+      TKC_RC(rc);
+      TKC_RC(bfs_reach(g->ctx, g->off, g->col, g->ioff, g->icol, n, g->arcs, fw, 0, st, plist, np));
+      TKC_RC(bfs_reach(g->ctx, g->ioff, g->icol, g->off, g->col, n, g->arcs, bw, 0, st, plist, np));
+      TKC_LAUNCH(k_fwbw_mark_many<<<grid_of(n), 256, 0, st>>>(fw, bw, gid, piv, n, active, comp));
+      continue;  // trim again, then colour; pivot0 stays INF (fw/bw hold no single vertex's reach)
+    }
     if (round == 0) {
       // The BFS run over the whole graph, not only the untrimmed vertices: a
       // trimmed vertex is its own SCC, so the intersection is the same, and
