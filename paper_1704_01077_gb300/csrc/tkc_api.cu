@@ -619,6 +619,26 @@ __global__ void k_union_cols(const u64 *colptr, const u32 *vbase, const u64 *aba
   }
 }
 
+// flag[v] = 1 for the union's vertices of out-degree 0 (flag[nv] = 0).
+__global__ void k_zero_flags(const u32 *off_u, u32 nv, u32 *flag) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v <= nv; v += gridDim.x * blockDim.x)
+    flag[v] = v < nv && off_u[v + 1] == off_u[v];
+}
+
+// The out-degree-0 vertices of the union in id order, as graph-local ids (pos:
+// exclusive scan of k_zero_flags): graph g's are a contiguous run.
+__global__ void k_zero_compact(const u32 *off_u, const u32 *pos, const u32 *gid, const u32 *vbase, u32 nv, u32 *zl) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x)
+    if (off_u[v + 1] == off_u[v]) zl[pos[v]] = v - vbase[gid[v]];
+}
+
+// out[i] = a[idx[i]]
+__global__ void k_gather_u32(const u32 *a, const u32 *idx, u32 m, u32 *out) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) out[i] = a[idx[i]];
+}
+
+int scan_exclusive_u32(const u32 *in, u32 *out, u64 len, u32 *tmp, cudaStream_t st);
+
 }  // namespace tkc
 
 using namespace tkc;
@@ -1504,7 +1524,6 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   std::vector<u64> abase(ng + 1, 0), offptr(ng), colptr(ng);
   std::vector<uint8_t> gdir(ng);
   for (u32 i = 0; i < ng; ++i) {
-    TKC_RC(ensure_degree_order(gs[i]));
     vbase[i + 1] = vbase[i] + gs[i]->n;
     abase[i + 1] = abase[i] + gs[i]->arcs;
     offptr[i] = (u64)gs[i]->off;
@@ -1517,6 +1536,7 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   U.arcs = na;
   U.directed = 1;
   u32 *gid = nullptr, *d_vbase = nullptr;
+  u32 *zflag = nullptr, *zlist = nullptr, *zat = nullptr;  // out-degree-0 vertices of every graph
   u64 *d_abase = nullptr, *d_offptr = nullptr, *d_colptr = nullptr;
   uint8_t *d_gdir = nullptr;
   int rc = TKC_OK;
@@ -1525,7 +1545,8 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
     free_search_csr(&U);
     void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.scc_size, U.comp, U.nb_S, U.nb_r,
                     U.nb_key, U.nb_hkey,
-                    U.nb_order, U.nb_horder, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir};
+                    U.nb_order, U.nb_horder, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir, zflag, zlist,
+                    zat};
     for (void *q : ptrs)
       if (q) cudaFree(q);
   };
@@ -1564,6 +1585,24 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   unsigned ga = (unsigned)std::max<u64>(1, std::min<u64>((na + 255) / 256, (u64)ctx->num_sms * 16));
   if (na) TKC_LAUNCH(k_union_cols<<<ga, 256, 0, st>>>(d_colptr, d_vbase, d_abase, ng, na, U.col));
   MULTI_TRY(cudaGetLastError());
+  // each graph's vertices of out-degree 0 in id order (they fill a list that
+  // fewer than k vertices with reach reach), from one pass over the union:
+  // graph g's run starts at zflag's scan at vbase[g]
+  std::vector<u32> zpos(ng + 1);
+  {
+    u32 *ztmp = nullptr;
+    MULTI_TRY(cudaMallocAsync(&zflag, ((size_t)nv + 1) * sizeof(u32), st));
+    MULTI_TRY(cudaMallocAsync(&zlist, std::max<size_t>(nv, 1) * sizeof(u32), st));
+    MULTI_TRY(cudaMallocAsync(&zat, ((size_t)ng + 1) * sizeof(u32), st));
+    MULTI_TRY(cudaMallocAsync(&ztmp, (((size_t)nv + 1) / 4096 + 2) * sizeof(u32), st));
+    TKC_LAUNCH(k_zero_flags<<<gb, 256, 0, st>>>(U.off, nv, zflag));
+    MULTI_RC(scan_exclusive_u32(zflag, zflag, (u64)nv + 1, ztmp, st));
+    TKC_LAUNCH(k_zero_compact<<<gb, 256, 0, st>>>(U.off, zflag, gid, d_vbase, nv, zlist));
+    TKC_LAUNCH(k_gather_u32<<<1, 256, 0, st>>>(zflag, d_vbase, ng + 1, zat));
+    MULTI_TRY(cudaGetLastError());
+    MULTI_TRY(cudaMemcpyAsync(zpos.data(), zat, ((size_t)ng + 1) * sizeof(u32), cudaMemcpyDeviceToHost, st));
+    MULTI_TRY(cudaFreeAsync(ztmp, st));
+  }
   MULTI_RC(build_in_csr(&U));
   // reach bounds once over the union, as a directed graph: the SCCs of the
   // union are the graphs' SCCs (an undirected graph's are its components, each
@@ -1603,8 +1642,8 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
     go[i].n = gs[i]->n;
     go[i].base = vbase[i];
     go[i].kk = std::min<u32>(k, gs[i]->n);
-    go[i].nzero = gs[i]->n - gs[i]->n_src_deg;
-    go[i].zero_ids = gs[i]->deg_order + gs[i]->n_src_deg;
+    go[i].nzero = zpos[i + 1] - zpos[i];
+    go[i].zero_ids = zlist + zpos[i];
   }
   std::vector<unsigned> ntop, tied;
   std::vector<u64> gctr;

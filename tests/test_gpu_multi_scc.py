@@ -5,7 +5,8 @@ The union's reach bounds start with one forward-backward search from a pivot
 in every graph at once; the rest of each graph's SCCs come from trimming and
 colouring.  Whatever the pivots, every result must equal the textbook top-k of
 each graph on its own (ids, S, r, ties, farness bits), under both orders and
-several batch widths."""
+several batch widths, including graphs whose lists end with vertices of
+out-degree 0."""
 import numpy as np
 import pytest
 
@@ -33,6 +34,10 @@ def _graphs():
             src.append(b)
             dst.append(b + 6)
     gs.append(gg.from_arcs(48, src, dst, True, "cycle_chain"))
+    # fewer than k vertices that reach another: the lists end with out-degree-0 vertices in id order
+    gs.append(gg.from_arcs(7, [], [], True, "empty7"))
+    gs.append(gg.from_arcs(6, [3, 4], [4, 0], True, "tiny"))
+    gs.append(gg.from_arcs(1, [], [], True, "single"))
     gs.append(gg.erdos_renyi(800, 2400, seed=91))
     gs.append(gg.barabasi_albert(600, 3, 92))
     return gs
