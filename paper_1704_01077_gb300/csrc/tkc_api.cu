@@ -267,6 +267,9 @@ struct RunSetup {
   // size that decides the library's labelling choice: the largest graph of a
   // multi-graph union (0: g->n)
   u32 size_n;
+  // several graphs, sources graph by graph: one past each graph's last position
+  // in `order` (nullptr: graphs interleaved)
+  const u32 *g_end;
 };
 
 // Teams used when the options leave it to the library: one team for small
@@ -352,6 +355,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.norder = rs.norder;
   p.ng = rs.ng;
   p.gid = rs.gid;
+  p.g_end = rs.g_end;
   p.g_directed = rs.g_directed;
   p.g_ntop = w.g_ntop;
   p.g_ctr = rs.ng > 1 ? w.g_ctr : nullptr;
@@ -637,7 +641,19 @@ __global__ void k_gather_u32(const u32 *a, const u32 *idx, u32 m, u32 *out) {
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) out[i] = a[idx[i]];
 }
 
+// key[i] = graph of order[i]
+__global__ void k_order_gid(const u32 *order, u32 m, const u32 *gid, u32 *key) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) key[i] = gid[order[i]];
+}
+
+// gend[g] = one past the last position of graph g in the sorted keys
+__global__ void k_segment_ends(const u32 *key, u32 m, u32 *gend) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    if (i + 1 == m || key[i + 1] != key[i]) gend[key[i]] = i + 1;
+}
+
 int scan_exclusive_u32(const u32 *in, u32 *out, u64 len, u32 *tmp, cudaStream_t st);
+int radix_sort_u32_pairs(u32 *key, u32 *val, u32 n, int bits, cudaStream_t st);
 
 }  // namespace tkc
 
@@ -1537,6 +1553,7 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   U.directed = 1;
   u32 *gid = nullptr, *d_vbase = nullptr;
   u32 *zflag = nullptr, *zlist = nullptr, *zat = nullptr;  // out-degree-0 vertices of every graph
+  u32 *gorder = nullptr, *gkey = nullptr, *gend = nullptr;  // the order graph by graph
   u64 *d_abase = nullptr, *d_offptr = nullptr, *d_colptr = nullptr;
   uint8_t *d_gdir = nullptr;
   int rc = TKC_OK;
@@ -1546,7 +1563,7 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
     void *ptrs[] = {U.off, U.col, U.ioff, U.icol, U.deg_order, U.alpha, U.omega, U.scc_size, U.comp, U.nb_S, U.nb_r,
                     U.nb_key, U.nb_hkey,
                     U.nb_order, U.nb_horder, gid, d_vbase, d_abase, d_offptr, d_colptr, d_gdir, zflag, zlist,
-                    zat};
+                    zat, gorder, gkey, gend};
     for (void *q : ptrs)
       if (q) cudaFree(q);
   };
@@ -1635,6 +1652,27 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   rs.gid = gid;
   rs.g_directed = d_gdir;
   rs.size_n = maxn;
+  // The sources graph by graph, each graph's in its own order (a stable sort
+  // by graph): a batch then holds searches of one graph, which share its
+  // frontier rows and arcs, and a graph's stop moves the cursor to the next
+  // graph.  Each graph still sees its sources in the order it would alone,
+  // and its threshold depends only on its own searches, so pruning is the same.
+  if (rs.norder > 0) {
+    MULTI_TRY(cudaMallocAsync(&gorder, (size_t)rs.norder * sizeof(u32), st));
+    MULTI_TRY(cudaMallocAsync(&gkey, (size_t)rs.norder * sizeof(u32), st));
+    MULTI_TRY(cudaMallocAsync(&gend, (size_t)ng * sizeof(u32), st));
+    MULTI_TRY(cudaMemsetAsync(gend, 0, (size_t)ng * sizeof(u32), st));
+    MULTI_TRY(cudaMemcpyAsync(gorder, rs.order, (size_t)rs.norder * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+    const unsigned go_grid = (unsigned)std::max<u64>(1, std::min<u64>((rs.norder + 255) / 256, (u64)ctx->num_sms * 16));
+    TKC_LAUNCH(k_order_gid<<<go_grid, 256, 0, st>>>(rs.order, rs.norder, gid, gkey));
+    int gbits = 0;
+    while (gbits < 32 && ((ng - 1) >> gbits) != 0) ++gbits;
+    MULTI_RC(radix_sort_u32_pairs(gkey, gorder, rs.norder, gbits, st));
+    TKC_LAUNCH(k_segment_ends<<<go_grid, 256, 0, st>>>(gkey, rs.norder, gend));
+    MULTI_TRY(cudaGetLastError());
+    rs.order = gorder;
+    rs.g_end = gend;
+  }
   Ctl hc;
   MULTI_RC(run_search(ctx, rs, &hc));
   std::vector<GraphOut> go(ng);

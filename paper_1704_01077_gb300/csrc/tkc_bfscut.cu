@@ -945,10 +945,13 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
     }
     // nothing after a stopped position of its graph is searched, by any team
     if (stop) {
-      if (!p.gid)
+      if (!p.gid) {
         atomicMax(&p.sh->cursor, p.norder);
-      else
+      } else {
         *(volatile unsigned *)&p.g_stop[gv] = 1u;
+        // sources graph by graph: the rest of this graph's run is skipped at once
+        if (p.g_end) atomicMax(&p.sh->cursor, p.g_end[gv]);
+      }
     }
     const bool take = valid && !cut && !stop && !stopped;
     uint32_t total;
