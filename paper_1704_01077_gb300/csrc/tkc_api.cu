@@ -267,9 +267,11 @@ struct RunSetup {
   // size that decides the library's labelling choice: the largest graph of a
   // multi-graph union (0: g->n)
   u32 size_n;
-  // several graphs, sources graph by graph: one past each graph's last position
-  // in `order` (nullptr: graphs interleaved)
+  // several graphs, sources graph by graph after every graph's opening batch:
+  // one past each graph's last position in `order` (nullptr: graphs
+  // interleaved), and the first position after the openings
   const u32 *g_end;
+  u32 g_rest;
 };
 
 // Teams used when the options leave it to the library: one team for small
@@ -356,6 +358,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.ng = rs.ng;
   p.gid = rs.gid;
   p.g_end = rs.g_end;
+  p.g_rest = rs.g_rest;
   p.g_directed = rs.g_directed;
   p.g_ntop = w.g_ntop;
   p.g_ctr = rs.ng > 1 ? w.g_ctr : nullptr;
@@ -646,10 +649,27 @@ __global__ void k_order_gid(const u32 *order, u32 m, const u32 *gid, u32 *key) {
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) key[i] = gid[order[i]];
 }
 
-// gend[g] = one past the last position of graph g in the sorted keys
-__global__ void k_segment_ends(const u32 *key, u32 m, u32 *gend) {
+// gbeg[g] / gend[g] = first / one past the last position of key g in the
+// sorted keys (either may be null)
+__global__ void k_segment_bounds(const u32 *key, u32 m, u32 *gbeg, u32 *gend) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    if (gbeg && (i == 0 || key[i - 1] != key[i])) gbeg[key[i]] = i;
+    if (gend && (i + 1 == m || key[i + 1] != key[i])) gend[key[i]] = i + 1;
+  }
+}
+
+// Graph-major keys (sorted): key += ng for every position past the first B of
+// its graph, so that a second stable sort puts every graph's first B sources
+// ahead of all the rest; *p1 = the first position of those rest (m if none),
+// found after that sort.
+__global__ void k_phase_keys(u32 *key, u32 m, const u32 *gbeg, u32 B, u32 ng) {
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    if (i + 1 == m || key[i + 1] != key[i]) gend[key[i]] = i + 1;
+    if (i - gbeg[key[i]] >= B) key[i] += ng;
+}
+
+__global__ void k_phase_start(const u32 *key, u32 m, u32 ng, u32 *p1) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    if (key[i] >= ng && (i == 0 || key[i - 1] < ng)) *p1 = i;
 }
 
 int scan_exclusive_u32(const u32 *in, u32 *out, u64 len, u32 *tmp, cudaStream_t st);
@@ -1652,26 +1672,42 @@ static int topk_many(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k
   rs.gid = gid;
   rs.g_directed = d_gdir;
   rs.size_n = maxn;
-  // The sources graph by graph, each graph's in its own order (a stable sort
-  // by graph): a batch then holds searches of one graph, which share its
-  // frontier rows and arcs, and a graph's stop moves the cursor to the next
-  // graph.  Each graph still sees its sources in the order it would alone,
-  // and its threshold depends only on its own searches, so pruning is the same.
-  if (rs.norder > 0) {
+  // The sources graph by graph, each graph's in its own order: first the
+  // first B sources of every graph (one opening batch per graph, searched
+  // before the graph has a threshold), then the rest of every graph, graph by
+  // graph (stable sorts by (phase, graph)).  A batch of the second part holds
+  // searches of one graph, which share its frontier rows and arcs and cut
+  // against the threshold its opening batch set; a graph's NB stop there moves
+  // the shared cursor past the rest of its run.  Each graph still sees its
+  // sources in the order it would alone, and its threshold depends only on its
+  // own searches.
+  if (rs.norder > 0 && ng > 1) {
+    u32 *gbeg = nullptr, *p1 = nullptr;
     MULTI_TRY(cudaMallocAsync(&gorder, (size_t)rs.norder * sizeof(u32), st));
     MULTI_TRY(cudaMallocAsync(&gkey, (size_t)rs.norder * sizeof(u32), st));
-    MULTI_TRY(cudaMallocAsync(&gend, (size_t)ng * sizeof(u32), st));
-    MULTI_TRY(cudaMemsetAsync(gend, 0, (size_t)ng * sizeof(u32), st));
+    MULTI_TRY(cudaMallocAsync(&gend, (size_t)2 * ng * sizeof(u32), st));
+    MULTI_TRY(cudaMallocAsync(&gbeg, (size_t)ng * sizeof(u32), st));
+    MULTI_TRY(cudaMallocAsync(&p1, sizeof(u32), st));
+    MULTI_TRY(cudaMemsetAsync(gend, 0, (size_t)2 * ng * sizeof(u32), st));
     MULTI_TRY(cudaMemcpyAsync(gorder, rs.order, (size_t)rs.norder * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+    MULTI_TRY(cudaMemcpyAsync(p1, &rs.norder, sizeof(u32), cudaMemcpyHostToDevice, st));
     const unsigned go_grid = (unsigned)std::max<u64>(1, std::min<u64>((rs.norder + 255) / 256, (u64)ctx->num_sms * 16));
     TKC_LAUNCH(k_order_gid<<<go_grid, 256, 0, st>>>(rs.order, rs.norder, gid, gkey));
     int gbits = 0;
-    while (gbits < 32 && ((ng - 1) >> gbits) != 0) ++gbits;
-    MULTI_RC(radix_sort_u32_pairs(gkey, gorder, rs.norder, gbits, st));
-    TKC_LAUNCH(k_segment_ends<<<go_grid, 256, 0, st>>>(gkey, rs.norder, gend));
+    while (gbits < 32 && ((2 * ng - 1) >> gbits) != 0) ++gbits;
+    MULTI_RC(radix_sort_u32_pairs(gkey, gorder, rs.norder, gbits, st));  // by graph
+    TKC_LAUNCH(k_segment_bounds<<<go_grid, 256, 0, st>>>(gkey, rs.norder, gbeg, nullptr));
+    TKC_LAUNCH(k_phase_keys<<<go_grid, 256, 0, st>>>(gkey, rs.norder, gbeg, rs.B, ng));
+    MULTI_RC(radix_sort_u32_pairs(gkey, gorder, rs.norder, gbits, st));  // openings first
+    TKC_LAUNCH(k_segment_bounds<<<go_grid, 256, 0, st>>>(gkey, rs.norder, nullptr, gend));
+    TKC_LAUNCH(k_phase_start<<<go_grid, 256, 0, st>>>(gkey, rs.norder, ng, p1));
     MULTI_TRY(cudaGetLastError());
+    MULTI_TRY(cudaMemcpyAsync(&rs.g_rest, p1, sizeof(u32), cudaMemcpyDeviceToHost, st));
+    MULTI_TRY(cudaStreamSynchronize(st));
+    MULTI_TRY(cudaFreeAsync(gbeg, st));
+    MULTI_TRY(cudaFreeAsync(p1, st));
     rs.order = gorder;
-    rs.g_end = gend;
+    rs.g_end = gend + ng;  // ends of the graphs' runs after their openings
   }
   Ctl hc;
   MULTI_RC(run_search(ctx, rs, &hc));

@@ -949,10 +949,12 @@ __device__ void epilogue_seed(const RunParams &p, Smem<W> &sm) {
         atomicMax(&p.sh->cursor, p.norder);
       } else {
         *(volatile unsigned *)&p.g_stop[gv] = 1u;
-        // sources graph by graph: the rest of this graph's run is skipped at once
-        if (p.g_end) atomicMax(&p.sh->cursor, p.g_end[gv]);
+        // sources graph by graph: the rest of this graph's run is skipped at
+        // once (only after the openings, where the run is contiguous)
+        if (p.g_end && idx >= p.g_rest) atomicMax(&p.sh->cursor, p.g_end[gv]);
       }
     }
+    if (stopped && p.g_end && idx >= p.g_rest) atomicMax(&p.sh->cursor, p.g_end[gv]);
     const bool take = valid && !cut && !stop && !stopped;
     uint32_t total;
     uint32_t pre = block_exscan(sm, take ? 1u : 0u, &total);

@@ -162,7 +162,11 @@ struct RunParams {
   // several graphs in one run, as their disjoint union (ng = 1: one graph)
   uint32_t ng;
   const uint32_t *gid;        // graph of each vertex (nullptr: every vertex in graph 0)
-  const uint32_t *g_end;      // sources graph by graph: one past each graph's last order position (nullable)
+  // sources graph by graph after every graph's opening batch: one past each
+  // graph's last order position (nullable), and the first position after the
+  // openings (a stop there may skip the rest of its graph at once)
+  const uint32_t *g_end;
+  uint32_t g_rest;
   const uint8_t *g_directed;  // per graph (nullptr: `directed` for all)
   unsigned int *g_ntop;       // entries in each graph's top list
   unsigned long long *g_ctr;  // per graph: edges_visited, bfs_started, bfs_cut, bfs_finished (nullable)
