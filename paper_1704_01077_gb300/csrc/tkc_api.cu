@@ -776,14 +776,13 @@ int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offset
   if (!offsets || (arcs && !cols)) return TKC_EINVAL;
   TKC_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  if (!ptr_on_device) {
-    if (offsets[0] != 0 || offsets[n] != arcs) return TKC_EGRAPH;
-  } else {
-    u32 ends[2] = {1, 0};
-    TKC_TRY(cudaMemcpyAsync(&ends[0], offsets, sizeof(u32), cudaMemcpyDeviceToHost, st));
-    TKC_TRY(cudaMemcpyAsync(&ends[1], offsets + n, sizeof(u32), cudaMemcpyDeviceToHost, st));
-    TKC_TRY(cudaStreamSynchronize(st));
-    if (ends[0] != 0 || ends[1] != arcs) return TKC_EGRAPH;
+  // device offsets of a graph with vertices: offsets[0] = 0 and offsets[n] =
+  // arcs are checked with the rest of the validation, on the copy
+  if (!ptr_on_device && (offsets[0] != 0 || offsets[n] != arcs)) return TKC_EGRAPH;
+  if (ptr_on_device && n == 0) {
+    u32 end0 = 1;
+    TKC_TRY(cudaMemcpy(&end0, offsets, sizeof(u32), cudaMemcpyDeviceToHost));
+    if (end0 != 0 || arcs != 0) return TKC_EGRAPH;
   }
   tkc_graph *g = new (std::nothrow) tkc_graph();
   if (!g) return TKC_ENOMEM;
@@ -826,15 +825,18 @@ void tkc_free_graph(tkc_graph *g) {
   if (!g) return;
   if (g->ctx->last_shard == g) g->ctx->last_shard = nullptr;
   cudaSetDevice(g->ctx->device);
-  cudaStreamSynchronize(g->ctx->stream);
-  if (g->ioff && g->ioff != g->off) cudaFree(g->ioff);
-  if (g->icol && g->icol != g->col) cudaFree(g->icol);
+  // every buffer came from the stream-ordered allocator on the context's
+  // stream: freed in stream order, after the work that used it, without
+  // waiting for it here
+  cudaStream_t st = g->ctx->stream;
+  if (g->ioff && g->ioff != g->off) cudaFreeAsync(g->ioff, st);
+  if (g->icol && g->icol != g->col) cudaFreeAsync(g->icol, st);
   free_search_csr(g);
   void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega, g->scc_size, g->features,
                   g->learned_order, g->seeded_order, g->nb_order, g->nb_S, g->nb_r, g->nb_key, g->nb_hkey,
                   g->nb_horder, g->comp};
   for (void *p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, st);
   g->ctx->graphs_alive--;
   delete g;
 }

@@ -286,7 +286,8 @@ struct tkc_graph {
   uint64_t arcs = 0;
   int directed = 0;
   uint32_t *off = nullptr, *col = nullptr;    // out-arcs
-  uint32_t *ioff = nullptr, *icol = nullptr;  // in-arcs (aliases of out-arcs when undirected)
+  mutable uint32_t *ioff = nullptr, *icol = nullptr;  // in-arcs (aliases of out-arcs when undirected; directed: built
+                                                      // on first use, ensure_in_csr)
   uint32_t *deg_order = nullptr;              // computeBoundsDeg order (all n vertices)
   uint32_t n_src_deg = 0;                     // vertices with out-degree >= 1 (prefix of deg_order)
   uint32_t *given_order = nullptr;            // filtered caller order
@@ -327,7 +328,8 @@ struct tkc_graph {
 namespace tkc {
 // tkc_prep.cu
 int validate_and_transpose(tkc_graph *g);
-int build_in_csr(tkc_graph *g);
+int build_in_csr(const tkc_graph *g);
+int ensure_in_csr(const tkc_graph *g);
 int ensure_degree_order(tkc_graph *g);
 // gid/ng (several graphs as one union, graphs in contiguous vertex ranges):
 // one pivot per graph in the first forward-backward round

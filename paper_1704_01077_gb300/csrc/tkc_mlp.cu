@@ -364,6 +364,7 @@ static int reset_adam(tkc_ctx *ctx) {
 int ensure_features(tkc_graph *g) {
   if (g->features) return TKC_OK;
   TKC_RC(ensure_reach_bounds(g));  // provides the SCC sizes
+  TKC_RC(ensure_in_csr(g));
   cudaStream_t st = g->ctx->stream;
   const u32 n = g->n;
   if (n == 0) return TKC_OK;

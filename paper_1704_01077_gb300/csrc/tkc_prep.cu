@@ -109,12 +109,13 @@ static int scan_exclusive(const u32 *in, u32 *out, u64 len, u32 *tmp, cudaStream
 
 enum : u32 { kBadOffsets = 1, kBadRange = 2, kSelfLoop = 4, kUnsorted = 8, kAsymmetric = 16 };
 
-// Offsets monotone and within arcs (a thread per vertex); ids in range, no
-// self-loop, each row strictly increasing (sorted, no duplicates), checked
-// arc by arc.
+// Offsets from 0 to arcs, monotone and within arcs (a thread per vertex); ids
+// in range, no self-loop, each row strictly increasing (sorted, no
+// duplicates), checked arc by arc.
 __global__ void k_validate(const u32 *off, const u32 *col, u32 n, u64 arcs, u32 *flags) {
   const int lane = threadIdx.x & 31;
   u32 f = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[n] != arcs)) f |= kBadOffsets;
   for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (u64)gridDim.x * blockDim.x) {
     const u32 b = off[v], e = off[v + 1];
     if (e < b || e > arcs) f |= kBadOffsets;
@@ -223,9 +224,8 @@ int validate_and_transpose(tkc_graph *g) {
   if (!g->directed) {
     g->ioff = g->off;
     g->icol = g->col;
-    return TKC_OK;
   }
-  return build_in_csr(g);
+  return TKC_OK;  // a directed graph's in-arc CSR is built on first use (ensure_in_csr)
 }
 
 // Fills the in-arc columns of the CSR (off, col) with n vertices into icol,
@@ -264,9 +264,16 @@ static int transpose_csr(const u32 *off, const u32 *col, u32 n, u64 arcs, u32 **
 }
 
 // In-arc CSR of g.
-int build_in_csr(tkc_graph *g) {
+int build_in_csr(const tkc_graph *g) {
   if (g->n == 0) return TKC_OK;
   return transpose_csr(g->off, g->col, g->n, g->arcs, &g->ioff, &g->icol, g->ctx->stream);
+}
+
+// The in-arc CSR, built the first time a step needs it (a graph loaded only
+// to join a multi-graph launch never does: the union builds its own).
+int ensure_in_csr(const tkc_graph *g) {
+  if (g->ioff || g->n == 0) return TKC_OK;
+  return build_in_csr(g);
 }
 
 // ------------------------------------------------------------------ stable LSD radix sort (4-bit digits)
@@ -499,11 +506,12 @@ __global__ void k_relabel_cols(const u32 *__restrict__ s_off, const u32 *__restr
 }
 
 void free_search_csr(const tkc_graph *g) {
-  if (g->s_ioff && g->s_ioff != g->s_off) cudaFree(g->s_ioff);
-  if (g->s_icol && g->s_icol != g->s_col) cudaFree(g->s_icol);
+  cudaStream_t st = g->ctx->stream;  // stream-ordered: after the work that used them
+  if (g->s_ioff && g->s_ioff != g->s_off) cudaFreeAsync(g->s_ioff, st);
+  if (g->s_icol && g->s_icol != g->s_col) cudaFreeAsync(g->s_icol, st);
   void *ptrs[] = {g->s_off, g->s_col, g->s_lab, g->s_unlab, g->bu_list};
   for (void *q : ptrs)
-    if (q) cudaFree(q);
+    if (q) cudaFreeAsync(q, st);
   g->s_off = g->s_col = g->s_ioff = g->s_icol = g->s_lab = g->s_unlab = nullptr;
   g->bu_list = nullptr;
   g->n_bu = g->n_bu_heavy = 0;
@@ -525,6 +533,7 @@ void free_search_csr(const tkc_graph *g) {
 int ensure_search_csr(const tkc_graph *g, bool relabel) {
   const int want = relabel ? 1 : 0;
   if (g->s_mode == want || g->n == 0) return TKC_OK;
+  TKC_RC(ensure_in_csr(g));
   free_search_csr(g);  // the other labelling's copy, or what a failed build left
   cudaStream_t st = g->ctx->stream;
   const u32 n = g->n;
@@ -722,6 +731,7 @@ int ensure_reach_bounds(tkc_graph *g, const u32 *gid, u32 ng) {
   if (!g->omega) TKC_TRY(cudaMallocAsync(&g->omega, (size_t)g->n * sizeof(u32), st));
   if (!g->scc_size) TKC_TRY(cudaMallocAsync(&g->scc_size, (size_t)g->n * sizeof(u32), st));
   if (!g->comp) TKC_TRY(cudaMallocAsync(&g->comp, (size_t)g->n * sizeof(u32), st));
+  TKC_RC(ensure_in_csr(g));
   TKC_RC(g->directed ? reach_directed_gpu(g, gid, ng) : reach_undirected(g));
   g->have_reach = true;
   return TKC_OK;

@@ -198,6 +198,37 @@ def test_malformed_graphs_rejected(gpu_lib, ctx):
         t.tkc_free_graph(h)
 
 
+def test_malformed_device_input_rejected(gpu_lib, ctx):
+    """Device-resident CSR: the first and last offsets are checked on the
+    device with the rest of the validation (no separate host read)."""
+    import torch
+
+    t = gpu_lib
+    bad = [
+        (3, [1, 1, 1, 1], [], True),          # offsets do not start at 0
+        (3, [0, 1, 1, 2], [1], True),         # last offset is not the arc count
+        (3, [0, 1, 1, 1], [7], True),         # id out of range
+        (3, [0, 2, 2, 2], [2, 1], True),      # unsorted row
+        (3, [0, 1, 1, 1], [1], False),        # undirected but not symmetric
+        (0, [2], [], True),                   # no vertex, offsets[0] != 0
+    ]
+    for n, off, col, directed in bad:
+        o = torch.tensor(off, dtype=torch.int32, device="cuda")
+        c = torch.tensor(col if col else [0], dtype=torch.int32, device="cuda")[: len(col)]
+        with pytest.raises(t.TkcError) as e:
+            t.tkc_load_csr(ctx, n, o, c, directed)
+        assert e.value.code == t.TKC_EGRAPH, (off, col)
+    # the context still works
+    g = gg.path(5, directed=True)
+    h = t.tkc_load_csr(ctx, g.n, torch.from_numpy(g.offsets.astype(np.int32)).cuda(),
+                       torch.from_numpy(g.cols.astype(np.int32)).cuda(), True)
+    try:
+        got = t.tkc_topk_closeness(h, 3)
+    finally:
+        t.tkc_free_graph(h)
+    _expect_equal(got, oracle.textbook_topk(g, 3), g, 3)
+
+
 def test_zero_and_one_vertex(gpu_lib, ctx):
     t = gpu_lib
     t.tkc_set_options(ctx, t.Options(batch_bits=64))
