@@ -286,6 +286,14 @@ static u32 default_teams(u32 n, u32 B, u32 maxb, bool nb) {
   return std::max<u32>(1, maxb / 8);  // eight blocks (SMs) per team, every SM used
 }
 
+// Whether the search walks the in-degree labelling: batched searches of
+// large graphs (its hot rows stay in L2); one-source searches and small
+// graphs (of a union: when no graph is large, each one's rows fit L2 anyway)
+// the graph itself.
+static bool labelled_search(const tkc_options &o, u32 B, u32 size_n) {
+  return o.relabel == 1 || (o.relabel == 0 && B > 1 && size_n >= (1u << 20));
+}
+
 static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   const tkc_graph *g = rs.g;
   Workspace &w = ctx->ws;
@@ -333,11 +341,7 @@ static int run_search(tkc_ctx *ctx, const RunSetup &rs, Ctl *hctl) {
   p.n = g->n;
   p.directed = g->directed;
   p.arcs = g->arcs;
-  // batched searches of large graphs walk the in-degree labelling (its hot
-  // rows stay in L2); one-source searches and small graphs (of a union: when
-  // no graph is large, each one's rows fit L2 anyway) the graph itself
-  const u32 size_n = rs.size_n ? rs.size_n : g->n;
-  const bool relabel = o.relabel == 1 || (o.relabel == 0 && rs.B > 1 && size_n >= (1u << 20));
+  const bool relabel = labelled_search(o, rs.B, rs.size_n ? rs.size_n : g->n);
   TKC_RC(ensure_search_csr(g, relabel));
   const bool lab = g->s_mode == 1;
   p.off = lab ? g->s_off : g->off;
@@ -765,6 +769,11 @@ void tkc_destroy(tkc_ctx *ctx) {
   free_mlp(ctx);
   for (auto &ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->aux);
+    cudaStreamDestroy(ctx->aux);
+  }
+  if (ctx->aux_in) cudaEventDestroy(ctx->aux_in);
   delete ctx;
 }
 
@@ -829,9 +838,9 @@ void tkc_free_graph(tkc_graph *g) {
   // stream: freed in stream order, after the work that used it, without
   // waiting for it here
   cudaStream_t st = g->ctx->stream;
+  free_search_csr(g);  // first: it orders the stream after a copy still being built from the graph
   if (g->ioff && g->ioff != g->off) cudaFreeAsync(g->ioff, st);
   if (g->icol && g->icol != g->col) cudaFreeAsync(g->icol, st);
-  free_search_csr(g);
   void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega, g->scc_size, g->features,
                   g->learned_order, g->seeded_order, g->nb_order, g->nb_S, g->nb_r, g->nb_key, g->nb_hkey,
                   g->nb_horder, g->comp};
@@ -1025,11 +1034,13 @@ static int topk_one(tkc_graph *g, uint32_t k, tkc_result *out, int harmonic) {
   }
   cudaStream_t st = ctx->stream;
   TKC_TRY(cudaEventRecord(ctx->ev[0], st));
+  const tkc_options &o = ctx->opt;
+  // a labelled search's copy of the graph is built alongside the preprocessing
+  if (labelled_search(o, o.batch_bits ? o.batch_bits : 64u, g->n)) TKC_RC(start_search_csr(g));
   TKC_RC(ensure_degree_order(g));
   TKC_RC(ensure_reach_bounds(g));
   RunSetup rs;
   memset(&rs, 0, sizeof(rs));
-  const tkc_options &o = ctx->opt;
   TKC_RC(source_order_of(g, o, kk, harmonic, &rs.order, &rs.norder, &rs.lb_key));
   TKC_TRY(cudaEventRecord(ctx->ev[1], st));
   u32 bits = o.batch_bits ? o.batch_bits : default_batch_bits(g->n, rs.lb_key != nullptr);

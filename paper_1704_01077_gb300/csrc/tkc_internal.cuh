@@ -277,6 +277,8 @@ struct tkc_ctx {
   int num_sms = 0;
   tkc::Workspace ws;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t aux = nullptr;    // helper stream: the labelled copy, built while `stream` preprocesses
+  cudaEvent_t aux_in = nullptr;  // orders the helper stream after `stream`'s work so far
   int graphs_alive = 0;
 };
 
@@ -320,6 +322,8 @@ struct tkc_graph {
   mutable int s_mode = -1;
   mutable uint32_t *s_off = nullptr, *s_col = nullptr, *s_ioff = nullptr, *s_icol = nullptr;
   mutable uint32_t *s_lab = nullptr, *s_unlab = nullptr;
+  mutable uint32_t *s_cnt = nullptr;          // device: the bottom-up list's counts (n_bu, n_bu_heavy)
+  mutable cudaEvent_t s_ready = nullptr;      // the copy is being built on the context's helper stream
   mutable uint32_t *bu_list = nullptr;        // bottom-up sweep order of that CSR: vertices with an in-arc, hubs first
   mutable uint32_t n_bu = 0, n_bu_heavy = 0;
   mutable uint32_t heavy_in = 0;              // the list's long-row threshold (kHeavyIn or kHeavyInLabelled)
@@ -336,6 +340,7 @@ int ensure_degree_order(tkc_graph *g);
 int ensure_reach_bounds(tkc_graph *g, const uint32_t *gid = nullptr, uint32_t ng = 0);
 // the search kernel's CSR and bottom-up list (relabel: the in-degree labelling)
 int ensure_search_csr(const tkc_graph *g, bool relabel);
+int start_search_csr(const tkc_graph *g);  // the labelled copy, on the helper stream
 void free_search_csr(const tkc_graph *g);
 int filter_order(tkc_graph *g, const uint32_t *d_order_all, uint32_t *d_out, uint32_t *count);
 // tkc_nb.cu

@@ -450,35 +450,28 @@ __global__ void k_bu_keys(const u32 *ioff, u32 n, u32 heavy_in, u32 *key, u32 *v
 // whose rows a whole warp walks, longest rows first (bit length of the
 // in-degree, then id); then the others by id, so that a warp's 32 entries
 // share a few frontier-bitmap words.  Only the order of work depends on it,
-// not any result.  *list is allocated here.
-static int build_bu_list(const u32 *ioff, u32 n, u32 heavy_in, cudaStream_t st, u32 **list, u32 *n_bu,
-                         u32 *n_heavy) {
-  u32 *keys = nullptr, *ids = nullptr, *cnt = nullptr;
+// not any result.  *list is allocated here; cnt (device, 2 words) receives
+// the number of vertices with an in-arc and of long rows.
+static int build_bu_list(const u32 *ioff, u32 n, u32 heavy_in, cudaStream_t st, u32 **list, u32 *cnt) {
+  u32 *keys = nullptr, *ids = nullptr;
   TKC_TRY(cudaMallocAsync(&ids, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&keys, (size_t)n * sizeof(u32), st));
-  TKC_TRY(cudaMallocAsync(&cnt, 2 * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(u32), st));
   TKC_LAUNCH(k_bu_keys<<<grid_for(n, 256), 256, 0, st>>>(ioff, n, heavy_in, keys, ids, cnt));
   TKC_TRY(cudaGetLastError());
   TKC_RC(radix_sort_pairs(keys, ids, n, 6, st));
-  u32 c[2] = {0, 0};
-  TKC_TRY(cudaMemcpyAsync(c, cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
   TKC_TRY(cudaFreeAsync(keys, st));
-  TKC_TRY(cudaFreeAsync(cnt, st));
-  TKC_TRY(cudaStreamSynchronize(st));
   *list = ids;
-  *n_bu = c[0];
-  *n_heavy = c[1];
   return TKC_OK;
 }
 
 // ------------------------------------------------------------------ the search kernel's copy of the graph
 
-// Relabelling key: in-degree, larger first (the stable sort keeps ids
-// ascending among equal in-degrees).
-__global__ void k_relabel_keys(const u32 *ioff, u32 n, u32 maxd, u32 *key, u32 *val) {
+// Relabelling key: in-degree, larger first (top is at least every in-degree;
+// the stable sort keeps ids ascending among equal in-degrees).
+__global__ void k_relabel_keys(const u32 *ioff, u32 n, u32 top, u32 *key, u32 *val) {
   for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    key[v] = maxd - (ioff[v + 1] - ioff[v]);
+    key[v] = top - (ioff[v + 1] - ioff[v]);
     val[v] = v;
   }
 }
@@ -507,18 +500,23 @@ __global__ void k_relabel_cols(const u32 *__restrict__ s_off, const u32 *__restr
 
 void free_search_csr(const tkc_graph *g) {
   cudaStream_t st = g->ctx->stream;  // stream-ordered: after the work that used them
+  if (g->s_ready) {  // a copy still being built on the helper stream
+    cudaStreamWaitEvent(st, g->s_ready, 0);
+    cudaEventDestroy(g->s_ready);
+    g->s_ready = nullptr;
+  }
   if (g->s_ioff && g->s_ioff != g->s_off) cudaFreeAsync(g->s_ioff, st);
   if (g->s_icol && g->s_icol != g->s_col) cudaFreeAsync(g->s_icol, st);
-  void *ptrs[] = {g->s_off, g->s_col, g->s_lab, g->s_unlab, g->bu_list};
+  void *ptrs[] = {g->s_off, g->s_col, g->s_lab, g->s_unlab, g->bu_list, g->s_cnt};
   for (void *q : ptrs)
     if (q) cudaFreeAsync(q, st);
-  g->s_off = g->s_col = g->s_ioff = g->s_icol = g->s_lab = g->s_unlab = nullptr;
+  g->s_off = g->s_col = g->s_ioff = g->s_icol = g->s_lab = g->s_unlab = g->s_cnt = nullptr;
   g->bu_list = nullptr;
   g->n_bu = g->n_bu_heavy = 0;
   g->s_mode = -1;
 }
 
-// The graph as the search kernel walks it.  Plain: the graph itself.
+// The graph as the search kernel walks it (ensure_search_csr below).  Plain: the graph itself.
 // Relabelled: vertex i of the copy is vertex unlab[i] of the graph, the
 // vertices taken by in-degree, largest first.  Bottom-up levels gather the
 // frontier rows of in-neighbours, and in-neighbours are mostly vertices of
@@ -530,42 +528,28 @@ void free_search_csr(const tkc_graph *g) {
 // directions (its transpose is itself).  Every result is the same: sources,
 // slots, ties and outputs keep the graph's own ids; only the search's rows
 // are indexed by labels.
-int ensure_search_csr(const tkc_graph *g, bool relabel) {
-  const int want = relabel ? 1 : 0;
-  if (g->s_mode == want || g->n == 0) return TKC_OK;
-  TKC_RC(ensure_in_csr(g));
-  free_search_csr(g);  // the other labelling's copy, or what a failed build left
-  cudaStream_t st = g->ctx->stream;
+// The labelled copy and its bottom-up list, enqueued on `st` without a host
+// wait (the list's counts land in g->s_cnt).  The graph's in-arc CSR exists.
+static int build_labelled_copy(const tkc_graph *g, cudaStream_t st) {
   const u32 n = g->n;
-  if (!relabel) {
-    g->heavy_in = kHeavyIn;
-    TKC_RC(build_bu_list(g->ioff, n, g->heavy_in, st, &g->bu_list, &g->n_bu, &g->n_bu_heavy));
-    g->s_mode = 0;
-    return TKC_OK;
-  }
-  u32 *keys = nullptr, *stats = nullptr, *gcol = nullptr, *tmp = nullptr;
+  u32 *keys = nullptr, *gcol = nullptr, *tmp = nullptr;
+  TKC_TRY(cudaMallocAsync(&g->s_cnt, 2 * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&g->s_unlab, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&g->s_lab, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&g->s_off, ((size_t)n + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&g->s_ioff, ((size_t)n + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&g->s_icol, std::max<size_t>(g->arcs, 1) * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&gcol, std::max<size_t>(g->arcs, 1) * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&keys, (size_t)n * sizeof(u32), st));
   TKC_TRY(cudaMallocAsync(&tmp, (((size_t)n + 1) / kScanTile + 2) * sizeof(u32), st));
-  TKC_TRY(cudaMallocAsync(&stats, 2 * sizeof(u32), st));
-  TKC_TRY(cudaMemsetAsync(stats, 0, 2 * sizeof(u32), st));
-  TKC_LAUNCH(k_maxdeg<<<grid_for(n, 256), 256, 0, st>>>(g->ioff, n, stats, stats + 1));
-  TKC_TRY(cudaGetLastError());
-  u32 hs[2];
-  TKC_TRY(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
-  TKC_TRY(cudaStreamSynchronize(st));
-  TKC_LAUNCH(k_relabel_keys<<<grid_for(n, 256), 256, 0, st>>>(g->ioff, n, hs[0], keys, g->s_unlab));
+  // key n - indegree (in [1, n]: no vertex has n in-arcs), ascending
+  TKC_LAUNCH(k_relabel_keys<<<grid_for(n, 256), 256, 0, st>>>(g->ioff, n, n, keys, g->s_unlab));
   TKC_TRY(cudaGetLastError());
   int bits = 0;
-  while (bits < 32 && (hs[0] >> bits) != 0) ++bits;
+  while (bits < 32 && (n >> bits) != 0) ++bits;
   TKC_RC(radix_sort_pairs(keys, g->s_unlab, n, bits, st));
   // the copy's row lengths are the graph's degrees in label order: its
   // in-rows need no counting pass
-  TKC_TRY(cudaMallocAsync(&g->s_ioff, ((size_t)n + 1) * sizeof(u32), st));
-  TKC_TRY(cudaMallocAsync(&g->s_icol, std::max<size_t>(g->arcs, 1) * sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(g->s_off + n, 0, sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(g->s_ioff + n, 0, sizeof(u32), st));
   TKC_LAUNCH(k_relabel_rows<<<grid_for(n, 256), 256, 0, st>>>(g->s_unlab, g->off, g->ioff, n, g->s_lab, g->s_off,
@@ -590,9 +574,69 @@ int ensure_search_csr(const tkc_graph *g, bool relabel) {
   }
   TKC_TRY(cudaFreeAsync(keys, st));
   TKC_TRY(cudaFreeAsync(tmp, st));
-  TKC_TRY(cudaFreeAsync(stats, st));
   g->heavy_in = kHeavyInLabelled;
-  TKC_RC(build_bu_list(g->s_ioff, n, g->heavy_in, st, &g->bu_list, &g->n_bu, &g->n_bu_heavy));
+  return build_bu_list(g->s_ioff, n, g->heavy_in, st, &g->bu_list, g->s_cnt);
+}
+
+// Reads the bottom-up list's counts once the work that writes them is done.
+static int read_bu_counts(const tkc_graph *g) {
+  cudaStream_t st = g->ctx->stream;
+  u32 c[2] = {0, 0};
+  TKC_TRY(cudaMemcpyAsync(c, g->s_cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  g->n_bu = c[0];
+  g->n_bu_heavy = c[1];
+  return TKC_OK;
+}
+
+// A copy started on the helper stream: the context's stream waits for it.
+static int finish_started_copy(const tkc_graph *g) {
+  if (!g->s_ready) return TKC_OK;
+  TKC_TRY(cudaStreamWaitEvent(g->ctx->stream, g->s_ready, 0));
+  TKC_TRY(cudaEventDestroy(g->s_ready));
+  g->s_ready = nullptr;
+  return read_bu_counts(g);
+}
+
+int ensure_search_csr(const tkc_graph *g, bool relabel) {
+  TKC_RC(finish_started_copy(g));
+  const int want = relabel ? 1 : 0;
+  if (g->s_mode == want || g->n == 0) return TKC_OK;
+  TKC_RC(ensure_in_csr(g));
+  free_search_csr(g);  // the other labelling's copy, or what a failed build left
+  cudaStream_t st = g->ctx->stream;
+  if (!relabel) {
+    g->heavy_in = kHeavyIn;
+    TKC_TRY(cudaMallocAsync(&g->s_cnt, 2 * sizeof(u32), st));
+    TKC_RC(build_bu_list(g->ioff, g->n, g->heavy_in, st, &g->bu_list, g->s_cnt));
+  } else {
+    TKC_RC(build_labelled_copy(g, st));
+  }
+  TKC_RC(read_bu_counts(g));
+  g->s_mode = want;
+  return TKC_OK;
+}
+
+// Starts the labelled copy on the context's helper stream, so that it is
+// built while the context's stream runs the preprocessing (degree order,
+// reach bounds, NB bounds) with its host waits: it needs only the CSR and
+// the in-arc CSR.  ensure_search_csr completes it.
+int start_search_csr(const tkc_graph *g) {
+  if (g->s_mode == 1 || g->s_ready || g->n == 0) return TKC_OK;
+  TKC_RC(ensure_in_csr(g));
+  free_search_csr(g);
+  tkc_ctx *ctx = g->ctx;
+  if (!ctx->aux) {
+    TKC_TRY(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    TKC_TRY(cudaEventCreateWithFlags(&ctx->aux_in, cudaEventDisableTiming));
+  }
+  TKC_TRY(cudaEventRecord(ctx->aux_in, ctx->stream));
+  TKC_TRY(cudaStreamWaitEvent(ctx->aux, ctx->aux_in, 0));
+  TKC_RC(build_labelled_copy(g, ctx->aux));
+  cudaEvent_t ready = nullptr;
+  TKC_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  TKC_TRY(cudaEventRecord(ready, ctx->aux));
+  g->s_ready = ready;
   g->s_mode = 1;
   return TKC_OK;
 }

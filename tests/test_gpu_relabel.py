@@ -185,3 +185,29 @@ def test_distance_sums(gpu_lib, ctx, name):
         t.tkc_set_options(ctx, t.Options())
     S0, r0 = oracle.bfs_sums(g, src)
     assert np.array_equal(S, S0) and np.array_equal(r, r0)
+
+
+def test_one_handle_switching_labellings(gpu_lib, ctx):
+    """One graph handle searched with the labelling, without it, and with it
+    again (the copy is built alongside the preprocessing, dropped, rebuilt),
+    then freed right after a call: every result equals the textbook."""
+    t = gpu_lib
+    g = _graph("rmat14")
+    ref = oracle.textbook_topk(g, 10)
+    h = _load(t, ctx, g)
+    try:
+        for relabel in (1, 2, 1, 0):
+            t.tkc_set_options(ctx, t.Options(batch_bits=128, order=t.TKC_ORDER_NB, relabel=relabel))
+            _expect_topk(t.tkc_topk_closeness(h, 10), ref, g, relabel)
+            S, r = t.tkc_distance_sums(h, np.asarray(ref.ids, np.uint32))
+            assert np.array_equal(S, ref.S) and np.array_equal(r, ref.r), relabel
+    finally:
+        t.tkc_free_graph(h)
+        t.tkc_set_options(ctx, t.Options())
+    h = _load(t, ctx, g)
+    t.tkc_set_options(ctx, t.Options(batch_bits=128, relabel=1))
+    try:
+        _expect_topk(t.tkc_topk_closeness(h, 10), oracle.textbook_topk(g, 10), g, "fresh")
+    finally:
+        t.tkc_free_graph(h)
+        t.tkc_set_options(ctx, t.Options())
