@@ -149,14 +149,31 @@ int tkc_set_options(tkc_ctx *ctx, const tkc_options *opt);
  * loaded on it must be freed first.  NULL is a no-op. */
 void tkc_destroy(tkc_ctx *ctx);
 
-/* Copies a CSR graph to the device, validates it, and builds its in-arc CSR
- * (directed) -- the input of Algorithm 1 (Section 4).  offsets/cols are host
- * pointers if ptr_on_device = 0, device pointers otherwise.  directed = 0
- * declares an undirected graph (symmetry is checked).  n may be 0.
- * Errors: TKC_EINVAL (null out, arcs != offsets[n]), TKC_EGRAPH, TKC_EOVERFLOW,
- * TKC_ENOMEM, TKC_ECUDA. */
+/* Copies a CSR graph to the device and validates it -- the input of
+ * Algorithm 1 (Section 4); a directed graph's in-arc CSR is built when a call
+ * first needs it.  offsets/cols are host pointers if ptr_on_device = 0,
+ * device pointers otherwise.  directed = 0 declares an undirected graph
+ * (symmetry is checked).  n may be 0.  Errors: TKC_EINVAL (null ctx, out,
+ * offsets, or cols with arcs > 0), TKC_EGRAPH (offsets[0] != 0, offsets[n] !=
+ * arcs, offsets decreasing, an id out of range, a self-loop, an unsorted or
+ * repeated row entry, an undirected graph that is not symmetric),
+ * TKC_EOVERFLOW (n >= 2^26 or arcs >= 2^32), TKC_ENOMEM, TKC_ECUDA; *out is
+ * NULL on error. */
 int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offsets, const uint32_t *cols,
                  int directed, int ptr_on_device, tkc_graph **out);
+
+/* Loads ng graphs as tkc_load_csr does, with one host wait for all their
+ * checks (two when some are undirected) instead of one or two per graph: for
+ * callers that load many small graphs, e.g. for tkc_topk_closeness_multi (no
+ * paper counterpart).  Graph i is n[i], arcs[i], offsets[i], cols[i],
+ * directed[i]; ptr_on_device applies to all.  out[ng] receives the handles.
+ * On error no graph is kept (every out[i] is NULL) and *first_bad (may be
+ * NULL) is the first graph at fault, ng when none is (an allocation or CUDA
+ * error).  Errors: as tkc_load_csr; TKC_EINVAL also for a null array with
+ * ng > 0.  ng = 0 returns TKC_OK. */
+int tkc_load_csr_many(tkc_ctx *ctx, uint32_t ng, const uint32_t *n, const uint64_t *arcs,
+                      const uint32_t *const *offsets, const uint32_t *const *cols, const int *directed,
+                      int ptr_on_device, tkc_graph **out, uint32_t *first_bad);
 
 /* Frees a graph and everything derived from it (orders, reach and NB bounds,
  * features).  NULL is a no-op. */

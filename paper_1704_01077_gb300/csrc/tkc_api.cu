@@ -777,56 +777,126 @@ void tkc_destroy(tkc_ctx *ctx) {
   delete ctx;
 }
 
-int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offsets, const uint32_t *cols,
-                 int directed, int ptr_on_device, tkc_graph **out) {
-  if (!ctx || !out) return TKC_EINVAL;
+// A new graph handle with the CSR copied to the device (stream-ordered, no
+// host wait, nothing validated yet).  Host offsets' ends are checked here;
+// device ones with the validation.
+static int upload_graph(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offsets, const uint32_t *cols,
+                        int directed, int ptr_on_device, tkc_graph **out) {
   *out = nullptr;
   if (n >= kMaxN || arcs >= (1ull << 32)) return TKC_EOVERFLOW;
   if (!offsets || (arcs && !cols)) return TKC_EINVAL;
-  TKC_TRY(cudaSetDevice(ctx->device));
-  cudaStream_t st = ctx->stream;
-  // device offsets of a graph with vertices: offsets[0] = 0 and offsets[n] =
-  // arcs are checked with the rest of the validation, on the copy
   if (!ptr_on_device && (offsets[0] != 0 || offsets[n] != arcs)) return TKC_EGRAPH;
   if (ptr_on_device && n == 0) {
     u32 end0 = 1;
     TKC_TRY(cudaMemcpy(&end0, offsets, sizeof(u32), cudaMemcpyDeviceToHost));
     if (end0 != 0 || arcs != 0) return TKC_EGRAPH;
   }
+  cudaStream_t st = ctx->stream;
   tkc_graph *g = new (std::nothrow) tkc_graph();
   if (!g) return TKC_ENOMEM;
   g->ctx = ctx;
   g->n = n;
   g->arcs = arcs;
   g->directed = directed ? 1 : 0;
+  ctx->graphs_alive++;
   cudaMemcpyKind kind = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  int rc = TKC_OK;
-  do {
-    cudaError_t e = cudaMallocAsync(&g->off, ((size_t)n + 1) * sizeof(u32), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&g->col, std::max<size_t>(arcs, 1) * sizeof(u32), st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g->off, offsets, ((size_t)n + 1) * sizeof(u32), kind, st);
-    if (e == cudaSuccess && arcs) e = cudaMemcpyAsync(g->col, cols, arcs * sizeof(u32), kind, st);
-    if (e != cudaSuccess) {
-      tkc_set_last_cuda_error(e, "graph upload", __FILE__, __LINE__);
-      rc = e == cudaErrorMemoryAllocation ? TKC_ENOMEM : TKC_ECUDA;
-      break;
-    }
-    rc = validate_and_transpose(g);
-  } while (0);
+  cudaError_t e = cudaMallocAsync(&g->off, ((size_t)n + 1) * sizeof(u32), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&g->col, std::max<size_t>(arcs, 1) * sizeof(u32), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->off, offsets, ((size_t)n + 1) * sizeof(u32), kind, st);
+  if (e == cudaSuccess && arcs) e = cudaMemcpyAsync(g->col, cols, arcs * sizeof(u32), kind, st);
+  if (e != cudaSuccess) {
+    tkc_set_last_cuda_error(e, "graph upload", __FILE__, __LINE__);
+    tkc_free_graph(g);
+    return e == cudaErrorMemoryAllocation ? TKC_ENOMEM : TKC_ECUDA;
+  }
+  *out = g;
+  return TKC_OK;
+}
+
+int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offsets, const uint32_t *cols,
+                 int directed, int ptr_on_device, tkc_graph **out) {
+  if (!ctx || !out) return TKC_EINVAL;
+  *out = nullptr;
+  TKC_TRY(cudaSetDevice(ctx->device));
+  tkc_graph *g = nullptr;
+  TKC_RC(upload_graph(ctx, n, arcs, offsets, cols, directed, ptr_on_device, &g));
+  int rc = validate_and_transpose(g);
   if (rc == TKC_OK) {
-    cudaError_t e = cudaStreamSynchronize(st);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
       tkc_set_last_cuda_error(e, "graph upload", __FILE__, __LINE__);
       rc = TKC_ECUDA;
     }
   }
   if (rc != TKC_OK) {
-    ctx->graphs_alive++;
     tkc_free_graph(g);
     return rc;
   }
-  ctx->graphs_alive++;
   *out = g;
+  return TKC_OK;
+}
+
+int tkc_load_csr_many(tkc_ctx *ctx, uint32_t ng, const uint32_t *n, const uint64_t *arcs,
+                      const uint32_t *const *offsets, const uint32_t *const *cols, const int *directed,
+                      int ptr_on_device, tkc_graph **out, uint32_t *first_bad) {
+  if (!ctx || (ng && (!n || !arcs || !offsets || !cols || !directed || !out))) return TKC_EINVAL;
+  if (first_bad) *first_bad = ng;
+  if (ng == 0) return TKC_OK;
+  TKC_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  for (u32 i = 0; i < ng; ++i) out[i] = nullptr;
+  auto fail = [&](int rc, u32 bad) {
+    for (u32 i = 0; i < ng; ++i) {
+      tkc_free_graph(out[i]);
+      out[i] = nullptr;
+    }
+    if (first_bad) *first_bad = bad;
+    return rc;
+  };
+  for (u32 i = 0; i < ng; ++i) {
+    const int rc = upload_graph(ctx, n[i], arcs[i], offsets[i], cols[i], directed[i], ptr_on_device, &out[i]);
+    if (rc != TKC_OK) return fail(rc, i);
+  }
+  // every graph's checks, then one host read of all their flags; the symmetry
+  // checks of the undirected ones follow (they need checked rows)
+  u32 *flags = nullptr;
+  std::vector<u32> hf(ng, 0);
+  cudaError_t e = cudaMallocAsync(&flags, (size_t)ng * sizeof(u32), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, (size_t)ng * sizeof(u32), st);
+  if (e != cudaSuccess) {
+    tkc_set_last_cuda_error(e, "tkc_load_csr_many", __FILE__, __LINE__);
+    return fail(e == cudaErrorMemoryAllocation ? TKC_ENOMEM : TKC_ECUDA, ng);
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    bool any = false;
+    for (u32 i = 0; i < ng; ++i) {
+      const int rc = pass == 0 ? enqueue_validate(out[i], flags + i) : enqueue_symmetric(out[i], flags + i);
+      if (rc != TKC_OK) {
+        cudaFreeAsync(flags, st);
+        return fail(rc, i);
+      }
+      any |= pass == 0 || !out[i]->directed;
+    }
+    if (!any) break;
+    e = cudaMemcpyAsync(hf.data(), flags, (size_t)ng * sizeof(u32), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      tkc_set_last_cuda_error(e, "tkc_load_csr_many", __FILE__, __LINE__);
+      cudaFreeAsync(flags, st);
+      return fail(TKC_ECUDA, ng);
+    }
+    for (u32 i = 0; i < ng; ++i)
+      if (hf[i]) {
+        cudaFreeAsync(flags, st);
+        return fail(TKC_EGRAPH, i);
+      }
+  }
+  cudaFreeAsync(flags, st);
+  for (u32 i = 0; i < ng; ++i)
+    if (!out[i]->directed) {
+      out[i]->ioff = out[i]->off;
+      out[i]->icol = out[i]->col;
+    }
   return TKC_OK;
 }
 

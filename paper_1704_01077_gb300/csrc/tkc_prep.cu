@@ -199,23 +199,40 @@ static unsigned grid_for(u64 work, unsigned tpb, unsigned cap = 152 * 16) {
   return (unsigned)b;
 }
 
+// Enqueues the structural checks of g's CSR (offsets, ids, self-loops, row
+// order); violations are ORed into the device word *flag.  No host wait.
+int enqueue_validate(const tkc_graph *g, u32 *flag) {
+  if (g->n == 0) return TKC_OK;
+  cudaStream_t st = g->ctx->stream;
+  TKC_LAUNCH(k_validate<<<grid_for(std::max<u64>(g->n, (g->arcs + kArcChunk - 1) / kArcChunk * 32), 256), 256, 0,
+                          st>>>(g->off, g->col, g->n, g->arcs, flag));
+  TKC_TRY(cudaGetLastError());
+  return TKC_OK;
+}
+
+// Enqueues the symmetry check of an undirected graph into *flag; only for a
+// CSR that passed enqueue_validate (it searches rows for ids).
+int enqueue_symmetric(const tkc_graph *g, u32 *flag) {
+  if (g->n == 0 || g->directed) return TKC_OK;
+  cudaStream_t st = g->ctx->stream;
+  TKC_LAUNCH(k_symmetric<<<grid_for((g->arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
+      g->off, g->col, g->n, g->arcs, flag));
+  TKC_TRY(cudaGetLastError());
+  return TKC_OK;
+}
+
 int validate_and_transpose(tkc_graph *g) {
   cudaStream_t st = g->ctx->stream;
-  const u32 n = g->n;
-  if (n == 0) return TKC_OK;
+  if (g->n == 0) return TKC_OK;
   u32 *flags = nullptr;
   TKC_TRY(cudaMallocAsync(&flags, sizeof(u32), st));
   TKC_TRY(cudaMemsetAsync(flags, 0, sizeof(u32), st));
-  TKC_LAUNCH(k_validate<<<grid_for(std::max<u64>(n, (g->arcs + kArcChunk - 1) / kArcChunk * 32), 256), 256, 0, st>>>(
-      g->off, g->col, n, g->arcs, flags));
-  TKC_TRY(cudaGetLastError());
+  TKC_RC(enqueue_validate(g, flags));
   u32 hf = 0;
   TKC_TRY(cudaMemcpyAsync(&hf, flags, sizeof(u32), cudaMemcpyDeviceToHost, st));
   TKC_TRY(cudaStreamSynchronize(st));
   if (hf == 0 && !g->directed) {
-    TKC_LAUNCH(k_symmetric<<<grid_for((g->arcs + kArcChunk - 1) / kArcChunk * 32, 256), 256, 0, st>>>(
-        g->off, g->col, n, g->arcs, flags));
-    TKC_TRY(cudaGetLastError());
+    TKC_RC(enqueue_symmetric(g, flags));
     TKC_TRY(cudaMemcpyAsync(&hf, flags, sizeof(u32), cudaMemcpyDeviceToHost, st));
     TKC_TRY(cudaStreamSynchronize(st));
   }

@@ -78,7 +78,7 @@ class tkc_run_stats(ctypes.Structure):
                 ("alg_bytes", ctypes.c_uint64), ("ms_kernel", ctypes.c_double)]
 
 
-EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc_free_graph",
+EXPORTED = ["tkc_create", "tkc_set_options", "tkc_destroy", "tkc_load_csr", "tkc_load_csr_many", "tkc_free_graph",
             "tkc_topk_closeness", "tkc_topk_closeness_multi", "tkc_source_order", "tkc_set_source_order",
             "tkc_reach_bounds", "tkc_distance_sums", "tkc_distance_sums_noalloc", "tkc_kernel_launches",
             "tkc_strerror", "tkc_vertex_features", "tkc_mlp_init", "tkc_set_source_model", "tkc_get_source_model",
@@ -100,6 +100,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tkc_destroy.restype = None
     lib.tkc_load_csr.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(vp)]
+    lib.tkc_load_csr_many.argtypes = [vp, ctypes.c_uint32, u32p, u64p, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(vp), u32p]
     lib.tkc_free_graph.argtypes = [vp]
     lib.tkc_free_graph.restype = None
     lib.tkc_topk_closeness.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(tkc_result)]
@@ -271,6 +273,46 @@ def tkc_load_csr(ctx, n: int, offsets, cols, directed: bool) -> ctypes.c_void_p:
                                ctypes.byref(g))
     _check(rc, "tkc_load_csr")
     return g
+
+
+def tkc_load_csr_many(ctx, graphs) -> list:
+    """graphs: (n, offsets, cols, directed) tuples, arrays as for tkc_load_csr
+    (all CUDA tensors, or all host arrays).  Returns the handles.  On a
+    malformed graph raises TkcError with .first_bad = its index."""
+    ng = len(graphs)
+    if ng == 0:
+        return []
+    keep, offp, colp = [], [], []
+    dev = [hasattr(o, "data_ptr") and o.is_cuda for _, o, _, _ in graphs]
+    if any(dev) and not all(dev):
+        raise ValueError("tkc_load_csr_many: all CSRs on the device or all on the host")
+    nn = np.array([int(x[0]) for x in graphs], np.uint32)
+    arcs = np.zeros(ng, np.uint64)
+    for i, (n, offsets, cols, _) in enumerate(graphs):
+        if hasattr(offsets, "data_ptr"):
+            if not (offsets.is_contiguous() and cols.is_contiguous()) or offsets.element_size() != 4:
+                raise ValueError("CSR tensors must be contiguous 32-bit")
+            arcs[i] = int(cols.numel())
+            offp.append(offsets.data_ptr())
+            colp.append(cols.data_ptr() if arcs[i] else 0)
+        else:
+            off = np.ascontiguousarray(offsets, dtype=np.uint32)
+            col = np.ascontiguousarray(cols, dtype=np.uint32)
+            keep += [off, col]
+            arcs[i] = col.size
+            offp.append(off.ctypes.data)
+            colp.append(col.ctypes.data if col.size else 0)
+    VP = ctypes.c_void_p * ng
+    dirs = (ctypes.c_int * ng)(*[int(bool(x[3])) for x in graphs])
+    out = VP()
+    bad = ctypes.c_uint32(ng)
+    rc = _lib.tkc_load_csr_many(ctx, ng, _u32p(nn), arcs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                VP(*offp), VP(*colp), dirs, 1 if all(dev) else 0, out, ctypes.byref(bad))
+    if rc != TKC_OK:
+        err = TkcError(rc, "tkc_load_csr_many")
+        err.first_bad = int(bad.value)
+        raise err
+    return [ctypes.c_void_p(out[i]) for i in range(ng)]
 
 
 def tkc_free_graph(g) -> None:

@@ -111,7 +111,7 @@ def test_argument_errors_before_any_device_call(lib):
     good = tkc.Options().to_c()
     assert lib.tkc_create(None, ctypes.byref(good)) == EINVAL
     for bad in (dict(batch_bits=96), dict(batch_bits=1024), dict(order=5), dict(nb_levels=65536),
-                dict(large_blocks=3), dict(deterministic=2)):
+                dict(large_blocks=3), dict(deterministic=2), dict(relabel=3)):
         out = vp(1234)
         assert lib.tkc_create(ctypes.byref(out), ctypes.byref(tkc.Options(**bad).to_c())) == EINVAL, bad
         assert out.value is None, bad
@@ -120,6 +120,10 @@ def test_argument_errors_before_any_device_call(lib):
     lib.tkc_load_csr.argtypes = [vp, u32, u64, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
     g = vp(1234)
     assert lib.tkc_load_csr(None, 4, 0, None, None, 1, 0, ctypes.byref(g)) == EINVAL
+    lib.tkc_load_csr_many.argtypes = [vp, u32, vp, vp, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(u32)]
+    bad = u32(7)
+    assert lib.tkc_load_csr_many(None, 0, None, None, None, None, None, 0, None, ctypes.byref(bad)) == EINVAL
+    assert lib.tkc_load_csr_many(vp(1234), 2, None, None, None, None, None, 0, None, ctypes.byref(bad)) == EINVAL
     res = tkc.tkc_result()
     for name in ("tkc_topk_closeness", "tkc_topk_harmonic", "tkc_topk_closeness_bound"):
         fn = getattr(lib, name)

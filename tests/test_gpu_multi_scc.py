@@ -71,3 +71,56 @@ def test_union_of_many_scc_graphs(gpu_lib, ctx, nb, bits):
         for i in range(len(ref.ids)):
             f, _ = oracle.farness(g.n, ref.S[i], ref.r[i])
             assert got.farness[i].tobytes() == np.float64(f).tobytes(), g.name
+
+
+def _expect_all(gs, res, k):
+    for g, got in zip(gs, res):
+        ref = oracle.textbook_topk(g, k)
+        assert list(got.ids) == list(ref.ids), g.name
+        assert np.array_equal(got.dist_sum, ref.S) and np.array_equal(got.reach, ref.r), g.name
+        assert got.n_tied_at_kth == ref.n_tied, g.name
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_load_many_then_one_launch(gpu_lib, ctx, on_device):
+    """tkc_load_csr_many: every graph validated with one host wait, then one
+    multi-graph launch; results equal the textbook per graph."""
+    import torch
+
+    t = gpu_lib
+    gs = _graphs()
+    if on_device:
+        spec = [(g.n, torch.from_numpy(g.offsets.astype(np.int32)).cuda(),
+                 torch.from_numpy(g.cols.astype(np.int32)).cuda(), g.directed) for g in gs]
+    else:
+        spec = [(g.n, g.offsets, g.cols, g.directed) for g in gs]
+    t.tkc_set_options(ctx, t.Options(batch_bits=64, order=t.TKC_ORDER_NB))
+    hs = t.tkc_load_csr_many(ctx, spec)
+    try:
+        res = t.tkc_topk_closeness_multi(ctx, hs, 5)
+    finally:
+        for h in hs:
+            t.tkc_free_graph(h)
+        t.tkc_set_options(ctx, t.Options())
+    _expect_all(gs, res, 5)
+
+
+def test_load_many_reports_the_first_malformed_graph(gpu_lib, ctx):
+    t = gpu_lib
+    gs = _graphs()[:6]
+    for bad_at, bad in ((3, (3, np.array([0, 1, 1, 1], np.uint32), np.array([7], np.uint32), True)),
+                        (5, (3, np.array([0, 1, 1, 1], np.uint32), np.array([1], np.uint32), False)),
+                        (0, (3, np.array([0, 1, 1, 2], np.uint32), np.array([1], np.uint32), True))):
+        spec = [(g.n, g.offsets, g.cols, g.directed) for g in gs]
+        spec.insert(bad_at, bad)
+        with pytest.raises(t.TkcError) as e:
+            t.tkc_load_csr_many(ctx, spec)
+        assert e.value.code == t.TKC_EGRAPH and e.value.first_bad == bad_at
+    # the context still loads and searches
+    hs = t.tkc_load_csr_many(ctx, [(g.n, g.offsets, g.cols, g.directed) for g in gs])
+    try:
+        res = t.tkc_topk_closeness_multi(ctx, hs, 5)
+    finally:
+        for h in hs:
+            t.tkc_free_graph(h)
+    _expect_all(gs, res, 5)
