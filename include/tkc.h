@@ -165,7 +165,8 @@ int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offset
 /* Loads ng graphs as tkc_load_csr does, with one host wait for all their
  * checks (two when some are undirected) instead of one or two per graph: for
  * callers that load many small graphs, e.g. for tkc_topk_closeness_multi (no
- * paper counterpart).  Graph i is n[i], arcs[i], offsets[i], cols[i],
+ * paper counterpart).  As there, a directed graph's in-arc CSR is built when a
+ * call first needs it (a multi-graph launch builds the union's instead).  Graph i is n[i], arcs[i], offsets[i], cols[i],
  * directed[i]; ptr_on_device applies to all.  out[ng] receives the handles.
  * On error no graph is kept (every out[i] is NULL) and *first_bad (may be
  * NULL) is the first graph at fault, ng when none is (an allocation or CUDA

@@ -913,7 +913,7 @@ void tkc_free_graph(tkc_graph *g) {
   if (g->icol && g->icol != g->col) cudaFreeAsync(g->icol, st);
   void *ptrs[] = {g->off, g->col, g->deg_order, g->given_order, g->alpha, g->omega, g->scc_size, g->features,
                   g->learned_order, g->seeded_order, g->nb_order, g->nb_S, g->nb_r, g->nb_key, g->nb_hkey,
-                  g->nb_horder, g->comp};
+                  g->nb_horder, g->comp, g->zero_ids};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, st);
   g->ctx->graphs_alive--;
@@ -1107,7 +1107,9 @@ static int topk_one(tkc_graph *g, uint32_t k, tkc_result *out, int harmonic) {
   const tkc_options &o = ctx->opt;
   // a labelled search's copy of the graph is built alongside the preprocessing
   if (labelled_search(o, o.batch_bits ? o.batch_bits : 64u, g->n)) TKC_RC(start_search_csr(g));
-  TKC_RC(ensure_degree_order(g));
+  // the degree order only where it orders the sources (the NB order has its own)
+  if (o.order == TKC_ORDER_DEG || o.order == TKC_ORDER_LEARNED) TKC_RC(ensure_degree_order(g));
+  TKC_RC(ensure_zero_list(g));
   TKC_RC(ensure_reach_bounds(g));
   RunSetup rs;
   memset(&rs, 0, sizeof(rs));
@@ -1144,8 +1146,8 @@ static int topk_one(tkc_graph *g, uint32_t k, tkc_result *out, int harmonic) {
   go[0].n = g->n;
   go[0].base = 0;
   go[0].kk = kk;
-  go[0].nzero = g->n - g->n_src_deg;
-  go[0].zero_ids = g->deg_order + g->n_src_deg;
+  go[0].nzero = g->n_zero;
+  go[0].zero_ids = g->zero_ids;
   std::vector<unsigned> ntop, tied;
   std::vector<u64> gctr;
   TKC_RC(finish_run(ctx, rs, go, &r, ntop, tied, gctr));

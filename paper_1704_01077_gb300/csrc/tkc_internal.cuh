@@ -292,6 +292,9 @@ struct tkc_graph {
                                                       // on first use, ensure_in_csr)
   uint32_t *deg_order = nullptr;              // computeBoundsDeg order (all n vertices)
   uint32_t n_src_deg = 0;                     // vertices with out-degree >= 1 (prefix of deg_order)
+  mutable uint32_t *zero_ids = nullptr;       // vertices of out-degree 0, id order (ensure_zero_list)
+  mutable uint32_t n_zero = 0;
+  mutable bool have_zero = false;
   uint32_t *given_order = nullptr;            // filtered caller order
   uint32_t n_src_given = 0;
   uint32_t *alpha = nullptr, *omega = nullptr;
@@ -337,6 +340,7 @@ int enqueue_symmetric(const tkc_graph *g, uint32_t *flag);  // after enqueue_val
 int build_in_csr(const tkc_graph *g);
 int ensure_in_csr(const tkc_graph *g);
 int ensure_degree_order(tkc_graph *g);
+int ensure_zero_list(const tkc_graph *g);
 // gid/ng (several graphs as one union, graphs in contiguous vertex ranges):
 // one pivot per graph in the first forward-backward round
 int ensure_reach_bounds(tkc_graph *g, const uint32_t *gid = nullptr, uint32_t ng = 0);

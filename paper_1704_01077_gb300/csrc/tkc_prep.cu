@@ -440,6 +440,47 @@ int ensure_degree_order(tkc_graph *g) {
   return TKC_OK;
 }
 
+// ------------------------------------------------------------------ vertices of out-degree 0
+
+__global__ void k_zero_flag(const u32 *off, u32 n, u32 *flag) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x)
+    flag[v] = v < n && off[v + 1] == off[v];
+}
+
+__global__ void k_zero_out(const u32 *off, const u32 *pos, u32 n, u32 *out) {
+  for (u32 v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (off[v + 1] == off[v]) out[pos[v]] = v;
+}
+
+// The vertices of out-degree 0 in id order (closeness 0: they end a list
+// that fewer than k vertices with reach above 1 fill), by one compaction;
+// the degree order's tail holds the same, but needs a sort.
+int ensure_zero_list(const tkc_graph *g) {
+  if (g->have_zero) return TKC_OK;
+  cudaStream_t st = g->ctx->stream;
+  const u32 n = g->n;
+  if (n == 0) {
+    g->have_zero = true;
+    return TKC_OK;
+  }
+  u32 *flag = nullptr, *tmp = nullptr;
+  TKC_TRY(cudaMallocAsync(&flag, ((size_t)n + 1) * sizeof(u32), st));
+  TKC_TRY(cudaMallocAsync(&tmp, (((size_t)n + 1) / kScanTile + 2) * sizeof(u32), st));
+  if (!g->zero_ids) TKC_TRY(cudaMallocAsync(&g->zero_ids, (size_t)n * sizeof(u32), st));
+  TKC_LAUNCH(k_zero_flag<<<grid_for((u64)n + 1, 256), 256, 0, st>>>(g->off, n, flag));
+  TKC_RC(scan_exclusive(flag, flag, (u64)n + 1, tmp, st));
+  TKC_LAUNCH(k_zero_out<<<grid_for(n, 256), 256, 0, st>>>(g->off, flag, n, g->zero_ids));
+  TKC_TRY(cudaGetLastError());
+  u32 cnt = 0;
+  TKC_TRY(cudaMemcpyAsync(&cnt, flag + n, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  TKC_TRY(cudaFreeAsync(flag, st));
+  TKC_TRY(cudaFreeAsync(tmp, st));
+  TKC_TRY(cudaStreamSynchronize(st));
+  g->n_zero = cnt;
+  g->have_zero = true;
+  return TKC_OK;
+}
+
 // ------------------------------------------------------------------ bottom-up work order
 
 __global__ void k_bu_keys(const u32 *ioff, u32 n, u32 heavy_in, u32 *key, u32 *val, u32 *count) {
