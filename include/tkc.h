@@ -196,7 +196,9 @@ int tkc_topk_closeness(tkc_graph *g, uint32_t k, tkc_result *out);
  * Counters are per graph and may differ from a run of the graph alone (the
  * reach bounds are computed once on the union, and the threshold evolves
  * differently); ms_* are shared.  options.order: TKC_ORDER_DEG or
- * TKC_ORDER_NB (each graph stops on its own).  Errors: TKC_EINVAL (null ctx,
+ * TKC_ORDER_NB (each graph stops on its own).  The union's sources run as
+ * every graph's first batch, then the rest graph by graph, each graph's in its
+ * own order, so a batch shares one graph's rows and arcs.  Errors: TKC_EINVAL (null ctx,
  * null gs or outs with ng > 0, k > TKC_MAX_K, another order, a capacity too
  * small), TKC_ENOMEM, TKC_ECUDA, TKC_ETIMEOUT. */
 int tkc_topk_closeness_multi(tkc_ctx *ctx, tkc_graph *const *gs, uint32_t ng, uint32_t k, tkc_result *outs);
