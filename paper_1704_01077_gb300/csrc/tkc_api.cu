@@ -820,7 +820,7 @@ int tkc_load_csr(tkc_ctx *ctx, uint32_t n, uint64_t arcs, const uint32_t *offset
   TKC_TRY(cudaSetDevice(ctx->device));
   tkc_graph *g = nullptr;
   TKC_RC(upload_graph(ctx, n, arcs, offsets, cols, directed, ptr_on_device, &g));
-  int rc = validate_and_transpose(g);
+  int rc = validate_graph(g);
   if (rc == TKC_OK) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {

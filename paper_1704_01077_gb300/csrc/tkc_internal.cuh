@@ -334,7 +334,7 @@ struct tkc_graph {
 
 namespace tkc {
 // tkc_prep.cu
-int validate_and_transpose(tkc_graph *g);
+int validate_graph(tkc_graph *g);
 int enqueue_validate(const tkc_graph *g, uint32_t *flag);   // no host wait
 int enqueue_symmetric(const tkc_graph *g, uint32_t *flag);  // after enqueue_validate passed
 int build_in_csr(const tkc_graph *g);

@@ -221,7 +221,7 @@ int enqueue_symmetric(const tkc_graph *g, u32 *flag) {
   return TKC_OK;
 }
 
-int validate_and_transpose(tkc_graph *g) {
+int validate_graph(tkc_graph *g) {
   cudaStream_t st = g->ctx->stream;
   if (g->n == 0) return TKC_OK;
   u32 *flags = nullptr;
