@@ -71,9 +71,15 @@ __global__ void k_core_init(const u32 *off, const u32 *ioff, u32 n, int directed
 // changes it is the core number.  Only vertices with a neighbour whose value
 // changed in the previous step (dirty_in) are recomputed; a vertex whose value
 // changes marks its neighbours in dirty_out and sets *changed.
-__global__ void k_core_step(const u32 *off, const u32 *col, const u32 *ioff, const u32 *icol, u32 n, int directed,
-                            const u32 *c, u32 *c2, const uint8_t *dirty_in, uint8_t *dirty_out, u32 *changed) {
+constexpr int kCoreTPB = 256;      // threads per block of k_core_step
+constexpr u32 kCoreBuckets = 256;  // histogram buckets per warp
+
+__global__ void __launch_bounds__(kCoreTPB) k_core_step(const u32 *off, const u32 *col, const u32 *ioff,
+                                                        const u32 *icol, u32 n, int directed, const u32 *c, u32 *c2,
+                                                        const uint8_t *dirty_in, uint8_t *dirty_out, u32 *changed) {
+  __shared__ u32 hist_all[kCoreTPB / 32][kCoreBuckets];
   const int lane = threadIdx.x & 31;
+  u32 *hist = hist_all[threadIdx.x >> 5];
   for (u32 base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += gridDim.x * blockDim.x) {
     // lane per vertex: copy the clean ones; the warp then takes the dirty ones
     const u32 mine = base + lane;
@@ -85,22 +91,73 @@ __global__ void k_core_step(const u32 *off, const u32 *col, const u32 *ioff, con
     for (unsigned dm = __ballot_sync(FULL, dirty); dm; dm &= dm - 1) {
       const u32 v = base + (__ffs(dm) - 1);
       const u32 cv = c[v];
-      // the value never rises: one pass checks whether it stays (the common
-      // case once most values have settled), else a binary search lowers it
-      auto count_at_least = [&](u32 h) {
-        u32 cnt = 0;
-        for (u32 i = off[v] + lane; i < off[v + 1]; i += 32) cnt += c[col[i]] >= h;
+      // neighbours' values (out-arcs, and in-arcs when directed), visited by the warp
+      auto for_each_value = [&](auto &&f) {
+        for (u32 i = off[v] + lane; i < off[v + 1]; i += 32) f(c[col[i]]);
         if (directed)
-          for (u32 i = ioff[v] + lane; i < ioff[v + 1]; i += 32) cnt += c[icol[i]] >= h;
-        return __reduce_add_sync(FULL, cnt);
+          for (u32 i = ioff[v] + lane; i < ioff[v + 1]; i += 32) f(c[icol[i]]);
       };
-      u32 lo = 0, hi = cv;  // answer in [lo, hi]
-      if (count_at_least(cv) >= cv) lo = cv;
-      else hi = cv - 1;
-      while (lo < hi) {
-        const u32 mid = (lo + hi + 1) >> 1;
-        if (count_at_least(mid) >= mid) lo = mid;
-        else hi = mid - 1;
+      // the value never rises: one pass checks whether it stays (the common
+      // case once most values have settled)
+      u32 cnt = 0;
+      for_each_value([&](u32 x) { cnt += x >= cv; });
+      u32 above = __reduce_add_sync(FULL, cnt);  // neighbours with a value above the range searched
+      u32 lo = 0, hi = cv;                       // the new value h lies in [lo, hi]
+      if (above >= cv) {
+        lo = cv;
+      } else {
+        // h < cv: h = the largest h with (neighbours whose value is >= h) >= h.
+        // Each pass spreads [lo, hi] over 256 buckets, counts the neighbours'
+        // values per bucket, and keeps the highest bucket whose start still
+        // satisfies the condition (the count only falls as h rises, and h = lo
+        // always satisfies it): one pass when cv <= 256, at most three below
+        // 2^24 -- instead of one pass per halving of [0, cv].
+        hi = cv - 1;
+        while (lo < hi) {
+          const u32 width = (hi - lo) / kCoreBuckets + 1;
+          for (u32 j = lane; j < kCoreBuckets; j += 32) hist[j] = 0;
+          __syncwarp();
+          for_each_value([&](u32 x) {
+            if (x >= lo && x <= hi) atomicAdd(&hist[(x - lo) / width], 1u);
+          });
+          __syncwarp();
+          // lane j holds buckets 8j .. 8j+7; suffix sums over the warp from the top
+          u32 loc[kCoreBuckets / 32];
+          u32 part = 0;
+#pragma unroll
+          for (int q = kCoreBuckets / 32 - 1; q >= 0; --q) {
+            part += hist[lane * (kCoreBuckets / 32) + q];
+            loc[q] = part;  // buckets q.. of this lane's group
+          }
+          u32 incl = part;  // this lane's group total, then the sum of groups j..31
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const u32 t = __shfl_down_sync(FULL, incl, o);
+            if (lane + o < 32) incl += t;
+          }
+          const u32 later = incl - part;  // groups above this lane's
+          // highest bucket b with above + (count in buckets >= b) >= lo + b * width
+          int best = -1;
+#pragma unroll
+          for (int q = kCoreBuckets / 32 - 1; q >= 0; --q) {
+            const u32 b = lane * (kCoreBuckets / 32) + q;
+            const u64 start = (u64)lo + (u64)b * width;
+            if (best < 0 && start <= hi && (u64)above + later + loc[q] >= start) best = (int)b;
+          }
+          const unsigned has = __ballot_sync(FULL, best >= 0);
+          const int src = 31 - __clz(has);  // the highest group with such a bucket (group 0 always has one)
+          const u32 b = (u32)__shfl_sync(FULL, best, src);
+          // neighbours in buckets above b
+          const u32 b_above = __shfl_sync(FULL, later + loc[b % (kCoreBuckets / 32)] -
+                                                     hist[lane * (kCoreBuckets / 32) + b % (kCoreBuckets / 32)],
+                                          src);
+          __syncwarp();
+          const u32 nlo = lo + b * width;
+          const u32 nhi = (u64)nlo + width - 1 < hi ? nlo + width - 1 : hi;
+          above += b_above;
+          lo = nlo;
+          hi = nhi;
+        }
       }
       if (lane == 0) c2[v] = lo;
       if (lo != cv) {
@@ -390,7 +447,7 @@ int ensure_features(tkc_graph *g) {
     if (it > 2 * g->arcs + 1) return TKC_ETIMEOUT;
     TKC_TRY(cudaMemsetAsync(flag, 0, sizeof(u32), st));
     TKC_TRY(cudaMemsetAsync(d1, 0, n, st));
-    TKC_LAUNCH(k_core_step<<<grid_of(n), 256, 0, st>>>(g->off, g->col, g->ioff, g->icol, n, g->directed, c0, c1, d0,
+    TKC_LAUNCH(k_core_step<<<grid_of(n, kCoreTPB), kCoreTPB, 0, st>>>(g->off, g->col, g->ioff, g->icol, n, g->directed, c0, c1, d0,
                                                        d1, flag));
     std::swap(c0, c1);
     std::swap(d0, d1);

@@ -85,6 +85,45 @@ def test_features_match_oracle(gpu_lib, ctx, make):
     assert np.allclose(x, ref, rtol=1e-4, atol=1e-4), np.abs(x - ref).max()
 
 
+def _hub_graph():
+    """Undirected: a hub joined to 70 000 leaves, a 40-clique among leaves
+    and a chain: the hub's core number is searched over a range
+    of 70 000 values (three histogram passes), the clique's over 39."""
+    leaves = 70_000
+    src = [0] * leaves
+    dst = list(range(1, leaves + 1))
+    for a in range(1, 41):
+        for b in range(a + 1, 41):
+            src.append(a)
+            dst.append(b)
+    for a in range(41, 400):
+        src.append(a)
+        dst.append(a + 1)
+    # a triangle and an isolated vertex apart, so that no feature is constant
+    # (a constant column standardizes to rounding noise over a zero spread)
+    t = leaves + 1
+    src += [t, t + 1, t]
+    dst += [t + 1, t + 2, t + 2]
+    return gg.from_arcs(leaves + 5, src, dst, False, "hub70k")
+
+
+@pytest.mark.parametrize("make", [lambda: gg.rmat(14, 16, seed=21), _hub_graph,
+                                  lambda: gg.disjoint_union(gg.barabasi_albert(20_000, 6, 22), gg.cycle(5),
+                                                            gg.path(1))])
+def test_core_numbers_of_high_degree_vertices(gpu_lib, ctx, make):
+    """Graphs whose largest degrees (hundreds to 70 000) take the core-number
+    search through several histogram passes; features equal the oracle's."""
+    g = make()
+    h = gpu_lib.tkc_load_csr(ctx, g.n, g.offsets, g.cols, g.directed)
+    try:
+        x = gpu_lib.tkc_vertex_features(h, g.n).cpu().numpy()
+    finally:
+        gpu_lib.tkc_free_graph(h)
+    ref = ofeat.features(g)
+    err = np.abs(x - ref)
+    assert np.allclose(x, ref, rtol=1e-4, atol=1e-4), (err.max(axis=0), np.unravel_index(err.argmax(), err.shape))
+
+
 def test_learned_order_gives_exact_topk(gpu_lib, ctx):
     import torch
 
