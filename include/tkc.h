@@ -87,7 +87,7 @@ typedef struct {
                               before the teams start. */
   uint32_t nb_levels;      /* TKC_ORDER_NB: most level sweeps of computeBoundsNB, 1..65535 (0 = 256) */
   uint32_t large_blocks;   /* threads per block of the search kernel: 0 = library choice (the larger blocks -- 1024
-                              threads for 64-bit batches, 768 for 128-bit -- for batched searches on graphs of
+                              threads for 64- and 128-bit batches -- for batched searches on graphs of
                               2^20 vertices or more, else 512), 1 = always the larger blocks, 2 = always 512;
                               wider batches always use 512.  Results never depend on it. */
   uint32_t deterministic;  /* 1: one team of SMs whatever `teams` says, so the threshold x changes only at
