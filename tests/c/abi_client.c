@@ -1,7 +1,8 @@
 /* A plain C99 client of the C ABI: compiled and linked against libtkc.so by
  * tests/test_abi.py to show that include/tkc.h is valid C and that every call
  * below resolves.  Run on a GPU it prints the exact top-3 closeness of a
- * 4 x 4 grid; the test only builds it. */
+ * 4 x 4 grid, then the best vertex of two copies searched in one launch; the
+ * test only builds it. */
 #include <stdint.h>
 #include <stdio.h>
 
@@ -48,6 +49,24 @@ int main(void) {
   else
     fprintf(stderr, "tkc: %s\n", tkc_strerror(rc));
   tkc_free_graph(g);
+  /* the same grid twice, loaded together, then both in one launch */
+  if (rc == TKC_OK) {
+    const uint32_t ns[2] = {N, N};
+    const uint64_t ms[2] = {m, m};
+    const uint32_t *offs[2] = {off, off}, *colss[2] = {cols, cols};
+    const int dirs[2] = {0, 0};
+    tkc_graph *gs[2] = {NULL, NULL};
+    uint32_t bad = 2;
+    rc = tkc_load_csr_many(ctx, 2, ns, ms, offs, colss, dirs, 0, gs, &bad);
+    tkc_result outs[2] = {res, res};
+    if (rc == TKC_OK) rc = tkc_topk_closeness_multi(ctx, gs, 2, 3, outs);
+    if (rc == TKC_OK)
+      printf("two grids in one launch: best %u and %u\n", outs[0].ids[0], outs[1].ids[0]);
+    else
+      fprintf(stderr, "tkc (graph %u): %s\n", bad, tkc_strerror(rc));
+    tkc_free_graph(gs[0]);
+    tkc_free_graph(gs[1]);
+  }
   tkc_destroy(ctx);
   return rc == TKC_OK ? 0 : 1;
 }
