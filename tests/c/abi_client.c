@@ -58,10 +58,15 @@ int main(void) {
     tkc_graph *gs[2] = {NULL, NULL};
     uint32_t bad = 2;
     rc = tkc_load_csr_many(ctx, 2, ns, ms, offs, colss, dirs, 0, gs, &bad);
-    tkc_result outs[2] = {res, res};
+    uint32_t ids2[2][3];
+    tkc_result outs[2] = {{0}, {0}};
+    for (int i = 0; i < 2; ++i) {
+      outs[i].ids = ids2[i];  /* the other arrays may stay NULL */
+      outs[i].capacity = 3;
+    }
     if (rc == TKC_OK) rc = tkc_topk_closeness_multi(ctx, gs, 2, 3, outs);
     if (rc == TKC_OK)
-      printf("two grids in one launch: best %u and %u\n", outs[0].ids[0], outs[1].ids[0]);
+      printf("two grids in one launch: best %u and %u\n", ids2[0][0], ids2[1][0]);
     else
       fprintf(stderr, "tkc (graph %u): %s\n", bad, tkc_strerror(rc));
     tkc_free_graph(gs[0]);
